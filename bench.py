@@ -1,0 +1,348 @@
+"""Benchmark: window updates/s of the sliding-window cumulant path on GB300.
+
+One step = one window shift of the whole hot path: ring append / X_(-)
+extraction, moment-sum update of orders 1..d, moment-to-cumulant recovery of
+orders 1..d, and the norm reduction (Algorithm 1, one loop iteration).
+
+Default workload: n=60 variables, orders 1..4, block size 3, window T=2^15,
+shift p=2^10, FP32 samples (Gaussian, then a Gaussian copula with
+exponential(1) marginals), seeded and synthetic.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16]
+    python bench.py --impl reference      # the CPU oracle on the same workload
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+independent stream (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1701_06446_gb300.streams import WORKLOADS  # noqa: E402
+
+METRIC = "window updates/s and TFLOP/s vs tensor-core peak at stated error vs FP64 oracle"
+UNIT = "window updates/s"
+DEFAULT_WORKLOAD = "n60_d4_b3_T32768_p1024"
+L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def algorithmic_flops(W) -> dict:
+    """Flops of one shift: update 2 * (2p) * E_s per order (one product per
+    multiply-add), recovery 2 * (2^{s-1} - 1) * E_s (one multiply-add per
+    subset term)."""
+    from paper_1701_06446_gb300 import layout_size
+    upd = sum(2.0 * 2 * W.p * layout_size(W.n, W.b, s) for s in range(1, W.d + 1))
+    rec = sum(2.0 * (2 ** (s - 1) - 1) * layout_size(W.n, W.b, s) for s in range(2, W.d + 1))
+    return {"update": upd, "recovery": rec}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if device_id:
+            cmd += ["-i", device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the --impl reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample_time(X: np.ndarray, W, per_order: int, seed: int) -> tuple[float, str]:
+    """Seconds one full oracle recomputation of C_1..C_d for window X would take,
+    from timing every sorted tuple of orders <= 2 and `per_order` seeded
+    sorted tuples of each higher order (extrapolated linearly by tuple count)."""
+    import oracle
+    t0 = time.perf_counter()
+    cen = oracle.center(X)
+    total = time.perf_counter() - t0
+    parts = []
+    for s in range(1, W.d + 1):
+        n_tuples = math.comb(W.n + s - 1, s)
+        if s <= 2 or n_tuples <= per_order:
+            import itertools
+            tup = np.array(list(itertools.combinations_with_replacement(range(W.n), s)), np.int32)
+            t0 = time.perf_counter()
+            oracle.cumulant_tuples(X, tup, centred=cen)
+            total += time.perf_counter() - t0
+            parts.append(f"order {s}: all {n_tuples}")
+        else:
+            tup = oracle.sample_sorted_tuples(W.n, s, per_order, seed + s)
+            t0 = time.perf_counter()
+            oracle.cumulant_tuples(X, tup, centred=cen)
+            dt = time.perf_counter() - t0
+            total += dt * n_tuples / per_order
+            parts.append(f"order {s}: {per_order} of {n_tuples} tuples, extrapolated")
+    return total, "; ".join(parts)
+
+
+def oracle_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, W, rank: int):
+    if rank != 0:
+        return
+    X = W.stream().rows(0, W.T).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_sample_time(X, W, 100, seed=0)
+    secs = []
+    sample = ""
+    for k in range(args.steps):
+        dt, sample = oracle_sample_time(X, W, args.ref_tuples, seed=k)
+        secs.append(dt)
+    per = statistics.mean(secs)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(W, "fp64-oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": f"full recomputation of one window from scratch per step; {sample}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(W, precision: str) -> dict:
+    return {"workload": W.name, "n": W.n, "orders": f"1..{W.d}", "b": W.b, "T": W.T, "p": W.p,
+            "precision": precision, "stream": W.kind,
+            "l2": "flushed (256 MB write) between timed steps"}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def sampled_error(h, X: np.ndarray, per_order: int = 200) -> dict:
+    import oracle
+    cen = oracle.center(X)
+    out = {}
+    for s in range(1, h.d + 1):
+        C = h.cumulants(s).cpu().numpy()
+        tup = oracle.sample_sorted_tuples(h.n, s, per_order, seed=1000 + s)
+        idx = np.array([oracle.storage_index(h.n, h.b, t) for t in tup])
+        ref = oracle.cumulant_tuples(X, tup, centred=cen)
+        out[str(s)] = float(np.linalg.norm(C[idx] - ref) / max(np.linalg.norm(ref), 1e-300))
+    return out
+
+
+def run_ours(args, W, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+    from paper_1701_06446_gb300 import CumWin
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    precision = args.precision
+    stream = W.stream()
+    # each rank advances its own independent stretch of the stream
+    base = rank * (W.T + (args.warmup + args.steps + 1) * W.p)
+    nsteps = args.warmup + args.steps
+    X = stream.rows(base, base + W.T + nsteps * W.p)
+    Xd = torch.from_numpy(X).to(dev)
+    h = CumWin(W.n, W.d, W.b, W.T, W.p, precision, device=dev)
+    h.fill(Xd[: W.T])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    batches = [Xd[W.T + k * W.p: W.T + (k + 1) * W.p] for k in range(nsteps)]
+    for k in range(args.warmup):
+        h.push(batches[k])
+    torch.cuda.synchronize()
+
+    st = torch.cuda.current_stream(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    h.set_timing(True)
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(st)
+        h.push(batches[args.warmup + k])
+        ends[k].record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    timing = h.get_timing()
+    h.set_timing(False)
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t.item())
+    ms_per_step = step_ms / args.steps
+    value = world * args.steps / (step_ms * 1e-3)
+
+    # end-to-end through the C ABI with host buffers: H2D of X_(+) and D2H of the norms inside
+    e2e_steps = min(args.steps, 200)
+    host = torch.from_numpy(stream.rows(base + W.T + nsteps * W.p,
+                                        base + W.T + (nsteps + e2e_steps) * W.p)).pin_memory()
+    hb = [host[k * W.p:(k + 1) * W.p] for k in range(e2e_steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        h.push_host(hb[k])
+        fro, nu = h.norms()
+    t1 = time.perf_counter()
+    e2e_t = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps / float(e2e_t.item())
+
+    # accuracy of the final window against the FP64 oracle (sampled tuples)
+    final = stream.rows(base + (nsteps + e2e_steps) * W.p, base + W.T + (nsteps + e2e_steps) * W.p)
+    err = sampled_error(h, final) if rank == 0 else None
+
+    if rank != 0:
+        h.close()
+        return
+    flops = algorithmic_flops(W)
+    peaks, peak_kind = _peaks()
+    upd_ms = timing["update_ms"] / max(timing["shifts"], 1)
+    rec_ms = timing["cumulant_ms"] / max(timing["shifts"], 1)
+    if precision == "fp64":
+        achieved = flops["update"] / (upd_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_update_f64", "bound": "alu", "achieved": achieved,
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_kind": "nominal FP64 (CUDA cores)", "traffic": None,
+                "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x 2p x E_s summed over orders)",
+                "avg_launch_ms": upd_ms}
+    else:
+        achieved = flops["update"] / (upd_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"kernel": "k_update_tc", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "peak_kind": f"{peak_kind} bf16 sustained",
+                "traffic": None, "avg_launch_ms": upd_ms}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        Xw = final.astype(np.float64)
+        secs, sample = oracle_sample_time(Xw, W, args.ref_tuples, seed=7)
+        cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+               "sample": f"full recomputation of one window; {sample}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == "fp64" else f"{precision}x3+f32acc+f64sum",
+        "data": "synthetic", "config": config_of(W, precision),
+        "samples_per_s": value * W.p,
+        "tflops": flops["update"] / (ms_per_step * 1e-3) / 1e12,
+        "update_ms": upd_ms, "recovery_ms": rec_ms,
+        "error_vs_oracle": {"metric": "relative Frobenius error per order on 200 sampled tuples",
+                            "per_order": err},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W.p * W.n * 4,
+                "d2h_bytes_per_step": W.d * 8 + 4, "steps": e2e_steps},
+        "gpu_launches": timing["launches"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "bf16", "fp16"], default="fp64")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--ref-tuples", type=int, default=3000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    W = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        # the oracle runs on the host cores of rank 0 only
+        run_reference(args, W, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, W, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

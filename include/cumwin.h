@@ -1,0 +1,212 @@
+/*
+ * cumwin — sliding-window cumulant tensors of orders 1..d on one GPU.
+ *
+ * C ABI of the library.  It follows the problem statement of Domino & Gawron,
+ * "Algorithm for an arbitrary-order cumulant tensor calculation in a sliding
+ * window of data streams":
+ *   - a window X^(w) holds the last T samples of an n-variate stream, one
+ *     sample per row (Section 2.1, Eqs. 1-4);
+ *   - each shift drops the oldest p rows X_(-) and appends p new rows X_(+)
+ *     (Algorithm 1), and the moment tensors of orders 1..d are updated by
+ *     M(X^(w+1)) = M(X^(w)) + (p/T)(M(X_(+)) - M(X_(-))) (Eqs. 6-7, Algorithm 2);
+ *   - the cumulant tensors C_1..C_d are recovered from the moments by the
+ *     moment-to-cumulant relation (Algorithms 3-4);
+ *   - their Frobenius norms and the non-Gaussianity estimator
+ *     nu_s = ||C_s||_2 / ||C_2||_2^{s/2} are reduced (Eqs. me, mef, Algorithm 5).
+ *
+ * Storage: super-symmetric tensors of order s are kept in the block
+ * ("hyper-pyramid") structure of Section 2.3: with nbar = ceil(n/b) blocks per
+ * mode, only blocks j1 <= j2 <= ... <= js are stored, in lexicographic order of
+ * (j1..js); each block is a dense b^s array, row-major over the in-block
+ * indices (a1..as) with a1 slowest, and diagonal blocks are stored whole.
+ * Element (block rank r, in-block offset o) lives at r * b^s + o and holds the
+ * tensor entry at variables (j1*b+a1, ..., js*b+as).  When b does not divide n,
+ * variables n..nbar*b-1 are zero padding and every entry that involves one of
+ * them is exactly 0.
+ *
+ * Conventions for every call:
+ *   - pointers named *_dev are CUDA device pointers owned by the caller; they
+ *     must stay valid until the handle's stream has executed the call;
+ *   - pointers named *_host are host pointers;
+ *   - samples are FP32, row-major, row stride `ld` (>= n) in elements;
+ *   - calls are asynchronous on the handle's stream unless stated otherwise;
+ *   - argument errors are returned synchronously and leave the state
+ *     unchanged; device-side conditions (a non-finite input sample) set a
+ *     sticky status word that the next synchronising call reports;
+ *   - a handle is not thread-safe: one host thread at a time.
+ */
+#ifndef CUMWIN_H
+#define CUMWIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cumwin_s* cumwin_t;
+
+/* Return codes. */
+enum {
+    CUMWIN_OK = 0,
+    CUMWIN_EINVAL = -1,     /* bad argument (sizes, order, null pointer)          */
+    CUMWIN_ENOMEM = -2,     /* device allocation failed                           */
+    CUMWIN_ECUDA = -3,      /* a CUDA runtime call failed (see cumwin_last_error) */
+    CUMWIN_ESTATE = -4,     /* call out of sequence (e.g. push before fill)       */
+    CUMWIN_ENONFINITE = -5, /* a non-finite sample entered the window             */
+    CUMWIN_ETIMEOUT = -6,   /* a bounded device wait gave up                      */
+    CUMWIN_ENOTSUP = -7     /* combination not supported on this device/build     */
+};
+
+/* Arithmetic of the moment-sum update (the cumulant recovery and all running
+ * sums are FP64 in every form). */
+enum {
+    CUMWIN_FP64 = 0,        /* FP64 products and FP64 accumulation                 */
+    CUMWIN_MIXED_BF16 = 1,  /* tensor cores: BF16 hi+lo split products (3 MMAs),
+                               FP32 accumulation per batch, FP64 running sums     */
+    CUMWIN_MIXED_FP16 = 2   /* as above with FP16 hi+lo splits                     */
+};
+
+/* Largest supported order d and variable count n. */
+#define CUMWIN_MAX_ORDER 8
+#define CUMWIN_MAX_N 256
+
+/*
+ * Create a handle for n variables, orders 1..d, block size b (1 <= b), window
+ * length T samples, nominal shift size p (the paper's t_up, 1 <= p <= T),
+ * arithmetic `precision`, issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = legacy default stream).  Allocates all device state (ring buffer of
+ * T samples, FP64 moment sums and cumulants of every order, tables) with
+ * cudaMalloc on the current device.  Synchronous.
+ * In the mixed forms the FP32 tile sums are formed per batch of p samples and
+ * the first window is summed in batches of p aligned with the later shifts,
+ * so when every push has p rows and p divides T a batch's FP32 sum leaving
+ * the window is bitwise the one that entered it and the running FP64 sums do
+ * not drift.  Pushes of another size are accepted.
+ * Errors: EINVAL (n < 1, n > CUMWIN_MAX_N, d < 1, d > CUMWIN_MAX_ORDER, b < 1,
+ * T < 1, p outside [1, T], unknown precision), ENOTSUP (mixed precision on a
+ * device other than sm_103), ENOMEM, ECUDA.
+ */
+int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream,
+                  cumwin_t* out);
+
+/* Free all device state.  Synchronises the handle's stream first.  NULL is a no-op. */
+int cumwin_destroy(cumwin_t h);
+
+/* Change the stream later calls are issued on. */
+int cumwin_set_stream(cumwin_t h, void* cuda_stream);
+
+/*
+ * Load the first window X^(1) (T rows, row stride ldx >= n, device) and compute
+ * its moments, cumulants and norms in full (Algorithm 1, "calculate moments
+ * M_1(X^(1))..M_d(X^(1))").  In the mixed forms this also fixes the shift
+ * vector (the FP32-rounded column means of X^(1)) about which all moments are
+ * accumulated; cumulants of order >= 2 do not depend on it.
+ */
+int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx);
+
+/*
+ * One window shift (one pass of the loop of Algorithm 1): append the p rows of
+ * x_in_dev (X_(+)), drop the p oldest rows (X_(-)), update the moment sums of
+ * every order by sum_{in} x^{(x)s} - sum_{out} x^{(x)s} (Eqs. 6-7), recover
+ * C_1..C_d (Algorithms 3-4) and reduce their norms on the device.
+ * x_out_dev == NULL: X_(-) is taken from the ring buffer (Algorithm 1, "first
+ * t_up rows of X^(w)").  Non-NULL: the caller supplies X_(-) (the inputs of
+ * momentsupdate in Algorithm 2); the ring buffer is still advanced with x_in.
+ * Requires 1 <= p <= T and a prior cumulant fill.  Errors: EINVAL, ESTATE.
+ * Allocates nothing and does not synchronise (capturable into a CUDA graph).
+ */
+int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p, int64_t ld);
+
+/*
+ * As cumwin_push with X_(+) in HOST memory (pinned memory gives an
+ * asynchronous copy; pageable memory makes the copy synchronous).  The copy
+ * goes to a device staging buffer owned by the handle.
+ */
+int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld);
+
+/* Copy C_s (1 <= order <= d) of the current window, block layout, FP64,
+ * cumwin_layout_size(n, b, order) elements, into out_dev. */
+int cumwin_cumulants(cumwin_t h, int order, double* out_dev);
+
+/* Copy the current moment tensor M_s about the shift vector, i.e. the moments
+ * (Eq. 5) of x - shift; the shift is zero in the FP64 form.  Block layout. */
+int cumwin_moments(cumwin_t h, int order, double* out_dev);
+
+/* The shift vector (n floats) into shift_host.  Synchronous. */
+int cumwin_shift(cumwin_t h, float* shift_host);
+
+/*
+ * Norms of the current cumulants.  Synchronises the handle's stream.
+ * fro_host[s-1] = ||C_s||_F (the entry-wise 2-norm of the full n^s tensor,
+ * Eq. me; ||C_1|| is the Euclidean norm of the mean), s = 1..d.
+ * nu_host[s-1] = nu_s = ||C_s|| / ||C_2||^{s/2} (Eq. mef) for s >= 3, NaN for
+ * s < 3; ||C_2|| = 0 (a constant window) gives NaN.  Either pointer may be NULL.
+ * Returns ENONFINITE if a non-finite sample has entered the window.
+ */
+int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host);
+
+/* Squared norms ||C_s||_F^2, s = 1..d, as d doubles in device memory (no sync). */
+int cumwin_norms_device(cumwin_t h, double* fro2_dev);
+
+/* Recompute the moment sums from the window held in the ring buffer (the
+ * "simple recalculation" the update is compared against in Section 3.2), then
+ * the cumulants and norms. */
+int cumwin_recompute(cumwin_t h);
+
+/* Copy the current window, oldest sample first, T x n FP32 row-major (ld = n). */
+int cumwin_window(cumwin_t h, float* out_dev);
+
+/*
+ * Gradient of L = sum_{s=1..d} w[s] ||C_s||_F^2 (w has d+1 entries, w[0]
+ * ignored; full-tensor norms, i.e. each stored block weighted by its
+ * multiplicity d!/prod r_l! of Algorithm 5) with respect to the current
+ * window, oldest sample first, into dX_dev (T x n FP32, ld = n).  Requires
+ * d <= 4.  Not in the paper: it is the adjoint of Algorithms 2-4.
+ */
+int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev);
+
+/*
+ * Kernel timing.  With timing enabled, each later fill / push / recompute
+ * records CUDA events on the handle's stream around its moment-sum update
+ * kernel and around its cumulant-recovery + norm kernels (at most 65536 shifts
+ * are recorded; later ones are not timed).  cumwin_get_timing synchronises and
+ * returns the summed event times in milliseconds, the number of timed shifts
+ * and the number of kernels the library launched since timing was enabled.
+ * Enabling resets the counters.  Not for use inside stream capture.
+ */
+int cumwin_set_timing(cumwin_t h, int enable);
+int cumwin_get_timing(cumwin_t h, double* update_ms, double* cumulant_ms, int64_t* shifts,
+                      int64_t* launches);
+
+/* Sticky device status of the handle (CUMWIN_OK or ENONFINITE / ETIMEOUT).
+ * Synchronises the handle's stream.  Reading it clears nothing. */
+int cumwin_status(cumwin_t h);
+
+/* Host-only layout helpers (no GPU needed). */
+/* Stored elements of order `order`: C(nbar + order - 1, order) * b^order. */
+int64_t cumwin_layout_size(int n, int b, int order);
+/* Lexicographic rank of the sorted block multi-index j (order entries,
+ * 0 <= j[0] <= ... < nbar); -1 if j is not sorted or out of range. */
+int64_t cumwin_block_rank(int n, int b, int order, const int* j);
+/* Storage index of the tensor entry at variable multi-index i (any order of
+ * its entries, each in [0, n)); -1 on a bad argument. */
+int64_t cumwin_element_index(int n, int b, int order, const int* i);
+/* Self-test of the host tables that map update tiles and cumulant sub-blocks
+ * to storage indices against a direct enumeration (0 = pass). */
+int cumwin_selftest_tables(int n, int b, int order);
+
+/* Message for a return code, and the detail of the last CUDA error seen by
+ * the calling thread. */
+const char* cumwin_strerror(int code);
+const char* cumwin_last_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int cumwin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUMWIN_H */

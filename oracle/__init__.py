@@ -117,6 +117,30 @@ def block_elements(n: int, b: int, s: int) -> np.ndarray:
     return idx.reshape(-1, s)
 
 
+def storage_index(n: int, b: int, i) -> int:
+    """Storage index of the tensor entry at variable multi-index i (its sorted form).
+
+    The sorted block tuple j maps to strictly increasing c_k = j_k + k over
+    [0, nbar + s - 1) (stars and bars); its lexicographic rank counts the
+    combinations that first differ from c at some position k with a smaller
+    value there.
+    """
+    v = sorted(int(x) for x in i)
+    s = len(v)
+    N = nbar(n, b) + s - 1
+    c = [v[k] // b + k for k in range(s)]
+    rank = 0
+    lo = 0
+    for k in range(s):
+        for u in range(lo, c[k]):
+            rank += math.comb(N - 1 - u, s - 1 - k)
+        lo = c[k] + 1
+    off = 0
+    for k in range(s):
+        off = off * b + v[k] % b
+    return rank * b ** s + off
+
+
 def block_multiplicity(j: tuple[int, ...]) -> int:
     """d! / prod_l r_l! with r_l the run lengths of equal indices (Algorithm 5)."""
     r = math.factorial(len(j))

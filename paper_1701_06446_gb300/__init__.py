@@ -1,0 +1,230 @@
+"""Sliding-window cumulant tensors on one GB300 GPU.
+
+Python binding of ``libcumwin.so`` (C ABI in ``include/cumwin.h``).  Every
+step of the path runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch supplies device memory and streams.
+
+    cw = CumWin(n=60, d=4, b=3, T=32768, p=1024, precision="bf16")
+    cw.fill(X0)             # first window, (T, n) float32 on the GPU
+    cw.push(x_in)           # one window shift, (p, n) float32 on the GPU
+    C4 = cw.cumulants(4)    # block layout, float64
+    fro, nu = cw.norms()    # ||C_s||_F and nu_s (Eqs. me, mef)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CumwinError, check
+
+__all__ = ["CumWin", "CumwinError", "CumulantNormLoss", "layout_size", "block_rank",
+           "element_index", "selftest_tables", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.path()
+
+
+def layout_size(n: int, b: int, order: int) -> int:
+    r = _lib.load().cumwin_layout_size(n, b, order)
+    if r < 0:
+        raise ValueError("bad layout arguments")
+    return int(r)
+
+
+def block_rank(n: int, b: int, order: int, j) -> int:
+    arr = (ctypes.c_int * order)(*[int(x) for x in j])
+    return int(_lib.load().cumwin_block_rank(n, b, order, arr))
+
+
+def element_index(n: int, b: int, order: int, i) -> int:
+    arr = (ctypes.c_int * order)(*[int(x) for x in i])
+    return int(_lib.load().cumwin_element_index(n, b, order, arr))
+
+
+def selftest_tables(n: int, b: int, order: int) -> int:
+    return int(_lib.load().cumwin_selftest_tables(n, b, order))
+
+
+def _dev_ptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    return t.data_ptr()
+
+
+class CumWin:
+    """One sliding window of an n-variate stream with cumulants of orders 1..d."""
+
+    def __init__(self, n: int, d: int, b: int, T: int, p: int, precision: str = "fp64",
+                 device=None):
+        self.lib = _lib.load()
+        if precision not in _lib.PRECISION:
+            raise ValueError(f"precision must be one of {list(_lib.PRECISION)}")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.n, self.d, self.b, self.T, self.p = n, d, b, T, p
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._stream = torch.cuda.current_stream(self.device).cuda_stream
+            check(self.lib.cumwin_create(n, d, b, T, p, _lib.PRECISION[precision],
+                                         ctypes.c_void_p(self._stream), ctypes.byref(self._h)),
+                  "cumwin_create")
+        self.sizes = [layout_size(n, b, s) for s in range(1, d + 1)]
+
+    # -- stream management ---------------------------------------------------
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        if s != self._stream:
+            check(self.lib.cumwin_set_stream(self._h, ctypes.c_void_p(s)), "cumwin_set_stream")
+            self._stream = s
+
+    def close(self):
+        if self._h:
+            self.lib.cumwin_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path --------------------------------------------------------------
+    def fill(self, X: torch.Tensor):
+        if X.dim() != 2 or X.shape[0] != self.T or X.shape[1] < self.n or X.stride(1) != 1:
+            raise ValueError("fill expects a (T, n) float32 tensor with unit column stride")
+        self._sync_stream()
+        check(self.lib.cumwin_fill(self._h, _dev_ptr(X, torch.float32, "X"), X.stride(0)),
+              "cumwin_fill")
+
+    def push(self, x_in: torch.Tensor, x_out: torch.Tensor | None = None):
+        if x_in.dim() != 2 or x_in.shape[1] < self.n or x_in.stride(1) != 1:
+            raise ValueError("push expects (p, n) float32 tensors with unit column stride")
+        p = x_in.shape[0]
+        out_ptr = None
+        if x_out is not None:
+            if x_out.shape != x_in.shape or x_out.stride() != x_in.stride():
+                raise ValueError("x_out must match x_in in shape and strides")
+            out_ptr = ctypes.c_void_p(_dev_ptr(x_out, torch.float32, "x_out"))
+        self._sync_stream()
+        check(self.lib.cumwin_push(self._h, _dev_ptr(x_in, torch.float32, "x_in"), out_ptr, p,
+                                   x_in.stride(0)), "cumwin_push")
+
+    def push_host(self, x_in):
+        """Shift with X_(+) in host memory (numpy array or CPU tensor, pinned if possible)."""
+        if isinstance(x_in, torch.Tensor):
+            if x_in.is_cuda or x_in.dtype != torch.float32:
+                raise ValueError("push_host expects a CPU float32 tensor")
+            ptr, p, ld = x_in.data_ptr(), x_in.shape[0], x_in.stride(0)
+        else:
+            x_in = np.ascontiguousarray(x_in, dtype=np.float32)
+            ptr, p, ld = x_in.ctypes.data, x_in.shape[0], x_in.shape[1]
+        self._sync_stream()
+        check(self.lib.cumwin_push_host(self._h, ctypes.c_void_p(ptr), p, ld), "cumwin_push_host")
+
+    def cumulants(self, order: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.sizes[order - 1], dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_cumulants(self._h, order, _dev_ptr(out, torch.float64, "out")),
+              "cumwin_cumulants")
+        return out
+
+    def moments(self, order: int) -> torch.Tensor:
+        out = torch.empty(self.sizes[order - 1], dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_moments(self._h, order, out.data_ptr()), "cumwin_moments")
+        return out
+
+    def shift(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.float32)
+        self._sync_stream()
+        check(self.lib.cumwin_shift(self._h, out.ctypes.data), "cumwin_shift")
+        return out
+
+    def norms(self) -> tuple[np.ndarray, np.ndarray]:
+        fro = np.zeros(self.d)
+        nu = np.zeros(self.d)
+        self._sync_stream()
+        check(self.lib.cumwin_norms(self._h, fro.ctypes.data, nu.ctypes.data), "cumwin_norms")
+        return fro, nu
+
+    def norms_device(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_norms_device(self._h, _dev_ptr(out, torch.float64, "out")),
+              "cumwin_norms_device")
+        return out
+
+    def recompute(self):
+        self._sync_stream()
+        check(self.lib.cumwin_recompute(self._h), "cumwin_recompute")
+
+    def window(self) -> torch.Tensor:
+        out = torch.empty(self.T, self.n, dtype=torch.float32, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_window(self._h, out.data_ptr()), "cumwin_window")
+        return out
+
+    def grad(self, w) -> torch.Tensor:
+        """d(sum_s w[s] ||C_s||_F^2)/d window (T x n, oldest sample first)."""
+        wa = np.zeros(self.d + 1)
+        wa[:len(w)] = np.asarray(w, dtype=np.float64)[: self.d + 1]
+        out = torch.empty(self.T, self.n, dtype=torch.float32, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_grad(self._h, wa.ctypes.data, out.data_ptr()), "cumwin_grad")
+        return out
+
+    def set_timing(self, enable: bool = True):
+        check(self.lib.cumwin_set_timing(self._h, int(bool(enable))), "cumwin_set_timing")
+
+    def get_timing(self) -> dict:
+        u, c = ctypes.c_double(), ctypes.c_double()
+        k, L = ctypes.c_int64(), ctypes.c_int64()
+        check(self.lib.cumwin_get_timing(self._h, ctypes.byref(u), ctypes.byref(c), ctypes.byref(k),
+                                         ctypes.byref(L)), "cumwin_get_timing")
+        return {"update_ms": u.value, "cumulant_ms": c.value, "shifts": k.value,
+                "launches": L.value}
+
+    def status(self) -> int:
+        self._sync_stream()
+        return int(self.lib.cumwin_status(self._h))
+
+
+class CumulantNormLoss(torch.autograd.Function):
+    """L(X) = sum_s w[s] ||C_s(X)||_F^2 for a window X (T x n), with a hand-written adjoint.
+
+    Forward loads X as a fresh window into a handle and reads the norms;
+    backward calls ``cumwin_grad`` on the same handle.
+    """
+
+    @staticmethod
+    def forward(ctx, X: torch.Tensor, w, b: int = 4):
+        T, n = X.shape
+        d = len(w) - 1
+        cw = CumWin(n, d, b, T, T, "fp64", device=X.device)
+        cw.fill(X.detach().contiguous())
+        fro, _ = cw.norms()
+        val = sum(float(w[s]) * fro[s - 1] ** 2 for s in range(1, d + 1))
+        ctx.cw = cw
+        ctx.w = list(w)
+        return torch.tensor(val, dtype=torch.float64, device=X.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        g = ctx.cw.grad(ctx.w)
+        ctx.cw.close()
+        return (g * gout.to(g.dtype)).to(torch.float32), None, None

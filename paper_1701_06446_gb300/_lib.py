@@ -1,0 +1,86 @@
+"""ctypes loader of ``libcumwin.so``: declares the C ABI of ``include/cumwin.h``.
+
+There is no fallback: if the library cannot be built or loaded, importing the
+binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_int, c_i64, c_vp, c_dp, c_fp = (ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float))
+_handle_p = ctypes.POINTER(c_vp)
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "cumwin_create": (c_int, [c_int, c_int, c_int, c_i64, c_int, c_int, c_vp, _handle_p]),
+    "cumwin_destroy": (c_int, [c_vp]),
+    "cumwin_set_stream": (c_int, [c_vp, c_vp]),
+    "cumwin_fill": (c_int, [c_vp, c_vp, c_i64]),
+    "cumwin_push": (c_int, [c_vp, c_vp, c_vp, c_int, c_i64]),
+    "cumwin_push_host": (c_int, [c_vp, c_vp, c_int, c_i64]),
+    "cumwin_cumulants": (c_int, [c_vp, c_int, c_vp]),
+    "cumwin_moments": (c_int, [c_vp, c_int, c_vp]),
+    "cumwin_shift": (c_int, [c_vp, c_vp]),
+    "cumwin_norms": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_norms_device": (c_int, [c_vp, c_vp]),
+    "cumwin_recompute": (c_int, [c_vp]),
+    "cumwin_window": (c_int, [c_vp, c_vp]),
+    "cumwin_grad": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_status": (c_int, [c_vp]),
+    "cumwin_set_timing": (c_int, [c_vp, c_int]),
+    "cumwin_get_timing": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "cumwin_layout_size": (c_i64, [c_int, c_int, c_int]),
+    "cumwin_block_rank": (c_i64, [c_int, c_int, c_int, c_vp]),
+    "cumwin_element_index": (c_i64, [c_int, c_int, c_int, c_vp]),
+    "cumwin_selftest_tables": (c_int, [c_int, c_int, c_int]),
+    "cumwin_strerror": (ctypes.c_char_p, [c_int]),
+    "cumwin_last_error": (ctypes.c_char_p, []),
+    "cumwin_version": (c_int, []),
+}
+
+
+def path() -> str:
+    return _build.OUT
+
+
+def load():
+    """Build (if stale) and load ``libcumwin.so``; raises on any failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = _build.build()
+            lib = ctypes.CDLL(so)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class CumwinError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.cumwin_strerror(code).decode()
+        detail = lib.cumwin_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code})" + (f": {detail}" if detail else ""))
+        self.code = code
+
+
+def check(code: int, where: str) -> int:
+    if code != 0:
+        raise CumwinError(code, where)
+    return code
+
+
+CODES = dict(OK=0, EINVAL=-1, ENOMEM=-2, ECUDA=-3, ESTATE=-4, ENONFINITE=-5, ETIMEOUT=-6,
+             ENOTSUP=-7)
+PRECISION = {"fp64": 0, "bf16": 1, "fp16": 2}

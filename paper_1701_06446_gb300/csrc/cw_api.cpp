@@ -1,0 +1,633 @@
+// C ABI of the sliding-window cumulant library: handle state, table upload,
+// and the sequence of kernels of one window shift (Algorithm 1).
+#include "../../include/cumwin.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cw_internal.h"
+#include "cw_layout.h"
+#include "cw_tc.h"
+
+using namespace cw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail_cuda(cudaError_t e, const char* what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CUMWIN_ENOMEM : CUMWIN_ECUDA;
+}
+
+#define CW_TRY(expr)                                    \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return fail_cuda(_e, #expr); \
+    } while (0)
+
+}  // namespace
+
+struct cumwin_s {
+    int n = 0, d = 0, b = 0, nbar = 0, npad = 0, prec = 0;
+    int64_t T = 0;
+    int p = 1;  // nominal shift size (batch of the mixed-form FP32 sums)
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    int64_t* head = nullptr;  // device: ring slot of the oldest sample
+    bool filled = false;
+    std::vector<void*> allocs;
+
+    float* ring = nullptr;      // [T][npad] raw samples
+    float* stage = nullptr;     // [2T][npad] X_(+) then X_(-)
+    float* hin = nullptr;       // [T][npad] device copy of host X_(+)
+    float* shift = nullptr;     // [npad]
+    float* shift_zero = nullptr;
+    int* status = nullptr;
+    double* S[kMaxOrder + 1] = {};
+    double* C[kMaxOrder + 1] = {};
+    int64_t E[kMaxOrder + 1] = {};
+
+    UpdateArgs upd{};
+    UpdTile* tiles = nullptr;
+    int ntiles = 0;
+    TcPlan tc{};  // tensor-core update plan (mixed forms)
+
+    CumArgs cum[kMaxOrder + 1]{};
+    int cum_grid[kMaxOrder + 1] = {};
+    double* normpart = nullptr;
+    int32_t* part_off = nullptr;
+    double* fro2 = nullptr;
+
+    // kernel timing (cumwin_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;  // 3 per timed shift
+    int64_t timed = 0, launches = 0;
+
+    template <class T>
+    cudaError_t alloc(T** p, size_t count)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) return e;
+        allocs.push_back(q);
+        *p = (T*)q;
+        return cudaSuccess;
+    }
+    template <class T>
+    cudaError_t upload(T** p, const std::vector<T>& v)
+    {
+        cudaError_t e = alloc(p, v.size());
+        if (e != cudaSuccess) return e;
+        if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return e;
+    }
+    void release()
+    {
+        for (void* q : allocs) cudaFree(q);
+        allocs.clear();
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+    }
+    // event slot k of the current timed shift, or null when not timing
+    cudaEvent_t mark(int k)
+    {
+        if (!timing || timed * 3 + k >= (int64_t)ev.size()) return nullptr;
+        cudaEvent_t e = ev[timed * 3 + k];
+        cudaEventRecord(e, stream);
+        return e;
+    }
+};
+
+namespace {
+
+int run_cumulants(cumwin_t h, int64_t advance)
+{
+    for (int s = 1; s <= h->d; ++s) CW_TRY(launch_cumulants(h->cum[s], h->cum_grid[s], h->stream));
+    CW_TRY(launch_norm_final(h->normpart, h->part_off, h->d, h->fro2, h->head, advance, h->T,
+                             h->stream));
+    h->launches += h->d + 1;
+    if (h->mark(2) != nullptr) h->timed++;
+    return CUMWIN_OK;
+}
+
+// Moment sums over `K` staged rows; the first `npos` enter with +, the rest with -.
+int run_update(cumwin_t h, const float* rows, int64_t K, int64_t npos, int64_t batch)
+{
+    h->mark(0);
+    if (h->prec == CUMWIN_FP64) {
+        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, rows, K, npos, h->shift, h->stream));
+        h->launches += 1;
+    } else {
+        CW_TRY(launch_update_tc(h->tc, h->upd, rows, K, npos, batch, h->shift, h->stream));
+        h->launches += tc_launch_count(h->tc, K, npos, batch);
+    }
+    h->mark(1);
+    return CUMWIN_OK;
+}
+
+int zero_sums(cumwin_t h)
+{
+    for (int s = 1; s <= h->d; ++s) CW_TRY(launch_zero(h->S[s], h->E[s], h->stream));
+    return CUMWIN_OK;
+}
+
+int64_t element_index_impl(int n, int b, int order, const int* i)
+{
+    if (n < 1 || b < 1 || order < 1 || order > kMaxOrder || i == nullptr) return -1;
+    int v[kMaxOrder], j[kMaxOrder];
+    for (int k = 0; k < order; ++k) {
+        if (i[k] < 0 || i[k] >= n) return -1;
+        v[k] = i[k];
+    }
+    std::sort(v, v + order);
+    for (int k = 0; k < order; ++k) j[k] = v[k] / b;
+    const int nbar = (n + b - 1) / b;
+    int64_t off = 0;
+    for (int k = 0; k < order; ++k) off = off * b + v[k] % b;
+    return rank_sorted(j, order, nbar) * ipow(b, order) + off;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cumwin_version(void) { return 100; }
+
+const char* cumwin_strerror(int code)
+{
+    switch (code) {
+    case CUMWIN_OK: return "ok";
+    case CUMWIN_EINVAL: return "invalid argument";
+    case CUMWIN_ENOMEM: return "device allocation failed";
+    case CUMWIN_ECUDA: return "CUDA runtime error";
+    case CUMWIN_ESTATE: return "call out of sequence";
+    case CUMWIN_ENONFINITE: return "non-finite sample in the window";
+    case CUMWIN_ETIMEOUT: return "bounded device wait timed out";
+    case CUMWIN_ENOTSUP: return "not supported on this device or build";
+    default: return "unknown error";
+    }
+}
+
+const char* cumwin_last_error(void) { return g_last_error.c_str(); }
+
+int64_t cumwin_layout_size(int n, int b, int order)
+{
+    if (n < 1 || b < 1 || order < 1 || order > kMaxOrder) return -1;
+    const int nbar = (n + b - 1) / b;
+    return n_sorted(nbar, order) * ipow(b, order);
+}
+
+int64_t cumwin_block_rank(int n, int b, int order, const int* j)
+{
+    if (n < 1 || b < 1 || order < 1 || order > kMaxOrder || j == nullptr) return -1;
+    return rank_sorted(j, order, (n + b - 1) / b);
+}
+
+int64_t cumwin_element_index(int n, int b, int order, const int* i)
+{
+    return element_index_impl(n, b, order, i);
+}
+
+int cumwin_selftest_tables(int n, int b, int s)
+{
+    if (n < 1 || n > kMaxN || b < 1 || s < 1 || s > kMaxOrder) return CUMWIN_EINVAL;
+    const int nbar = (n + b - 1) / b;
+    const int64_t E = n_sorted(nbar, s) * ipow(b, s);
+    if (E > (int64_t)1 << 26) return CUMWIN_EINVAL;
+    const int64_t bs = ipow(b, s);
+    // 1. update tables: every stored element produced exactly once, at the
+    //    storage index of its (row vars ++ col vars) multi-index.
+    UpdateTables t = build_update_tables(n, b, s);
+    std::vector<int> hits(E, 0);
+    const int ncols = (int)t.colvar.size();
+    for (int m = 0; m < nbar; ++m) {
+        for (int r = t.rowstart[m]; r < t.rowstart[m + 1]; ++r) {
+            for (int c = t.colstart[m]; c < ncols; ++c) {
+                int vars[kMaxOrder], jj[kMaxOrder];
+                for (int k = 0; k < t.h; ++k) vars[k] = (t.rowvar[r] >> (8 * k)) & 0xff;
+                for (int k = 0; k < t.sh; ++k) vars[t.h + k] = (t.colvar[c] >> (8 * k)) & 0xff;
+                for (int k = 0; k < s; ++k) jj[k] = vars[k] / b;
+                const int64_t rk = rank_sorted(jj, s, nbar);
+                if (rk < 0) return 1;  // not a sorted block
+                int64_t off = 0;
+                for (int k = 0; k < s; ++k) off = off * b + vars[k] % b;
+                const int64_t want = rk * bs + off;
+                const int64_t got = t.rowoff[r] + t.coloff[c];
+                if (got != want || got < 0 || got >= E) return 2;
+                hits[got]++;
+            }
+        }
+    }
+    for (int64_t e = 0; e < E; ++e)
+        if (hits[e] != 1) return 3;
+    // 2. cumulant tables: sub-block lookups of a synthetic symmetric tensor
+    //    f(i) = prod_k (i_k + 1.5) return f of the sub-multi-index.
+    if (s >= 2) {
+        CumTables ct = build_cum_tables(n, b, s);
+        const std::vector<int> blocks = enumerate_sorted(nbar, s);
+        const int64_t nb = (int64_t)blocks.size() / s;
+        for (int64_t q = 0; q < nb; ++q) {
+            const int* j = &blocks[q * s];
+            for (int64_t o = 0; o < bs; ++o) {
+                int dig[kMaxOrder];
+                int64_t rem = o;
+                for (int k = s - 1; k >= 0; --k) {
+                    dig[k] = (int)(rem % b);
+                    rem /= b;
+                }
+                for (int u = 0; u < ct.nsub; ++u) {
+                    const unsigned mask = ct.masks[u];
+                    int la = 0, lr = 0;
+                    int64_t offA = 0, offR = 0;
+                    int va[kMaxOrder], vr[kMaxOrder];
+                    for (int k = 0; k < s; ++k) {
+                        const int var = j[k] * b + dig[k];
+                        if ((mask >> k) & 1u) {
+                            offA = offA * b + dig[k];
+                            va[la++] = var;
+                        } else {
+                            offR = offR * b + dig[k];
+                            vr[lr++] = var;
+                        }
+                    }
+                    const int64_t ia = (int64_t)ct.subrank[(q * ct.nsub + u) * 2] * ipow(b, la) + offA;
+                    const int64_t ir = (int64_t)ct.subrank[(q * ct.nsub + u) * 2 + 1] * ipow(b, lr) + offR;
+                    // the storage index of the sub-tuple in its own order must hold
+                    // the same multiset of variables
+                    int padA = 0, padR = 0;
+                    for (int k = 0; k < la; ++k) padA |= va[k] >= n;
+                    for (int k = 0; k < lr; ++k) padR |= vr[k] >= n;
+                    if (!padA && element_index_impl(n, b, la, va) >= 0) {
+                        // same block & offset as canonical storage up to the in-block
+                        // permutation: compare the decoded multiset
+                        int64_t rk = ia / ipow(b, la), of = ia % ipow(b, la);
+                        std::vector<int> jb = enumerate_sorted(nbar, la);
+                        int dec[kMaxOrder];
+                        int64_t rr = of;
+                        for (int k = la - 1; k >= 0; --k) {
+                            dec[k] = jb[rk * la + k] * b + (int)(rr % b);
+                            rr /= b;
+                        }
+                        std::sort(dec, dec + la);
+                        std::sort(va, va + la);
+                        for (int k = 0; k < la; ++k)
+                            if (dec[k] != va[k]) return 4;
+                    }
+                    if (!padR) {
+                        int64_t rk = ir / ipow(b, lr), of = ir % ipow(b, lr);
+                        std::vector<int> jb = enumerate_sorted(nbar, lr);
+                        int dec[kMaxOrder];
+                        int64_t rr = of;
+                        for (int k = lr - 1; k >= 0; --k) {
+                            dec[k] = jb[rk * lr + k] * b + (int)(rr % b);
+                            rr /= b;
+                        }
+                        std::sort(dec, dec + lr);
+                        std::sort(vr, vr + lr);
+                        for (int k = 0; k < lr; ++k)
+                            if (dec[k] != vr[k]) return 5;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream,
+                  cumwin_t* out)
+{
+    if (out == nullptr) return CUMWIN_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > kMaxN || d < 1 || d > kMaxOrder || b < 1 || T < 1) return CUMWIN_EINVAL;
+    if (p < 1 || p > T) return CUMWIN_EINVAL;
+    if (precision != CUMWIN_FP64 && precision != CUMWIN_MIXED_BF16 && precision != CUMWIN_MIXED_FP16)
+        return CUMWIN_EINVAL;
+    const int nbar = (n + b - 1) / b;
+    if ((int64_t)nbar * b > kMaxN) return CUMWIN_EINVAL;
+    if (T > ((int64_t)1 << 40)) return CUMWIN_EINVAL;
+
+    cumwin_s* h = new cumwin_s();
+    h->n = n;
+    h->d = d;
+    h->b = b;
+    h->nbar = nbar;
+    h->npad = nbar * b;
+    h->T = T;
+    h->p = p;
+    h->prec = precision;
+    h->stream = (cudaStream_t)cuda_stream;
+
+    auto bail = [&](int code) {
+        h->release();
+        delete h;
+        return code;
+    };
+#define CW_CREATE_TRY(expr)                               \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return bail(fail_cuda(_e, #expr)); \
+    } while (0)
+
+    CW_CREATE_TRY(cudaGetDevice(&h->device));
+    CW_CREATE_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+    if (precision != CUMWIN_FP64) {
+        int major = 0, minor = 0;
+        CW_CREATE_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device));
+        CW_CREATE_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device));
+        if (!(major == 10 && minor == 3)) {
+            g_last_error = "mixed precision needs an sm_103 device";
+            return bail(CUMWIN_ENOTSUP);
+        }
+    }
+    const int npad = h->npad;
+    CW_CREATE_TRY(h->alloc(&h->ring, (size_t)T * npad));
+    CW_CREATE_TRY(h->alloc(&h->stage, (size_t)2 * T * npad));
+    CW_CREATE_TRY(h->alloc(&h->hin, (size_t)T * npad));
+    CW_CREATE_TRY(h->alloc(&h->shift, npad));
+    CW_CREATE_TRY(cudaMemset(h->shift, 0, sizeof(float) * npad));
+    CW_CREATE_TRY(h->alloc(&h->status, 1));
+    CW_CREATE_TRY(h->alloc(&h->head, 1));
+    CW_CREATE_TRY(cudaMemset(h->head, 0, sizeof(int64_t)));
+    CW_CREATE_TRY(cudaMemset(h->status, 0, sizeof(int)));
+    CW_CREATE_TRY(cudaMemset(h->ring, 0, sizeof(float) * (size_t)T * npad));
+    for (int s = 1; s <= d; ++s) {
+        h->E[s] = n_sorted(nbar, s) * ipow(b, s);
+        CW_CREATE_TRY(h->alloc(&h->S[s], h->E[s]));
+        CW_CREATE_TRY(h->alloc(&h->C[s], h->E[s]));
+        CW_CREATE_TRY(cudaMemset(h->S[s], 0, sizeof(double) * h->E[s]));
+        CW_CREATE_TRY(cudaMemset(h->C[s], 0, sizeof(double) * h->E[s]));
+    }
+
+    // update tables and tiles
+    h->upd.npad = npad;
+    std::vector<UpdTile> tiles;
+    std::vector<UpdateTables> ut(d + 1);
+    for (int s = 1; s <= d; ++s) {
+        ut[s] = build_update_tables(n, b, s);
+        const UpdateTables& t = ut[s];
+        OrderTables& ot = h->upd.ord[s];
+        CW_CREATE_TRY(h->upload((uint32_t**)&ot.rowvar, t.rowvar));
+        CW_CREATE_TRY(h->upload((int64_t**)&ot.rowoff, t.rowoff));
+        CW_CREATE_TRY(h->upload((uint32_t**)&ot.colvar, t.colvar));
+        CW_CREATE_TRY(h->upload((int64_t**)&ot.coloff, t.coloff));
+        ot.S = h->S[s];
+        ot.h = t.h;
+        ot.sh = t.sh;
+        ot.nrows = (int32_t)t.rowvar.size();
+        ot.ncols = (int32_t)t.colvar.size();
+        for (int m = 0; m < nbar; ++m) {
+            const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
+            const int c0 = t.colstart[m], c1 = ot.ncols;
+            for (int r = r0; r < r1; r += 64)
+                for (int c = c0; c < c1; c += 64) {
+                    UpdTile u{};
+                    u.s = s;
+                    u.row0 = r;
+                    u.nrows = std::min(64, r1 - r);
+                    u.col0 = c;
+                    u.ncols = std::min(64, c1 - c);
+                    tiles.push_back(u);
+                }
+        }
+    }
+    h->ntiles = (int)tiles.size();
+    if (precision == CUMWIN_FP64) {
+        CW_CREATE_TRY(h->upload(&h->tiles, tiles));
+    } else {
+        int rc = tc_plan_create(h->tc, ut, d, n, b, npad, (int)T, h->sm_count, precision,
+                                [&](size_t bytes, void** p) { return h->alloc((char**)p, bytes); });
+        if (rc != 0) {
+            g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
+            return bail(CUMWIN_ECUDA);
+        }
+    }
+
+    // cumulant recovery tables
+    std::vector<int32_t> part_off(d + 1, 0);
+    for (int s = 1; s <= d; ++s) {
+        CumTables ct = build_cum_tables(n, b, s);
+        CumArgs& a = h->cum[s];
+        for (int k = 1; k <= d; ++k) {
+            a.S[k] = h->S[k];
+            a.C[k] = h->C[k];
+        }
+        a.Cout = h->C[s];
+        CW_CREATE_TRY(h->upload((int32_t**)&a.subrank, ct.subrank));
+        CW_CREATE_TRY(h->upload((double**)&a.mult, ct.mult));
+        a.shift = h->shift;
+        a.invT = 1.0 / (double)T;
+        a.E = h->E[s];
+        a.s = s;
+        a.b = b;
+        a.bs = (int32_t)ipow(b, s);
+        a.nsub = ct.nsub;
+        for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
+        int64_t g = (h->E[s] + 255) / 256;
+        g = std::min<int64_t>(g, 4 * (int64_t)h->sm_count);
+        h->cum_grid[s] = (int)std::max<int64_t>(g, 1);
+        part_off[s] = part_off[s - 1] + h->cum_grid[s];
+    }
+    // part_off[s-1]..part_off[s] are the partials of order s
+    std::vector<int32_t> po(part_off.begin(), part_off.end());
+    CW_CREATE_TRY(h->alloc(&h->normpart, (size_t)part_off[d]));
+    for (int s = 1; s <= d; ++s) h->cum[s].normpart = h->normpart + part_off[s - 1];
+    CW_CREATE_TRY(h->upload(&h->part_off, po));
+    CW_CREATE_TRY(h->alloc(&h->fro2, d));
+    CW_CREATE_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
+    CW_CREATE_TRY(cudaDeviceSynchronize());
+#undef CW_CREATE_TRY
+    *out = h;
+    return CUMWIN_OK;
+}
+
+int cumwin_destroy(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_OK;
+    cudaStreamSynchronize(h->stream);
+    h->release();
+    delete h;
+    return CUMWIN_OK;
+}
+
+int cumwin_set_stream(cumwin_t h, void* cuda_stream)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    h->stream = (cudaStream_t)cuda_stream;
+    return CUMWIN_OK;
+}
+
+int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx)
+{
+    if (h == nullptr || X_dev == nullptr || ldx < h->n) return CUMWIN_EINVAL;
+    CW_TRY(launch_fill_ring(X_dev, ldx, h->ring, h->T, h->n, h->npad, h->status, h->stream));
+    if (h->prec != CUMWIN_FP64)
+        CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
+    int rc = zero_sums(h);
+    if (rc) return rc;
+    rc = run_update(h, h->ring, h->T, h->T, h->p);
+    if (rc) return rc;
+    CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
+    rc = run_cumulants(h, 0);
+    if (rc) return rc;
+    h->filled = true;
+    return CUMWIN_OK;
+}
+
+int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p, int64_t ld)
+{
+    if (h == nullptr || x_in_dev == nullptr || p < 1 || p > h->T || ld < h->n) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(launch_stage(x_in_dev, ld, x_out_dev, ld, h->ring, h->T, h->head, p, h->n, h->npad,
+                        h->stage, h->status, h->stream));
+    h->launches += 1;
+    int rc = run_update(h, h->stage, 2 * (int64_t)p, p, p);
+    if (rc) return rc;
+    return run_cumulants(h, p);
+}
+
+int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld)
+{
+    if (h == nullptr || x_in_host == nullptr || p < 1 || p > h->T || ld < h->n) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(cudaMemcpy2DAsync(h->hin, sizeof(float) * h->npad, x_in_host, sizeof(float) * ld,
+                             sizeof(float) * h->n, p, cudaMemcpyHostToDevice, h->stream));
+    return cumwin_push(h, h->hin, nullptr, p, h->npad);
+}
+
+int cumwin_cumulants(cumwin_t h, int order, double* out_dev)
+{
+    if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    if (order == 1) {
+        CW_TRY(launch_add_shift(h->C[1], h->shift, h->n, h->npad, out_dev, h->stream));
+    } else {
+        CW_TRY(cudaMemcpyAsync(out_dev, h->C[order], sizeof(double) * h->E[order],
+                               cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return CUMWIN_OK;
+}
+
+int cumwin_moments(cumwin_t h, int order, double* out_dev)
+{
+    if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(launch_scale(h->S[order], 1.0 / (double)h->T, h->E[order], out_dev, h->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_shift(cumwin_t h, float* shift_host)
+{
+    if (h == nullptr || shift_host == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(cudaMemcpyAsync(shift_host, h->shift, sizeof(float) * h->n, cudaMemcpyDeviceToHost,
+                           h->stream));
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_norms_device(cumwin_t h, double* fro2_dev)
+{
+    if (h == nullptr || fro2_dev == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(cudaMemcpyAsync(fro2_dev, h->fro2, sizeof(double) * h->d, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    double z[kMaxOrder];
+    int st = 0;
+    CW_TRY(cudaMemcpyAsync(z, h->fro2, sizeof(double) * h->d, cudaMemcpyDeviceToHost, h->stream));
+    CW_TRY(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    double fro[kMaxOrder];
+    for (int s = 0; s < h->d; ++s) fro[s] = std::sqrt(z[s]);
+    if (fro_host)
+        for (int s = 0; s < h->d; ++s) fro_host[s] = fro[s];
+    if (nu_host)
+        for (int s = 1; s <= h->d; ++s)
+            nu_host[s - 1] = (s < 3 || h->d < 2) ? NAN : fro[s - 1] / std::pow(fro[1], 0.5 * s);
+    if (st & kStatusNonFinite) return CUMWIN_ENONFINITE;
+    if (st & kStatusTimeout) return CUMWIN_ETIMEOUT;
+    return CUMWIN_OK;
+}
+
+int cumwin_recompute(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    int rc = zero_sums(h);
+    if (rc) return rc;
+    rc = run_update(h, h->ring, h->T, h->T, h->p);
+    if (rc) return rc;
+    return run_cumulants(h, 0);
+}
+
+int cumwin_window(cumwin_t h, float* out_dev)
+{
+    if (h == nullptr || out_dev == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(launch_window_copy(h->ring, h->T, h->head, h->n, h->npad, out_dev, h->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
+{
+    if (h == nullptr || w_host == nullptr || dX_dev == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    return CUMWIN_ENOTSUP;
+}
+
+int cumwin_set_timing(cumwin_t h, int enable)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    h->timing = enable != 0;
+    h->timed = 0;
+    h->launches = 0;
+    if (h->timing && h->ev.empty()) {
+        h->ev.resize(3 * 65536);
+        for (auto& e : h->ev) CW_TRY(cudaEventCreate(&e));
+    }
+    return CUMWIN_OK;
+}
+
+int cumwin_get_timing(cumwin_t h, double* update_ms, double* cumulant_ms, int64_t* shifts,
+                      int64_t* launches)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    double u = 0.0, c = 0.0;
+    for (int64_t k = 0; k < h->timed; ++k) {
+        float a = 0.f, b = 0.f;
+        CW_TRY(cudaEventElapsedTime(&a, h->ev[3 * k], h->ev[3 * k + 1]));
+        CW_TRY(cudaEventElapsedTime(&b, h->ev[3 * k + 1], h->ev[3 * k + 2]));
+        u += a;
+        c += b;
+    }
+    if (update_ms) *update_ms = u;
+    if (cumulant_ms) *cumulant_ms = c;
+    if (shifts) *shifts = h->timed;
+    if (launches) *launches = h->launches;
+    return CUMWIN_OK;
+}
+
+int cumwin_status(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    int st = 0;
+    CW_TRY(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    if (st & kStatusNonFinite) return CUMWIN_ENONFINITE;
+    if (st & kStatusTimeout) return CUMWIN_ETIMEOUT;
+    return CUMWIN_OK;
+}
+
+}  // extern "C"

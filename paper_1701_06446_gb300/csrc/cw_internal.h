@@ -1,0 +1,97 @@
+// Internal definitions shared by the host library and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cw {
+
+constexpr int kMaxOrder = 8;
+constexpr int kMaxN = 256;
+
+// ---------------------------------------------------------------------------
+// Moment-sum update (Eqs. 6-7, Algorithm 2) as a set of dense GEMMs.
+//
+// For order s the stored elements are split between a left factor of h = ceil(s/2)
+// indices and a right factor of sh = s - h indices.  Left rows are (sorted
+// block h-tuple jL, in-block aL) grouped by the last block index m of jL;
+// right columns are (sorted block sh-tuple jR, aR) in lexicographic order.
+// Group m pairs its rows with every column whose first block index is >= m,
+// so that jL ++ jR is a sorted block s-tuple, and every stored element is
+// produced exactly once:
+//     dS[rowoff[r] + coloff[c]] = sum_t sign_t * prod_{k<h} y[t, rowvar_k(r)]
+//                                              * prod_{k<sh} y[t, colvar_k(c)]
+// rowvar/colvar pack the variable indices one byte each (lowest byte first).
+// ---------------------------------------------------------------------------
+struct OrderTables {
+    const uint32_t* rowvar;
+    const int64_t* rowoff;
+    const uint32_t* colvar;
+    const int64_t* coloff;
+    double* S;      // running FP64 sums of order s (block layout)
+    int32_t h, sh;  // factors on the row side / column side
+    int32_t nrows, ncols;
+};
+
+struct UpdateArgs {
+    OrderTables ord[kMaxOrder + 1];  // index = order
+    int32_t npad;                    // row stride of the sample buffers
+};
+
+// One output tile of the update: rows [row0, row0+nrows) and columns
+// [col0, col0+ncols) of the order-s GEMM of one group.
+struct UpdTile {
+    int32_t s, row0, nrows, col0, ncols, pad0, pad1, pad2;
+};
+
+// ---------------------------------------------------------------------------
+// Moment-to-cumulant recovery (Algorithms 3-4) through the subset recursion
+//     C_s[i] = M_s[i] - sum_{A contains position 0, A != all} C_|A|[i_A] M_{s-|A|}[i_rest]
+// For a sorted block j every sub-tuple j_A is sorted, hence a stored block;
+// subrank holds (rank(j_A), rank(j_rest)) for each block and each subset.
+// ---------------------------------------------------------------------------
+struct CumArgs {
+    const double* S[kMaxOrder + 1];  // running sums per order (moments = S * invT)
+    const double* C[kMaxOrder + 1];  // cumulants per order (order 1 about the shift)
+    double* Cout;                    // = C[s]
+    const int32_t* subrank;          // [nblocks][nsub][2]
+    const double* mult;              // [nblocks] block multiplicity s!/prod r_l!
+    double* normpart;                // [gridDim.x] partial sums of mult * C^2
+    const float* shift;              // order-1 norm uses C_1 + shift
+    double invT;
+    int64_t E;                       // stored elements of order s
+    int32_t s, b, bs, nsub;
+    uint8_t mask[128];               // subset bitmasks over the s positions
+};
+
+// Device-side status bits (sticky).
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusTimeout = 2;
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+cudaError_t launch_stage(const float* x_in, int64_t ld_in, const float* x_out, int64_t ld_out,
+                         float* ring, int64_t T, const int64_t* head, int p, int n, int npad,
+                         float* stage, int* status, cudaStream_t st);
+cudaError_t launch_fill_ring(const float* X, int64_t ldx, float* ring, int64_t T, int n, int npad,
+                             int* status, cudaStream_t st);
+cudaError_t launch_column_mean(const float* ring, int64_t T, int n, int npad, float* shift,
+                               cudaStream_t st);
+cudaError_t launch_window_copy(const float* ring, int64_t T, const int64_t* head, int n, int npad,
+                               float* out, cudaStream_t st);
+cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int ntiles,
+                              const float* rows, int64_t K, int64_t npos, const float* shift,
+                              cudaStream_t st);
+cudaError_t launch_cumulants(const CumArgs& a, int grid, cudaStream_t st);
+// Also advances the ring head by `advance` rows (mod T): the head lives in
+// device memory so that a captured shift can be replayed.
+cudaError_t launch_norm_final(const double* normpart, const int32_t* part_off, int d,
+                              double* fro2, int64_t* head, int64_t advance, int64_t T,
+                              cudaStream_t st);
+cudaError_t launch_zero(double* p, int64_t count, cudaStream_t st);
+cudaError_t launch_add_shift(const double* C1, const float* shift, int n, int npad, double* out,
+                             cudaStream_t st);
+cudaError_t launch_scale(const double* S, double invT, int64_t count, double* out, cudaStream_t st);
+
+}  // namespace cw

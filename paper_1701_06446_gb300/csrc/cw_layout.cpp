@@ -1,0 +1,183 @@
+// Host-side block-layout arithmetic and the tables of the update and
+// cumulant-recovery kernels.
+#include "cw_layout.h"
+
+#include <algorithm>
+#include <cmath>
+
+#include "cw_internal.h"
+
+namespace cw {
+
+int64_t binom(int64_t n, int64_t k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    k = std::min(k, n - k);
+    int64_t r = 1;
+    for (int64_t i = 1; i <= k; ++i) r = r * (n - k + i) / i;  // exact at every step
+    return r;
+}
+
+int64_t n_sorted(int nbar, int s)
+{
+    if (s == 0) return 1;
+    return binom((int64_t)nbar + s - 1, s);
+}
+
+int64_t ipow(int64_t b, int e)
+{
+    int64_t r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+int64_t rank_sorted(const int* j, int s, int nbar)
+{
+    int64_t r = 0;
+    int prev = 0;
+    for (int k = 0; k < s; ++k) {
+        if (j[k] < prev || j[k] >= nbar) return -1;
+        // tuples that agree on positions < k and hold v < j[k] at position k:
+        // the remaining s-k-1 positions are any sorted tuple over [v, nbar)
+        for (int v = prev; v < j[k]; ++v) r += n_sorted(nbar - v, s - k - 1);
+        prev = j[k];
+    }
+    return r;
+}
+
+std::vector<int> enumerate_sorted(int nbar, int s)
+{
+    std::vector<int> out;
+    if (s == 0) return out;
+    std::vector<int> j(s, 0);
+    for (;;) {
+        out.insert(out.end(), j.begin(), j.end());
+        int k = s - 1;
+        while (k >= 0 && j[k] == nbar - 1) --k;
+        if (k < 0) break;
+        j[k]++;
+        for (int q = k + 1; q < s; ++q) j[q] = j[k];
+    }
+    return out;
+}
+
+double block_multiplicity(const int* j, int s)
+{
+    double f = 1.0;
+    for (int i = 2; i <= s; ++i) f *= i;
+    int run = 1;
+    for (int k = 1; k <= s; ++k) {
+        if (k < s && j[k] == j[k - 1]) {
+            run++;
+        } else {
+            for (int i = 2; i <= run; ++i) f /= i;
+            run = 1;
+        }
+    }
+    return f;
+}
+
+static uint32_t pack_vars(const int* v, int cnt)
+{
+    uint32_t p = 0;
+    for (int k = 0; k < cnt; ++k) p |= (uint32_t)v[k] << (8 * k);
+    return p;
+}
+
+UpdateTables build_update_tables(int n, int b, int s)
+{
+    UpdateTables t;
+    const int nbar = (n + b - 1) / b;
+    const int h = split_rows(s), sh = s - h;
+    t.s = s;
+    t.h = h;
+    t.sh = sh;
+    const int64_t bs = ipow(b, s), bh = ipow(b, h), bsh = ipow(b, sh);
+    auto off_first_below = [&](int m) -> int64_t {  // sorted sh-tuples whose first entry < m
+        if (sh == 0) return 0;
+        return n_sorted(nbar, sh) - n_sorted(nbar - m, sh);
+    };
+
+    // left rows, grouped by the last block index m
+    const std::vector<int> left = enumerate_sorted(nbar, h);
+    const int64_t nleft = (int64_t)left.size() / h;
+    t.rowstart.assign(nbar + 1, 0);
+    std::vector<int> full(s), vars(kMaxOrder);
+    for (int m = 0; m < nbar; ++m) {
+        t.rowstart[m] = (int32_t)t.rowvar.size();
+        const int64_t off_m = off_first_below(m);
+        for (int64_t q = 0; q < nleft; ++q) {
+            const int* jl = &left[q * h];
+            if (jl[h - 1] != m) continue;
+            for (int k = 0; k < h; ++k) full[k] = jl[k];
+            for (int k = h; k < s; ++k) full[k] = m;
+            const int64_t P = rank_sorted(full.data(), s, nbar);
+            for (int64_t a = 0; a < bh; ++a) {
+                int64_t rem = a;
+                for (int k = h - 1; k >= 0; --k) {
+                    vars[k] = jl[k] * b + (int)(rem % b);
+                    rem /= b;
+                }
+                t.rowvar.push_back(pack_vars(vars.data(), h));
+                t.rowoff.push_back((P - off_m) * bs + a * bsh);
+            }
+        }
+    }
+    t.rowstart[nbar] = (int32_t)t.rowvar.size();
+
+    // right columns, lexicographic
+    t.colstart.assign(nbar, 0);
+    if (sh == 0) {
+        t.colvar.push_back(0u);
+        t.coloff.push_back(0);
+    } else {
+        const std::vector<int> right = enumerate_sorted(nbar, sh);
+        const int64_t nright = (int64_t)right.size() / sh;
+        for (int64_t q = 0; q < nright; ++q) {
+            const int* jr = &right[q * sh];
+            for (int64_t a = 0; a < bsh; ++a) {
+                int64_t rem = a;
+                for (int k = sh - 1; k >= 0; --k) {
+                    vars[k] = jr[k] * b + (int)(rem % b);
+                    rem /= b;
+                }
+                t.colvar.push_back(pack_vars(vars.data(), sh));
+                t.coloff.push_back(q * bs + a);
+            }
+        }
+        for (int m = 0; m < nbar; ++m) t.colstart[m] = (int32_t)(off_first_below(m) * bsh);
+    }
+    return t;
+}
+
+CumTables build_cum_tables(int n, int b, int s)
+{
+    CumTables t;
+    const int nbar = (n + b - 1) / b;
+    t.s = s;
+    const unsigned full = (1u << s) - 1u;
+    for (unsigned A = 1; A < full; ++A)
+        if (A & 1u) t.masks.push_back((uint8_t)A);
+    t.nsub = (int)t.masks.size();
+    const std::vector<int> blocks = enumerate_sorted(nbar, s);
+    const int64_t nb = (int64_t)blocks.size() / s;
+    t.subrank.resize((size_t)nb * t.nsub * 2);
+    t.mult.resize(nb);
+    int ja[kMaxOrder], jc[kMaxOrder];
+    for (int64_t q = 0; q < nb; ++q) {
+        const int* j = &blocks[q * s];
+        t.mult[q] = block_multiplicity(j, s);
+        for (int u = 0; u < t.nsub; ++u) {
+            int na = 0, nc = 0;
+            for (int k = 0; k < s; ++k) {
+                if ((t.masks[u] >> k) & 1u) ja[na++] = j[k];
+                else jc[nc++] = j[k];
+            }
+            t.subrank[((size_t)q * t.nsub + u) * 2 + 0] = (int32_t)rank_sorted(ja, na, nbar);
+            t.subrank[((size_t)q * t.nsub + u) * 2 + 1] = (int32_t)rank_sorted(jc, nc, nbar);
+        }
+    }
+    return t;
+}
+
+}  // namespace cw

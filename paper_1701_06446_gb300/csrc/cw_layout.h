@@ -1,0 +1,46 @@
+// Host-side block-layout arithmetic and table generation.
+//
+// Block structure of Section 2.3 / Algorithm 5: sorted block multi-indices
+// j1 <= ... <= js over nbar = ceil(n/b) blocks per mode, lexicographic order,
+// each block a dense b^s array (a1 slowest).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace cw {
+
+int64_t binom(int64_t n, int64_t k);
+// Number of sorted s-tuples over [0, nbar).
+int64_t n_sorted(int nbar, int s);
+// Lexicographic rank of a sorted s-tuple over [0, nbar); -1 if invalid.
+int64_t rank_sorted(const int* j, int s, int nbar);
+// All sorted s-tuples over [0, nbar) in lexicographic order, flattened.
+std::vector<int> enumerate_sorted(int nbar, int s);
+// Block multiplicity s!/prod r_l! (Algorithm 5), r_l the runs of equal entries.
+double block_multiplicity(const int* j, int s);
+int64_t ipow(int64_t b, int e);
+
+// Tables of the order-s update GEMMs (see UpdateArgs in cw_internal.h).
+struct UpdateTables {
+    int s = 0, h = 0, sh = 0;
+    std::vector<uint32_t> rowvar, colvar;
+    std::vector<int64_t> rowoff, coloff;
+    std::vector<int32_t> rowstart;  // [nbar + 1] rows of group m
+    std::vector<int32_t> colstart;  // [nbar] first column of group m
+};
+UpdateTables build_update_tables(int n, int b, int s);
+
+// Tables of the order-s cumulant recovery (see CumArgs in cw_internal.h).
+struct CumTables {
+    int s = 0, nsub = 0;
+    std::vector<uint8_t> masks;      // [nsub]
+    std::vector<int32_t> subrank;    // [nblocks][nsub][2]
+    std::vector<double> mult;        // [nblocks]
+};
+CumTables build_cum_tables(int n, int b, int s);
+
+// Split of order s into row factors (h) and column factors (s - h).
+inline int split_rows(int s) { return (s + 1) / 2; }
+
+}  // namespace cw

@@ -1,0 +1,90 @@
+"""CPU-only checks of the C ABI: the library builds, loads and exports every
+symbol declared in include/*.h; its host-side layout helpers agree with the
+oracle's independently written block layout (Section 2.3, Algorithm 5); the
+update and cumulant tables pass their enumeration self-test.  No GPU calls."""
+import ctypes
+import glob
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1701_06446_gb300 as cw
+from paper_1701_06446_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(cumwin_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_lib.load()._name)
+    names = declared_functions()
+    assert "cumwin_create" in names and "cumwin_push" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding declares exactly the header's functions
+    assert set(_lib.SIGNATURES) == set(names)
+
+
+def test_version_and_errors():
+    lib = _lib.load()
+    assert lib.cumwin_version() >= 100
+    for code in range(0, -8, -1):
+        assert lib.cumwin_strerror(code)
+    with pytest.raises(ValueError):
+        cw.layout_size(4, 2, 9)
+    with pytest.raises(ValueError):
+        cw.layout_size(0, 2, 3)
+
+
+@pytest.mark.parametrize("n,b,s", [(4, 2, 4), (60, 3, 2), (60, 3, 3), (48, 4, 3), (7, 3, 4),
+                                   (5, 2, 5), (3, 4, 6)])
+def test_layout_size_and_rank_match_oracle(n, b, s):
+    blocks = oracle.sorted_block_tuples(n, b, s)
+    assert cw.layout_size(n, b, s) == len(blocks) * b ** s == oracle.layout_size(n, b, s)
+    step = max(1, len(blocks) // 300)
+    for r in range(0, len(blocks), step):
+        assert cw.block_rank(n, b, s, blocks[r]) == r
+
+
+@pytest.mark.parametrize("n,b,s", [(4, 2, 4), (7, 3, 3), (5, 2, 5), (6, 4, 2)])
+def test_element_index_matches_oracle_layout(n, b, s):
+    idx = oracle.block_elements(n, b, s)
+    keep = np.all(idx < n, axis=1)
+    for e in np.nonzero(keep)[0]:
+        t = idx[e]
+        got = cw.element_index(n, b, s, t)
+        # storage index of the canonical (sorted) tuple holds the same multiset
+        srt = np.sort(t)
+        assert np.array_equal(np.sort(idx[got]), srt)
+        for perm in itertools.permutations(t):
+            assert cw.element_index(n, b, s, perm) == got
+
+
+@pytest.mark.parametrize("n,b,s", [(4, 2, 1), (4, 2, 4), (60, 3, 2), (20, 3, 4), (7, 3, 5),
+                                   (12, 4, 6), (9, 2, 6), (6, 2, 8), (5, 5, 3), (1, 1, 4)])
+def test_update_and_cumulant_tables_selftest(n, b, s):
+    assert cw.selftest_tables(n, b, s) == 0
+
+
+def test_bad_arguments_rejected_without_gpu():
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    # argument checks run before any CUDA call
+    for args in [(0, 4, 2, 100, 10), (4, 0, 2, 100, 10), (4, 9, 2, 100, 10), (4, 4, 0, 100, 10),
+                 (4, 4, 2, 0, 1), (4, 4, 2, 100, 0), (4, 4, 2, 100, 101), (300, 2, 1, 10, 1)]:
+        assert lib.cumwin_create(*args, 0, None, ctypes.byref(h)) == _lib.CODES["EINVAL"]
+    assert lib.cumwin_create(4, 4, 2, 100, 10, 7, None, ctypes.byref(h)) == _lib.CODES["EINVAL"]
+    assert lib.cumwin_push(None, None, None, 1, 4) == _lib.CODES["EINVAL"]
+    assert lib.cumwin_norms(None, None, None) == _lib.CODES["EINVAL"]

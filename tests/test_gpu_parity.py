@@ -1,0 +1,241 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bar (FP64 form): relative Frobenius error <= 1e-10 per order against the FP64
+oracle, element by element on windows the oracle recomputes in seconds, and on
+seeded samples of sorted tuples at the full workload sizes.  Integer-valued
+windows (exact products and sums) must match to 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1701_06446_gb300 import CumWin, CumwinError
+from paper_1701_06446_gb300.streams import WORKLOADS, Stream
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def gpu_cumulants(h):
+    return [h.cumulants(s).cpu().numpy() for s in range(1, h.d + 1)]
+
+
+def rel_fro(got, ref):
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)
+
+
+def assert_window_parity(h, X, tol=TOL_FP64):
+    ref = oracle.cumulants(X, h.d, h.b)
+    got = gpu_cumulants(h)
+    for s in range(1, h.d + 1):
+        assert got[s - 1].shape == ref[s - 1].shape
+        err = rel_fro(got[s - 1], ref[s - 1])
+        assert err <= tol, (s, err)
+    fro, nu = h.norms()
+    ofro, onu = oracle.norms(X, h.d)
+    assert np.allclose(fro, ofro, rtol=tol, atol=0), (fro, ofro)
+    for s in range(3, h.d + 1):
+        assert abs(nu[s - 1] - onu[s - 1]) <= tol * abs(onu[s - 1])
+
+
+def test_small_gauss_then_t_every_shift():
+    """n=4, d=4, b=2, T=1000, p=100: every one of the 190 shifts vs the oracle."""
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, W.length)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(Xd[: W.T])
+        assert_window_parity(h, X[: W.T])
+        for w in range(W.shifts):
+            h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+            if w % 10 == 9 or w == W.shifts - 1:
+                assert_window_parity(h, X[(w + 1) * W.p: (w + 1) * W.p + W.T])
+            else:
+                ref = oracle.cumulants(X[(w + 1) * W.p: (w + 1) * W.p + W.T], W.d, W.b)
+                got = gpu_cumulants(h)
+                for s in range(1, W.d + 1):
+                    assert rel_fro(got[s - 1], ref[s - 1]) <= TOL_FP64
+
+
+@pytest.mark.parametrize("n,d,b,T,p", [(3, 4, 2, 12, 4), (2, 6, 1, 9, 3), (5, 5, 2, 16, 5),
+                                       (3, 3, 4, 10, 10), (1, 6, 1, 11, 1)])
+def test_integer_windows_exact(n, d, b, T, p):
+    rng = np.random.default_rng(n * 100 + d)
+    X = rng.integers(-3, 4, size=(T + 3 * p, n)).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "fp64") as h:
+        h.fill(Xd[:T])
+        assert_window_parity(h, X[:T], tol=1e-12)
+        for w in range(3):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        assert_window_parity(h, X[3 * p: 3 * p + T], tol=1e-12)
+
+
+@pytest.mark.parametrize("n,d,b,T,p", [(7, 4, 3, 64, 7), (5, 5, 2, 50, 7), (9, 3, 4, 33, 33),
+                                       (6, 4, 1, 40, 1), (10, 6, 3, 80, 16), (33, 3, 4, 300, 64),
+                                       (2, 8, 1, 30, 4)])
+def test_ragged_shapes_and_shift_sizes(n, d, b, T, p):
+    """Padding (b does not divide n), p not dividing T, p = 1, p = T, high orders."""
+    rng = np.random.default_rng(7 * n + d)
+    steps = 5
+    X = (rng.standard_t(5, size=(T + steps * p, n)) @ rng.standard_normal((n, n))).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "fp64") as h:
+        h.fill(Xd[:T])
+        for w in range(steps):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        assert_window_parity(h, X[steps * p: steps * p + T])
+        win = h.window().cpu().numpy()
+        assert np.array_equal(win, X[steps * p: steps * p + T])
+
+
+def test_padding_entries_are_exact_zero():
+    rng = np.random.default_rng(3)
+    n, b, d, T = 7, 3, 4, 100
+    X = rng.standard_normal((T, n)).astype(np.float32)
+    with CumWin(n, d, b, T, 10, "fp64") as h:
+        h.fill(dev(X))
+        for s in range(1, d + 1):
+            C = h.cumulants(s).cpu().numpy()
+            pad = np.any(oracle.block_elements(n, b, s) >= n, axis=1)
+            assert np.all(C[pad] == 0.0)
+
+
+def test_explicit_outgoing_rows_match_ring():
+    """push(x_in, x_out = the oldest rows) is bitwise the ring-buffer shift."""
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, 3000)
+    Xd = dev(X)
+    with CumWin(4, 4, 2, 1000, 100) as a, CumWin(4, 4, 2, 1000, 100) as b:
+        a.fill(Xd[:1000])
+        b.fill(Xd[:1000])
+        for w in range(20):
+            a.push(Xd[1000 + w * 100: 1100 + w * 100])
+            b.push(Xd[1000 + w * 100: 1100 + w * 100], Xd[w * 100: (w + 1) * 100].clone())
+        for s in range(1, 5):
+            assert torch.equal(a.cumulants(s), b.cumulants(s))
+
+
+def test_sliding_equals_fresh_after_1e4_shifts():
+    """10^4 shifts of the n=4 workload, extended with the same generator."""
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    shifts = 10_000
+    X = W.stream().rows(0, W.T + shifts * W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(Xd[: W.T])
+        for w in range(shifts):
+            h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+        slide = gpu_cumulants(h)
+        assert_window_parity(h, X[shifts * W.p:])
+        h.recompute()
+        fresh = gpu_cumulants(h)
+        for s in range(1, W.d + 1):
+            assert rel_fro(slide[s - 1], fresh[s - 1]) <= TOL_FP64
+
+
+def test_ica_mix_forward_all_elements():
+    """n=32, d=4, b=4, T=4096: every stored element of every order."""
+    W = WORKLOADS["n32_d4_b4_T4096_ica"]
+    X = W.stream().rows(0, W.T)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(dev(X))
+        assert_window_parity(h, X)
+
+
+def _sampled_parity(h, X, per_order, seed, tol=TOL_FP64):
+    n, b = h.n, h.b
+    cen = oracle.center(X)
+    for s in range(1, h.d + 1):
+        C = h.cumulants(s).cpu().numpy()
+        tup = oracle.sample_sorted_tuples(n, s, per_order, seed=seed + s)
+        idx = np.array([oracle.storage_index(n, b, t) for t in tup])
+        ref = oracle.cumulant_tuples(X, tup, centred=cen)
+        err = rel_fro(C[idx], ref)
+        assert err <= tol, (s, err)
+
+
+def test_n60_workload_sampled():
+    """n=60, d=4, b=3, T=2^15, p=2^10: fill and 3 shifts, sampled tuples per order."""
+    W = WORKLOADS["n60_d4_b3_T32768_p1024"]
+    start = (1 << 19) - W.T - W.p  # straddle the Gaussian -> copula switch
+    X = W.stream().rows(start, start + W.T + 3 * W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(Xd[: W.T])
+        for w in range(3):
+            h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+        _sampled_parity(h, X[3 * W.p:], 1500, seed=60)
+
+
+def test_n48_order6_workload_sampled():
+    """n=48, d=6, b=4, T=2^16, p=2^12: fill and one shift, sampled tuples per order."""
+    W = WORKLOADS["n48_d6_b4_T65536_p4096"]
+    X = W.stream().rows(0, W.T + W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(Xd[: W.T])
+        h.push(Xd[W.T:])
+        _sampled_parity(h, X[W.p:], 300, seed=48)
+
+
+def test_cuda_graph_replay_matches_eager():
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, 4000)
+    Xd = dev(X)
+    with CumWin(4, 4, 2, 1000, 100) as eager, CumWin(4, 4, 2, 1000, 100) as cap:
+        eager.fill(Xd[:1000])
+        cap.fill(Xd[:1000])
+        buf = torch.empty(100, 4, device="cuda")
+        buf.copy_(Xd[1000:1100])
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                cap.push(buf)
+        torch.cuda.synchronize()
+        # capture does not execute: replay the captured shift 20 times with fresh data
+        for w in range(20):
+            buf.copy_(Xd[1000 + w * 100: 1100 + w * 100])
+            g.replay()
+            eager.push(Xd[1000 + w * 100: 1100 + w * 100])
+        torch.cuda.synchronize()
+        for k in range(1, 5):
+            assert torch.equal(eager.cumulants(k), cap.cumulants(k))
+
+
+def test_nonfinite_sample_sets_status():
+    X = np.random.default_rng(0).standard_normal((60, 3)).astype(np.float32)
+    with CumWin(3, 3, 2, 50, 5) as h:
+        h.fill(dev(X[:50]))
+        assert h.status() == 0
+        bad = X[50:55].copy()
+        bad[2, 1] = np.nan
+        h.push(dev(bad))
+        assert h.status() == -5
+        with pytest.raises(CumwinError) as ei:
+            h.norms()
+        assert ei.value.code == -5
+
+
+def test_call_sequence_and_argument_errors():
+    with CumWin(3, 3, 2, 50, 5) as h:
+        x = torch.zeros(5, 3, device="cuda")
+        with pytest.raises(CumwinError) as ei:
+            h.push(x)
+        assert ei.value.code == -4  # push before fill
+        h.fill(torch.zeros(50, 3, device="cuda"))
+        with pytest.raises(CumwinError):
+            h.cumulants(4)
+        with pytest.raises(CumwinError):
+            h.push(torch.zeros(51, 3, device="cuda"))
+        fro, nu = h.norms()
+        assert fro[1] == 0.0 and np.isnan(nu[2])  # constant window: nu is 0/0

@@ -326,3 +326,12 @@ def test_grad_invariants():
     fro, _ = oracle.norms(X, 4)
     euler = sum(2 * s * w[s] * fro[s - 1] ** 2 for s in range(1, 5))
     assert abs(np.sum(X * g) - euler) < 1e-9 * euler
+
+
+def test_storage_index_agrees_with_enumerated_layout():
+    for n, b, s in [(7, 3, 4), (5, 2, 3), (4, 4, 5), (6, 1, 3)]:
+        idx = oracle.block_elements(n, b, s)
+        keep = np.all(idx < n, axis=1)
+        for e in np.nonzero(keep)[0]:
+            g = oracle.storage_index(n, b, idx[e])
+            assert np.array_equal(np.sort(idx[g]), np.sort(idx[e]))
