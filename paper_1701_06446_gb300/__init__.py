@@ -134,7 +134,12 @@ class CumWin:
         self._sync_stream()
         check(self.lib.cumwin_push_host(self._h, ctypes.c_void_p(ptr), p, ld), "cumwin_push_host")
 
+    def _order(self, order: int):
+        if not 1 <= order <= self.d:
+            raise ValueError(f"order must be in 1..{self.d}")
+
     def cumulants(self, order: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._order(order)
         if out is None:
             out = torch.empty(self.sizes[order - 1], dtype=torch.float64, device=self.device)
         self._sync_stream()
@@ -143,6 +148,7 @@ class CumWin:
         return out
 
     def moments(self, order: int) -> torch.Tensor:
+        self._order(order)
         out = torch.empty(self.sizes[order - 1], dtype=torch.float64, device=self.device)
         self._sync_stream()
         check(self.lib.cumwin_moments(self._h, order, out.data_ptr()), "cumwin_moments")

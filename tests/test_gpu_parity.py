@@ -233,8 +233,10 @@ def test_call_sequence_and_argument_errors():
             h.push(x)
         assert ei.value.code == -4  # push before fill
         h.fill(torch.zeros(50, 3, device="cuda"))
-        with pytest.raises(CumwinError):
+        with pytest.raises(ValueError):
             h.cumulants(4)
+        out = torch.empty(100, dtype=torch.float64, device="cuda")
+        assert h.lib.cumwin_cumulants(h._h, 4, out.data_ptr()) == -1  # EINVAL from the ABI
         with pytest.raises(CumwinError):
             h.push(torch.zeros(51, 3, device="cuda"))
         fro, nu = h.norms()
