@@ -115,16 +115,38 @@ int run_cumulants(cumwin_t h, int64_t advance)
     return CUMWIN_OK;
 }
 
-// Moment sums over `K` staged rows; the first `npos` enter with +, the rest with -.
-int run_update(cumwin_t h, const float* rows, int64_t K, int64_t npos, int64_t batch)
+// Moment sums of the whole window held in the ring buffer (fill, recompute).
+int update_window(cumwin_t h)
 {
-    h->mark(0);
     if (h->prec == CUMWIN_FP64) {
-        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, rows, K, npos, h->shift, h->stream));
+        h->mark(0);
+        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->ring, h->T, h->T, h->shift,
+                                 h->stream));
         h->launches += 1;
     } else {
-        CW_TRY(launch_update_tc(h->tc, h->upd, rows, K, npos, batch, h->shift, h->stream));
-        h->launches += tc_launch_count(h->tc, K, npos, batch);
+        h->mark(0);
+        CW_TRY(tc_update_window(h->tc, h->ring, h->head, h->n, h->shift, h->stream));
+        h->launches += 2;
+    }
+    h->mark(1);
+    return CUMWIN_OK;
+}
+
+// One shift: stage X_(+) / X_(-), move X_(+) into the ring, update the sums.
+int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld)
+{
+    if (h->prec == CUMWIN_FP64) {
+        CW_TRY(launch_stage(x_in, ld, x_out, ld, h->ring, h->T, h->head, p, h->n, h->npad,
+                            h->stage, h->status, h->stream));
+        h->mark(0);
+        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, 2 * (int64_t)p, p,
+                                 h->shift, h->stream));
+        h->launches += 2;
+    } else {
+        h->mark(0);
+        CW_TRY(tc_update_push(h->tc, x_in, ld, x_out, ld, h->ring, h->head, p, h->n, h->shift,
+                              h->stream));
+        h->launches += 2;
     }
     h->mark(1);
     return CUMWIN_OK;
@@ -336,6 +358,10 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
 
     CW_CREATE_TRY(cudaGetDevice(&h->device));
     CW_CREATE_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+    if (precision == CUMWIN_MIXED_FP16) {
+        g_last_error = "the FP16 split form is not available in this build";
+        return bail(CUMWIN_ENOTSUP);
+    }
     if (precision != CUMWIN_FP64) {
         int major = 0, minor = 0;
         CW_CREATE_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device));
@@ -400,8 +426,9 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
     if (precision == CUMWIN_FP64) {
         CW_CREATE_TRY(h->upload(&h->tiles, tiles));
     } else {
-        int rc = tc_plan_create(h->tc, ut, d, n, b, npad, (int)T, h->sm_count, precision,
-                                [&](size_t bytes, void** p) { return h->alloc((char**)p, bytes); });
+        int rc = tc_plan_create(h->tc, ut, h->upd, d, n, b, npad, T, p, h->sm_count, precision,
+                                h->status,
+                                [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
         if (rc != 0) {
             g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
             return bail(CUMWIN_ECUDA);
@@ -466,13 +493,13 @@ int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx)
 {
     if (h == nullptr || X_dev == nullptr || ldx < h->n) return CUMWIN_EINVAL;
     CW_TRY(launch_fill_ring(X_dev, ldx, h->ring, h->T, h->n, h->npad, h->status, h->stream));
+    CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
     if (h->prec != CUMWIN_FP64)
         CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
     int rc = zero_sums(h);
     if (rc) return rc;
-    rc = run_update(h, h->ring, h->T, h->T, h->p);
+    rc = update_window(h);
     if (rc) return rc;
-    CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
     rc = run_cumulants(h, 0);
     if (rc) return rc;
     h->filled = true;
@@ -483,10 +510,7 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
 {
     if (h == nullptr || x_in_dev == nullptr || p < 1 || p > h->T || ld < h->n) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
-    CW_TRY(launch_stage(x_in_dev, ld, x_out_dev, ld, h->ring, h->T, h->head, p, h->n, h->npad,
-                        h->stage, h->status, h->stream));
-    h->launches += 1;
-    int rc = run_update(h, h->stage, 2 * (int64_t)p, p, p);
+    int rc = update_push(h, x_in_dev, x_out_dev, p, ld);
     if (rc) return rc;
     return run_cumulants(h, p);
 }
@@ -566,7 +590,7 @@ int cumwin_recompute(cumwin_t h)
     if (!h->filled) return CUMWIN_ESTATE;
     int rc = zero_sums(h);
     if (rc) return rc;
-    rc = run_update(h, h->ring, h->T, h->T, h->p);
+    rc = update_window(h);
     if (rc) return rc;
     return run_cumulants(h, 0);
 }

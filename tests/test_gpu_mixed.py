@@ -1,0 +1,182 @@
+"""GPU parity of the tensor-core (BF16 hi+lo split, FP32 accumulate, FP64 sums)
+form of the moment-sum update, through the C ABI.
+
+Per-order bound: the split represents each FP32 product to about 2^-16 relative
+(hi and lo carry 8 significant bits each, and lo*lo is dropped), so moments
+carry ~1e-5 relative error and cumulants of order s amplify it by the
+cancellation in the moment-to-cumulant relation.  The bounds below are stated
+per order as relative Frobenius errors against the FP64 oracle.
+
+Exactness of the sliding update: a batch is reduced by the same instruction
+sequence when it enters (D_in) and when it leaves (D_out), so its FP32 sum
+cancels bitwise and the running FP64 sums agree with a fresh recomputation to
+FP64 rounding.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1701_06446_gb300 import CumWin, CumwinError
+from paper_1701_06446_gb300.streams import WORKLOADS
+
+pytestmark = pytest.mark.gpu
+
+# relative Frobenius error bound per order (index = order)
+MIXED_BOUND = {1: 2e-5, 2: 5e-5, 3: 5e-4, 4: 2e-3, 5: 5e-3, 6: 2e-2, 7: 5e-2, 8: 1e-1}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel_fro(got, ref):
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(got - ref) / (den if den > 0 else 1.0)
+
+
+def errors_vs_oracle(h, X):
+    ref = oracle.cumulants(X, h.d, h.b)
+    return {s: rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) for s in range(1, h.d + 1)}
+
+
+def check_bounds(errs, scale=1.0):
+    for s, e in errs.items():
+        assert e <= MIXED_BOUND[s] * scale, (s, e, errs)
+
+
+def test_mixed_small_stream_every_tenth_shift():
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, W.length)
+    Xd = dev(X)
+    worst = {}
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as h:
+        h.fill(Xd[: W.T])
+        check_bounds(errors_vs_oracle(h, X[: W.T]))
+        for w in range(W.shifts):
+            h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+            if w % 10 == 9:
+                errs = errors_vs_oracle(h, X[(w + 1) * W.p: (w + 1) * W.p + W.T])
+                for s, e in errs.items():
+                    worst[s] = max(worst.get(s, 0.0), e)
+                check_bounds(errs)
+    print("worst per-order error", worst)
+
+
+@pytest.mark.parametrize("n,d,b,T,p", [(7, 4, 3, 256, 40), (5, 5, 2, 200, 33), (9, 3, 4, 97, 97),
+                                       (10, 6, 3, 300, 64), (33, 3, 4, 600, 100), (3, 8, 1, 120, 24),
+                                       (100, 3, 8, 512, 128), (64, 4, 4, 400, 50), (1, 6, 1, 64, 8)])
+def test_mixed_ragged_shapes(n, d, b, T, p):
+    rng = np.random.default_rng(11 * n + d)
+    steps = 4
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    X = (rng.gamma(2.0, size=(T + steps * p, n)) @ A + 0.5).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        for w in range(steps):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        errs = errors_vs_oracle(h, X[steps * p: steps * p + T])
+        print((n, d, b, T, p), errs)
+        check_bounds(errs, scale=2.0)
+        assert np.array_equal(h.window().cpu().numpy(), X[steps * p: steps * p + T])
+
+
+def test_mixed_sliding_equals_recompute_exactly():
+    """Two full window rotations: the sliding sums equal a fresh recomputation
+    to FP64 rounding, because in/out batch sums cancel bitwise."""
+    n, d, b, T, p = 12, 4, 3, 2048, 256
+    rng = np.random.default_rng(5)
+    X = (rng.standard_t(5, size=(T + 40 * p, n)) + 3.0).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        for w in range(40):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        slide = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        h.recompute()
+        fresh = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        for s in range(1, d + 1):
+            assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
+
+
+def test_mixed_vs_fp64_form_n60():
+    """n=60, d=4, b=3, T=2^15, p=2^10: the mixed form against the FP64 GPU form
+    (every element) and against the oracle (sampled tuples)."""
+    W = WORKLOADS["n60_d4_b3_T32768_p1024"]
+    start = (1 << 19) - W.T - W.p
+    X = W.stream().rows(start, start + W.T + 3 * W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as f64, \
+            CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as mix:
+        f64.fill(Xd[: W.T])
+        mix.fill(Xd[: W.T])
+        for w in range(3):
+            f64.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+            mix.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+        errs = {}
+        for s in range(1, W.d + 1):
+            errs[s] = rel_fro(mix.cumulants(s).cpu().numpy(), f64.cumulants(s).cpu().numpy())
+        print("mixed vs FP64 form", errs)
+        check_bounds(errs)
+        Xw = X[3 * W.p:]
+        cen = oracle.center(Xw)
+        for s in range(1, W.d + 1):
+            tup = oracle.sample_sorted_tuples(W.n, s, 800, seed=600 + s)
+            idx = np.array([oracle.storage_index(W.n, W.b, t) for t in tup])
+            ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
+            assert rel_fro(mix.cumulants(s).cpu().numpy()[idx], ref) <= MIXED_BOUND[s]
+        fm, nm = mix.norms()
+        ff, nf = f64.norms()
+        assert np.allclose(fm, ff, rtol=1e-3)
+
+
+def test_mixed_n48_order6_sampled():
+    W = WORKLOADS["n48_d6_b4_T65536_p4096"]
+    X = W.stream().rows(0, W.T + W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as h:
+        h.fill(Xd[: W.T])
+        h.push(Xd[W.T:])
+        Xw = X[W.p:]
+        cen = oracle.center(Xw)
+        errs = {}
+        for s in range(1, W.d + 1):
+            tup = oracle.sample_sorted_tuples(W.n, s, 200, seed=480 + s)
+            idx = np.array([oracle.storage_index(W.n, W.b, t) for t in tup])
+            ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
+            errs[s] = rel_fro(h.cumulants(s).cpu().numpy()[idx], ref)
+        print("n48 order-6 mixed errors", errs)
+        check_bounds(errs)
+
+
+def test_mixed_graph_replay_matches_eager():
+    n, d, b, T, p = 20, 4, 4, 512, 64
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((T + 12 * p, n)).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as eager, CumWin(n, d, b, T, p, "bf16") as cap:
+        eager.fill(Xd[:T])
+        cap.fill(Xd[:T])
+        buf = torch.empty(p, n, device="cuda")
+        buf.copy_(Xd[T:T + p])
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                cap.push(buf)
+        torch.cuda.synchronize()
+        for w in range(12):
+            buf.copy_(Xd[T + w * p: T + (w + 1) * p])
+            g.replay()
+            eager.push(Xd[T + w * p: T + (w + 1) * p])
+        torch.cuda.synchronize()
+        for k in range(1, d + 1):
+            assert torch.equal(eager.cumulants(k), cap.cumulants(k))
+
+
+def test_fp16_form_reports_not_supported():
+    with pytest.raises(CumwinError) as ei:
+        CumWin(4, 3, 2, 64, 8, "fp16")
+    assert ei.value.code == -7
