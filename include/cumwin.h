@@ -184,6 +184,32 @@ int cumwin_get_timing(cumwin_t h, double* update_ms, double* cumulant_ms, int64_
  * Synchronises the handle's stream.  Reading it clears nothing. */
 int cumwin_status(cumwin_t h);
 
+/*
+ * Allocation-free squared norm of a tensor in the block layout.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as code running inside another framework's memory pool or
+ * under a device-memory budget that forbids new allocations, or a thread that
+ * must not risk the implicit synchronisation an allocation can bring.
+ *
+ * out_dev[0] = sum over stored blocks j of (order!/prod r_l!) * sum_{e in block j} e^2,
+ * i.e. ||A||_F^2 of the full n^order tensor (Algorithm 5 with k = 2, before the
+ * root), for A_dev in the block layout (cumwin_layout_size(n, b, order)
+ * doubles, device).  Asynchronous on cuda_stream; the caller passes the input
+ * and the output and the call allocates nothing: its scratch, one double per
+ * stored block, is a fixed array of CUMWIN_NOALLOC_MAX_BLOCKS doubles in the
+ * library's device memory, which every GPU that loads the library holds until
+ * the process exits.  Tensors with more stored blocks than that are rejected
+ * with CUMWIN_EINVAL and a message in cumwin_last_error().
+ * The first call on a device looks up the scratch's device address (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one scratch array and each call overwrites
+ * the slots it reads, so calls that overlap on the GPU (different streams
+ * without ordering) race and may return wrong sums.
+ */
+#define CUMWIN_NOALLOC_MAX_BLOCKS 16384
+int cumwin_block_norm2_noalloc(int n, int b, int order, const double* A_dev, double* out_dev,
+                               void* cuda_stream);
+
 /* Host-only layout helpers (no GPU needed). */
 /* Stored elements of order `order`: C(nbar + order - 1, order) * b^order. */
 int64_t cumwin_layout_size(int n, int b, int order);

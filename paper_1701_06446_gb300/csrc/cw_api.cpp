@@ -32,6 +32,8 @@ int fail_cuda(cudaError_t e, const char* what)
 
 }  // namespace
 
+void cw::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct cumwin_s {
     int n = 0, d = 0, b = 0, nbar = 0, npad = 0, prec = 0;
     int64_t T = 0;

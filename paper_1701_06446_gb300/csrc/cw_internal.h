@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace cw {
@@ -63,6 +65,9 @@ struct CumArgs {
     int32_t s, b, bs, nsub;
     uint8_t mask[128];               // subset bitmasks over the s positions
 };
+
+// Message returned by cumwin_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // Device-side status bits (sticky).
 constexpr int kStatusNonFinite = 1;
