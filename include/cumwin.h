@@ -169,16 +169,17 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev);
 
 /*
  * Kernel timing.  With timing enabled, each later fill / push / recompute
- * records CUDA events on the handle's stream around its moment-sum update
- * kernel and around its cumulant-recovery + norm kernels (at most 65536 shifts
- * are recorded; later ones are not timed).  cumwin_get_timing synchronises and
- * returns the summed event times in milliseconds, the number of timed shifts
- * and the number of kernels the library launched since timing was enabled.
- * Enabling resets the counters.  Not for use inside stream capture.
+ * records CUDA events on the handle's stream that split it into staging
+ * (X_(+)/X_(-) staging and, in the mixed forms, the operand build), the
+ * moment-sum update kernel, and the cumulant recovery + norm kernels (at most
+ * 65536 shifts are recorded; later ones are not timed).  cumwin_get_timing
+ * synchronises and returns the summed event times in milliseconds, the number
+ * of timed shifts and the number of kernels the library launched since timing
+ * was enabled.  Enabling resets the counters.  Not for use inside stream capture.
  */
 int cumwin_set_timing(cumwin_t h, int enable);
-int cumwin_get_timing(cumwin_t h, double* update_ms, double* cumulant_ms, int64_t* shifts,
-                      int64_t* launches);
+int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* cumulant_ms,
+                      int64_t* shifts, int64_t* launches);
 
 /* Sticky device status of the handle (CUMWIN_OK or ENONFINITE / ETIMEOUT).
  * Synchronises the handle's stream.  Reading it clears nothing. */

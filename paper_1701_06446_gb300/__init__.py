@@ -198,12 +198,12 @@ class CumWin:
         check(self.lib.cumwin_set_timing(self._h, int(bool(enable))), "cumwin_set_timing")
 
     def get_timing(self) -> dict:
-        u, c = ctypes.c_double(), ctypes.c_double()
+        a, u, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         k, L = ctypes.c_int64(), ctypes.c_int64()
-        check(self.lib.cumwin_get_timing(self._h, ctypes.byref(u), ctypes.byref(c), ctypes.byref(k),
-                                         ctypes.byref(L)), "cumwin_get_timing")
-        return {"update_ms": u.value, "cumulant_ms": c.value, "shifts": k.value,
-                "launches": L.value}
+        check(self.lib.cumwin_get_timing(self._h, ctypes.byref(a), ctypes.byref(u), ctypes.byref(c),
+                                         ctypes.byref(k), ctypes.byref(L)), "cumwin_get_timing")
+        return {"stage_ms": a.value, "update_ms": u.value, "cumulant_ms": c.value,
+                "shifts": k.value, "launches": L.value}
 
     def status(self) -> int:
         self._sync_stream()

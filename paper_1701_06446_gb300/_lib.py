@@ -36,7 +36,7 @@ SIGNATURES = {
     "cumwin_grad": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_status": (c_int, [c_vp]),
     "cumwin_set_timing": (c_int, [c_vp, c_int]),
-    "cumwin_get_timing": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "cumwin_get_timing": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "cumwin_block_norm2_noalloc": (c_int, [c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "cumwin_layout_size": (c_i64, [c_int, c_int, c_int]),
     "cumwin_block_rank": (c_i64, [c_int, c_int, c_int, c_vp]),

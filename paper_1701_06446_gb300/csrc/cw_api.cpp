@@ -53,6 +53,7 @@ struct cumwin_s {
     double* S[kMaxOrder + 1] = {};
     double* C[kMaxOrder + 1] = {};
     int64_t E[kMaxOrder + 1] = {};
+    int64_t Eoff[kMaxOrder + 2] = {};  // offsets of the orders in one concatenated index space
 
     UpdateArgs upd{};
     UpdTile* tiles = nullptr;
@@ -67,7 +68,7 @@ struct cumwin_s {
 
     // kernel timing (cumwin_set_timing)
     bool timing = false;
-    std::vector<cudaEvent_t> ev;  // 3 per timed shift
+    std::vector<cudaEvent_t> ev;  // 4 per timed shift: start, staged, updated, recovered
     int64_t timed = 0, launches = 0;
 
     template <class T>
@@ -98,8 +99,8 @@ struct cumwin_s {
     // event slot k of the current timed shift, or null when not timing
     cudaEvent_t mark(int k)
     {
-        if (!timing || timed * 3 + k >= (int64_t)ev.size()) return nullptr;
-        cudaEvent_t e = ev[timed * 3 + k];
+        if (!timing || timed * 4 + k >= (int64_t)ev.size()) return nullptr;
+        cudaEvent_t e = ev[timed * 4 + k];
         cudaEventRecord(e, stream);
         return e;
     }
@@ -107,50 +108,65 @@ struct cumwin_s {
 
 namespace {
 
-int run_cumulants(cumwin_t h, int64_t advance)
+// Recovery of C_1..C_d and norms.  accum: fold the tensor-core workspace of
+// the shift into the sums first (mixed forms, after a push).
+int run_cumulants(cumwin_t h, int64_t advance, bool accum = false)
 {
-    for (int s = 1; s <= h->d; ++s) CW_TRY(launch_cumulants(h->cum[s], h->cum_grid[s], h->stream));
+    for (int s = 1; s <= h->d; ++s) {
+        CumArgs a = h->cum[s];
+        a.accum = accum ? 1 : 0;
+        CW_TRY(launch_cumulants(a, h->cum_grid[s], h->stream));
+    }
     CW_TRY(launch_norm_final(h->normpart, h->part_off, h->d, h->fro2, h->head, advance, h->T,
                              h->stream));
     h->launches += h->d + 1;
-    if (h->mark(2) != nullptr) h->timed++;
+    if (h->mark(3) != nullptr) h->timed++;
     return CUMWIN_OK;
 }
 
 // Moment sums of the whole window held in the ring buffer (fill, recompute).
 int update_window(cumwin_t h)
 {
+    h->mark(0);
+    h->mark(1);
     if (h->prec == CUMWIN_FP64) {
-        h->mark(0);
         CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->ring, h->T, h->T, h->shift,
                                  h->stream));
         h->launches += 1;
     } else {
-        h->mark(0);
-        CW_TRY(tc_update_window(h->tc, h->ring, h->head, h->n, h->shift, h->stream));
-        h->launches += 2;
+        TcAccArgs acc{};
+        for (int s = 1; s <= h->d; ++s) acc.S[s] = h->S[s];
+        for (int s = 0; s <= h->d + 1; ++s) acc.Eoff[s] = h->Eoff[s];
+        acc.d = h->d;
+        for (int q = 0; q < h->tc.nbatch; ++q) {
+            CW_TRY(tc_update_window_batch(h->tc, h->ring, h->head, q, h->n, h->shift, h->stream));
+            CW_TRY(launch_tc_accumulate(h->tc, acc, h->stream));
+        }
+        h->launches += (int64_t)kTcBatchLaunches * h->tc.nbatch;
     }
-    h->mark(1);
+    h->mark(2);
     return CUMWIN_OK;
 }
 
 // One shift: stage X_(+) / X_(-), move X_(+) into the ring, update the sums.
 int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld)
 {
+    h->mark(0);
     if (h->prec == CUMWIN_FP64) {
         CW_TRY(launch_stage(x_in, ld, x_out, ld, h->ring, h->T, h->head, p, h->n, h->npad,
                             h->stage, h->status, h->stream));
-        h->mark(0);
+        h->mark(1);
         CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, 2 * (int64_t)p, p,
                                  h->shift, h->stream));
         h->launches += 2;
     } else {
-        h->mark(0);
-        CW_TRY(tc_update_push(h->tc, x_in, ld, x_out, ld, h->ring, h->head, p, h->n, h->shift,
-                              h->stream));
-        h->launches += 2;
+        CW_TRY(tc_stage_push(h->tc, x_in, ld, x_out, ld, h->ring, h->head, p, h->n, h->shift,
+                             h->stream));
+        h->mark(1);
+        CW_TRY(tc_gemm_push(h->tc, h->stream));
+        h->launches += 3;
     }
-    h->mark(1);
+    h->mark(2);
     return CUMWIN_OK;
 }
 
@@ -425,10 +441,13 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         }
     }
     h->ntiles = (int)tiles.size();
+    h->Eoff[1] = 0;
+    for (int s = 1; s <= d; ++s) h->Eoff[s + 1] = h->Eoff[s] + h->E[s];
     if (precision == CUMWIN_FP64) {
         CW_CREATE_TRY(h->upload(&h->tiles, tiles));
     } else {
-        int rc = tc_plan_create(h->tc, ut, h->upd, d, n, b, npad, T, p, h->sm_count, precision,
+        int rc = tc_plan_create(h->tc, ut, h->upd, h->Eoff, d, n, b, npad, T, p, h->sm_count,
+                                precision,
                                 h->status,
                                 [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
         if (rc != 0) {
@@ -450,6 +469,11 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         CW_CREATE_TRY(h->upload((int32_t**)&a.subrank, ct.subrank));
         CW_CREATE_TRY(h->upload((double**)&a.mult, ct.mult));
         a.shift = h->shift;
+        a.W = h->tc.W;
+        a.wslice = h->tc.wslice;
+        a.woff = h->Eoff[s];
+        a.ksplit = h->tc.ksplit;
+        a.accum = 0;
         a.invT = 1.0 / (double)T;
         a.E = h->E[s];
         a.s = s;
@@ -457,7 +481,8 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         a.bs = (int32_t)ipow(b, s);
         a.nsub = ct.nsub;
         for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
-        int64_t g = (h->E[s] + 255) / 256;
+        // one warp per stored block, 8 warps per CTA
+        int64_t g = (n_sorted(nbar, s) + 7) / 8;
         g = std::min<int64_t>(g, 4 * (int64_t)h->sm_count);
         h->cum_grid[s] = (int)std::max<int64_t>(g, 1);
         part_off[s] = part_off[s - 1] + h->cum_grid[s];
@@ -512,9 +537,13 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
 {
     if (h == nullptr || x_in_dev == nullptr || p < 1 || p > h->T || ld < h->n) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    if (h->prec != CUMWIN_FP64 && p > h->p) {
+        g_last_error = "the mixed forms accept shifts of at most the nominal p given at create";
+        return CUMWIN_EINVAL;
+    }
     int rc = update_push(h, x_in_dev, x_out_dev, p, ld);
     if (rc) return rc;
-    return run_cumulants(h, p);
+    return run_cumulants(h, p, h->prec != CUMWIN_FP64);
 }
 
 int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld)
@@ -619,25 +648,28 @@ int cumwin_set_timing(cumwin_t h, int enable)
     h->timed = 0;
     h->launches = 0;
     if (h->timing && h->ev.empty()) {
-        h->ev.resize(3 * 65536);
+        h->ev.resize(4 * 65536);
         for (auto& e : h->ev) CW_TRY(cudaEventCreate(&e));
     }
     return CUMWIN_OK;
 }
 
-int cumwin_get_timing(cumwin_t h, double* update_ms, double* cumulant_ms, int64_t* shifts,
-                      int64_t* launches)
+int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* cumulant_ms,
+                      int64_t* shifts, int64_t* launches)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
     CW_TRY(cudaStreamSynchronize(h->stream));
-    double u = 0.0, c = 0.0;
+    double a = 0.0, u = 0.0, c = 0.0;
     for (int64_t k = 0; k < h->timed; ++k) {
-        float a = 0.f, b = 0.f;
-        CW_TRY(cudaEventElapsedTime(&a, h->ev[3 * k], h->ev[3 * k + 1]));
-        CW_TRY(cudaEventElapsedTime(&b, h->ev[3 * k + 1], h->ev[3 * k + 2]));
-        u += a;
-        c += b;
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        CW_TRY(cudaEventElapsedTime(&t0, h->ev[4 * k], h->ev[4 * k + 1]));
+        CW_TRY(cudaEventElapsedTime(&t1, h->ev[4 * k + 1], h->ev[4 * k + 2]));
+        CW_TRY(cudaEventElapsedTime(&t2, h->ev[4 * k + 2], h->ev[4 * k + 3]));
+        a += t0;
+        u += t1;
+        c += t2;
     }
+    if (stage_ms) *stage_ms = a;
     if (update_ms) *update_ms = u;
     if (cumulant_ms) *cumulant_ms = c;
     if (shifts) *shifts = h->timed;

@@ -53,7 +53,7 @@ struct UpdTile {
 // subrank holds (rank(j_A), rank(j_rest)) for each block and each subset.
 // ---------------------------------------------------------------------------
 struct CumArgs {
-    const double* S[kMaxOrder + 1];  // running sums per order (moments = S * invT)
+    double* S[kMaxOrder + 1];        // running sums per order (moments = S * invT)
     const double* C[kMaxOrder + 1];  // cumulants per order (order 1 about the shift)
     double* Cout;                    // = C[s]
     const int32_t* subrank;          // [nblocks][nsub][2]
@@ -64,6 +64,11 @@ struct CumArgs {
     int64_t E;                       // stored elements of order s
     int32_t s, b, bs, nsub;
     uint8_t mask[128];               // subset bitmasks over the s positions
+    // tensor-core form: before recovering C_s, fold the FP32 tile sums of the
+    // shift into S_s:  S += (double)(sum_k W[k][0]) - (double)(sum_k W[k][1])
+    const float* W;                  // [ksplit][2][wslice]
+    int64_t wslice, woff;
+    int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = fold it in
 };
 
 // Message returned by cumwin_last_error() on the calling thread.

@@ -1,14 +1,25 @@
 // Tensor-core (tcgen05) form of the moment-sum update: plan and launchers.
 //
-// The order-s update is the set of GEMMs described in cw_internal.h.  Here the
-// right factor (s - h indices, "columns") is the MMA M side (128 per item) and
-// the left factor (h indices, "rows") the MMA N side (up to 256 per item).
-// Each K-chunk of samples is staged in shared memory by TMA (FP32, already
-// shifted), the Khatri-Rao products are formed on the CUDA cores and split
-// into 16-bit hi + lo parts, and hi*hi + hi*lo + lo*hi are accumulated in
-// FP32 in tensor memory: samples entering the window into one accumulator,
-// samples leaving it into another.  The epilogue adds (double)D_in -
-// (double)D_out to the FP64 running sums.
+// The order-s update is the set of GEMMs described in cw_internal.h: the
+// right factor (s - h indices, "columns") is the MMA M side (128 per item),
+// the left factor (h indices, "rows") the MMA N side (up to kTcNmax rows).
+//
+// Per shift:
+//   1. k_tc_stage_push: X_(+) and X_(-), minus the shift vector, transposed to
+//      [variable][sample] (FP32), zero-padded to P samples each.
+//   2. k_kr_build: every distinct Khatri-Rao operand row (the products of its
+//      variables over the staged samples) is formed once in FP32, split into
+//      bf16 hi + lo and written as [sample/8][row][8] for both parts, so that
+//      one 4-D TMA box lands in shared memory in the canonical K-major layout.
+//   3. k_kr_gemm: per unit (item x K-split) a TMA warp streams the item's
+//      A (128 columns) and B (rows) tiles through a 3-stage mbarrier ring, an
+//      MMA warp issues hi*hi + hi*lo + lo*hi per 16-sample step into TMEM
+//      (entering samples into D_in, leaving samples into D_out), and four
+//      epilogue warps store the FP32 tiles into a workspace W[split][in/out].
+//   4. the recovery kernel of each order first folds the workspace into the
+//      FP64 sums: S += (double)(sum_k D_in,k) - (double)(sum_k D_out,k), the
+//      FP32 sums over splits taken in a fixed order, so that a batch's sum is
+//      bitwise the same when it enters and when it leaves the window.
 #pragma once
 
 #include <cstdint>
@@ -22,46 +33,55 @@
 namespace cw {
 
 constexpr int kTcKC = 32;      // samples per K-chunk
-constexpr int kTcXS = 36;      // shared-memory row stride of the staged samples (floats)
 constexpr int kTcM = 128;      // columns per item (MMA M)
-constexpr int kTcNmax = 256;   // rows per item (MMA N)
+constexpr int kTcNmax = 128;   // rows per item (MMA N, multiple of 16)
+constexpr int kTcStages = 3;   // TMA / MMA pipeline depth
 
 struct TcItem {
-    int32_t s, row0, nrows, col0, ncols, pad0, pad1, pad2;
+    int32_t s;      // order
+    int32_t row0;   // first row in the order's left table
+    int32_t nrows;  // rows (<= kTcNmax)
+    int32_t col0;   // first column in the order's right table
+    int32_t ncols;  // columns (<= kTcM)
+    int32_t brow;   // TMA row coordinate of row0 in the operand array
+    int32_t acol;   // TMA row coordinate of col0 in the operand array
+    int32_t pad;
 };
 
 struct TcOrder {
-    const uint32_t* rowvar;
     const int64_t* rowoff;
     const int32_t* rowcolmin;  // first valid column of each row (its group's start)
-    const uint32_t* colvar;
     const int64_t* coloff;
-    double* S;
-    int32_t h, sh;
+    int64_t woff;              // offset of this order in one workspace slice
 };
 
-struct TcArgs {
+struct TcGemmArgs {
     TcOrder ord[kMaxOrder + 1];
     const TcItem* items;
-    int32_t nitems;
-    int32_t npad;
-    // pass structure (sample counts, multiples of kTcKC): pair j adds the
-    // plus segment [j*seg_stride, j*seg_stride + seglen) and, for j == 0, the
-    // minus segment [minus_off, minus_off + minus_len); one epilogue per pair.
-    int32_t npairs, seglen, seg_stride, minus_off, minus_len;
+    float* W;            // [ksplit][2][Etot] FP32 tile sums
+    int64_t wslice;      // Etot
+    int32_t nitems, ksplit;
+    int32_t nplus, nminus;  // K-chunks of the entering / leaving segment
+    int32_t minus_kb;       // first kb (sample / 8) of the leaving segment
     int* status;
 };
 
 struct TcPlan {
     int ready = 0;
     int precision = 0;
-    int npad = 0, p = 0, nbatch = 0, P = 0;
+    int npad = 0, p = 0, P = 0, nbatch = 0;
     int64_t T = 0, Kcap = 0;
-    float* XT = nullptr;  // [npad][Kcap] shifted samples, var-major
-    CUtensorMap xmap{};
+    float* XT = nullptr;           // [npad][Kcap] shifted samples, variable-major
+    // operand array: rows of all Khatri-Rao sets, [part][Kcap/8][rows][8] bf16
+    uint16_t* ops = nullptr;
+    int64_t oprows = 0;
+    uint64_t* opvars = nullptr;    // per operand row: packed variables | factors << 32
+    CUtensorMap mapA{}, mapB{};
     TcItem* items = nullptr;
-    int nitems = 0, grid = 0;
+    int nitems = 0, ksplit = 1;
     TcOrder ord[kMaxOrder + 1]{};
+    float* W = nullptr;
+    int64_t wslice = 0;
     int* status = nullptr;
     // planning statistics (host)
     double useful_macs_per_sample = 0, issued_macs_per_sample = 0;
@@ -71,20 +91,33 @@ using DevAlloc = std::function<cudaError_t(size_t, void**)>;
 
 // Returns 0 or a cudaError_t code.
 int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const UpdateArgs& upd,
-                   int d, int n, int b, int npad, int64_t T, int p, int sm_count, int precision,
-                   int* status, const DevAlloc& alloc);
+                   const int64_t* Eoff, int d, int n, int b, int npad, int64_t T, int p,
+                   int sm_count, int precision, int* status, const DevAlloc& alloc);
 
-// Number of kernels one tc_update_* call issues.
-int tc_launch_count(const TcPlan& plan);
+// One window shift, first half: stage X_(+) / X_(-) (moving X_(+) into the
+// ring) and build the Khatri-Rao operands (2 launches).
+cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
+                          int64_t ld_out, float* ring, const int64_t* head, int p, int n,
+                          const float* shift, cudaStream_t st);
+// Second half: the GEMM units (1 launch).  The FP64 sums are then updated by
+// the recovery kernels in accumulate mode.
+cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st);
 
-// One window shift: stage X_(+) / X_(-) (shifted, transposed) and update the sums.
-cudaError_t tc_update_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
-                           int64_t ld_out, float* ring, const int64_t* head, int p, int n,
-                           const float* shift, cudaStream_t st);
+// Batch q of the window held in the ring (window order, p_nominal samples):
+// stage, build and GEMM with no leaving segment; the caller then folds the
+// workspace into the sums (launch_tc_accumulate).
+cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const int64_t* head,
+                                   int q, int n, const float* shift, cudaStream_t st);
 
-// Sums of the whole window held in the ring buffer, in batches of the nominal
-// shift size taken in window order (fill and recompute).
-cudaError_t tc_update_window(const TcPlan& plan, const float* ring, const int64_t* head, int n,
-                             const float* shift, cudaStream_t st);
+// S_s += (double)sum_k W[k][0] (entering only), all orders.
+struct TcAccArgs {
+    double* S[kMaxOrder + 1];
+    int64_t Eoff[kMaxOrder + 2];
+    int32_t d;
+};
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccArgs& a, cudaStream_t st);
+
+// Kernels one window batch launches (with the accumulation).
+constexpr int kTcBatchLaunches = 4;
 
 }  // namespace cw

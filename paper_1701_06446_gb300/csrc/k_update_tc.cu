@@ -1,24 +1,10 @@
 // Moment-sum update on the 5th-generation tensor cores (Eqs. 6-7, Algorithm 2).
 //
-// Per item: 128 columns (right factor, MMA M) x up to 256 rows (left factor,
-// MMA N) of one order's GEMM.  For every K-chunk of 32 samples:
-//   1. one thread TMA-loads the chunk of the transposed, shifted sample buffer
-//      (npad variables x 36 samples, FP32) into shared memory (2 stages);
-//   2. all 256 threads form the Khatri-Rao products of the item's columns and
-//      rows for the chunk's samples on the CUDA cores, split each FP32 product
-//      into 16-bit hi + lo parts and store them in the canonical K-major
-//      no-swizzle layout (8-row x 16-byte core matrices);
-//   3. one thread issues hi*hi + hi*lo + lo*hi tcgen05 MMAs per 16-sample step
-//      into an FP32 accumulator in tensor memory: samples entering the window
-//      into D_in (columns 0..255), samples leaving it into D_out (256..511).
-// After the last chunk of a pass, every thread reads its TMEM lane and adds
-// (double)D_in - (double)D_out to the FP64 running sums.  Because a batch is
-// reduced by the same instruction sequence when it enters and when it leaves,
-// its FP32 sum is bitwise the same both times.
-//
-// Every wait on an mbarrier is bounded; on a timeout the CTA records
-// kStatusTimeout, drains its own copies and MMAs (bounded), frees its tensor
-// memory and returns.
+// See cw_tc.h for the pipeline.  This file holds the staging kernels, the
+// Khatri-Rao operand builder, the warp-specialized tcgen05 GEMM and the host
+// planner.  Every mbarrier wait is bounded: on a timeout the CTA records
+// kStatusTimeout, drains the copies and MMAs it issued (bounded), frees its
+// tensor memory and returns.
 #include <climits>
 #include <cstring>
 
@@ -27,7 +13,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 
+#include "cw_device.cuh"
 #include "cw_tc.h"
 #include "tc_ptx.cuh"
 
@@ -37,274 +25,19 @@ namespace {
 
 using namespace ptx;
 
-constexpr int KC = kTcKC, XS = kTcXS, TM = kTcM, NMAX = kTcNmax;
-constexpr int NT = 256;
+constexpr int KC = kTcKC, TM = kTcM, NMAX = kTcNmax, STAGES = kTcStages;
+constexpr int GEMM_THREADS = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr long long kWaitLimit = 1LL << 32;  // clock cycles (~2 s)
 
-constexpr int A_BYTES = TM * KC * 2;    // one 16-bit part of the A tile
-constexpr int B_BYTES = NMAX * KC * 2;  // one 16-bit part of the B tile (max rows)
-constexpr int OFF_A = 0;                // A[stage][hi/lo]
-constexpr int OFF_B = OFF_A + 4 * A_BYTES;
-constexpr int OFF_X = OFF_B + 4 * B_BYTES;
-
-// Byte stride of the two staged-sample buffers (TMA destinations, 1024-aligned).
-__host__ __device__ constexpr uint32_t tc_xstride(int npad)
-{
-    return ((uint32_t)npad * XS * 4 + 1023u) & ~1023u;
-}
-
-__host__ __device__ constexpr size_t tc_smem_bytes(int npad)
-{
-    return (size_t)OFF_X + 2ull * tc_xstride(npad) + 1024;  // + alignment slack
-}
-
-template <bool BF16>
-__device__ __forceinline__ void split_store(const float (&p)[8], unsigned char* hi, unsigned char* lo)
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if constexpr (BF16) {
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
-            const float2 hf = __bfloat1622float2(hv);
-            const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
-            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-        } else {
-            const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
-            const float2 hf = __half22float2(hv);
-            const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
-            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-        }
-    }
-    *reinterpret_cast<uint4*>(hi) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// Products over `nf` variables (packed one byte each) of 8 consecutive samples.
-__device__ __forceinline__ void kr8(const float* __restrict__ xs, uint32_t vars, int nf, int grp,
-                                    float (&p)[8])
-{
-#pragma unroll
-    for (int e = 0; e < 8; ++e) p[e] = 1.0f;
-    for (int f = 0; f < nf; ++f) {
-        const float* xr = xs + ((vars >> (8 * f)) & 0xffu) * XS + 8 * grp;
-        const float4 a = *reinterpret_cast<const float4*>(xr);
-        const float4 b = *reinterpret_cast<const float4*>(xr + 4);
-        p[0] *= a.x; p[1] *= a.y; p[2] *= a.z; p[3] *= a.w;
-        p[4] *= b.x; p[5] *= b.y; p[6] *= b.z; p[7] *= b.w;
-    }
-}
-
-template <bool BF16>
-__global__ void __launch_bounds__(NT, 1)
-k_update_tc(const __grid_constant__ CUtensorMap xmap, const TcArgs args)
-{
-    extern __shared__ unsigned char dsm_raw[];
-    unsigned char* dsm = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar_x[2], bar_mma[2], bar_acc;
-    __shared__ uint32_t s_tbase;
-    __shared__ uint32_t s_rowvar[NMAX], s_colvar[TM];
-    __shared__ int32_t s_rowcolmin[NMAX];
-    __shared__ int64_t s_rowoff[NMAX], s_coloff[TM];
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int npad = args.npad;
-    const uint32_t xbytes = (uint32_t)npad * XS * 4;   // bytes of one TMA box
-    const uint32_t xstride = tc_xstride(npad);
-
-    if (tid == 0) {
-        mbar_init(&bar_x[0], 1);
-        mbar_init(&bar_x[1], 1);
-        mbar_init(&bar_mma[0], 1);
-        mbar_init(&bar_mma[1], 1);
-        mbar_init(&bar_acc, 1);
-        fence_mbar_init();
-        prefetch_tensormap(&xmap);
-    }
-    if (warp == 0) {
-        tmem_alloc(&s_tbase, 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = s_tbase;
-
-    uint32_t g = 0;                  // K-chunks consumed by this CTA
-    uint32_t npairs_done = 0;        // completed passes (bar_acc phases)
-    uint32_t tma_issued[2] = {0, 0}; // thread 0 only
-    uint32_t tma_waited[2] = {0, 0}; // thread 0 only
-    bool bad = false;
-
-    for (int it = blockIdx.x; it < args.nitems && !bad; it += gridDim.x) {
-        const TcItem item = args.items[it];
-        const TcOrder& od = args.ord[item.s];
-        const int NB = (item.nrows + 31) & ~31;
-        for (int r = tid; r < NMAX; r += NT) {
-            const bool v = r < item.nrows;
-            s_rowvar[r] = v ? od.rowvar[item.row0 + r] : 0u;
-            s_rowoff[r] = v ? od.rowoff[item.row0 + r] : 0;
-            s_rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
-        }
-        if (tid < TM) {
-            const bool v = tid < item.ncols;
-            s_colvar[tid] = v ? od.colvar[item.col0 + tid] : 0u;
-            s_coloff[tid] = v ? od.coloff[item.col0 + tid] : 0;
-        }
-        __syncthreads();
-        const uint32_t idesc = idesc_f16(TM, NB, BF16);
-        const int h = od.h, sh = od.sh;
-
-        for (int j = 0; j < args.npairs && !bad; ++j) {
-            const int nplus = args.seglen / KC;
-            const int nminus = (j == 0) ? args.minus_len / KC : 0;
-            const int nch = nplus + nminus;
-            const int plus0 = j * args.seg_stride;
-            if (tid == 0) {
-                for (int q = 0; q < 2 && q < nch; ++q) {
-                    const uint32_t st = (g + q) & 1;
-                    const int k = q < nplus ? plus0 + q * KC : args.minus_off + (q - nplus) * KC;
-                    mbar_arrive_expect_tx(&bar_x[st], xbytes);
-                    tma_load_2d(dsm + OFF_X + st * xstride, &xmap, &bar_x[st], k, 0);
-                    tma_issued[st]++;
-                }
-            }
-            for (int q = 0; q < nch; ++q) {
-                const uint32_t gc = g + q, st = gc & 1, use = gc >> 1;
-                bool ok = mbar_wait(&bar_x[st], use & 1, kWaitLimit);
-                if (tid == 0 && ok) tma_waited[st]++;
-                if (ok && gc >= 2) ok = mbar_wait(&bar_mma[st], (use - 1) & 1, kWaitLimit);
-                unsigned char* Ahi = dsm + OFF_A + (st * 2 + 0) * A_BYTES;
-                unsigned char* Alo = dsm + OFF_A + (st * 2 + 1) * A_BYTES;
-                unsigned char* Bhi = dsm + OFF_B + (st * 2 + 0) * B_BYTES;
-                unsigned char* Blo = dsm + OFF_B + (st * 2 + 1) * B_BYTES;
-                if (ok) {
-                    const float* xs = reinterpret_cast<const float*>(dsm + OFF_X + st * xstride);
-                    // A: 128 columns x 4 groups of 8 samples
-                    for (int task = tid; task < TM * (KC / 8); task += NT) {
-                        const int r = task % TM, grp = task / TM;
-                        float p[8];
-                        if (r < item.ncols) {
-                            kr8(xs, s_colvar[r], sh, grp, p);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) p[e] = 0.0f;
-                        }
-                        const int off = grp * (TM * 16) + (r >> 3) * 128 + (r & 7) * 16;
-                        split_store<BF16>(p, Ahi + off, Alo + off);
-                    }
-                    // B: NB rows x 4 groups of 8 samples
-                    for (int task = tid; task < NB * (KC / 8); task += NT) {
-                        const int r = task % NB, grp = task / NB;
-                        float p[8];
-                        if (r < item.nrows) {
-                            kr8(xs, s_rowvar[r], h, grp, p);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) p[e] = 0.0f;
-                        }
-                        const int off = grp * (NB * 16) + (r >> 3) * 128 + (r & 7) * 16;
-                        split_store<BF16>(p, Bhi + off, Blo + off);
-                    }
-                }
-                fence_proxy_async_smem();
-                if (__syncthreads_or(!ok)) {
-                    bad = true;
-                    break;
-                }
-                if (tid == 0) {
-                    tc_fence_after();
-                    const bool plus = q < nplus;
-                    const bool first = (q == 0) || (q == nplus);
-                    const uint32_t d = tbase + (plus ? 0u : 256u);
-#pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint64_t ah = smem_desc_kmajor(smem_u32(Ahi) + ks * 2 * (TM * 16), TM * 16, 128);
-                        const uint64_t al = smem_desc_kmajor(smem_u32(Alo) + ks * 2 * (TM * 16), TM * 16, 128);
-                        const uint64_t bh = smem_desc_kmajor(smem_u32(Bhi) + ks * 2 * (NB * 16), NB * 16, 128);
-                        const uint64_t bl = smem_desc_kmajor(smem_u32(Blo) + ks * 2 * (NB * 16), NB * 16, 128);
-                        tc_mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
-                        tc_mma_f16(d, ah, bl, idesc, 1u);
-                        tc_mma_f16(d, al, bh, idesc, 1u);
-                    }
-                    tc_commit(&bar_mma[st]);
-                    if (q == nch - 1) tc_commit(&bar_acc);
-                    if (q + 2 < nch) {
-                        const int k = (q + 2) < nplus ? plus0 + (q + 2) * KC
-                                                      : args.minus_off + (q + 2 - nplus) * KC;
-                        mbar_arrive_expect_tx(&bar_x[st], xbytes);
-                        tma_load_2d(dsm + OFF_X + st * xstride, &xmap, &bar_x[st], k, 0);
-                        tma_issued[st]++;
-                    }
-                }
-            }
-            if (bad) break;
-            g += nch;
-
-            // epilogue: S += D_in - D_out
-            const bool ok = mbar_wait(&bar_acc, npairs_done & 1, kWaitLimit);
-            npairs_done++;
-            if (__syncthreads_or(!ok)) {
-                bad = true;
-                break;
-            }
-            tc_fence_after();
-            {
-                const int quarter = warp & 3, half = warp >> 2;
-                const int i = 32 * quarter + lane;
-                const bool ivalid = i < item.ncols;
-                const int cglob = item.col0 + i;
-                const int64_t co = s_coloff[i];
-                const bool has_minus = nminus > 0;
-                double* __restrict__ S = od.S;
-                const int jb0 = half * (NB / 2), jb1 = jb0 + NB / 2;
-                for (int jb = jb0; jb < jb1; jb += 16) {
-                    uint32_t d0[16], d1[16];
-                    const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
-                    tmem_ld16(ta, d0);
-                    if (has_minus) tmem_ld16(ta + 256u, d1);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int r = jb + t;
-                        if (ivalid && r < item.nrows && cglob >= s_rowcolmin[r]) {
-                            double v = (double)__uint_as_float(d0[t]);
-                            if (has_minus) v -= (double)__uint_as_float(d1[t]);
-                            S[s_rowoff[r] + co] += v;
-                        }
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncthreads();
-        }
-    }
-
-    if (bad) {
-        if (tid == 0) {
-            atomicOr(args.status, kStatusTimeout);
-            // drain this CTA's own copies and MMAs before the memory goes away
-            for (int st = 0; st < 2; ++st)
-                while (tma_waited[st] < tma_issued[st]) {
-                    if (!mbar_wait(&bar_x[st], tma_waited[st] & 1, kWaitLimit)) break;
-                    tma_waited[st]++;
-                }
-            tc_commit(&bar_acc);
-            mbar_wait(&bar_acc, npairs_done & 1, kWaitLimit);
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tbase, 512);
-}
+constexpr int A_PART = TM * KC * 2;    // bytes of one 16-bit part of an A tile
+constexpr int B_PART = NMAX * KC * 2;  // bytes of one 16-bit part of a B tile
+constexpr int STAGE_BYTES = 2 * A_PART + 2 * B_PART;
+constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 
 // ---------------------------------------------------------------------------
 // staging: shifted samples, transposed to [variable][sample]
 // ---------------------------------------------------------------------------
-// Rows [0, P) of the K axis hold X_(+), rows [P, 2P) hold X_(-), zero beyond p.
+// Samples [0, P) of the K axis hold X_(+), [P, 2P) hold X_(-), zero beyond p.
 // The thread of (r, v) also moves X_(+) into the ring slot it reads X_(-) from.
 __global__ void __launch_bounds__(256)
 k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __restrict__ x_out,
@@ -340,57 +73,299 @@ k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __re
     if (badv) atomicOr(status, kStatusNonFinite);
 }
 
-// Window rows in batches of p (window order, oldest first): batch q at K
-// offset q*P, zero-padded to P.
+// Window rows [q*p, q*p + p) (window order, oldest first) into samples [0, P).
 __global__ void __launch_bounds__(256)
-k_tc_stage_window(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p,
-                  int p, int P, int nbatch, int n, int npad, const float* __restrict__ shift,
-                  float* __restrict__ XT, int64_t Kcap)
+k_tc_stage_batch(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p,
+                 int q, int p, int P, int n, int npad, const float* __restrict__ shift,
+                 float* __restrict__ XT, int64_t Kcap)
 {
-    const int64_t total = (int64_t)npad * nbatch * P;
+    const int64_t total = (int64_t)npad * P;
     const int64_t head = *head_p;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int v = (int)(e / ((int64_t)nbatch * P));
-        const int64_t k = e - (int64_t)v * nbatch * P;
-        const int64_t q = k / P;
-        const int r = (int)(k - q * P);
-        const int64_t w = q * p + r;
+        const int v = (int)(e / P);
+        const int r = (int)(e - (int64_t)v * P);
+        const int64_t w = (int64_t)q * p + r;
         float x = 0.0f;
         if (r < p && w < T && v < n) {
             int64_t slot = head + w;
             if (slot >= T) slot -= T;
             x = ring[slot * npad + v] - shift[v];
         }
-        XT[(int64_t)v * Kcap + k] = x;
+        XT[(int64_t)v * Kcap + r] = x;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Khatri-Rao operand rows: product over the row's variables of 8 consecutive
+// samples, split into 16-bit hi + lo, stored at [part][kb][row][8].
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restrict__ opvars,
+           int64_t rows, int nkb, int64_t kbcap, uint16_t* __restrict__ ops)
+{
+    const int64_t total = rows * nkb;
+    const int64_t part = kbcap * rows * 8;  // elements of one part
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int kb = (int)(e / rows);
+        const int64_t row = e - (int64_t)kb * rows;
+        const uint64_t w = opvars[row];
+        const uint32_t vars = (uint32_t)w;
+        const int nf = (int)(w >> 32);
+        float p[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) p[t] = 1.0f;
+        for (int f = 0; f < nf; ++f) {
+            const float* xr = XT + (int64_t)((vars >> (8 * f)) & 0xffu) * Kcap + 8 * kb;
+            const float4 a = *reinterpret_cast<const float4*>(xr);
+            const float4 c = *reinterpret_cast<const float4*>(xr + 4);
+            p[0] *= a.x; p[1] *= a.y; p[2] *= a.z; p[3] *= a.w;
+            p[4] *= c.x; p[5] *= c.y; p[6] *= c.z; p[7] *= c.w;
+        }
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (BF16) {
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
+                const float2 hf = __bfloat1622float2(hv);
+                const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+            } else {
+                const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
+                const float2 hf = __half22float2(hv);
+                const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+            }
+        }
+        const int64_t o = ((int64_t)kb * rows + row) * 8;
+        *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// 4-D TMA load: box {8, rows, KC/8, 1} at (0, row, kb, part).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int row,
+                                            int kb, int part)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(0), "r"(row), "r"(kb),
+        "r"(part)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// the GEMM: one CTA per (item, K-split) unit
+// ---------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(GEMM_THREADS, 2)
+k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+          const TcGemmArgs args)
+{
+    extern __shared__ unsigned char dsm_raw[];
+    unsigned char* dsm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc;
+    __shared__ uint32_t s_tbase;
+    __shared__ int s_abort;
+    __shared__ int64_t s_rowoff[NMAX], s_coloff[TM];
+    __shared__ int32_t s_rowcolmin[NMAX];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int unit = blockIdx.x;
+    const TcItem item = args.items[unit / args.ksplit];
+    const int split = unit % args.ksplit;
+    const int NB = (item.nrows + 15) & ~15;
+    const TcOrder& od = args.ord[item.s];
+
+    // this split's chunks of the entering and leaving segments
+    const int cps_p = (args.nplus + args.ksplit - 1) / args.ksplit;
+    const int p0 = min(args.nplus, split * cps_p), p1 = min(args.nplus, p0 + cps_p);
+    const int cps_m = (args.nminus + args.ksplit - 1) / args.ksplit;
+    const int m0 = min(args.nminus, split * cps_m), m1 = min(args.nminus, m0 + cps_m);
+    const int nplus = p1 - p0, nminus = m1 - m0;
+    const int nch = nplus + nminus;
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        mbar_init(&bar_acc, 1);
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tensormap(&mapA);
+        prefetch_tensormap(&mapB);
+    }
+    if (warp == 1) {
+        tmem_alloc(&s_tbase, 2 * NMAX);
+        tmem_relinquish();
+    }
+    for (int r = tid; r < NMAX; r += GEMM_THREADS) {
+        const bool v = r < item.nrows;
+        s_rowoff[r] = v ? od.rowoff[item.row0 + r] : 0;
+        s_rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
+    }
+    for (int c = tid; c < TM; c += GEMM_THREADS) s_coloff[c] = c < item.ncols ? od.coloff[item.col0 + c] : 0;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = s_tbase;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0 && nch > 0) {
+            int issued = 0;
+            for (int q = 0; q < nch; ++q) {
+                const int st = q % STAGES, use = q / STAGES;
+                if (q >= STAGES && !mbar_wait(&bar_empty[st], (use - 1) & 1, kWaitLimit)) {
+                    atomicOr(args.status, kStatusTimeout);
+                    s_abort = 1;
+                    break;
+                }
+                if (*(volatile int*)&s_abort) break;
+                const int kb = q < nplus ? (p0 + q) * (KC / 8) : args.minus_kb + (m0 + q - nplus) * (KC / 8);
+                unsigned char* sa = dsm + st * STAGE_BYTES;
+                unsigned char* sb = sa + 2 * A_PART;
+                mbar_arrive_expect_tx(&bar_full[st], STAGE_BYTES);
+                tma_load_4d(sa, &mapA, &bar_full[st], item.acol, kb, 0);
+                tma_load_4d(sa + A_PART, &mapA, &bar_full[st], item.acol, kb, 1);
+                tma_load_4d(sb, &mapB, &bar_full[st], item.brow, kb, 0);
+                tma_load_4d(sb + B_PART, &mapB, &bar_full[st], item.brow, kb, 1);
+                ++issued;
+            }
+            // drain: wait until every issued load has landed (bounded)
+            for (int q = max(0, issued - STAGES); q < issued; ++q)
+                mbar_wait(&bar_full[q % STAGES], (q / STAGES) & 1, kWaitLimit);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0 && nch > 0) {
+            const uint32_t idesc = idesc_f16(TM, NB, BF16);
+            int q = 0;
+            for (; q < nch; ++q) {
+                const int st = q % STAGES, use = q / STAGES;
+                if (!mbar_wait(&bar_full[st], use & 1, kWaitLimit)) {
+                    atomicOr(args.status, kStatusTimeout);
+                    s_abort = 1;
+                    break;
+                }
+                tc_fence_after();
+                const bool plus = q < nplus;
+                const bool first = (q == 0) || (q == nplus);
+                const uint32_t d = tbase + (plus ? 0u : (uint32_t)NMAX);
+                const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
+                const uint32_t sb = sa + 2 * A_PART;
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint64_t ah = smem_desc_kmajor(sa + ks * 2 * (TM * 16), TM * 16, 128);
+                    const uint64_t al = smem_desc_kmajor(sa + A_PART + ks * 2 * (TM * 16), TM * 16, 128);
+                    const uint64_t bh = smem_desc_kmajor(sb + ks * 2 * (NMAX * 16), NMAX * 16, 128);
+                    const uint64_t bl = smem_desc_kmajor(sb + B_PART + ks * 2 * (NMAX * 16), NMAX * 16, 128);
+                    tc_mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+                    tc_mma_f16(d, ah, bl, idesc, 1u);
+                    tc_mma_f16(d, al, bh, idesc, 1u);
+                }
+                tc_commit(&bar_empty[st]);
+            }
+            tc_commit(&bar_acc);
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> FP32 workspace ----------------
+        const bool ok = nch == 0 ? true : mbar_wait(&bar_acc, 0, kWaitLimit);
+        if (!ok) {
+            if (lane == 0) atomicOr(args.status, kStatusTimeout);
+        } else if (!*(volatile int*)&s_abort) {
+            tc_fence_after();
+            const int quarter = warp & 3;
+            const int i = 32 * quarter + lane;
+            const bool ivalid = i < item.ncols;
+            const int cglob = item.col0 + i;
+            const int64_t co = s_coloff[i];
+            float* Win = args.W + (int64_t)(2 * split) * args.wslice + od.woff;
+            float* Wout = Win + args.wslice;
+            for (int jb = 0; jb < NB; jb += 16) {
+                uint32_t d0[16], d1[16];
+                const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
+                if (nplus > 0) tmem_ld16(ta, d0);
+                if (nminus > 0) tmem_ld16(ta + (uint32_t)NMAX, d1);
+                tmem_ld_wait();
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int r = jb + t;
+                    if (ivalid && r < item.nrows && cglob >= s_rowcolmin[r]) {
+                        const int64_t e = s_rowoff[r] + co;
+                        Win[e] = nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
+                        if (args.nminus > 0) Wout[e] = nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tbase, 2 * NMAX);
+}
+
+// S_s[e] += (double)(sum_k W[k][0][e]) for every order (window batches).
+__global__ void __launch_bounds__(256)
+k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const TcAccArgs a)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < wslice;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int s = 1;
+        while (s < a.d && e >= a.Eoff[s + 1]) ++s;
+        float din = 0.0f;
+        for (int k = 0; k < ksplit; ++k) din += W[(int64_t)(2 * k) * wslice + e];
+        a.S[s][e - a.Eoff[s]] += f32_to_f64(din);
     }
 }
 
 inline int grid_for(int64_t work)
 {
     int64_t g = (work + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8192));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, 16384));
 }
 
-cudaError_t launch_tc_kernel(const TcPlan& plan, int npairs, int seglen, int seg_stride,
-                             int minus_off, int minus_len, cudaStream_t st)
+cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_kb, cudaStream_t st)
 {
-    TcArgs a{};
+    TcGemmArgs a{};
     for (int s = 0; s <= kMaxOrder; ++s) a.ord[s] = plan.ord[s];
     a.items = plan.items;
+    a.W = plan.W;
+    a.wslice = plan.wslice;
     a.nitems = plan.nitems;
-    a.npad = plan.npad;
-    a.npairs = npairs;
-    a.seglen = seglen;
-    a.seg_stride = seg_stride;
-    a.minus_off = minus_off;
-    a.minus_len = minus_len;
+    a.ksplit = plan.ksplit;
+    a.nplus = nplus;
+    a.nminus = nminus;
+    a.minus_kb = minus_kb;
     a.status = plan.status;
-    const size_t smem = tc_smem_bytes(plan.npad);
+    const int units = plan.nitems * plan.ksplit;
     if (plan.precision == 1)
-        k_update_tc<true><<<plan.grid, NT, smem, st>>>(plan.xmap, a);
+        k_kr_gemm<true><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB, a);
     else
-        k_update_tc<false><<<plan.grid, NT, smem, st>>>(plan.xmap, a);
+        k_kr_gemm<false><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
+{
+    const int nkb = nsamples / 8;
+    const int64_t kbcap = plan.Kcap / 8;
+    const int64_t work = plan.oprows * nkb;
+    if (plan.precision == 1)
+        k_kr_build<true><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
+                                                         nkb, kbcap, plan.ops);
+    else
+        k_kr_build<false><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
+                                                          nkb, kbcap, plan.ops);
     return cudaGetLastError();
 }
 
@@ -416,33 +391,47 @@ EncodeTiledFn get_encode_fn()
     return fn;
 }
 
-// Per-K-chunk cost model of one item (cycles): the larger of the tensor time
-// (3 MMAs of 128 x N x 32) and the operand build time, plus a fixed overhead.
-double item_cost(int nrows)
+int encode_operand_map(CUtensorMap* map, void* base, int64_t rows, int64_t kbcap, int boxrows)
 {
-    const int NB = (nrows + 31) & ~31;
+    EncodeTiledFn enc = get_encode_fn();
+    if (enc == nullptr) return (int)cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)rows, (cuuint64_t)kbcap, 2};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)rows * 16, (cuuint64_t)rows * kbcap * 16};
+    const cuuint32_t box[4] = {8, (cuuint32_t)boxrows, (cuuint32_t)(KC / 8), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return (int)cudaErrorInvalidValue;
+    return 0;
+}
+
+// Per-K-chunk cost model of one item (cycles): tensor time of 3 MMAs of
+// 128 x N x KC against the operand bytes streamed in, plus a fixed overhead.
+double item_chunk_cost(int nrows)
+{
+    const int NB = (nrows + 15) & ~15;
     const double mma = 3.0 * TM * NB * KC / 4096.0;
-    const double build = (TM + NB) * KC / 20.0;
-    return std::max(mma, build) + 120.0;
+    const double tma = (double)STAGE_BYTES / 128.0;
+    return std::max(mma, tma) + 40.0;
 }
 
 }  // namespace
 
 int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const UpdateArgs& upd,
-                   int d, int n, int b, int npad, int64_t T, int p, int sm_count, int precision,
-                   int* status, const DevAlloc& alloc)
+                   const int64_t* Eoff, int d, int n, int b, int npad, int64_t T, int p,
+                   int sm_count, int precision, int* status, const DevAlloc& alloc)
 {
     (void)n;
     (void)b;
+    (void)upd;
     plan.precision = precision;
     plan.npad = npad;
     plan.T = T;
     plan.p = p;
     plan.P = (p + KC - 1) / KC * KC;
     plan.nbatch = (int)((T + p - 1) / p);
-    const int64_t Pmax = (T + KC - 1) / KC * KC;
-    plan.Kcap = std::max<int64_t>((int64_t)plan.nbatch * plan.P, 2 * Pmax);
-    plan.Kcap = (plan.Kcap + 3) / 4 * 4;
+    plan.Kcap = 2 * (int64_t)plan.P;
     plan.status = status;
 
     cudaError_t e = alloc(sizeof(float) * (size_t)npad * plan.Kcap, (void**)&plan.XT);
@@ -450,31 +439,33 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
     e = cudaMemset(plan.XT, 0, sizeof(float) * (size_t)npad * plan.Kcap);
     if (e != cudaSuccess) return (int)e;
 
-    EncodeTiledFn enc = get_encode_fn();
-    if (enc == nullptr) return (int)cudaErrorNotSupported;
-    const cuuint64_t dims[2] = {(cuuint64_t)plan.Kcap, (cuuint64_t)npad};
-    const cuuint64_t strides[1] = {(cuuint64_t)plan.Kcap * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)XS, (cuuint32_t)npad};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&plan.xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, plan.XT, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return (int)cudaErrorInvalidValue;
+    // operand sets: key (factors, grouped?) -> first row; singles and the
+    // empty product have one ordering
+    std::map<std::pair<int, int>, int64_t> setoff;
+    std::vector<uint64_t> opvars;
+    auto add_set = [&](int k, int grouped, const std::vector<uint32_t>& vars) -> int64_t {
+        const std::pair<int, int> key(k, k <= 1 ? 0 : grouped);
+        auto it = setoff.find(key);
+        if (it != setoff.end()) return it->second;
+        const int64_t off = (int64_t)opvars.size();
+        for (uint32_t v : vars) opvars.push_back((uint64_t)v | ((uint64_t)k << 32));
+        // pad each set to a multiple of 8 rows so boxes of later sets stay aligned
+        while (opvars.size() % 8) opvars.push_back(0);
+        setoff[key] = off;
+        return off;
+    };
 
-    // per-order device tables (row/column tables are shared with the FP64 form)
     std::vector<TcItem> items;
     double useful = 0, issued = 0;
     for (int s = 1; s <= d; ++s) {
         const UpdateTables& t = tables[s];
         const OrderTables& ot = upd.ord[s];
         TcOrder& o = plan.ord[s];
-        o.rowvar = ot.rowvar;
         o.rowoff = ot.rowoff;
-        o.colvar = ot.colvar;
         o.coloff = ot.coloff;
-        o.S = ot.S;
-        o.h = t.h;
-        o.sh = t.sh;
+        o.woff = Eoff[s];
+        const int64_t loff = add_set(t.h, 1, t.rowvar);
+        const int64_t roff = add_set(t.sh, 0, t.colvar);
         const int nbar = (int)t.colstart.size();
         const int ncols = (int)t.colvar.size();
         std::vector<int32_t> colmin(t.rowvar.size());
@@ -488,7 +479,8 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
         o.rowcolmin = dcm;
 
         // row ranges: groups larger than NMAX rows are split; consecutive small
-        // groups are merged while that lowers the modelled cost
+        // groups are merged (invalid pairs are masked) while that lowers the
+        // modelled cost
         struct Range { int r0, r1, c0; };
         std::vector<Range> ranges;
         for (int m = 0; m < nbar; ++m) {
@@ -498,7 +490,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
         }
         auto cost = [&](const Range& R) {
             const int span = ncols - R.c0;
-            return ((span + TM - 1) / TM) * item_cost(R.r1 - R.r0);
+            return ((span + TM - 1) / TM) * item_chunk_cost(R.r1 - R.r0);
         };
         std::vector<Range> merged;
         for (const Range& R : ranges) {
@@ -522,57 +514,98 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
                 it.nrows = R.r1 - R.r0;
                 it.col0 = c;
                 it.ncols = std::min(TM, ncols - c);
+                it.brow = (int32_t)(loff + R.r0);
+                it.acol = (int32_t)(roff + c);
                 items.push_back(it);
-                issued += 3.0 * TM * ((it.nrows + 31) & ~31);
+                issued += 3.0 * TM * ((it.nrows + 15) & ~15);
             }
             for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, ncols - colmin[r]);
         }
     }
-    // larger items first, then round-robin over the persistent CTAs
+    // larger items first
     std::stable_sort(items.begin(), items.end(),
                      [](const TcItem& x, const TcItem& y) { return x.nrows > y.nrows; });
     plan.useful_macs_per_sample = useful;
     plan.issued_macs_per_sample = issued;
     plan.nitems = (int)items.size();
-    plan.grid = std::max(1, std::min(plan.nitems, sm_count));
+    // K-splits: about two waves of two CTAs per SM, at least 4 chunks per split
+    const int chunks = plan.P / KC;
+    const int target = 4 * sm_count;
+    int ks = (target + plan.nitems - 1) / std::max(1, plan.nitems);
+    ks = std::max(1, std::min(ks, std::max(1, chunks / 4)));
+    plan.ksplit = ks;
+
     e = alloc(sizeof(TcItem) * std::max<size_t>(items.size(), 1), (void**)&plan.items);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return (int)e;
 
-    const size_t smem = tc_smem_bytes(npad);
-    e = cudaFuncSetAttribute(k_update_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // operand array and its tensor maps
+    plan.oprows = (int64_t)opvars.size();
+    const int64_t kbcap = plan.Kcap / 8;
+    e = alloc(sizeof(uint64_t) * opvars.size(), (void**)&plan.opvars);
     if (e != cudaSuccess) return (int)e;
-    e = cudaFuncSetAttribute(k_update_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaMemcpy(plan.opvars, opvars.data(), sizeof(uint64_t) * opvars.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return (int)e;
+    const size_t opbytes = sizeof(uint16_t) * 2 * (size_t)kbcap * plan.oprows * 8;
+    e = alloc(opbytes, (void**)&plan.ops);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaMemset(plan.ops, 0, opbytes);
+    if (e != cudaSuccess) return (int)e;
+    int rc = encode_operand_map(&plan.mapA, plan.ops, plan.oprows, kbcap, TM);
+    if (rc) return rc;
+    rc = encode_operand_map(&plan.mapB, plan.ops, plan.oprows, kbcap, NMAX);
+    if (rc) return rc;
+
+    // workspace
+    plan.wslice = Eoff[d + 1];
+    e = alloc(sizeof(float) * 2 * (size_t)plan.ksplit * plan.wslice, (void**)&plan.W);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaMemset(plan.W, 0, sizeof(float) * 2 * (size_t)plan.ksplit * plan.wslice);
+    if (e != cudaSuccess) return (int)e;
+
+    e = cudaFuncSetAttribute(k_kr_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaFuncSetAttribute(k_kr_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return (int)e;
     plan.ready = 1;
     return 0;
 }
 
-int tc_launch_count(const TcPlan&) { return 2; }
-
-cudaError_t tc_update_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
-                           int64_t ld_out, float* ring, const int64_t* head, int p, int n,
-                           const float* shift, cudaStream_t st)
+cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
+                          int64_t ld_out, float* ring, const int64_t* head, int p, int n,
+                          const float* shift, cudaStream_t st)
 {
-    const int P = (p + KC - 1) / KC * KC;
-    if (2 * (int64_t)P > plan.Kcap) return cudaErrorInvalidValue;
-    k_tc_stage_push<<<grid_for((int64_t)plan.npad * P), 256, 0, st>>>(
-        x_in, ld_in, x_out, ld_out, ring, plan.T, head, p, P, n, plan.npad, shift, plan.XT,
+    if (p > plan.p) return cudaErrorInvalidValue;
+    k_tc_stage_push<<<grid_for((int64_t)plan.npad * plan.P), 256, 0, st>>>(
+        x_in, ld_in, x_out, ld_out, ring, plan.T, head, p, plan.P, n, plan.npad, shift, plan.XT,
         plan.Kcap, plan.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_tc_kernel(plan, 1, P, 0, P, P, st);
+    return launch_build(plan, 2 * plan.P, st);
 }
 
-cudaError_t tc_update_window(const TcPlan& plan, const float* ring, const int64_t* head, int n,
-                             const float* shift, cudaStream_t st)
+cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st)
 {
-    k_tc_stage_window<<<grid_for((int64_t)plan.npad * plan.nbatch * plan.P), 256, 0, st>>>(
-        ring, plan.T, head, plan.p, plan.P, plan.nbatch, n, plan.npad, shift, plan.XT, plan.Kcap);
+    return launch_gemm(plan, plan.P / KC, plan.P / KC, plan.P / 8, st);
+}
+
+cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const int64_t* head, int q,
+                                   int n, const float* shift, cudaStream_t st)
+{
+    k_tc_stage_batch<<<grid_for((int64_t)plan.npad * plan.P), 256, 0, st>>>(
+        ring, plan.T, head, q, plan.p, plan.P, n, plan.npad, shift, plan.XT, plan.Kcap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_tc_kernel(plan, plan.nbatch, plan.P, plan.P, 0, 0, st);
+    e = launch_build(plan, plan.P, st);
+    if (e != cudaSuccess) return e;
+    return launch_gemm(plan, plan.P / KC, 0, 0, st);
+}
+
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccArgs& a, cudaStream_t st)
+{
+    k_tc_accumulate<<<grid_for(plan.wslice), 256, 0, st>>>(plan.W, plan.wslice, plan.ksplit, a);
+    return cudaGetLastError();
 }
 
 }  // namespace cw
