@@ -61,7 +61,7 @@ struct cumwin_s {
     TcPlan tc{};  // tensor-core update plan (mixed forms)
 
     CumArgs cum[kMaxOrder + 1]{};
-    int cum_grid[kMaxOrder + 1] = {};
+    CumLaunch cum_launch[kMaxOrder + 1] = {};
     double* normpart = nullptr;
     int32_t* part_off = nullptr;
     double* fro2 = nullptr;
@@ -115,7 +115,7 @@ int run_cumulants(cumwin_t h, int64_t advance, bool accum = false)
     for (int s = 1; s <= h->d; ++s) {
         CumArgs a = h->cum[s];
         a.accum = accum ? 1 : 0;
-        CW_TRY(launch_cumulants(a, h->cum_grid[s], h->stream));
+        CW_TRY(launch_cumulants(a, h->cum_launch[s], h->stream));
     }
     CW_TRY(launch_norm_final(h->normpart, h->part_off, h->d, h->fro2, h->head, advance, h->T,
                              h->stream));
@@ -402,6 +402,10 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
     CW_CREATE_TRY(cudaMemset(h->ring, 0, sizeof(float) * (size_t)T * npad));
     for (int s = 1; s <= d; ++s) {
         h->E[s] = n_sorted(nbar, s) * ipow(b, s);
+        if (h->E[s] >= ((int64_t)1 << 31)) {
+            g_last_error = "a moment tensor of this size (2^31 stored elements or more) is not supported";
+            return bail(CUMWIN_EINVAL);
+        }
         CW_CREATE_TRY(h->alloc(&h->S[s], h->E[s]));
         CW_CREATE_TRY(h->alloc(&h->C[s], h->E[s]));
         CW_CREATE_TRY(cudaMemset(h->S[s], 0, sizeof(double) * h->E[s]));
@@ -481,11 +485,8 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         a.bs = (int32_t)ipow(b, s);
         a.nsub = ct.nsub;
         for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
-        // one warp per stored block, 8 warps per CTA
-        int64_t g = (n_sorted(nbar, s) + 7) / 8;
-        g = std::min<int64_t>(g, 4 * (int64_t)h->sm_count);
-        h->cum_grid[s] = (int)std::max<int64_t>(g, 1);
-        part_off[s] = part_off[s - 1] + h->cum_grid[s];
+        h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
+        part_off[s] = part_off[s - 1] + h->cum_launch[s].gx * h->cum_launch[s].gy;
     }
     // part_off[s-1]..part_off[s] are the partials of order s
     std::vector<int32_t> po(part_off.begin(), part_off.end());

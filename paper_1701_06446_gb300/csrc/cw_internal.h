@@ -93,7 +93,12 @@ cudaError_t launch_window_copy(const float* ring, int64_t T, const int64_t* head
 cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int ntiles,
                               const float* rows, int64_t K, int64_t npos, const float* shift,
                               cudaStream_t st);
-cudaError_t launch_cumulants(const CumArgs& a, int grid, cudaStream_t st);
+// Launch shape of the recovery kernel of one order (see plan_cumulants).
+struct CumLaunch {
+    int slots, gx, gy;
+};
+CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count);
+cudaError_t launch_cumulants(const CumArgs& a, const CumLaunch& L, cudaStream_t st);
 // Also advances the ring head by `advance` rows (mod T): the head lives in
 // device memory so that a captured shift can be replayed.
 cudaError_t launch_norm_final(const double* normpart, const int32_t* part_off, int d,

@@ -9,8 +9,9 @@
 //      [variable][sample] (FP32), zero-padded to P samples each.
 //   2. k_kr_build: every distinct Khatri-Rao operand row (the products of its
 //      variables over the staged samples) is formed once in FP32, split into
-//      bf16 hi + lo and written as [sample/8][row][8] for both parts, so that
-//      one 4-D TMA box lands in shared memory in the canonical K-major layout.
+//      bf16 hi + lo and written with the samples contiguous, so that a TMA box
+//      of 64 samples (128 bytes) x rows lands in shared memory in the
+//      128-byte-swizzled K-major layout the MMA descriptors read.
 //   3. k_kr_gemm: per unit (item x K-split) a TMA warp streams the item's
 //      A (128 columns) and B (rows) tiles through a 3-stage mbarrier ring, an
 //      MMA warp issues hi*hi + hi*lo + lo*hi per 16-sample step into TMEM
@@ -32,10 +33,10 @@
 
 namespace cw {
 
-constexpr int kTcKC = 32;      // samples per K-chunk
+constexpr int kTcKC = 64;      // samples per K-chunk (one 128-byte swizzle row)
 constexpr int kTcM = 128;      // columns per item (MMA M)
 constexpr int kTcNmax = 128;   // rows per item (MMA N, multiple of 16)
-constexpr int kTcStages = 3;   // TMA / MMA pipeline depth
+constexpr int kTcStages = 3;   // TMA / MMA pipeline depth (64 KB per stage)
 
 struct TcItem {
     int32_t s;      // order
@@ -45,7 +46,7 @@ struct TcItem {
     int32_t ncols;  // columns (<= kTcM)
     int32_t brow;   // TMA row coordinate of row0 in the operand array
     int32_t acol;   // TMA row coordinate of col0 in the operand array
-    int32_t pad;
+    int32_t bbox;   // rows of the B tile box (32, 64 or 128)
 };
 
 struct TcOrder {
@@ -62,7 +63,7 @@ struct TcGemmArgs {
     int64_t wslice;      // Etot
     int32_t nitems, ksplit;
     int32_t nplus, nminus;  // K-chunks of the entering / leaving segment
-    int32_t minus_kb;       // first kb (sample / 8) of the leaving segment
+    int32_t minus_k;        // first sample of the leaving segment
     int* status;
 };
 
@@ -72,11 +73,11 @@ struct TcPlan {
     int npad = 0, p = 0, P = 0, nbatch = 0;
     int64_t T = 0, Kcap = 0;
     float* XT = nullptr;           // [npad][Kcap] shifted samples, variable-major
-    // operand array: rows of all Khatri-Rao sets, [part][Kcap/8][rows][8] bf16
+    // operand array: rows of all Khatri-Rao sets, [part][row][Kcap] bf16
     uint16_t* ops = nullptr;
     int64_t oprows = 0;
     uint64_t* opvars = nullptr;    // per operand row: packed variables | factors << 32
-    CUtensorMap mapA{}, mapB{};
+    CUtensorMap mapA{}, mapB[3]{};  // A boxes of 128 rows; B boxes of 32, 64, 128 rows
     TcItem* items = nullptr;
     int nitems = 0, ksplit = 1;
     TcOrder ord[kMaxOrder + 1]{};

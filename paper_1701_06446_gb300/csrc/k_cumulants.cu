@@ -6,17 +6,20 @@
 // that holds the first index gives the equivalent subset recursion
 //     C_s[i] = M_s[i] - sum_{A contains index 1, A != all} C_|A|[i_A] M_{s-|A|}[i_rest]
 // (2^{s-1} - 1 terms instead of B(s) - 1), which is what runs here.  With
-// M = S/T it is evaluated as C_s = (S_s[i] - sum_A C_|A|[i_A] S_rest[i_rest]) / T,
+// M = S/T it is evaluated as C_s = (S_s[i] - sum_A C_|A|[i_A] S_rest[i_rest]) / T:
 // one FP64 multiply-add per subset and one scaling per element (FP64 is the
-// scarce pipe on this GPU).
+// scarce pipe on this GPU, so the kernel keeps everything else off it).
 //
-// For a sorted block j every sub-tuple j_A is sorted, so the operands are
-// stored blocks whose ranks come from a per-block table; the in-block offsets
-// follow from the element's own in-block digits because diagonal blocks are
-// stored whole.  One warp handles one block at a time, its lanes striding
-// over the block's b^s elements.  The same pass accumulates
-// multiplicity * C^2 (Algorithm 5 with k = 2) into one partial per CTA; a
-// second kernel adds the partials of each order in a fixed order.
+// For a sorted block j every sub-tuple j_A is sorted, so each operand is a
+// stored block whose rank comes from a per-block table, and its in-block
+// offset follows from the element's own in-block digits because diagonal
+// blocks are stored whole.  The kernel is specialised per order: the subset
+// masks are compile-time constants, each thread owns one in-block offset and
+// computes its per-subset operand offsets once, and the per-block operand
+// bases (rank * b^|A|) are staged in shared memory for a group of blocks.
+// The same pass accumulates multiplicity * C^2 (Algorithm 5 with k = 2) into
+// one partial per CTA; a second kernel adds the partials of each order in a
+// fixed order.
 #include "cw_device.cuh"
 #include "cw_internal.h"
 
@@ -26,109 +29,122 @@ namespace {
 
 constexpr int NT = 256;
 
-constexpr int WARPS = NT / 32;
+// Subset t (0 <= t < 2^{S-1} - 1) holds position 0 and the positions of the
+// set bits of t shifted by one: mask = 2t + 1 (the host tables use this order).
+template <int S>
+struct Subsets {
+    static constexpr int N = (1 << (S - 1)) - 1;
+};
 
-__global__ void __launch_bounds__(NT) k_cumulants(const CumArgs a)
+__host__ __device__ constexpr int popc_c(unsigned x) { return x ? (int)(x & 1u) + popc_c(x >> 1) : 0; }
+
+template <int S>
+__global__ void __launch_bounds__(NT) k_cumulants(const CumArgs a, int slots)
 {
-    const int s = a.s, b = a.b, bs = a.bs, nsub = a.nsub;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // per-subset digit weights: offA = sum_k dig[k] * wA[u][k], offR likewise
-    __shared__ int wA[128][kMaxOrder], wR[128][kMaxOrder];
-    __shared__ int la_s[128], lr_s[128];
-    __shared__ int bpow[kMaxOrder + 1];
-    if (threadIdx.x <= kMaxOrder) {
-        int p = 1;
-        for (int k = 0; k < (int)threadIdx.x; ++k) p *= b;
-        bpow[threadIdx.x] = p;
-    }
-    for (int u = threadIdx.x; u < nsub; u += NT) {
-        const unsigned mask = a.mask[u];
-        int na = 0, nr = 0;
-        for (int k = 0; k < s; ++k) na += (mask >> k) & 1u;
-        nr = s - na;
-        int ka = 0, kr = 0, pa = 1, pr = 1;
-        for (int k = 0; k < na; ++k) pa *= b;
-        for (int k = 0; k < nr; ++k) pr *= b;
-        for (int k = 0; k < s; ++k) {
-            if ((mask >> k) & 1u) {
-                pa /= b;
-                wA[u][k] = pa;
-                wR[u][k] = 0;
-                ++ka;
-            } else {
-                pr /= b;
-                wR[u][k] = pr;
-                wA[u][k] = 0;
-                ++kr;
-            }
-        }
-        la_s[u] = na;
-        lr_s[u] = nr;
-    }
-    __syncthreads();
+    constexpr int NS = Subsets<S>::N;
+    extern __shared__ int sbase[];  // [slots][NS][2]: rank(j_A) * b^|A|, rank(j_rest) * b^|rest|
+    const int b = a.b, bs = a.bs;
+    int bp[kMaxOrder + 1];
+    bp[0] = 1;
+#pragma unroll
+    for (int k = 1; k <= kMaxOrder; ++k) bp[k] = bp[k - 1] * b;
 
-    double* __restrict__ Ss = a.S[s];
+    // this thread's slot and in-block offset
+    int slot, off;
+    if (slots == 1) {
+        slot = 0;
+        off = blockIdx.y * NT + threadIdx.x;
+    } else {
+        slot = threadIdx.x / bs;
+        off = threadIdx.x - slot * bs;
+    }
+    const bool tvalid = slot < slots && off < bs;
+    int dig[S];
+    {
+        int rem = off;
+#pragma unroll
+        for (int k = S - 1; k >= 0; --k) {
+            const int q = rem / b;
+            dig[k] = rem - q * b;
+            rem = q;
+        }
+    }
+    int offA[NS > 0 ? NS : 1], offR[NS > 0 ? NS : 1];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+        const unsigned mask = 2u * t + 1u;
+        int oa = 0, orr = 0;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if ((mask >> k) & 1u) oa = oa * b + dig[k];
+            else orr = orr * b + dig[k];
+        }
+        offA[t] = oa;
+        offR[t] = orr;
+    }
+
+    double* __restrict__ Ss = a.S[S];
     double local = 0.0;
     const int64_t nblocks = a.E / bs;
-    for (int64_t blk = (int64_t)blockIdx.x * WARPS + warp; blk < nblocks;
-         blk += (int64_t)gridDim.x * WARPS) {
-        const int32_t* __restrict__ sr = a.subrank + (size_t)blk * nsub * 2;
-        const double mult = s > 1 ? a.mult[blk] : 1.0;
-        for (int off = lane; off < bs; off += 32) {
-            const int64_t e = blk * bs + off;
-            double acc = Ss[e];
-            if (a.accum) {
-                float din = 0.0f, dout = 0.0f;
-                const float* w = a.W + a.woff + e;
-                for (int k = 0; k < a.ksplit; ++k) {
-                    din += w[(int64_t)(2 * k) * a.wslice];
-                    dout += w[(int64_t)(2 * k + 1) * a.wslice];
+    const int64_t ngroups = (nblocks + slots - 1) / slots;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int64_t blk0 = grp * slots;
+        if (NS > 0) {
+            __syncthreads();
+            constexpr int NSD = NS > 0 ? NS : 1;
+            for (int i = threadIdx.x; i < slots * NS; i += NT) {
+                const int64_t blk = blk0 + i / NSD;
+                const int t = i - (i / NSD) * NSD;
+                if (blk < nblocks) {
+                    const int32_t* sr = a.subrank + ((size_t)blk * NS + t) * 2;
+                    const int la = __popc(2u * t + 1u), lr = S - la;
+                    sbase[2 * i] = sr[0] * bp[la];
+                    sbase[2 * i + 1] = sr[1] * bp[lr];
                 }
-                acc += f32_to_f64(din) - f32_to_f64(dout);
-                Ss[e] = acc;
             }
-            if (s == 1) {
-                const double c = acc * a.invT;
-                a.Cout[e] = c;
-                const double x = c + (double)a.shift[e];
-                local = fma(x, x, local);
-                continue;
+            __syncthreads();
+        }
+        const int64_t blk = blk0 + slot;
+        if (!tvalid || blk >= nblocks) continue;
+        const int64_t e = blk * bs + off;
+        double acc = Ss[e];
+        if (a.accum) {
+            float din = 0.0f, dout = 0.0f;
+            const float* w = a.W + a.woff + e;
+            for (int k = 0; k < a.ksplit; ++k) {
+                din += w[(int64_t)(2 * k) * a.wslice];
+                dout += w[(int64_t)(2 * k + 1) * a.wslice];
             }
-            int dig[kMaxOrder];
-            int rem = off;
-            for (int k = s - 1; k >= 0; --k) {
-                const int q = rem / b;
-                dig[k] = rem - q * b;
-                rem = q;
-            }
-            for (int u = 0; u < nsub; ++u) {
-                int offA = 0, offR = 0;
+            acc += f32_to_f64(din) - f32_to_f64(dout);
+            Ss[e] = acc;
+        }
+        const int* sb = sbase + 2 * slot * NS;
 #pragma unroll
-                for (int k = 0; k < kMaxOrder; ++k) {
-                    if (k < s) {
-                        offA += dig[k] * wA[u][k];
-                        offR += dig[k] * wR[u][k];
-                    }
-                }
-                const int la = la_s[u], lr = lr_s[u];
-                const double cA = a.C[la][(int64_t)sr[2 * u] * bpow[la] + offA];
-                const double sR = a.S[lr][(int64_t)sr[2 * u + 1] * bpow[lr] + offR];
-                acc = fma(-cA, sR, acc);
-            }
-            const double c = acc * a.invT;
-            a.Cout[e] = c;
-            local = fma(mult * c, c, local);
+        for (int t = 0; t < NS; ++t) {
+            const int la = popc_c(2u * t + 1u), lr = S - la;
+            const double cA = a.C[la][sb[2 * t] + offA[t]];
+            const double sR = a.S[lr][sb[2 * t + 1] + offR[t]];
+            acc = fma(-cA, sR, acc);
+        }
+        const double c = acc * a.invT;
+        a.Cout[e] = c;
+        if (S == 1) {
+            const double x = c + (double)a.shift[e];
+            local = fma(x, x, local);
+        } else {
+            local = fma(a.mult[blk] * c, c, local);
         }
     }
     // deterministic CTA reduction
     __shared__ double red[NT];
+    __syncthreads();
     red[threadIdx.x] = local;
     __syncthreads();
     for (int w = NT / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) a.normpart[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
 // One warp per order: lanes add strided partials, then a fixed shuffle tree.
@@ -145,12 +161,54 @@ __global__ void k_norm_final(const double* __restrict__ normpart, const int32_t*
     if (lane == 0) fro2[s] = z;
 }
 
+template <int S>
+cudaError_t launch_order(const CumArgs& a, const CumLaunch& L, cudaStream_t st)
+{
+    constexpr int NS = Subsets<S>::N;
+    const size_t smem = (size_t)L.slots * (NS > 0 ? NS : 1) * 2 * sizeof(int);
+    k_cumulants<S><<<dim3(L.gx, L.gy), NT, smem, st>>>(a, L.slots);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_cumulants(const CumArgs& a, int grid, cudaStream_t st)
+// Launch shape of order s: `slots` blocks per group when b^s < 256 (one thread
+// per element of each), else one block per group spread over gy CTAs of 256
+// offsets; gx groups in flight.  Partials: gx * gy per order.
+CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count)
 {
-    k_cumulants<<<grid, NT, 0, st>>>(a);
-    return cudaGetLastError();
+    CumLaunch L{};
+    const int ns = (1 << (s - 1)) - 1;
+    if (bs >= NT) {
+        L.slots = 1;
+        L.gy = (bs + NT - 1) / NT;
+    } else {
+        int slots = NT / bs;
+        const int cap = ns > 0 ? (40 * 1024) / (ns * 2 * (int)sizeof(int)) : NT;
+        if (slots > cap) slots = cap;
+        L.slots = slots < 1 ? 1 : slots;
+        L.gy = 1;
+    }
+    const int64_t groups = (nblocks + L.slots - 1) / L.slots;
+    int64_t gx = (4LL * sm_count + L.gy - 1) / L.gy;
+    if (gx > groups) gx = groups;
+    L.gx = (int)(gx < 1 ? 1 : gx);
+    return L;
+}
+
+cudaError_t launch_cumulants(const CumArgs& a, const CumLaunch& L, cudaStream_t st)
+{
+    switch (a.s) {
+    case 1: return launch_order<1>(a, L, st);
+    case 2: return launch_order<2>(a, L, st);
+    case 3: return launch_order<3>(a, L, st);
+    case 4: return launch_order<4>(a, L, st);
+    case 5: return launch_order<5>(a, L, st);
+    case 6: return launch_order<6>(a, L, st);
+    case 7: return launch_order<7>(a, L, st);
+    case 8: return launch_order<8>(a, L, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_norm_final(const double* normpart, const int32_t* part_off, int d, double* fro2,

@@ -28,9 +28,10 @@ using namespace ptx;
 constexpr int KC = kTcKC, TM = kTcM, NMAX = kTcNmax, STAGES = kTcStages;
 constexpr int GEMM_THREADS = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 constexpr long long kWaitLimit = 1LL << 32;  // clock cycles (~2 s)
+static_assert(KC * 2 == 128, "one K-chunk is one 128-byte swizzle row of bf16");
 
-constexpr int A_PART = TM * KC * 2;    // bytes of one 16-bit part of an A tile
-constexpr int B_PART = NMAX * KC * 2;  // bytes of one 16-bit part of a B tile
+constexpr int A_PART = TM * 128;      // bytes of one 16-bit part of an A tile (128 rows x 128 B)
+constexpr int B_PART = NMAX * 128;    // bytes of one 16-bit part of a B tile (up to NMAX rows)
 constexpr int STAGE_BYTES = 2 * A_PART + 2 * B_PART;
 constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 
@@ -98,19 +99,20 @@ k_tc_stage_batch(const float* __restrict__ ring, int64_t T, const int64_t* __res
 
 // ---------------------------------------------------------------------------
 // Khatri-Rao operand rows: product over the row's variables of 8 consecutive
-// samples, split into 16-bit hi + lo, stored at [part][kb][row][8].
+// samples, split into 16-bit hi + lo, stored at [part][row][sample]
+// (samples contiguous, Kcap per row).
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restrict__ opvars,
-           int64_t rows, int nkb, int64_t kbcap, uint16_t* __restrict__ ops)
+           int64_t rows, int nkb, uint16_t* __restrict__ ops)
 {
     const int64_t total = rows * nkb;
-    const int64_t part = kbcap * rows * 8;  // elements of one part
+    const int64_t part = rows * Kcap;  // elements of one part
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int kb = (int)(e / rows);
-        const int64_t row = e - (int64_t)kb * rows;
+        const int64_t row = e / nkb;
+        const int kb = (int)(e - row * nkb);
         const uint64_t w = opvars[row];
         const uint32_t vars = (uint32_t)w;
         const int nf = (int)(w >> 32);
@@ -141,21 +143,20 @@ k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restric
                 l[q] = *reinterpret_cast<const uint32_t*>(&lv);
             }
         }
-        const int64_t o = ((int64_t)kb * rows + row) * 8;
+        const int64_t o = row * Kcap + 8 * kb;
         *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 
-// 4-D TMA load: box {8, rows, KC/8, 1} at (0, row, kb, part).
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int row,
-                                            int kb, int part)
+// 3-D TMA load: box {64 samples, rows, 1} at (k, row, part), 128-byte swizzle.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int k,
+                                            int row, int part)
 {
     asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(0), "r"(row), "r"(kb),
-        "r"(part)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(k), "r"(row), "r"(part)
         : "memory");
 }
 
@@ -163,8 +164,9 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
 // the GEMM: one CTA per (item, K-split) unit
 // ---------------------------------------------------------------------------
 template <bool BF16>
-__global__ void __launch_bounds__(GEMM_THREADS, 2)
-k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB32,
+          const __grid_constant__ CUtensorMap mapB64, const __grid_constant__ CUtensorMap mapB128,
           const TcGemmArgs args)
 {
     extern __shared__ unsigned char dsm_raw[];
@@ -202,7 +204,7 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     if (warp == 0 && lane == 0) {
         prefetch_tensormap(&mapA);
-        prefetch_tensormap(&mapB);
+        prefetch_tensormap(item.bbox == 32 ? &mapB32 : item.bbox == 64 ? &mapB64 : &mapB128);
     }
     if (warp == 1) {
         tmem_alloc(&s_tbase, 2 * NMAX);
@@ -222,6 +224,8 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0 && nch > 0) {
+            const CUtensorMap* mapB = item.bbox == 32 ? &mapB32 : item.bbox == 64 ? &mapB64 : &mapB128;
+            const uint32_t bytes = 2u * A_PART + 2u * (uint32_t)item.bbox * 128u;
             int issued = 0;
             for (int q = 0; q < nch; ++q) {
                 const int st = q % STAGES, use = q / STAGES;
@@ -231,14 +235,14 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     break;
                 }
                 if (*(volatile int*)&s_abort) break;
-                const int kb = q < nplus ? (p0 + q) * (KC / 8) : args.minus_kb + (m0 + q - nplus) * (KC / 8);
+                const int k = q < nplus ? (p0 + q) * KC : args.minus_k + (m0 + q - nplus) * KC;
                 unsigned char* sa = dsm + st * STAGE_BYTES;
                 unsigned char* sb = sa + 2 * A_PART;
-                mbar_arrive_expect_tx(&bar_full[st], STAGE_BYTES);
-                tma_load_4d(sa, &mapA, &bar_full[st], item.acol, kb, 0);
-                tma_load_4d(sa + A_PART, &mapA, &bar_full[st], item.acol, kb, 1);
-                tma_load_4d(sb, &mapB, &bar_full[st], item.brow, kb, 0);
-                tma_load_4d(sb + B_PART, &mapB, &bar_full[st], item.brow, kb, 1);
+                mbar_arrive_expect_tx(&bar_full[st], bytes);
+                tma_load_3d(sa, &mapA, &bar_full[st], k, item.acol, 0);
+                tma_load_3d(sa + A_PART, &mapA, &bar_full[st], k, item.acol, 1);
+                tma_load_3d(sb, mapB, &bar_full[st], k, item.brow, 0);
+                tma_load_3d(sb + B_PART, mapB, &bar_full[st], k, item.brow, 1);
                 ++issued;
             }
             // drain: wait until every issued load has landed (bounded)
@@ -265,10 +269,10 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 const uint32_t sb = sa + 2 * A_PART;
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint64_t ah = smem_desc_kmajor(sa + ks * 2 * (TM * 16), TM * 16, 128);
-                    const uint64_t al = smem_desc_kmajor(sa + A_PART + ks * 2 * (TM * 16), TM * 16, 128);
-                    const uint64_t bh = smem_desc_kmajor(sb + ks * 2 * (NMAX * 16), NMAX * 16, 128);
-                    const uint64_t bl = smem_desc_kmajor(sb + B_PART + ks * 2 * (NMAX * 16), NMAX * 16, 128);
+                    const uint64_t ah = smem_desc_sw128(sa + ks * 32);
+                    const uint64_t al = smem_desc_sw128(sa + A_PART + ks * 32);
+                    const uint64_t bh = smem_desc_sw128(sb + ks * 32);
+                    const uint64_t bl = smem_desc_sw128(sb + B_PART + ks * 32);
                     tc_mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
                     tc_mma_f16(d, ah, bl, idesc, 1u);
                     tc_mma_f16(d, al, bh, idesc, 1u);
@@ -334,7 +338,7 @@ inline int grid_for(int64_t work)
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 16384));
 }
 
-cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_kb, cudaStream_t st)
+cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, cudaStream_t st)
 {
     TcGemmArgs a{};
     for (int s = 0; s <= kMaxOrder; ++s) a.ord[s] = plan.ord[s];
@@ -345,27 +349,28 @@ cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_kb,
     a.ksplit = plan.ksplit;
     a.nplus = nplus;
     a.nminus = nminus;
-    a.minus_kb = minus_kb;
+    a.minus_k = minus_k;
     a.status = plan.status;
     const int units = plan.nitems * plan.ksplit;
     if (plan.precision == 1)
-        k_kr_gemm<true><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB, a);
+        k_kr_gemm<true><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
+                                                                plan.mapB[2], a);
     else
-        k_kr_gemm<false><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB, a);
+        k_kr_gemm<false><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
+                                                                 plan.mapB[2], a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
 {
     const int nkb = nsamples / 8;
-    const int64_t kbcap = plan.Kcap / 8;
     const int64_t work = plan.oprows * nkb;
     if (plan.precision == 1)
         k_kr_build<true><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
-                                                         nkb, kbcap, plan.ops);
+                                                         nkb, plan.ops);
     else
         k_kr_build<false><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
-                                                          nkb, kbcap, plan.ops);
+                                                          nkb, plan.ops);
     return cudaGetLastError();
 }
 
@@ -391,20 +396,24 @@ EncodeTiledFn get_encode_fn()
     return fn;
 }
 
-int encode_operand_map(CUtensorMap* map, void* base, int64_t rows, int64_t kbcap, int boxrows)
+// Operand array [part][row][Kcap] (16-bit), boxes of 64 samples x boxrows rows
+// landing in shared memory in the 128-byte-swizzled K-major layout.
+int encode_operand_map(CUtensorMap* map, void* base, int64_t rows, int64_t Kcap, int boxrows)
 {
     EncodeTiledFn enc = get_encode_fn();
     if (enc == nullptr) return (int)cudaErrorNotSupported;
-    const cuuint64_t dims[4] = {8, (cuuint64_t)rows, (cuuint64_t)kbcap, 2};
-    const cuuint64_t strides[3] = {16, (cuuint64_t)rows * 16, (cuuint64_t)rows * kbcap * 16};
-    const cuuint32_t box[4] = {8, (cuuint32_t)boxrows, (cuuint32_t)(KC / 8), 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const cuuint64_t dims[3] = {(cuuint64_t)Kcap, (cuuint64_t)rows, 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kcap * 2, (cuuint64_t)rows * Kcap * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)boxrows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, base, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return (int)cudaErrorInvalidValue;
     return 0;
 }
+
+int b_box_rows(int nrows) { return nrows <= 32 ? 32 : nrows <= 64 ? 64 : 128; }
 
 // Per-K-chunk cost model of one item (cycles): tensor time of 3 MMAs of
 // 128 x N x KC against the operand bytes streamed in, plus a fixed overhead.
@@ -412,8 +421,8 @@ double item_chunk_cost(int nrows)
 {
     const int NB = (nrows + 15) & ~15;
     const double mma = 3.0 * TM * NB * KC / 4096.0;
-    const double tma = (double)STAGE_BYTES / 128.0;
-    return std::max(mma, tma) + 40.0;
+    const double tma = (2.0 * A_PART + 2.0 * 128 * b_box_rows(nrows)) / 128.0;
+    return std::max(mma, tma) + 60.0;
 }
 
 }  // namespace
@@ -516,6 +525,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
                 it.ncols = std::min(TM, ncols - c);
                 it.brow = (int32_t)(loff + R.r0);
                 it.acol = (int32_t)(roff + c);
+                it.bbox = b_box_rows(it.nrows);
                 items.push_back(it);
                 issued += 3.0 * TM * ((it.nrows + 15) & ~15);
             }
@@ -542,20 +552,21 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
 
     // operand array and its tensor maps
     plan.oprows = (int64_t)opvars.size();
-    const int64_t kbcap = plan.Kcap / 8;
     e = alloc(sizeof(uint64_t) * opvars.size(), (void**)&plan.opvars);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.opvars, opvars.data(), sizeof(uint64_t) * opvars.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return (int)e;
-    const size_t opbytes = sizeof(uint16_t) * 2 * (size_t)kbcap * plan.oprows * 8;
+    const size_t opbytes = sizeof(uint16_t) * 2 * (size_t)plan.Kcap * plan.oprows;
     e = alloc(opbytes, (void**)&plan.ops);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemset(plan.ops, 0, opbytes);
     if (e != cudaSuccess) return (int)e;
-    int rc = encode_operand_map(&plan.mapA, plan.ops, plan.oprows, kbcap, TM);
+    int rc = encode_operand_map(&plan.mapA, plan.ops, plan.oprows, plan.Kcap, TM);
     if (rc) return rc;
-    rc = encode_operand_map(&plan.mapB, plan.ops, plan.oprows, kbcap, NMAX);
-    if (rc) return rc;
+    for (int i = 0; i < 3; ++i) {
+        rc = encode_operand_map(&plan.mapB[i], plan.ops, plan.oprows, plan.Kcap, 32 << i);
+        if (rc) return rc;
+    }
 
     // workspace
     plan.wslice = Eoff[d + 1];
@@ -587,7 +598,7 @@ cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, 
 
 cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st)
 {
-    return launch_gemm(plan, plan.P / KC, plan.P / KC, plan.P / 8, st);
+    return launch_gemm(plan, plan.P / KC, plan.P / KC, plan.P, st);
 }
 
 cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const int64_t* head, int q,

@@ -178,6 +178,21 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lb
     return d;                // base offset 0, relative LBO, no swizzle
 }
 
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row x 128-byte
+// atoms (1024 bytes, 1024-aligned) as written by a TMA load with
+// CU_TENSOR_MAP_SWIZZLE_128B; consecutive 8-row groups are 1024 bytes apart.
+// A K-step of k elements inside the 128-byte row advances `saddr` by k*2 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading offset: unused for swizzled K-major
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride offset: 1024 bytes between 8-row groups
+    d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of kind::f16: f32 accumulator, A and B of the same
 // 16-bit type (bf16 when `bf16`, else f16), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16)
