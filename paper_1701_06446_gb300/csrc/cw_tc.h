@@ -79,7 +79,7 @@ struct TcPlan {
     uint64_t* opvars = nullptr;    // per operand row: packed variables | factors << 32
     CUtensorMap mapA{}, mapB[3]{};  // A boxes of 128 rows; B boxes of 32, 64, 128 rows
     TcItem* items = nullptr;
-    int nitems = 0, ksplit = 1;
+    int nitems = 0, ksplit = 1, sm_count = 1;
     TcOrder ord[kMaxOrder + 1]{};
     float* W = nullptr;
     int64_t wslice = 0;

@@ -39,22 +39,24 @@ constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 // staging: shifted samples, transposed to [variable][sample]
 // ---------------------------------------------------------------------------
 // Samples [0, P) of the K axis hold X_(+), [P, 2P) hold X_(-), zero beyond p.
-// The thread of (r, v) also moves X_(+) into the ring slot it reads X_(-) from.
+// Each CTA moves a tile of 32 samples x 32 variables through shared memory so
+// that both the row-major reads and the variable-major writes are coalesced;
+// the thread that reads X_(-) from a ring slot also writes X_(+) into it.
 __global__ void __launch_bounds__(256)
 k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __restrict__ x_out,
                 int64_t ld_out, float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p,
                 int p, int P, int n, int npad, const float* __restrict__ shift, float* __restrict__ XT,
                 int64_t Kcap, int* __restrict__ status)
 {
-    const int64_t total = (int64_t)npad * P;
+    __shared__ float tin[32][33], tout[32][33];
     const int64_t head = *head_p;
+    const int r0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     bool badv = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int v = (int)(e / P);
-        const int r = (int)(e - (int64_t)v * P);
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr, v = v0 + tx;
         float xin = 0.0f, xo = 0.0f;
-        if (r < p) {
+        if (r < p && v < npad) {
             int64_t slot = head + r;
             if (slot >= T) slot -= T;
             const float raw_in = v < n ? x_in[(int64_t)r * ld_in + v] : 0.0f;
@@ -68,8 +70,16 @@ k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __re
                 xo = raw_out - shift[v];
             }
         }
-        XT[(int64_t)v * Kcap + r] = xin;
-        XT[(int64_t)v * Kcap + P + r] = xo;
+        tin[rr][tx] = xin;
+        tout[rr][tx] = xo;
+    }
+    __syncthreads();
+    for (int vv = ty; vv < 32; vv += 8) {
+        const int v = v0 + vv, r = r0 + tx;
+        if (v < npad && r < P) {
+            XT[(int64_t)v * Kcap + r] = tin[tx][vv];
+            XT[(int64_t)v * Kcap + P + r] = tout[tx][vv];
+        }
     }
     if (badv) atomicOr(status, kStatusNonFinite);
 }
@@ -107,12 +117,12 @@ __global__ void __launch_bounds__(256)
 k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restrict__ opvars,
            int64_t rows, int nkb, uint16_t* __restrict__ ops)
 {
-    const int64_t total = rows * nkb;
+    // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
+    const int total = (int)(rows * nkb);
     const int64_t part = rows * Kcap;  // elements of one part
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = e / nkb;
-        const int kb = (int)(e - row * nkb);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int row = e / nkb;
+        const int kb = e - row * nkb;
         const uint64_t w = opvars[row];
         const uint32_t vars = (uint32_t)w;
         const int nf = (int)(w >> 32);
@@ -143,7 +153,7 @@ k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restric
                 l[q] = *reinterpret_cast<const uint32_t*>(&lv);
             }
         }
-        const int64_t o = row * Kcap + 8 * kb;
+        const int64_t o = (int64_t)row * Kcap + 8 * kb;
         *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
@@ -161,8 +171,30 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 }
 
 // ---------------------------------------------------------------------------
-// the GEMM: one CTA per (item, K-split) unit
+// the GEMM: persistent, one CTA per SM looping over (item, K-split) units.
+// Warp 0 streams A/B tiles through the STAGES-deep ring continuously across
+// units; warp 1 issues the MMAs into one of two TMEM accumulator sets
+// (columns [256*ab, 256*ab + 256): D_in then D_out); warps 2-5 drain the
+// other set into the workspace while the next unit's MMAs run.
 // ---------------------------------------------------------------------------
+struct UnitRange {
+    int nplus, nminus, p0, m0;
+};
+
+__device__ __forceinline__ UnitRange unit_range(const TcGemmArgs& args, int split)
+{
+    UnitRange r;
+    const int cps_p = (args.nplus + args.ksplit - 1) / args.ksplit;
+    const int p0 = min(args.nplus, split * cps_p), p1 = min(args.nplus, p0 + cps_p);
+    const int cps_m = (args.nminus + args.ksplit - 1) / args.ksplit;
+    const int m0 = min(args.nminus, split * cps_m), m1 = min(args.nminus, m0 + cps_m);
+    r.nplus = p1 - p0;
+    r.nminus = m1 - m0;
+    r.p0 = p0;
+    r.m0 = m0;
+    return r;
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
 k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB32,
@@ -172,50 +204,39 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     extern __shared__ unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_acc;
+    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_final;
     __shared__ uint32_t s_tbase;
     __shared__ int s_abort;
-    __shared__ int64_t s_rowoff[NMAX], s_coloff[TM];
-    __shared__ int32_t s_rowcolmin[NMAX];
+    __shared__ int64_t s_rowoff[4][NMAX];    // one copy per epilogue warp
+    __shared__ int32_t s_rowcolmin[4][NMAX];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int unit = blockIdx.x;
-    const TcItem item = args.items[unit / args.ksplit];
-    const int split = unit % args.ksplit;
-    const int NB = (item.nrows + 15) & ~15;
-    const TcOrder& od = args.ord[item.s];
-
-    // this split's chunks of the entering and leaving segments
-    const int cps_p = (args.nplus + args.ksplit - 1) / args.ksplit;
-    const int p0 = min(args.nplus, split * cps_p), p1 = min(args.nplus, p0 + cps_p);
-    const int cps_m = (args.nminus + args.ksplit - 1) / args.ksplit;
-    const int m0 = min(args.nminus, split * cps_m), m1 = min(args.nminus, m0 + cps_m);
-    const int nplus = p1 - p0, nminus = m1 - m0;
-    const int nch = nplus + nminus;
+    const int nunits = args.nitems * args.ksplit;
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
             mbar_init(&bar_empty[s], 1);
         }
-        mbar_init(&bar_acc, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_accfull[b], 1);
+            mbar_init(&bar_accempty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&bar_final, 1);
         s_abort = 0;
         fence_mbar_init();
     }
     if (warp == 0 && lane == 0) {
         prefetch_tensormap(&mapA);
-        prefetch_tensormap(item.bbox == 32 ? &mapB32 : item.bbox == 64 ? &mapB64 : &mapB128);
+        prefetch_tensormap(&mapB32);
+        prefetch_tensormap(&mapB64);
+        prefetch_tensormap(&mapB128);
     }
     if (warp == 1) {
-        tmem_alloc(&s_tbase, 2 * NMAX);
+        tmem_alloc(&s_tbase, 512);
         tmem_relinquish();
     }
-    for (int r = tid; r < NMAX; r += GEMM_THREADS) {
-        const bool v = r < item.nrows;
-        s_rowoff[r] = v ? od.rowoff[item.row0 + r] : 0;
-        s_rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
-    }
-    for (int c = tid; c < TM; c += GEMM_THREADS) s_coloff[c] = c < item.ncols ? od.coloff[item.col0 + c] : 0;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -223,99 +244,149 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
-        if (lane == 0 && nch > 0) {
-            const CUtensorMap* mapB = item.bbox == 32 ? &mapB32 : item.bbox == 64 ? &mapB64 : &mapB128;
-            const uint32_t bytes = 2u * A_PART + 2u * (uint32_t)item.bbox * 128u;
-            int issued = 0;
-            for (int q = 0; q < nch; ++q) {
-                const int st = q % STAGES, use = q / STAGES;
-                if (q >= STAGES && !mbar_wait(&bar_empty[st], (use - 1) & 1, kWaitLimit)) {
-                    atomicOr(args.status, kStatusTimeout);
-                    s_abort = 1;
-                    break;
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool stop = false;
+            for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
+                const TcItem item = args.items[u / args.ksplit];
+                const UnitRange R = unit_range(args, u % args.ksplit);
+                const CUtensorMap* mapB = item.bbox == 32 ? &mapB32 : item.bbox == 64 ? &mapB64 : &mapB128;
+                const uint32_t bytes = 2u * A_PART + 2u * (uint32_t)item.bbox * 128u;
+                const int nch = R.nplus + R.nminus;
+                for (int q = 0; q < nch; ++q, ++g) {
+                    const uint32_t st = g % STAGES, use = g / STAGES;
+                    if (g >= STAGES && !mbar_wait(&bar_empty[st], (use - 1) & 1, kWaitLimit)) {
+                        atomicOr(args.status, kStatusTimeout);
+                        s_abort = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (*(volatile int*)&s_abort) {
+                        stop = true;
+                        break;
+                    }
+                    const int k = q < R.nplus ? (R.p0 + q) * KC : args.minus_k + (R.m0 + q - R.nplus) * KC;
+                    unsigned char* sa = dsm + st * STAGE_BYTES;
+                    unsigned char* sb = sa + 2 * A_PART;
+                    mbar_arrive_expect_tx(&bar_full[st], bytes);
+                    tma_load_3d(sa, &mapA, &bar_full[st], k, item.acol, 0);
+                    tma_load_3d(sa + A_PART, &mapA, &bar_full[st], k, item.acol, 1);
+                    tma_load_3d(sb, mapB, &bar_full[st], k, item.brow, 0);
+                    tma_load_3d(sb + B_PART, mapB, &bar_full[st], k, item.brow, 1);
                 }
-                if (*(volatile int*)&s_abort) break;
-                const int k = q < nplus ? (p0 + q) * KC : args.minus_k + (m0 + q - nplus) * KC;
-                unsigned char* sa = dsm + st * STAGE_BYTES;
-                unsigned char* sb = sa + 2 * A_PART;
-                mbar_arrive_expect_tx(&bar_full[st], bytes);
-                tma_load_3d(sa, &mapA, &bar_full[st], k, item.acol, 0);
-                tma_load_3d(sa + A_PART, &mapA, &bar_full[st], k, item.acol, 1);
-                tma_load_3d(sb, mapB, &bar_full[st], k, item.brow, 0);
-                tma_load_3d(sb + B_PART, mapB, &bar_full[st], k, item.brow, 1);
-                ++issued;
             }
-            // drain: wait until every issued load has landed (bounded)
-            for (int q = max(0, issued - STAGES); q < issued; ++q)
+            // drain: every issued load has landed before the CTA may exit (bounded)
+            for (uint32_t q = g > STAGES ? g - STAGES : 0; q < g; ++q)
                 mbar_wait(&bar_full[q % STAGES], (q / STAGES) & 1, kWaitLimit);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
-        if (lane == 0 && nch > 0) {
-            const uint32_t idesc = idesc_f16(TM, NB, BF16);
-            int q = 0;
-            for (; q < nch; ++q) {
-                const int st = q % STAGES, use = q / STAGES;
-                if (!mbar_wait(&bar_full[st], use & 1, kWaitLimit)) {
+        if (lane == 0) {
+            uint32_t g = 0, it = 0;
+            bool stop = false;
+            for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x, ++it) {
+                const TcItem item = args.items[u / args.ksplit];
+                const UnitRange R = unit_range(args, u % args.ksplit);
+                const int nch = R.nplus + R.nminus;
+                const uint32_t ab = it & 1, ause = it >> 1;
+                if (it >= 2 && !mbar_wait(&bar_accempty[ab], (ause - 1) & 1, kWaitLimit)) {
                     atomicOr(args.status, kStatusTimeout);
                     s_abort = 1;
                     break;
                 }
                 tc_fence_after();
-                const bool plus = q < nplus;
-                const bool first = (q == 0) || (q == nplus);
-                const uint32_t d = tbase + (plus ? 0u : (uint32_t)NMAX);
-                const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
-                const uint32_t sb = sa + 2 * A_PART;
+                const uint32_t idesc = idesc_f16(TM, (item.nrows + 15) & ~15, BF16);
+                for (int q = 0; q < nch; ++q, ++g) {
+                    const uint32_t st = g % STAGES, use = g / STAGES;
+                    if (!mbar_wait(&bar_full[st], use & 1, kWaitLimit)) {
+                        atomicOr(args.status, kStatusTimeout);
+                        s_abort = 1;
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const bool plus = q < R.nplus;
+                    const bool first = (q == 0) || (q == R.nplus);
+                    const uint32_t d = tbase + ab * 256u + (plus ? 0u : (uint32_t)NMAX);
+                    const uint32_t sa = smem_u32(dsm + st * STAGE_BYTES);
+                    const uint32_t sb = sa + 2 * A_PART;
 #pragma unroll
-                for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint64_t ah = smem_desc_sw128(sa + ks * 32);
-                    const uint64_t al = smem_desc_sw128(sa + A_PART + ks * 32);
-                    const uint64_t bh = smem_desc_sw128(sb + ks * 32);
-                    const uint64_t bl = smem_desc_sw128(sb + B_PART + ks * 32);
-                    tc_mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
-                    tc_mma_f16(d, ah, bl, idesc, 1u);
-                    tc_mma_f16(d, al, bh, idesc, 1u);
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint64_t ah = smem_desc_sw128(sa + ks * 32);
+                        const uint64_t al = smem_desc_sw128(sa + A_PART + ks * 32);
+                        const uint64_t bh = smem_desc_sw128(sb + ks * 32);
+                        const uint64_t bl = smem_desc_sw128(sb + B_PART + ks * 32);
+                        tc_mma_f16(d, ah, bh, idesc, (first && ks == 0) ? 0u : 1u);
+                        tc_mma_f16(d, ah, bl, idesc, 1u);
+                        tc_mma_f16(d, al, bh, idesc, 1u);
+                    }
+                    tc_commit(&bar_empty[st]);
                 }
-                tc_commit(&bar_empty[st]);
+                tc_commit(&bar_accfull[ab]);
             }
-            tc_commit(&bar_acc);
+            // every MMA issued by this CTA has completed before TMEM is freed (bounded)
+            tc_commit(&bar_final);
+            mbar_wait(&bar_final, 0, kWaitLimit);
         }
     } else {
         // ---------------- epilogue: TMEM -> FP32 workspace ----------------
-        const bool ok = nch == 0 ? true : mbar_wait(&bar_acc, 0, kWaitLimit);
-        if (!ok) {
-            if (lane == 0) atomicOr(args.status, kStatusTimeout);
-        } else if (!*(volatile int*)&s_abort) {
+        const int ew = warp - 2;  // 0..3
+        const int quarter = warp & 3;
+        uint32_t it = 0;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++it) {
+            const TcItem item = args.items[u / args.ksplit];
+            const int split = u % args.ksplit;
+            const UnitRange R = unit_range(args, split);
+            const TcOrder& od = args.ord[item.s];
+            const uint32_t ab = it & 1;
+            // this warp's copy of the item's row tables
+            int64_t* rowoff = s_rowoff[ew];
+            int32_t* rowcolmin = s_rowcolmin[ew];
+            __syncwarp();
+            for (int r = lane; r < NMAX; r += 32) {
+                const bool v = r < item.nrows;
+                rowoff[r] = v ? od.rowoff[item.row0 + r] : 0;
+                rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
+            }
+            __syncwarp();
+            const bool ok = mbar_wait(&bar_accfull[ab], (it >> 1) & 1, kWaitLimit);
+            if (!ok || *(volatile int*)&s_abort) {
+                if (!ok && lane == 0) atomicOr(args.status, kStatusTimeout);
+                s_abort = 1;
+                break;
+            }
             tc_fence_after();
-            const int quarter = warp & 3;
             const int i = 32 * quarter + lane;
             const bool ivalid = i < item.ncols;
             const int cglob = item.col0 + i;
-            const int64_t co = s_coloff[i];
+            const int64_t co = ivalid ? od.coloff[cglob] : 0;
             float* Win = args.W + (int64_t)(2 * split) * args.wslice + od.woff;
             float* Wout = Win + args.wslice;
+            const int NB = (item.nrows + 15) & ~15;
             for (int jb = 0; jb < NB; jb += 16) {
                 uint32_t d0[16], d1[16];
-                const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
-                if (nplus > 0) tmem_ld16(ta, d0);
-                if (nminus > 0) tmem_ld16(ta + (uint32_t)NMAX, d1);
+                const uint32_t ta = tbase + ab * 256u + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
+                if (R.nplus > 0) tmem_ld16(ta, d0);
+                if (R.nminus > 0) tmem_ld16(ta + (uint32_t)NMAX, d1);
                 tmem_ld_wait();
 #pragma unroll
                 for (int t = 0; t < 16; ++t) {
                     const int r = jb + t;
-                    if (ivalid && r < item.nrows && cglob >= s_rowcolmin[r]) {
-                        const int64_t e = s_rowoff[r] + co;
-                        Win[e] = nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
-                        if (args.nminus > 0) Wout[e] = nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
+                    if (ivalid && r < item.nrows && cglob >= rowcolmin[r]) {
+                        const int64_t e = rowoff[r] + co;
+                        Win[e] = R.nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
+                        if (args.nminus > 0) Wout[e] = R.nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_accempty[ab]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tbase, 2 * NMAX);
+    if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
 // S_s[e] += (double)(sum_k W[k][0][e]) for every order (window batches).
@@ -352,11 +423,12 @@ cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, 
     a.minus_k = minus_k;
     a.status = plan.status;
     const int units = plan.nitems * plan.ksplit;
+    const int grid = units < plan.sm_count ? units : plan.sm_count;
     if (plan.precision == 1)
-        k_kr_gemm<true><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
+        k_kr_gemm<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
                                                                 plan.mapB[2], a);
     else
-        k_kr_gemm<false><<<units, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
+        k_kr_gemm<false><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
                                                                  plan.mapB[2], a);
     return cudaGetLastError();
 }
@@ -442,6 +514,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
     plan.nbatch = (int)((T + p - 1) / p);
     plan.Kcap = 2 * (int64_t)plan.P;
     plan.status = status;
+    plan.sm_count = sm_count;
 
     cudaError_t e = alloc(sizeof(float) * (size_t)npad * plan.Kcap, (void**)&plan.XT);
     if (e != cudaSuccess) return (int)e;
@@ -538,11 +611,11 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
     plan.useful_macs_per_sample = useful;
     plan.issued_macs_per_sample = issued;
     plan.nitems = (int)items.size();
-    // K-splits: about two waves of two CTAs per SM, at least 4 chunks per split
+    // K-splits: a few units per persistent CTA, at least 2 chunks per split
     const int chunks = plan.P / KC;
-    const int target = 4 * sm_count;
+    const int target = 3 * sm_count;
     int ks = (target + plan.nitems - 1) / std::max(1, plan.nitems);
-    ks = std::max(1, std::min(ks, std::max(1, chunks / 4)));
+    ks = std::max(1, std::min(ks, std::max(1, chunks / 2)));
     plan.ksplit = ks;
 
     e = alloc(sizeof(TcItem) * std::max<size_t>(items.size(), 1), (void**)&plan.items);
@@ -552,6 +625,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
 
     // operand array and its tensor maps
     plan.oprows = (int64_t)opvars.size();
+    if (plan.oprows * (plan.Kcap / 8) >= ((int64_t)1 << 31)) return (int)cudaErrorInvalidValue;
     e = alloc(sizeof(uint64_t) * opvars.size(), (void**)&plan.opvars);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.opvars, opvars.data(), sizeof(uint64_t) * opvars.size(), cudaMemcpyHostToDevice);
@@ -588,9 +662,9 @@ cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, 
                           const float* shift, cudaStream_t st)
 {
     if (p > plan.p) return cudaErrorInvalidValue;
-    k_tc_stage_push<<<grid_for((int64_t)plan.npad * plan.P), 256, 0, st>>>(
-        x_in, ld_in, x_out, ld_out, ring, plan.T, head, p, plan.P, n, plan.npad, shift, plan.XT,
-        plan.Kcap, plan.status);
+    const dim3 grid((plan.P + 31) / 32, (plan.npad + 31) / 32);
+    k_tc_stage_push<<<grid, 256, 0, st>>>(x_in, ld_in, x_out, ld_out, ring, plan.T, head, p, plan.P, n,
+                                          plan.npad, shift, plan.XT, plan.Kcap, plan.status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_build(plan, 2 * plan.P, st);
