@@ -162,8 +162,11 @@ int cumwin_window(cumwin_t h, float* out_dev);
  * Gradient of L = sum_{s=1..d} w[s] ||C_s||_F^2 (w has d+1 entries, w[0]
  * ignored; full-tensor norms, i.e. each stored block weighted by its
  * multiplicity d!/prod r_l! of Algorithm 5) with respect to the current
- * window, oldest sample first, into dX_dev (T x n FP32, ld = n).  Requires
- * d <= 4.  Not in the paper: it is the adjoint of Algorithms 2-4.
+ * window, oldest sample first, into dX_dev (T x n FP32, ld = n).  Not in the
+ * paper: it is the adjoint of Algorithms 2-4.  The reverse recursion keeps
+ * full n^s tensors in FP64 (allocated by the first call; n^d must be at most
+ * 2^27, else ENOTSUP); the final contraction with the window runs in FP32.
+ * Asynchronous on the handle's stream; w_host is read before returning.
  */
 int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev);
 

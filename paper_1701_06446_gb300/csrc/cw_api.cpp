@@ -66,6 +66,23 @@ struct cumwin_s {
     int32_t* part_off = nullptr;
     double* fro2 = nullptr;
 
+    // adjoint workspace (allocated by the first cumwin_grad)
+    struct Grad {
+        bool ready = false;
+        double* Cf[kMaxOrder + 1] = {};   // full C_s (order 1 about the shift)
+        double* C1true = nullptr;         // full C_1 + shift
+        double* Mf[kMaxOrder + 1] = {};   // full M_s, s < d
+        double* G[kMaxOrder + 1] = {};    // adjoint of C_s
+        double* GM[kMaxOrder + 1] = {};   // adjoint of M_s
+        int64_t nf[kMaxOrder + 1] = {};   // n^s
+        int64_t* nst = nullptr;
+        uint32_t* uvars = nullptr;        // sorted (s-1)-tuples of all orders, concatenated
+        float* umult = nullptr;
+        uint8_t* unf = nullptr;
+        int uoff[kMaxOrder + 2] = {};
+        float* Gc = nullptr;              // [nu][n]
+    } grad;
+
     // kernel timing (cumwin_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev;  // 4 per timed shift: start, staged, updated, recovered
@@ -639,7 +656,87 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
 {
     if (h == nullptr || w_host == nullptr || dX_dev == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
-    return CUMWIN_ENOTSUP;
+    const int n = h->n, d = h->d;
+    auto& g = h->grad;
+    if (!g.ready) {
+        int64_t f = 1;
+        for (int s = 1; s <= d; ++s) {
+            f *= n;
+            g.nf[s] = f;
+        }
+        if (g.nf[d] > ((int64_t)1 << 27)) {
+            g_last_error = "the adjoint keeps full n^d tensors; n^d must be at most 2^27";
+            return CUMWIN_ENOTSUP;
+        }
+        for (int s = 1; s <= d; ++s) {
+            CW_TRY(h->alloc(&g.Cf[s], g.nf[s]));
+            CW_TRY(h->alloc(&g.G[s], g.nf[s]));
+            CW_TRY(h->alloc(&g.GM[s], g.nf[s]));
+            if (s < d) CW_TRY(h->alloc(&g.Mf[s], g.nf[s]));
+        }
+        CW_TRY(h->alloc(&g.C1true, n));
+        std::vector<int64_t> nst((size_t)(h->nbar + 1) * (kMaxOrder + 1));
+        for (int v = 0; v <= h->nbar; ++v)
+            for (int r = 0; r <= kMaxOrder; ++r) nst[v * (kMaxOrder + 1) + r] = n_sorted(h->nbar - v, r);
+        CW_TRY(h->upload(&g.nst, nst));
+        // sorted (s-1)-tuples of variables with their numbers of distinct orderings
+        std::vector<uint32_t> uv;
+        std::vector<float> um;
+        std::vector<uint8_t> unf;
+        for (int s = 1; s <= d; ++s) {
+            g.uoff[s] = (int)uv.size();
+            const int k = s - 1;
+            if (k == 0) {
+                uv.push_back(0u);
+                um.push_back(1.0f);
+                unf.push_back(0);
+                continue;
+            }
+            const std::vector<int> tup = enumerate_sorted(n, k);
+            for (size_t q = 0; q < tup.size() / k; ++q) {
+                uint32_t p = 0;
+                for (int i = 0; i < k; ++i) p |= (uint32_t)tup[q * k + i] << (8 * i);
+                uv.push_back(p);
+                um.push_back((float)block_multiplicity(&tup[q * k], k));
+                unf.push_back((uint8_t)k);
+            }
+        }
+        g.uoff[d + 1] = (int)uv.size();
+        CW_TRY(h->upload(&g.uvars, uv));
+        CW_TRY(h->upload(&g.umult, um));
+        CW_TRY(h->upload(&g.unf, unf));
+        CW_TRY(h->alloc(&g.Gc, (size_t)uv.size() * n));
+        g.ready = true;
+    }
+    const double invT = 1.0 / (double)h->T;
+    cudaStream_t st = h->stream;
+    // full tensors of the current window
+    for (int s = 1; s <= d; ++s) {
+        CW_TRY(launch_expand(h->C[s], g.nf[s], s, n, h->b, g.nst, 1.0, nullptr, g.Cf[s], st));
+        if (s < d) CW_TRY(launch_expand(h->S[s], g.nf[s], s, n, h->b, g.nst, invT, nullptr, g.Mf[s], st));
+        CW_TRY(cudaMemsetAsync(g.G[s], 0, sizeof(double) * g.nf[s], st));
+        CW_TRY(cudaMemsetAsync(g.GM[s], 0, sizeof(double) * g.nf[s], st));
+    }
+    CW_TRY(launch_expand(h->C[1], n, 1, n, h->b, g.nst, 1.0, h->shift, g.C1true, st));
+    // reverse of the subset recursion, highest order first
+    for (int s = d; s >= 2; --s) {
+        CW_TRY(launch_seed(g.Cf[s], 2.0 * w_host[s], g.nf[s], g.G[s], g.GM[s], st));
+        for (int k = 1; k < s; ++k) {
+            const int r = s - k;
+            const double coef = (double)binom(s - 1, k - 1);
+            CW_TRY(launch_contract(g.G[s], g.Mf[r], g.nf[k], g.nf[r], -coef, g.G[k], st));
+            CW_TRY(launch_contract(g.G[s], g.Cf[k], g.nf[r], g.nf[k], -coef, g.GM[r], st));
+        }
+    }
+    CW_TRY(launch_seed(g.C1true, 2.0 * w_host[1], n, g.G[1], g.GM[1], st));
+    // dL/dX = sum_s (s/T) sum_u mult(u) GM_s[a, u] prod y_{t,u}
+    for (int s = 1; s <= d; ++s)
+        CW_TRY(launch_compact(g.GM[s], s, n, g.uvars + g.uoff[s], g.umult + g.uoff[s],
+                              g.uoff[s + 1] - g.uoff[s], (double)s * invT,
+                              g.Gc + (size_t)g.uoff[s] * n, st));
+    CW_TRY(launch_grad_x(h->ring, h->T, h->head, n, h->npad, h->shift, g.uvars, g.unf, g.uoff[d + 1], g.Gc,
+                         dX_dev, st));
+    return CUMWIN_OK;
 }
 
 int cumwin_set_timing(cumwin_t h, int enable)

@@ -71,6 +71,20 @@ struct CumArgs {
     int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = fold it in
 };
 
+// Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
+// trailing indices, seeding, compaction over sorted tuples, and dL/dX.
+cudaError_t launch_expand(const double* blk, int64_t nfull, int s, int n, int b, const int64_t* nst,
+                          double scale, const float* add1, double* full, cudaStream_t st);
+cudaError_t launch_contract(const double* G, const double* V, int64_t nx, int64_t ny, double alpha,
+                            double* out, cudaStream_t st);
+cudaError_t launch_seed(const double* C, double two_w, int64_t nfull, double* G, double* GM,
+                        cudaStream_t st);
+cudaError_t launch_compact(const double* GM, int s, int n, const uint32_t* uvars, const float* umult,
+                           int nu, double coef, float* Gc, cudaStream_t st);
+cudaError_t launch_grad_x(const float* ring, int64_t T, const int64_t* head, int n, int npad,
+                          const float* shift, const uint32_t* uvars, const uint8_t* unf, int nu,
+                          const float* Gc, float* dX, cudaStream_t st);
+
 // Message returned by cumwin_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 
