@@ -184,6 +184,60 @@ int cumwin_set_timing(cumwin_t h, int enable);
 int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* cumulant_ms,
                       int64_t* shifts, int64_t* launches);
 
+/*
+ * Autotune the tensor-core update of this handle (mixed forms): time `reps`
+ * launches of the update GEMM for each candidate split of the samples over
+ * CTAs (1, 2, 4, ... up to a workspace limit) on the data of the last shift,
+ * keep the fastest, and report it in *ksplit_out (0 in the FP64 form).  When
+ * the environment variable CUMWIN_TUNE_CACHE names a file, the choice is
+ * appended to it and later handles of the same problem on the same device
+ * start from it.  Requires a prior fill; synchronises.
+ */
+int cumwin_tune(cumwin_t h, int reps, int* ksplit_out);
+
+/*
+ * Batches: many independent windows (streams) of uneven n and d, with a
+ * common block size b, shift size p and precision (mixed forms only), advanced
+ * together: every phase of a shift (staging, operand build, the tensor-core
+ * update, the recovery of each order, the norms) is one launch for all
+ * windows, so a shift costs the same number of launches for 1 or 1000
+ * windows and can be captured into one CUDA graph.
+ */
+typedef struct cumwin_batch_s* cumwin_batch_t;
+
+/* Create a batch of nwin windows: window i has n[i] variables, orders 1..d[i],
+ * window length T[i].  Errors as for cumwin_create; ENOTSUP for CUMWIN_FP64. */
+int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, int b, int p, int precision,
+                        void* cuda_stream, cumwin_batch_t* out);
+int cumwin_batch_destroy(cumwin_batch_t B);
+
+/* First windows: X_dev[i] (a host array of nwin device pointers) holds T[i] x n[i]
+ * samples of window i, row-major with row stride n[i]. */
+int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev);
+
+/* Element offset of window i's rows in the packed push buffer (i in [0, nwin];
+ * offset(nwin) is the buffer length), -1 on a bad argument. */
+int64_t cumwin_batch_offset(cumwin_batch_t B, int window);
+
+/* One shift of every window: x_dev holds, at cumwin_batch_offset(B, i), the p
+ * new rows of window i (p x n[i], row-major, row stride n[i]).  Asynchronous;
+ * allocates nothing (capturable into a CUDA graph). */
+int cumwin_batch_push(cumwin_batch_t B, const float* x_dev);
+
+/* C_s of window i (block layout, as cumwin_cumulants). */
+int cumwin_batch_cumulants(cumwin_batch_t B, int window, int order, double* out_dev);
+
+/* Norms of all windows: fro_host and nu_host are nwin x dmax (dmax = the
+ * largest d), row i for window i, NaN beyond d[i] (and for nu below order 3).
+ * Synchronises; returns ENONFINITE / ETIMEOUT if any window saw one. */
+int cumwin_batch_norms(cumwin_batch_t B, double* fro_host, double* nu_host);
+
+/* Autotune the batch's update GEMM (as cumwin_tune). */
+int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out);
+
+/* Sticky device status over all windows (synchronises). */
+int cumwin_batch_status(cumwin_batch_t B);
+
 /* Sticky device status of the handle (CUMWIN_OK or ENONFINITE / ETIMEOUT).
  * Synchronises the handle's stream.  Reading it clears nothing. */
 int cumwin_status(cumwin_t h);

@@ -20,7 +20,7 @@ import torch
 from . import _lib
 from ._lib import CumwinError, check
 
-__all__ = ["CumWin", "CumwinError", "CumulantNormLoss", "layout_size", "block_rank",
+__all__ = ["CumWin", "CumWinBatch", "CumwinError", "CumulantNormLoss", "layout_size", "block_rank",
            "element_index", "selftest_tables", "library_path"]
 
 
@@ -205,9 +205,109 @@ class CumWin:
         return {"stage_ms": a.value, "update_ms": u.value, "cumulant_ms": c.value,
                 "shifts": k.value, "launches": L.value}
 
+    def tune(self, reps: int = 5) -> int:
+        """Autotune the tensor-core update (K-split) on the last shift's data."""
+        ks = ctypes.c_int()
+        self._sync_stream()
+        check(self.lib.cumwin_tune(self._h, reps, ctypes.byref(ks)), "cumwin_tune")
+        return ks.value
+
     def status(self) -> int:
         self._sync_stream()
         return int(self.lib.cumwin_status(self._h))
+
+
+class CumWinBatch:
+    """Many independent windows (uneven n, d, T; shared b, p, precision) advanced together."""
+
+    def __init__(self, ns, ds, Ts, b: int, p: int, precision: str = "bf16", device=None):
+        self.lib = _lib.load()
+        if precision not in _lib.PRECISION:
+            raise ValueError(f"precision must be one of {list(_lib.PRECISION)}")
+        self.ns, self.ds, self.Ts = list(map(int, ns)), list(map(int, ds)), list(map(int, Ts))
+        if not (len(self.ns) == len(self.ds) == len(self.Ts)) or not self.ns:
+            raise ValueError("ns, ds and Ts must be non-empty and of equal length")
+        self.nwin, self.b, self.p = len(self.ns), b, p
+        self.dmax = max(self.ds)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self._h = ctypes.c_void_p()
+        na = (ctypes.c_int * self.nwin)(*self.ns)
+        da = (ctypes.c_int * self.nwin)(*self.ds)
+        ta = (ctypes.c_int64 * self.nwin)(*self.Ts)
+        with torch.cuda.device(self.device):
+            self._stream = torch.cuda.current_stream(self.device).cuda_stream
+            check(self.lib.cumwin_batch_create(self.nwin, na, da, ta, b, p, _lib.PRECISION[precision],
+                                               ctypes.c_void_p(self._stream), ctypes.byref(self._h)),
+                  "cumwin_batch_create")
+        self.offsets = [int(self.lib.cumwin_batch_offset(self._h, i)) for i in range(self.nwin + 1)]
+
+    def close(self):
+        if self._h:
+            self.lib.cumwin_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check_stream(self):
+        if torch.cuda.current_stream(self.device).cuda_stream != self._stream:
+            raise RuntimeError("a batch issues its work on the stream current at creation")
+
+    def fill(self, Xs):
+        if len(Xs) != self.nwin:
+            raise ValueError("one first window per stream")
+        ptrs = []
+        for X, n, T in zip(Xs, self.ns, self.Ts):
+            if X.shape != (T, n) or not X.is_contiguous():
+                raise ValueError("window i must be a contiguous (T_i, n_i) float32 tensor")
+            ptrs.append(_dev_ptr(X, torch.float32, "X"))
+        self._check_stream()
+        arr = (ctypes.c_void_p * self.nwin)(*ptrs)
+        check(self.lib.cumwin_batch_fill(self._h, arr), "cumwin_batch_fill")
+
+    def pack(self, rows) -> torch.Tensor:
+        """Concatenate the p new rows of every window into the packed push layout."""
+        return torch.cat([r.reshape(-1) for r in rows]).contiguous()
+
+    def push(self, x_packed: torch.Tensor):
+        if x_packed.dim() != 1 or x_packed.numel() < self.offsets[-1]:
+            raise ValueError("push expects the packed rows of all windows")
+        self._check_stream()
+        check(self.lib.cumwin_batch_push(self._h, _dev_ptr(x_packed, torch.float32, "x")),
+              "cumwin_batch_push")
+
+    def cumulants(self, window: int, order: int) -> torch.Tensor:
+        if not 0 <= window < self.nwin or not 1 <= order <= self.ds[window]:
+            raise ValueError("bad window or order")
+        out = torch.empty(layout_size(self.ns[window], self.b, order), dtype=torch.float64,
+                          device=self.device)
+        check(self.lib.cumwin_batch_cumulants(self._h, window, order, out.data_ptr()),
+              "cumwin_batch_cumulants")
+        return out
+
+    def norms(self):
+        fro = np.zeros((self.nwin, self.dmax))
+        nu = np.zeros((self.nwin, self.dmax))
+        check(self.lib.cumwin_batch_norms(self._h, fro.ctypes.data, nu.ctypes.data), "cumwin_batch_norms")
+        return fro, nu
+
+    def tune(self, reps: int = 5) -> int:
+        ks = ctypes.c_int()
+        check(self.lib.cumwin_batch_tune(self._h, reps, ctypes.byref(ks)), "cumwin_batch_tune")
+        return ks.value
+
+    def status(self) -> int:
+        return int(self.lib.cumwin_batch_status(self._h))
 
 
 class CumulantNormLoss(torch.autograd.Function):

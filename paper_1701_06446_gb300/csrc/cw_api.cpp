@@ -1,10 +1,16 @@
-// C ABI of the sliding-window cumulant library: handle state, table upload,
-// and the sequence of kernels of one window shift (Algorithm 1).
+// C ABI of the sliding-window cumulant library: window state, table upload,
+// the sequence of kernels of one window shift (Algorithm 1), batches of
+// independent windows, and the K-split autotuner.
 #include "../../include/cumwin.h"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -24,11 +30,46 @@ int fail_cuda(cudaError_t e, const char* what)
     return e == cudaErrorMemoryAllocation ? CUMWIN_ENOMEM : CUMWIN_ECUDA;
 }
 
-#define CW_TRY(expr)                                    \
-    do {                                                \
-        cudaError_t _e = (expr);                        \
+#define CW_TRY(expr)                                        \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
         if (_e != cudaSuccess) return fail_cuda(_e, #expr); \
     } while (0)
+
+// Device allocations of one object, freed together.
+struct Arena {
+    std::vector<void*> ptrs;
+    template <class T>
+    cudaError_t alloc(T** p, size_t count)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(q);
+        *p = (T*)q;
+        return cudaSuccess;
+    }
+    template <class T>
+    cudaError_t upload(T** p, const std::vector<T>& v)
+    {
+        cudaError_t e = alloc(p, v.size());
+        if (e != cudaSuccess) return e;
+        if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return e;
+    }
+    template <class T>
+    cudaError_t upload(T** p, const T* v, size_t count)
+    {
+        cudaError_t e = alloc(p, count);
+        if (e != cudaSuccess) return e;
+        return cudaMemcpy(*p, v, count * sizeof(T), cudaMemcpyHostToDevice);
+    }
+    void release()
+    {
+        for (void* q : ptrs) cudaFree(q);
+        ptrs.clear();
+    }
+};
 
 }  // namespace
 
@@ -42,29 +83,36 @@ struct cumwin_s {
     int device = 0, sm_count = 0;
     int64_t* head = nullptr;  // device: ring slot of the oldest sample
     bool filled = false;
-    std::vector<void*> allocs;
+    Arena mem;
 
-    float* ring = nullptr;      // [T][npad] raw samples
-    float* stage = nullptr;     // [2T][npad] X_(+) then X_(-)
-    float* hin = nullptr;       // [T][npad] device copy of host X_(+)
-    float* shift = nullptr;     // [npad]
-    float* shift_zero = nullptr;
+    float* ring = nullptr;   // [T][npad] raw samples
+    float* stage = nullptr;  // [2T][npad] X_(+) then X_(-) (FP64 form)
+    float* hin = nullptr;    // [T][npad] device copy of host X_(+)
+    float* shift = nullptr;  // [npad]
     int* status = nullptr;
     double* S[kMaxOrder + 1] = {};
     double* C[kMaxOrder + 1] = {};
     int64_t E[kMaxOrder + 1] = {};
     int64_t Eoff[kMaxOrder + 2] = {};  // offsets of the orders in one concatenated index space
 
+    // update tables (FP64 form tiles; tensor-core plan of this window or of its batch)
+    std::vector<UpdateTables> ut;
     UpdateArgs upd{};
     UpdTile* tiles = nullptr;
     int ntiles = 0;
-    TcPlan tc{};  // tensor-core update plan (mixed forms)
+    TcPlan tc_own{};
+    TcPlan* tc = nullptr;
 
+    // recovery: host arguments per order, device copies [2][order] (accumulate off / on)
     CumArgs cum[kMaxOrder + 1]{};
+    CumArgs* cum_dev = nullptr;
     CumLaunch cum_launch[kMaxOrder + 1] = {};
+    int parts = 0;  // norm partial slots per order
     double* normpart = nullptr;
-    int32_t* part_off = nullptr;
     double* fro2 = nullptr;
+    NormArgs* norm_dev = nullptr;
+    TcAccSeg* segs = nullptr;  // workspace segments of this window's orders (own plan)
+    int nsegs = 0;
 
     // adjoint workspace (allocated by the first cumwin_grad)
     struct Grad {
@@ -89,27 +137,12 @@ struct cumwin_s {
     int64_t timed = 0, launches = 0;
 
     template <class T>
-    cudaError_t alloc(T** p, size_t count)
-    {
-        void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-        if (e != cudaSuccess) return e;
-        allocs.push_back(q);
-        *p = (T*)q;
-        return cudaSuccess;
-    }
+    cudaError_t alloc(T** p, size_t count) { return mem.alloc(p, count); }
     template <class T>
-    cudaError_t upload(T** p, const std::vector<T>& v)
-    {
-        cudaError_t e = alloc(p, v.size());
-        if (e != cudaSuccess) return e;
-        if (!v.empty()) e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
-        return e;
-    }
+    cudaError_t upload(T** p, const std::vector<T>& v) { return mem.upload(p, v); }
     void release()
     {
-        for (void* q : allocs) cudaFree(q);
-        allocs.clear();
+        mem.release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         ev.clear();
     }
@@ -123,22 +156,272 @@ struct cumwin_s {
     }
 };
 
+struct cumwin_batch_s {
+    int nwin = 0, b = 0, p = 0, prec = 0, dmax = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    bool filled = false;
+    std::vector<cumwin_s*> wins;
+    std::vector<int64_t> xoff;  // packed push buffer offsets, [nwin + 1]
+    Arena mem;
+    TcPlan tc{};
+    int* status = nullptr;
+    CumArgs* cum_dev = nullptr;  // [2][kMaxOrder + 1][nwin]
+    CumLaunch cum_launch[kMaxOrder + 1] = {};
+    NormArgs* norm_dev = nullptr;
+    double* fro2 = nullptr;      // [nwin][dmax]
+    TcAccSeg* segs = nullptr;
+    int nsegs = 0;
+};
+
 namespace {
+
+// ---------------------------------------------------------------------------
+// tuning cache: one line per problem signature, "signature ksplit"
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+
+std::string tune_cache_path()
+{
+    const char* p = std::getenv("CUMWIN_TUNE_CACHE");
+    return p ? std::string(p) : std::string();
+}
+
+int tune_cache_get(const std::string& sig)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return 0;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::ifstream f(path);
+    std::string line;
+    int found = 0;
+    while (std::getline(f, line)) {
+        const size_t sp = line.rfind(' ');
+        if (sp != std::string::npos && line.substr(0, sp) == sig) found = std::atoi(line.c_str() + sp + 1);
+    }
+    return found;
+}
+
+void tune_cache_put(const std::string& sig, int ks)
+{
+    const std::string path = tune_cache_path();
+    if (path.empty()) return;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::ofstream f(path, std::ios::app);
+    f << sig << ' ' << ks << '\n';
+}
+
+std::string plan_signature(const TcPlan& tc, const std::vector<cumwin_s*>& wins, int device)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, device);
+    std::ostringstream o;
+    o << "cumwin1|" << prop.name << "|prec" << tc.precision << "|p" << tc.p << "|items" << tc.nitems << "|w";
+    uint64_t hsh = 1469598103934665603ull;
+    for (const cumwin_s* h : wins) {
+        const uint64_t v = ((uint64_t)h->n << 40) ^ ((uint64_t)h->d << 32) ^ ((uint64_t)h->b << 24) ^ (uint64_t)h->T;
+        hsh = (hsh ^ v) * 1099511628211ull;
+    }
+    o << wins.size() << ':' << std::hex << hsh;
+    return o.str();
+}
+
+// ---------------------------------------------------------------------------
+// one window: tables and device state
+// ---------------------------------------------------------------------------
+// Allocates and initialises everything a window needs.  own_tc: build the
+// window's own tensor-core plan (mixed forms); batch members leave that to
+// the batch.
+int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precision, cudaStream_t stream,
+                bool own_tc)
+{
+    const int nbar = (n + b - 1) / b;
+    h->n = n;
+    h->d = d;
+    h->b = b;
+    h->nbar = nbar;
+    h->npad = nbar * b;
+    h->T = T;
+    h->p = p;
+    h->prec = precision;
+    h->stream = stream;
+    CW_TRY(cudaGetDevice(&h->device));
+    CW_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+    if (precision != CUMWIN_FP64) {
+        int major = 0, minor = 0;
+        CW_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device));
+        CW_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device));
+        if (!(major == 10 && minor == 3)) {
+            g_last_error = "mixed precision needs an sm_103 device";
+            return CUMWIN_ENOTSUP;
+        }
+    }
+    const int npad = h->npad;
+    CW_TRY(h->alloc(&h->ring, (size_t)T * npad));
+    if (precision == CUMWIN_FP64) CW_TRY(h->alloc(&h->stage, (size_t)2 * T * npad));
+    CW_TRY(h->alloc(&h->hin, (size_t)T * npad));
+    CW_TRY(h->alloc(&h->shift, npad));
+    CW_TRY(cudaMemset(h->shift, 0, sizeof(float) * npad));
+    CW_TRY(h->alloc(&h->status, 1));
+    CW_TRY(cudaMemset(h->status, 0, sizeof(int)));
+    CW_TRY(h->alloc(&h->head, 1));
+    CW_TRY(cudaMemset(h->head, 0, sizeof(int64_t)));
+    CW_TRY(cudaMemset(h->ring, 0, sizeof(float) * (size_t)T * npad));
+    h->Eoff[1] = 0;
+    for (int s = 1; s <= d; ++s) {
+        h->E[s] = n_sorted(nbar, s) * ipow(b, s);
+        if (h->E[s] >= ((int64_t)1 << 31)) {
+            g_last_error = "a moment tensor of this size (2^31 stored elements or more) is not supported";
+            return CUMWIN_EINVAL;
+        }
+        h->Eoff[s + 1] = h->Eoff[s] + h->E[s];
+        CW_TRY(h->alloc(&h->S[s], h->E[s]));
+        CW_TRY(h->alloc(&h->C[s], h->E[s]));
+        CW_TRY(cudaMemset(h->S[s], 0, sizeof(double) * h->E[s]));
+        CW_TRY(cudaMemset(h->C[s], 0, sizeof(double) * h->E[s]));
+    }
+
+    // update tables
+    h->upd.npad = npad;
+    h->ut.assign(d + 1, UpdateTables{});
+    std::vector<UpdTile> tiles;
+    for (int s = 1; s <= d; ++s) {
+        h->ut[s] = build_update_tables(n, b, s);
+        const UpdateTables& t = h->ut[s];
+        OrderTables& ot = h->upd.ord[s];
+        CW_TRY(h->upload((uint32_t**)&ot.rowvar, t.rowvar));
+        CW_TRY(h->upload((int64_t**)&ot.rowoff, t.rowoff));
+        CW_TRY(h->upload((uint32_t**)&ot.colvar, t.colvar));
+        CW_TRY(h->upload((int64_t**)&ot.coloff, t.coloff));
+        ot.S = h->S[s];
+        ot.h = t.h;
+        ot.sh = t.sh;
+        ot.nrows = (int32_t)t.rowvar.size();
+        ot.ncols = (int32_t)t.colvar.size();
+        if (precision != CUMWIN_FP64) continue;
+        for (int m = 0; m < nbar; ++m) {
+            const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
+            const int c0 = t.colstart[m], c1 = ot.ncols;
+            for (int r = r0; r < r1; r += 64)
+                for (int c = c0; c < c1; c += 64) {
+                    UpdTile u{};
+                    u.s = s;
+                    u.row0 = r;
+                    u.nrows = std::min(64, r1 - r);
+                    u.col0 = c;
+                    u.ncols = std::min(64, c1 - c);
+                    tiles.push_back(u);
+                }
+        }
+    }
+    h->ntiles = (int)tiles.size();
+    if (precision == CUMWIN_FP64) CW_TRY(h->upload(&h->tiles, tiles));
+
+    // cumulant recovery tables (norm partials and workspace pointers are set later)
+    for (int s = 1; s <= d; ++s) {
+        CumTables ct = build_cum_tables(n, b, s);
+        CumArgs& a = h->cum[s];
+        for (int k = 1; k <= d; ++k) {
+            a.S[k] = h->S[k];
+            a.C[k] = h->C[k];
+        }
+        a.Cout = h->C[s];
+        CW_TRY(h->upload((int32_t**)&a.subrank, ct.subrank));
+        CW_TRY(h->upload((double**)&a.mult, ct.mult));
+        a.shift = h->shift;
+        a.invT = 1.0 / (double)T;
+        a.E = h->E[s];
+        a.s = s;
+        a.b = b;
+        a.bs = (int32_t)ipow(b, s);
+        a.nsub = ct.nsub;
+        for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
+        a.W = nullptr;
+        a.accum = 0;
+        h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
+    }
+    CW_TRY(h->alloc(&h->fro2, d));
+    CW_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
+
+    if (precision != CUMWIN_FP64 && own_tc) {
+        TcPlanStream ps{};
+        ps.tables = &h->ut;
+        ps.upd = &h->upd;
+        ps.Eoff = h->Eoff;
+        ps.d = d;
+        ps.n = n;
+        ps.npad = npad;
+        ps.T = T;
+        ps.ring = h->ring;
+        ps.head = h->head;
+        ps.shift = h->shift;
+        ps.status = h->status;
+        ps.xoff = 0;
+        int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status,
+                                [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
+        if (rc != 0) {
+            g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
+            return rc == (int)cudaErrorMemoryAllocation ? CUMWIN_ENOMEM : CUMWIN_ECUDA;
+        }
+        h->tc = &h->tc_own;
+    }
+    return CUMWIN_OK;
+}
+
+// Norm partial slots and the device copies of the recovery arguments of a
+// window: `parts` slots per order, workspace slice `wbase` of plan `tc`.
+int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int64_t wbase)
+{
+    h->parts = parts;
+    CW_TRY(h->alloc(&h->normpart, (size_t)parts * h->d));
+    CW_TRY(cudaMemset(h->normpart, 0, sizeof(double) * (size_t)parts * h->d));
+    CumArgs arr[2][kMaxOrder + 1] = {};
+    for (int s = 1; s <= h->d; ++s) {
+        CumArgs& a = h->cum[s];
+        a.normpart = h->normpart + (size_t)(s - 1) * parts;
+        if (tc != nullptr) {
+            a.W = tc->W;
+            a.wslice = tc->wslice;
+            a.woff = wbase + h->Eoff[s];
+            a.ksplit = tc->ksplit;
+        }
+        arr[0][s] = a;
+        arr[1][s] = a;
+        arr[0][s].accum = 0;
+        arr[1][s].accum = 1;
+    }
+    CW_TRY(h->mem.upload(&h->cum_dev, &arr[0][0], 2 * (kMaxOrder + 1)));
+    NormArgs na{};
+    na.normpart = h->normpart;
+    na.fro2 = h->fro2;
+    na.head = h->head;
+    na.T = h->T;
+    na.parts = parts;
+    na.d = h->d;
+    CW_TRY(h->mem.upload(&h->norm_dev, &na, 1));
+    return CUMWIN_OK;
+}
 
 // Recovery of C_1..C_d and norms.  accum: fold the tensor-core workspace of
 // the shift into the sums first (mixed forms, after a push).
 int run_cumulants(cumwin_t h, int64_t advance, bool accum = false)
 {
-    for (int s = 1; s <= h->d; ++s) {
-        CumArgs a = h->cum[s];
-        a.accum = accum ? 1 : 0;
-        CW_TRY(launch_cumulants(a, h->cum_launch[s], h->stream));
-    }
-    CW_TRY(launch_norm_final(h->normpart, h->part_off, h->d, h->fro2, h->head, advance, h->T,
-                             h->stream));
+    for (int s = 1; s <= h->d; ++s)
+        CW_TRY(launch_cumulants(s, h->cum_dev + (accum ? kMaxOrder + 1 : 0) + s, 1, h->cum_launch[s],
+                                h->stream));
+    CW_TRY(launch_norm_final(h->norm_dev, 1, advance, h->stream));
     h->launches += h->d + 1;
     if (h->mark(3) != nullptr) h->timed++;
     return CUMWIN_OK;
+}
+
+std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcPlan& tc)
+{
+    std::vector<TcAccSeg> segs;
+    for (size_t i = 0; i < wins.size(); ++i)
+        for (int s = 1; s <= wins[i]->d; ++s)
+            segs.push_back({wins[i]->S[s], tc.wbase[i] + wins[i]->Eoff[s]});
+    return segs;
 }
 
 // Moment sums of the whole window held in the ring buffer (fill, recompute).
@@ -151,15 +434,11 @@ int update_window(cumwin_t h)
                                  h->stream));
         h->launches += 1;
     } else {
-        TcAccArgs acc{};
-        for (int s = 1; s <= h->d; ++s) acc.S[s] = h->S[s];
-        for (int s = 0; s <= h->d + 1; ++s) acc.Eoff[s] = h->Eoff[s];
-        acc.d = h->d;
-        for (int q = 0; q < h->tc.nbatch; ++q) {
-            CW_TRY(tc_update_window_batch(h->tc, h->ring, h->head, q, h->n, h->shift, h->stream));
-            CW_TRY(launch_tc_accumulate(h->tc, acc, h->stream));
+        for (int q = 0; q < h->tc->nbatch; ++q) {
+            CW_TRY(tc_update_window_batch(*h->tc, q, h->stream));
+            CW_TRY(launch_tc_accumulate(*h->tc, h->segs, h->nsegs, h->stream));
         }
-        h->launches += (int64_t)kTcBatchLaunches * h->tc.nbatch;
+        h->launches += 4LL * h->tc->nbatch;
     }
     h->mark(2);
     return CUMWIN_OK;
@@ -175,14 +454,12 @@ int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_
         h->mark(1);
         CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, 2 * (int64_t)p, p,
                                  h->shift, h->stream));
-        h->launches += 2;
     } else {
-        CW_TRY(tc_stage_push(h->tc, x_in, ld, x_out, ld, h->ring, h->head, p, h->n, h->shift,
-                             h->stream));
+        CW_TRY(tc_stage_push(*h->tc, x_in, x_out, ld, p, h->stream));
         h->mark(1);
-        CW_TRY(tc_gemm_push(h->tc, h->stream));
-        h->launches += 3;
+        CW_TRY(tc_gemm_push(*h->tc, h->stream));
     }
+    h->launches += 2 + (h->prec != CUMWIN_FP64);
     h->mark(2);
     return CUMWIN_OK;
 }
@@ -190,6 +467,31 @@ int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_
 int zero_sums(cumwin_t h)
 {
     for (int s = 1; s <= h->d; ++s) CW_TRY(launch_zero(h->S[s], h->E[s], h->stream));
+    return CUMWIN_OK;
+}
+
+int fill_prepare(cumwin_t h, const float* X_dev, int64_t ldx)
+{
+    CW_TRY(launch_fill_ring(X_dev, ldx, h->ring, h->T, h->n, h->npad, h->status, h->stream));
+    CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
+    if (h->prec != CUMWIN_FP64)
+        CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
+    return zero_sums(h);
+}
+
+int check_args(int n, int d, int b, int64_t T, int p, int precision)
+{
+    if (n < 1 || n > kMaxN || d < 1 || d > kMaxOrder || b < 1 || T < 1) return CUMWIN_EINVAL;
+    if (p < 1 || p > T) return CUMWIN_EINVAL;
+    if (precision != CUMWIN_FP64 && precision != CUMWIN_MIXED_BF16 && precision != CUMWIN_MIXED_FP16)
+        return CUMWIN_EINVAL;
+    const int nbar = (n + b - 1) / b;
+    if ((int64_t)nbar * b > kMaxN) return CUMWIN_EINVAL;
+    if (T > ((int64_t)1 << 40)) return CUMWIN_EINVAL;
+    if (precision == CUMWIN_MIXED_FP16) {
+        g_last_error = "the FP16 split form is not available in this build";
+        return CUMWIN_ENOTSUP;
+    }
     return CUMWIN_OK;
 }
 
@@ -209,11 +511,12 @@ int64_t element_index_impl(int n, int b, int order, const int* i)
     return rank_sorted(j, order, nbar) * ipow(b, order) + off;
 }
 
+
 }  // namespace
 
 extern "C" {
 
-int cumwin_version(void) { return 100; }
+int cumwin_version(void) { return 110; }
 
 const char* cumwin_strerror(int code)
 {
@@ -361,159 +664,32 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
 {
     if (out == nullptr) return CUMWIN_EINVAL;
     *out = nullptr;
-    if (n < 1 || n > kMaxN || d < 1 || d > kMaxOrder || b < 1 || T < 1) return CUMWIN_EINVAL;
-    if (p < 1 || p > T) return CUMWIN_EINVAL;
-    if (precision != CUMWIN_FP64 && precision != CUMWIN_MIXED_BF16 && precision != CUMWIN_MIXED_FP16)
-        return CUMWIN_EINVAL;
-    const int nbar = (n + b - 1) / b;
-    if ((int64_t)nbar * b > kMaxN) return CUMWIN_EINVAL;
-    if (T > ((int64_t)1 << 40)) return CUMWIN_EINVAL;
-
+    int rc = check_args(n, d, b, T, p, precision);
+    if (rc) return rc;
     cumwin_s* h = new cumwin_s();
-    h->n = n;
-    h->d = d;
-    h->b = b;
-    h->nbar = nbar;
-    h->npad = nbar * b;
-    h->T = T;
-    h->p = p;
-    h->prec = precision;
-    h->stream = (cudaStream_t)cuda_stream;
-
-    auto bail = [&](int code) {
+    rc = window_init(h, n, d, b, T, p, precision, (cudaStream_t)cuda_stream, true);
+    int parts = 1;
+    for (int s = 1; s <= d; ++s) parts = std::max(parts, h->cum_launch[s].gx * h->cum_launch[s].gy);
+    if (rc == CUMWIN_OK && h->tc != nullptr) {
+        const int ks = tune_cache_get(plan_signature(*h->tc, {h}, h->device));
+        if (ks >= 1 && ks <= h->tc->ksplit_max) h->tc->ksplit = ks;
+    }
+    if (rc == CUMWIN_OK) rc = window_finish(h, parts, h->tc, 0);
+    if (rc == CUMWIN_OK && h->tc != nullptr) {
+        std::vector<TcAccSeg> segs = acc_segments({h}, *h->tc);
+        h->nsegs = (int)segs.size();
+        cudaError_t e = h->mem.upload(&h->segs, segs);
+        if (e != cudaSuccess) rc = fail_cuda(e, "create");
+    }
+    if (rc == CUMWIN_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = fail_cuda(e, "create");
+    }
+    if (rc != CUMWIN_OK) {
         h->release();
         delete h;
-        return code;
-    };
-#define CW_CREATE_TRY(expr)                               \
-    do {                                                  \
-        cudaError_t _e = (expr);                          \
-        if (_e != cudaSuccess) return bail(fail_cuda(_e, #expr)); \
-    } while (0)
-
-    CW_CREATE_TRY(cudaGetDevice(&h->device));
-    CW_CREATE_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
-    if (precision == CUMWIN_MIXED_FP16) {
-        g_last_error = "the FP16 split form is not available in this build";
-        return bail(CUMWIN_ENOTSUP);
+        return rc;
     }
-    if (precision != CUMWIN_FP64) {
-        int major = 0, minor = 0;
-        CW_CREATE_TRY(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device));
-        CW_CREATE_TRY(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device));
-        if (!(major == 10 && minor == 3)) {
-            g_last_error = "mixed precision needs an sm_103 device";
-            return bail(CUMWIN_ENOTSUP);
-        }
-    }
-    const int npad = h->npad;
-    CW_CREATE_TRY(h->alloc(&h->ring, (size_t)T * npad));
-    CW_CREATE_TRY(h->alloc(&h->stage, (size_t)2 * T * npad));
-    CW_CREATE_TRY(h->alloc(&h->hin, (size_t)T * npad));
-    CW_CREATE_TRY(h->alloc(&h->shift, npad));
-    CW_CREATE_TRY(cudaMemset(h->shift, 0, sizeof(float) * npad));
-    CW_CREATE_TRY(h->alloc(&h->status, 1));
-    CW_CREATE_TRY(h->alloc(&h->head, 1));
-    CW_CREATE_TRY(cudaMemset(h->head, 0, sizeof(int64_t)));
-    CW_CREATE_TRY(cudaMemset(h->status, 0, sizeof(int)));
-    CW_CREATE_TRY(cudaMemset(h->ring, 0, sizeof(float) * (size_t)T * npad));
-    for (int s = 1; s <= d; ++s) {
-        h->E[s] = n_sorted(nbar, s) * ipow(b, s);
-        if (h->E[s] >= ((int64_t)1 << 31)) {
-            g_last_error = "a moment tensor of this size (2^31 stored elements or more) is not supported";
-            return bail(CUMWIN_EINVAL);
-        }
-        CW_CREATE_TRY(h->alloc(&h->S[s], h->E[s]));
-        CW_CREATE_TRY(h->alloc(&h->C[s], h->E[s]));
-        CW_CREATE_TRY(cudaMemset(h->S[s], 0, sizeof(double) * h->E[s]));
-        CW_CREATE_TRY(cudaMemset(h->C[s], 0, sizeof(double) * h->E[s]));
-    }
-
-    // update tables and tiles
-    h->upd.npad = npad;
-    std::vector<UpdTile> tiles;
-    std::vector<UpdateTables> ut(d + 1);
-    for (int s = 1; s <= d; ++s) {
-        ut[s] = build_update_tables(n, b, s);
-        const UpdateTables& t = ut[s];
-        OrderTables& ot = h->upd.ord[s];
-        CW_CREATE_TRY(h->upload((uint32_t**)&ot.rowvar, t.rowvar));
-        CW_CREATE_TRY(h->upload((int64_t**)&ot.rowoff, t.rowoff));
-        CW_CREATE_TRY(h->upload((uint32_t**)&ot.colvar, t.colvar));
-        CW_CREATE_TRY(h->upload((int64_t**)&ot.coloff, t.coloff));
-        ot.S = h->S[s];
-        ot.h = t.h;
-        ot.sh = t.sh;
-        ot.nrows = (int32_t)t.rowvar.size();
-        ot.ncols = (int32_t)t.colvar.size();
-        for (int m = 0; m < nbar; ++m) {
-            const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
-            const int c0 = t.colstart[m], c1 = ot.ncols;
-            for (int r = r0; r < r1; r += 64)
-                for (int c = c0; c < c1; c += 64) {
-                    UpdTile u{};
-                    u.s = s;
-                    u.row0 = r;
-                    u.nrows = std::min(64, r1 - r);
-                    u.col0 = c;
-                    u.ncols = std::min(64, c1 - c);
-                    tiles.push_back(u);
-                }
-        }
-    }
-    h->ntiles = (int)tiles.size();
-    h->Eoff[1] = 0;
-    for (int s = 1; s <= d; ++s) h->Eoff[s + 1] = h->Eoff[s] + h->E[s];
-    if (precision == CUMWIN_FP64) {
-        CW_CREATE_TRY(h->upload(&h->tiles, tiles));
-    } else {
-        int rc = tc_plan_create(h->tc, ut, h->upd, h->Eoff, d, n, b, npad, T, p, h->sm_count,
-                                precision,
-                                h->status,
-                                [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
-        if (rc != 0) {
-            g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
-            return bail(CUMWIN_ECUDA);
-        }
-    }
-
-    // cumulant recovery tables
-    std::vector<int32_t> part_off(d + 1, 0);
-    for (int s = 1; s <= d; ++s) {
-        CumTables ct = build_cum_tables(n, b, s);
-        CumArgs& a = h->cum[s];
-        for (int k = 1; k <= d; ++k) {
-            a.S[k] = h->S[k];
-            a.C[k] = h->C[k];
-        }
-        a.Cout = h->C[s];
-        CW_CREATE_TRY(h->upload((int32_t**)&a.subrank, ct.subrank));
-        CW_CREATE_TRY(h->upload((double**)&a.mult, ct.mult));
-        a.shift = h->shift;
-        a.W = h->tc.W;
-        a.wslice = h->tc.wslice;
-        a.woff = h->Eoff[s];
-        a.ksplit = h->tc.ksplit;
-        a.accum = 0;
-        a.invT = 1.0 / (double)T;
-        a.E = h->E[s];
-        a.s = s;
-        a.b = b;
-        a.bs = (int32_t)ipow(b, s);
-        a.nsub = ct.nsub;
-        for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
-        h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
-        part_off[s] = part_off[s - 1] + h->cum_launch[s].gx * h->cum_launch[s].gy;
-    }
-    // part_off[s-1]..part_off[s] are the partials of order s
-    std::vector<int32_t> po(part_off.begin(), part_off.end());
-    CW_CREATE_TRY(h->alloc(&h->normpart, (size_t)part_off[d]));
-    for (int s = 1; s <= d; ++s) h->cum[s].normpart = h->normpart + part_off[s - 1];
-    CW_CREATE_TRY(h->upload(&h->part_off, po));
-    CW_CREATE_TRY(h->alloc(&h->fro2, d));
-    CW_CREATE_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
-    CW_CREATE_TRY(cudaDeviceSynchronize());
-#undef CW_CREATE_TRY
     *out = h;
     return CUMWIN_OK;
 }
@@ -537,11 +713,7 @@ int cumwin_set_stream(cumwin_t h, void* cuda_stream)
 int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx)
 {
     if (h == nullptr || X_dev == nullptr || ldx < h->n) return CUMWIN_EINVAL;
-    CW_TRY(launch_fill_ring(X_dev, ldx, h->ring, h->T, h->n, h->npad, h->status, h->stream));
-    CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
-    if (h->prec != CUMWIN_FP64)
-        CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
-    int rc = zero_sums(h);
+    int rc = fill_prepare(h, X_dev, ldx);
     if (rc) return rc;
     rc = update_window(h);
     if (rc) return rc;
@@ -612,6 +784,12 @@ int cumwin_norms_device(cumwin_t h, double* fro2_dev)
     return CUMWIN_OK;
 }
 
+static void nu_from_fro(const double* fro, int d, double* nu)
+{
+    for (int s = 1; s <= d; ++s)
+        nu[s - 1] = (s < 3 || d < 2) ? NAN : fro[s - 1] / std::pow(fro[1], 0.5 * s);
+}
+
 int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
@@ -625,9 +803,7 @@ int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host)
     for (int s = 0; s < h->d; ++s) fro[s] = std::sqrt(z[s]);
     if (fro_host)
         for (int s = 0; s < h->d; ++s) fro_host[s] = fro[s];
-    if (nu_host)
-        for (int s = 1; s <= h->d; ++s)
-            nu_host[s - 1] = (s < 3 || h->d < 2) ? NAN : fro[s - 1] / std::pow(fro[1], 0.5 * s);
+    if (nu_host) nu_from_fro(fro, h->d, nu_host);
     if (st & kStatusNonFinite) return CUMWIN_ENONFINITE;
     if (st & kStatusTimeout) return CUMWIN_ETIMEOUT;
     return CUMWIN_OK;
@@ -739,6 +915,30 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
     return CUMWIN_OK;
 }
 
+int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
+{
+    if (h == nullptr || reps < 1) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    if (h->tc == nullptr) {
+        if (ksplit_out) *ksplit_out = 0;
+        return CUMWIN_OK;  // nothing to tune in the FP64 form
+    }
+    const int ks = tc_autotune(*h->tc, reps, h->stream, nullptr);
+    if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
+    for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
+    CumArgs arr[2][kMaxOrder + 1] = {};
+    for (int s = 1; s <= h->d; ++s) {
+        arr[0][s] = h->cum[s];
+        arr[1][s] = h->cum[s];
+        arr[0][s].accum = 0;
+        arr[1][s].accum = 1;
+    }
+    CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0], sizeof(arr), cudaMemcpyHostToDevice));
+    tune_cache_put(plan_signature(*h->tc, {h}, h->device), ks);
+    if (ksplit_out) *ksplit_out = ks;
+    return CUMWIN_OK;
+}
+
 int cumwin_set_timing(cumwin_t h, int enable)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
@@ -784,6 +984,236 @@ int cumwin_status(cumwin_t h)
     if (st & kStatusNonFinite) return CUMWIN_ENONFINITE;
     if (st & kStatusTimeout) return CUMWIN_ETIMEOUT;
     return CUMWIN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent windows
+// ---------------------------------------------------------------------------
+int cumwin_batch_destroy(cumwin_batch_t B)
+{
+    if (B == nullptr) return CUMWIN_OK;
+    cudaStreamSynchronize(B->stream);
+    for (cumwin_s* h : B->wins) {
+        h->release();
+        delete h;
+    }
+    B->mem.release();
+    delete B;
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, int b, int p, int precision,
+                        void* cuda_stream, cumwin_batch_t* out)
+{
+    if (out == nullptr || n == nullptr || d == nullptr || T == nullptr || nwin < 1 || nwin > 65535)
+        return CUMWIN_EINVAL;
+    *out = nullptr;
+    if (precision == CUMWIN_FP64) {
+        g_last_error = "batches run the tensor-core forms";
+        return CUMWIN_ENOTSUP;
+    }
+    for (int i = 0; i < nwin; ++i) {
+        const int rc = check_args(n[i], d[i], b, T[i], p, precision);
+        if (rc) return rc;
+    }
+    cumwin_batch_s* B = new cumwin_batch_s();
+    B->nwin = nwin;
+    B->b = b;
+    B->p = p;
+    B->prec = precision;
+    B->stream = (cudaStream_t)cuda_stream;
+    auto bail = [&](int code) {
+        cumwin_batch_destroy(B);
+        return code;
+    };
+    B->xoff.assign(nwin + 1, 0);
+    std::vector<TcPlanStream> ps(nwin);
+    for (int i = 0; i < nwin; ++i) {
+        cumwin_s* h = new cumwin_s();
+        B->wins.push_back(h);
+        const int rc = window_init(h, n[i], d[i], b, T[i], p, precision, B->stream, false);
+        if (rc) return bail(rc);
+        B->dmax = std::max(B->dmax, d[i]);
+        B->sm_count = h->sm_count;
+        B->xoff[i + 1] = B->xoff[i] + (int64_t)p * n[i];
+        TcPlanStream& q = ps[i];
+        q.tables = &h->ut;
+        q.upd = &h->upd;
+        q.Eoff = h->Eoff;
+        q.d = d[i];
+        q.n = n[i];
+        q.npad = h->npad;
+        q.T = T[i];
+        q.ring = h->ring;
+        q.head = h->head;
+        q.shift = h->shift;
+        q.status = h->status;
+        q.xoff = B->xoff[i];
+    }
+    cudaError_t e0 = B->mem.alloc(&B->status, 1);
+    if (e0 != cudaSuccess) return bail(fail_cuda(e0, "alloc"));
+    cudaMemset(B->status, 0, sizeof(int));
+    int rc = tc_plan_create(B->tc, ps, b, p, B->sm_count, precision, B->status,
+                            [&](size_t bytes, void** q) { return B->mem.alloc((char**)q, bytes); });
+    if (rc != 0) {
+        g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
+        return bail(rc == (int)cudaErrorMemoryAllocation ? CUMWIN_ENOMEM : CUMWIN_ECUDA);
+    }
+    const int ks = tune_cache_get(plan_signature(B->tc, B->wins, B->wins[0]->device));
+    if (ks >= 1 && ks <= B->tc.ksplit_max) B->tc.ksplit = ks;
+    // recovery launch shapes over all windows (b is shared, so b^s is too)
+    int parts = 1;
+    for (int s = 1; s <= B->dmax; ++s) {
+        int64_t nb = 0;
+        for (cumwin_s* h : B->wins)
+            if (s <= h->d) nb = std::max<int64_t>(nb, n_sorted(h->nbar, s));
+        B->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), nb, B->sm_count);
+        parts = std::max(parts, B->cum_launch[s].gx * B->cum_launch[s].gy);
+    }
+    std::vector<CumArgs> arr((size_t)2 * (kMaxOrder + 1) * nwin);
+    std::vector<NormArgs> na(nwin);
+    cudaError_t e = B->mem.alloc(&B->fro2, (size_t)nwin * B->dmax);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "alloc"));
+    for (int i = 0; i < nwin; ++i) {
+        cumwin_s* h = B->wins[i];
+        h->fro2 = B->fro2 + (size_t)i * B->dmax;
+        h->tc = &B->tc;
+        rc = window_finish(h, parts, &B->tc, B->tc.wbase[i]);
+        if (rc) return bail(rc);
+        for (int s = 1; s <= B->dmax; ++s) {
+            for (int acc = 0; acc < 2; ++acc) {
+                CumArgs a{};
+                if (s <= h->d) {
+                    a = h->cum[s];
+                    a.accum = acc;
+                }  // else E = 0: the kernel skips this window
+                arr[((size_t)acc * (kMaxOrder + 1) + s) * nwin + i] = a;
+            }
+        }
+        na[i].normpart = h->normpart;
+        na[i].fro2 = h->fro2;
+        na[i].head = h->head;
+        na[i].T = h->T;
+        na[i].parts = parts;
+        na[i].d = h->d;
+    }
+    e = B->mem.upload(&B->cum_dev, arr);
+    if (e == cudaSuccess) e = B->mem.upload(&B->norm_dev, na);
+    std::vector<TcAccSeg> segs = acc_segments(B->wins, B->tc);
+    B->nsegs = (int)segs.size();
+    if (e == cudaSuccess) e = B->mem.upload(&B->segs, segs);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(fail_cuda(e, "batch create"));
+    *out = B;
+    return CUMWIN_OK;
+}
+
+int64_t cumwin_batch_offset(cumwin_batch_t B, int window)
+{
+    if (B == nullptr || window < 0 || window > B->nwin) return -1;
+    return B->xoff[window];
+}
+
+static int batch_recover(cumwin_batch_t B, int64_t advance, bool accum)
+{
+    for (int s = 1; s <= B->dmax; ++s)
+        CW_TRY(launch_cumulants(s, B->cum_dev + ((size_t)(accum ? 1 : 0) * (kMaxOrder + 1) + s) * B->nwin,
+                                B->nwin, B->cum_launch[s], B->stream));
+    CW_TRY(launch_norm_final(B->norm_dev, B->nwin, advance, B->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev)
+{
+    if (B == nullptr || X_dev == nullptr) return CUMWIN_EINVAL;
+    for (int i = 0; i < B->nwin; ++i)
+        if (X_dev[i] == nullptr) return CUMWIN_EINVAL;
+    for (int i = 0; i < B->nwin; ++i) {
+        cumwin_s* h = B->wins[i];
+        h->stream = B->stream;
+        const int rc = fill_prepare(h, X_dev[i], h->n);
+        if (rc) return rc;
+    }
+    for (int q = 0; q < B->tc.nbatch; ++q) {
+        CW_TRY(tc_update_window_batch(B->tc, q, B->stream));
+        CW_TRY(launch_tc_accumulate(B->tc, B->segs, B->nsegs, B->stream));
+    }
+    const int rc = batch_recover(B, 0, false);
+    if (rc) return rc;
+    for (cumwin_s* h : B->wins) h->filled = true;
+    B->filled = true;
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_push(cumwin_batch_t B, const float* x_dev)
+{
+    if (B == nullptr || x_dev == nullptr) return CUMWIN_EINVAL;
+    if (!B->filled) return CUMWIN_ESTATE;
+    CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, B->stream));
+    CW_TRY(tc_gemm_push(B->tc, B->stream));
+    return batch_recover(B, B->p, true);
+}
+
+int cumwin_batch_cumulants(cumwin_batch_t B, int window, int order, double* out_dev)
+{
+    if (B == nullptr || window < 0 || window >= B->nwin) return CUMWIN_EINVAL;
+    cumwin_s* h = B->wins[window];
+    h->stream = B->stream;
+    return cumwin_cumulants(h, order, out_dev);
+}
+
+int cumwin_batch_norms(cumwin_batch_t B, double* fro_host, double* nu_host)
+{
+    if (B == nullptr) return CUMWIN_EINVAL;
+    if (!B->filled) return CUMWIN_ESTATE;
+    std::vector<double> z((size_t)B->nwin * B->dmax);
+    int st = 0;
+    CW_TRY(cudaMemcpyAsync(z.data(), B->fro2, sizeof(double) * z.size(), cudaMemcpyDeviceToHost, B->stream));
+    CW_TRY(cudaMemcpyAsync(&st, B->status, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+    CW_TRY(cudaStreamSynchronize(B->stream));
+    for (int i = 0; i < B->nwin; ++i) {
+        const int d = B->wins[i]->d;
+        double fro[kMaxOrder];
+        for (int s = 0; s < B->dmax; ++s) fro[s] = s < d ? std::sqrt(z[(size_t)i * B->dmax + s]) : NAN;
+        if (fro_host)
+            for (int s = 0; s < B->dmax; ++s) fro_host[(size_t)i * B->dmax + s] = fro[s];
+        if (nu_host) {
+            double nu[kMaxOrder];
+            nu_from_fro(fro, d, nu);
+            for (int s = 0; s < B->dmax; ++s) nu_host[(size_t)i * B->dmax + s] = s < d ? nu[s] : NAN;
+        }
+    }
+    for (cumwin_s* h : B->wins) {
+        int ws = 0;
+        CW_TRY(cudaMemcpy(&ws, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+        st |= ws;
+    }
+    if (st & kStatusNonFinite) return CUMWIN_ENONFINITE;
+    if (st & kStatusTimeout) return CUMWIN_ETIMEOUT;
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out)
+{
+    if (B == nullptr || reps < 1) return CUMWIN_EINVAL;
+    if (!B->filled) return CUMWIN_ESTATE;
+    const int ks = tc_autotune(B->tc, reps, B->stream, nullptr);
+    if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
+    std::vector<CumArgs> arr((size_t)2 * (kMaxOrder + 1) * B->nwin);
+    CW_TRY(cudaMemcpy(arr.data(), B->cum_dev, sizeof(CumArgs) * arr.size(), cudaMemcpyDeviceToHost));
+    for (CumArgs& a : arr) a.ksplit = ks;
+    CW_TRY(cudaMemcpy(B->cum_dev, arr.data(), sizeof(CumArgs) * arr.size(), cudaMemcpyHostToDevice));
+    for (cumwin_s* h : B->wins)
+        for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
+    tune_cache_put(plan_signature(B->tc, B->wins, B->wins[0]->device), ks);
+    if (ksplit_out) *ksplit_out = ks;
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_status(cumwin_batch_t B)
+{
+    if (B == nullptr) return CUMWIN_EINVAL;
+    return cumwin_batch_norms(B, nullptr, nullptr);
 }
 
 }  // extern "C"

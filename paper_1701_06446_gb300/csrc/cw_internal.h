@@ -112,12 +112,21 @@ struct CumLaunch {
     int slots, gx, gy;
 };
 CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count);
-cudaError_t launch_cumulants(const CumArgs& a, const CumLaunch& L, cudaStream_t st);
-// Also advances the ring head by `advance` rows (mod T): the head lives in
+// Recovery of order s for nwin windows at once (args_dev[w] for window w;
+// windows without order s have E = 0).
+cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const CumLaunch& L, cudaStream_t st);
+
+// Norm reduction of one window: partials of order s at normpart[(s-1)*parts ..].
+struct NormArgs {
+    const double* normpart;
+    double* fro2;      // [d]
+    int64_t* head;     // ring head, advanced by `advance` rows (mod T)
+    int64_t T;
+    int32_t parts, d;
+};
+// Also advances each ring head by `advance` rows (mod T): the head lives in
 // device memory so that a captured shift can be replayed.
-cudaError_t launch_norm_final(const double* normpart, const int32_t* part_off, int d,
-                              double* fro2, int64_t* head, int64_t advance, int64_t T,
-                              cudaStream_t st);
+cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, cudaStream_t st);
 cudaError_t launch_zero(double* p, int64_t count, cudaStream_t st);
 cudaError_t launch_add_shift(const double* C1, const float* shift, int n, int npad, double* out,
                              cudaStream_t st);

@@ -1,10 +1,12 @@
 // Tensor-core (tcgen05) form of the moment-sum update: plan and launchers.
 //
-// The order-s update is the set of GEMMs described in cw_internal.h: the
-// right factor (s - h indices, "columns") is the MMA M side (128 per item),
-// the left factor (h indices, "rows") the MMA N side (up to kTcNmax rows).
+// One plan serves one or many independent windows ("streams", each with its
+// own n, d, T, ring buffer and sums; b and p are shared).  The order-s update
+// of a stream is the set of GEMMs described in cw_internal.h: the right factor
+// (s - h indices, "columns") is the MMA M side (128 per item), the left factor
+// (h indices, "rows") the MMA N side (up to kTcNmax rows).
 //
-// Per shift:
+// Per shift, for all streams at once (one launch per phase):
 //   1. k_tc_stage_push: X_(+) and X_(-), minus the shift vector, transposed to
 //      [variable][sample] (FP32), zero-padded to P samples each.
 //   2. k_kr_build: every distinct Khatri-Rao operand row (the products of its
@@ -12,14 +14,15 @@
 //      bf16 hi + lo and written with the samples contiguous, so that a TMA box
 //      of 64 samples (128 bytes) x rows lands in shared memory in the
 //      128-byte-swizzled K-major layout the MMA descriptors read.
-//   3. k_kr_gemm: per unit (item x K-split) a TMA warp streams the item's
-//      A (128 columns) and B (rows) tiles through a 3-stage mbarrier ring, an
-//      MMA warp issues hi*hi + hi*lo + lo*hi per 16-sample step into TMEM
-//      (entering samples into D_in, leaving samples into D_out), and four
-//      epilogue warps store the FP32 tiles into a workspace W[split][in/out].
-//   4. the recovery kernel of each order first folds the workspace into the
-//      FP64 sums: S += (double)(sum_k D_in,k) - (double)(sum_k D_out,k), the
-//      FP32 sums over splits taken in a fixed order, so that a batch's sum is
+//   3. k_kr_gemm (persistent): per unit (item x K-split) a TMA warp streams the
+//      item's A (128 columns) and B (rows) tiles through a 3-stage mbarrier
+//      ring, an MMA warp issues hi*hi + hi*lo + lo*hi per 16-sample step into
+//      one of two TMEM accumulator sets (entering samples into D_in, leaving
+//      samples into D_out), and four epilogue warps store the FP32 tiles into
+//      a workspace W[split][in/out] while the next unit's MMAs run.
+//   4. the recovery kernel of each order folds the workspace into the FP64
+//      sums: S += (double)(sum_k D_in,k) - (double)(sum_k D_out,k), the FP32
+//      sums over splits taken in a fixed order, so that a batch's sum is
 //      bitwise the same when it enters and when it leaves the window.
 #pragma once
 
@@ -38,6 +41,18 @@ constexpr int kTcM = 128;      // columns per item (MMA M)
 constexpr int kTcNmax = 128;   // rows per item (MMA N, multiple of 16)
 constexpr int kTcStages = 3;   // TMA / MMA pipeline depth (64 KB per stage)
 
+// Per-stream state the staging / build kernels read (device array).
+struct TcStreamDesc {
+    float* ring;
+    const int64_t* head;
+    const float* shift;
+    float* XT;          // [npad][Kcap]
+    int* status;
+    int64_t T;
+    int64_t xoff;       // offset of this stream's X_(+) rows in a packed push buffer
+    int32_t n, npad;
+};
+
 struct TcItem {
     int32_t s;      // order
     int32_t row0;   // first row in the order's left table
@@ -47,78 +62,96 @@ struct TcItem {
     int32_t brow;   // TMA row coordinate of row0 in the operand array
     int32_t acol;   // TMA row coordinate of col0 in the operand array
     int32_t bbox;   // rows of the B tile box (32, 64 or 128)
+    int32_t stream; // index of the stream
+    int32_t pad0, pad1, pad2;
 };
 
+// Per (stream, order) tables of the epilogue (device array [stream][kMaxOrder + 1]).
 struct TcOrder {
     const int64_t* rowoff;
     const int32_t* rowcolmin;  // first valid column of each row (its group's start)
     const int64_t* coloff;
-    int64_t woff;              // offset of this order in one workspace slice
+    int64_t woff;              // offset of this (stream, order) in one workspace slice
 };
 
 struct TcGemmArgs {
-    TcOrder ord[kMaxOrder + 1];
+    const TcOrder* ord;
     const TcItem* items;
-    float* W;            // [ksplit][2][Etot] FP32 tile sums
-    int64_t wslice;      // Etot
+    float* W;            // [ksplit][2][wslice] FP32 tile sums
+    int64_t wslice;
     int32_t nitems, ksplit;
     int32_t nplus, nminus;  // K-chunks of the entering / leaving segment
     int32_t minus_k;        // first sample of the leaving segment
     int* status;
 };
 
+// Host description of one stream for the planner.
+struct TcPlanStream {
+    const std::vector<UpdateTables>* tables;  // [order]
+    const UpdateArgs* upd;                    // device tables of the update
+    const int64_t* Eoff;                      // [order] element offsets inside the stream
+    int d, n, npad;
+    int64_t T;
+    float* ring;
+    const int64_t* head;
+    const float* shift;
+    int* status;
+    int64_t xoff;
+};
+
 struct TcPlan {
     int ready = 0;
     int precision = 0;
-    int npad = 0, p = 0, P = 0, nbatch = 0;
-    int64_t T = 0, Kcap = 0;
-    float* XT = nullptr;           // [npad][Kcap] shifted samples, variable-major
-    // operand array: rows of all Khatri-Rao sets, [part][row][Kcap] bf16
+    int nstreams = 0, p = 0, P = 0, nbatch = 0, sm_count = 1;
+    int64_t Kcap = 0;
+    TcStreamDesc* sdesc = nullptr;  // device [nstreams]
+    int npad_max = 0;
+    // operand array: rows of all Khatri-Rao sets of all streams, [part][row][Kcap] bf16
     uint16_t* ops = nullptr;
     int64_t oprows = 0;
-    uint64_t* opvars = nullptr;    // per operand row: packed variables | factors << 32
+    uint64_t* opvars = nullptr;    // per row: packed variables | factors << 32 | stream << 40
     CUtensorMap mapA{}, mapB[3]{};  // A boxes of 128 rows; B boxes of 32, 64, 128 rows
     TcItem* items = nullptr;
-    int nitems = 0, ksplit = 1, sm_count = 1;
-    TcOrder ord[kMaxOrder + 1]{};
+    int nitems = 0, ksplit = 1, ksplit_max = 1;
+    TcOrder* ord = nullptr;        // device [nstreams][kMaxOrder + 1]
     float* W = nullptr;
     int64_t wslice = 0;
+    std::vector<int64_t> wbase;    // per stream: offset of the stream in a workspace slice
+    std::vector<int> nbatch_stream;
     int* status = nullptr;
-    // planning statistics (host)
     double useful_macs_per_sample = 0, issued_macs_per_sample = 0;
 };
 
 using DevAlloc = std::function<cudaError_t(size_t, void**)>;
 
 // Returns 0 or a cudaError_t code.
-int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const UpdateArgs& upd,
-                   const int64_t* Eoff, int d, int n, int b, int npad, int64_t T, int p,
-                   int sm_count, int precision, int* status, const DevAlloc& alloc);
+int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
+                   int precision, int* status, const DevAlloc& alloc);
 
-// One window shift, first half: stage X_(+) / X_(-) (moving X_(+) into the
-// ring) and build the Khatri-Rao operands (2 launches).
-cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
-                          int64_t ld_out, float* ring, const int64_t* head, int p, int n,
-                          const float* shift, cudaStream_t st);
-// Second half: the GEMM units (1 launch).  The FP64 sums are then updated by
-// the recovery kernels in accumulate mode.
+// Staging + operand build for all streams (2 launches).  Stream i reads its
+// X_(+) at xin + xoff_i (row stride ld, or n_i when ld < 0) and, when xout is
+// not null, its X_(-) at xout + xoff_i; otherwise from its ring buffer.
+cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
+                          cudaStream_t st);
+// The GEMM units of a shift (1 launch).
 cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st);
 
-// Batch q of the window held in the ring (window order, p_nominal samples):
-// stage, build and GEMM with no leaving segment; the caller then folds the
-// workspace into the sums (launch_tc_accumulate).
-cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const int64_t* head,
-                                   int q, int n, const float* shift, cudaStream_t st);
+// Batch q (window order, p samples) of every stream's ring buffer: stage, build
+// and GEMM with no leaving segment (3 launches); streams with fewer batches
+// contribute zeros.  Then fold the workspace into the sums with
+// launch_tc_accumulate.
+cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st);
 
-// S_s += (double)sum_k W[k][0] (entering only), all orders.
-struct TcAccArgs {
-    double* S[kMaxOrder + 1];
-    int64_t Eoff[kMaxOrder + 2];
-    int32_t d;
+// S += (double)sum_k W[k][0] for every (stream, order) segment.
+struct TcAccSeg {
+    double* S;
+    int64_t begin;  // first element of the segment in a workspace slice
 };
-cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccArgs& a, cudaStream_t st);
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs,
+                                 cudaStream_t st);
 
-// Kernels one window batch launches (with the accumulation).
-constexpr int kTcBatchLaunches = 4;
+// Time the GEMM for each candidate K-split on the data currently staged and
+// keep the fastest; returns the chosen K-split (or a negative cudaError_t).
+int tc_autotune(TcPlan& plan, int reps, cudaStream_t st, double* best_ms);
 
 }  // namespace cw

@@ -39,9 +39,11 @@ struct Subsets {
 __host__ __device__ constexpr int popc_c(unsigned x) { return x ? (int)(x & 1u) + popc_c(x >> 1) : 0; }
 
 template <int S>
-__global__ void __launch_bounds__(NT) k_cumulants(const CumArgs a, int slots)
+__global__ void __launch_bounds__(NT) k_cumulants(const CumArgs* __restrict__ args, int slots)
 {
     constexpr int NS = Subsets<S>::N;
+    const CumArgs& a = args[blockIdx.z];  // one window per blockIdx.z
+    if (a.E == 0) return;                 // this window has no order S
     extern __shared__ int sbase[];  // [slots][NS][2]: rank(j_A) * b^|A|, rank(j_rest) * b^|rest|
     const int b = a.b, bs = a.bs;
     int bp[kMaxOrder + 1];
@@ -147,26 +149,27 @@ __global__ void __launch_bounds__(NT) k_cumulants(const CumArgs a, int slots)
     if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
-// One warp per order: lanes add strided partials, then a fixed shuffle tree.
-__global__ void k_norm_final(const double* __restrict__ normpart, const int32_t* __restrict__ part_off,
-                             int d, double* __restrict__ fro2, int64_t* __restrict__ head,
-                             int64_t advance, int64_t T)
+// One CTA per window, one warp per order: lanes add strided partials, then a
+// fixed shuffle tree.  Also advances the window's ring head.
+__global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance)
 {
+    const NormArgs& a = args[blockIdx.x];
     const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
-    if (threadIdx.x == 0 && advance != 0) *head = (*head + advance) % T;
-    if (s >= d) return;
+    if (threadIdx.x == 0 && advance != 0) *a.head = (*a.head + advance) % a.T;
+    if (s >= a.d) return;
     double z = 0.0;
-    for (int q = part_off[s] + lane; q < part_off[s + 1]; q += 32) z += normpart[q];
+    const double* part = a.normpart + (int64_t)s * a.parts;
+    for (int q = lane; q < a.parts; q += 32) z += part[q];
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) fro2[s] = z;
+    if (lane == 0) a.fro2[s] = z;
 }
 
 template <int S>
-cudaError_t launch_order(const CumArgs& a, const CumLaunch& L, cudaStream_t st)
+cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cudaStream_t st)
 {
     constexpr int NS = Subsets<S>::N;
     const size_t smem = (size_t)L.slots * (NS > 0 ? NS : 1) * 2 * sizeof(int);
-    k_cumulants<S><<<dim3(L.gx, L.gy), NT, smem, st>>>(a, L.slots);
+    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots);
     return cudaGetLastError();
 }
 
@@ -196,25 +199,24 @@ CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count)
     return L;
 }
 
-cudaError_t launch_cumulants(const CumArgs& a, const CumLaunch& L, cudaStream_t st)
+cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const CumLaunch& L, cudaStream_t st)
 {
-    switch (a.s) {
-    case 1: return launch_order<1>(a, L, st);
-    case 2: return launch_order<2>(a, L, st);
-    case 3: return launch_order<3>(a, L, st);
-    case 4: return launch_order<4>(a, L, st);
-    case 5: return launch_order<5>(a, L, st);
-    case 6: return launch_order<6>(a, L, st);
-    case 7: return launch_order<7>(a, L, st);
-    case 8: return launch_order<8>(a, L, st);
+    switch (s) {
+    case 1: return launch_order<1>(args_dev, nwin, L, st);
+    case 2: return launch_order<2>(args_dev, nwin, L, st);
+    case 3: return launch_order<3>(args_dev, nwin, L, st);
+    case 4: return launch_order<4>(args_dev, nwin, L, st);
+    case 5: return launch_order<5>(args_dev, nwin, L, st);
+    case 6: return launch_order<6>(args_dev, nwin, L, st);
+    case 7: return launch_order<7>(args_dev, nwin, L, st);
+    case 8: return launch_order<8>(args_dev, nwin, L, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_norm_final(const double* normpart, const int32_t* part_off, int d, double* fro2,
-                              int64_t* head, int64_t advance, int64_t T, cudaStream_t st)
+cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, cudaStream_t st)
 {
-    k_norm_final<<<1, 32 * kMaxOrder, 0, st>>>(normpart, part_off, d, fro2, head, advance, T);
+    k_norm_final<<<nwin, 32 * kMaxOrder, 0, st>>>(args_dev, advance);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
-// Moment-sum update on the 5th-generation tensor cores (Eqs. 6-7, Algorithm 2).
+// Moment-sum update on the 5th-generation tensor cores (Eqs. 6-7, Algorithm 2),
+// for one or many independent windows at once.
 //
 // See cw_tc.h for the pipeline.  This file holds the staging kernels, the
-// Khatri-Rao operand builder, the warp-specialized tcgen05 GEMM and the host
-// planner.  Every mbarrier wait is bounded: on a timeout the CTA records
-// kStatusTimeout, drains the copies and MMAs it issued (bounded), frees its
-// tensor memory and returns.
+// Khatri-Rao operand builder, the warp-specialized persistent tcgen05 GEMM,
+// the host planner and the K-split autotuner.  Every mbarrier wait is
+// bounded: on a timeout the CTA records kStatusTimeout, drains the copies and
+// MMAs it issued (bounded), frees its tensor memory and returns.
 #include <climits>
 #include <cstring>
 
@@ -39,35 +40,39 @@ constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 // staging: shifted samples, transposed to [variable][sample]
 // ---------------------------------------------------------------------------
 // Samples [0, P) of the K axis hold X_(+), [P, 2P) hold X_(-), zero beyond p.
-// Each CTA moves a tile of 32 samples x 32 variables through shared memory so
-// that both the row-major reads and the variable-major writes are coalesced;
-// the thread that reads X_(-) from a ring slot also writes X_(+) into it.
+// Each CTA (blockIdx.z = stream) moves a tile of 32 samples x 32 variables
+// through shared memory so that both the row-major reads and the
+// variable-major writes are coalesced; the thread that reads X_(-) from a ring
+// slot also writes X_(+) into it.
 __global__ void __launch_bounds__(256)
-k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __restrict__ x_out,
-                int64_t ld_out, float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p,
-                int p, int P, int n, int npad, const float* __restrict__ shift, float* __restrict__ XT,
-                int64_t Kcap, int* __restrict__ status)
+k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict__ xin_base,
+                const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap)
 {
     __shared__ float tin[32][33], tout[32][33];
-    const int64_t head = *head_p;
+    const TcStreamDesc sd = sdesc[blockIdx.z];
     const int r0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
+    if (v0 >= sd.npad) return;
+    const int64_t head = *sd.head;
+    const int64_t ld = ld_arg < 0 ? sd.n : ld_arg;
+    const float* x_in = xin_base + sd.xoff;
+    const float* x_out = xout_base != nullptr ? xout_base + sd.xoff : nullptr;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
     bool badv = false;
     for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr, v = v0 + tx;
         float xin = 0.0f, xo = 0.0f;
-        if (r < p && v < npad) {
+        if (r < p && v < sd.npad) {
             int64_t slot = head + r;
-            if (slot >= T) slot -= T;
-            const float raw_in = v < n ? x_in[(int64_t)r * ld_in + v] : 0.0f;
+            if (slot >= sd.T) slot -= sd.T;
+            const float raw_in = v < sd.n ? x_in[(int64_t)r * ld + v] : 0.0f;
             float raw_out;
-            if (x_out != nullptr) raw_out = v < n ? x_out[(int64_t)r * ld_out + v] : 0.0f;
-            else raw_out = ring[slot * npad + v];
-            ring[slot * npad + v] = raw_in;
+            if (x_out != nullptr) raw_out = v < sd.n ? x_out[(int64_t)r * ld + v] : 0.0f;
+            else raw_out = sd.ring[slot * sd.npad + v];
+            sd.ring[slot * sd.npad + v] = raw_in;
             badv |= !isfinite(raw_in);
-            if (v < n) {
-                xin = raw_in - shift[v];
-                xo = raw_out - shift[v];
+            if (v < sd.n) {
+                xin = raw_in - sd.shift[v];
+                xo = raw_out - sd.shift[v];
             }
         }
         tin[rr][tx] = xin;
@@ -76,34 +81,34 @@ k_tc_stage_push(const float* __restrict__ x_in, int64_t ld_in, const float* __re
     __syncthreads();
     for (int vv = ty; vv < 32; vv += 8) {
         const int v = v0 + vv, r = r0 + tx;
-        if (v < npad && r < P) {
-            XT[(int64_t)v * Kcap + r] = tin[tx][vv];
-            XT[(int64_t)v * Kcap + P + r] = tout[tx][vv];
+        if (v < sd.npad && r < P) {
+            sd.XT[(int64_t)v * Kcap + r] = tin[tx][vv];
+            sd.XT[(int64_t)v * Kcap + P + r] = tout[tx][vv];
         }
     }
-    if (badv) atomicOr(status, kStatusNonFinite);
+    if (badv) atomicOr(sd.status, kStatusNonFinite);
 }
 
-// Window rows [q*p, q*p + p) (window order, oldest first) into samples [0, P).
+// Window rows [q*p, q*p + p) (window order, oldest first) into samples [0, P);
+// blockIdx.y = stream.
 __global__ void __launch_bounds__(256)
-k_tc_stage_batch(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p,
-                 int q, int p, int P, int n, int npad, const float* __restrict__ shift,
-                 float* __restrict__ XT, int64_t Kcap)
+k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, int64_t Kcap)
 {
-    const int64_t total = (int64_t)npad * P;
-    const int64_t head = *head_p;
+    const TcStreamDesc sd = sdesc[blockIdx.y];
+    const int64_t head = *sd.head;
+    const int64_t total = (int64_t)sd.npad * P;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int v = (int)(e / P);
         const int r = (int)(e - (int64_t)v * P);
         const int64_t w = (int64_t)q * p + r;
         float x = 0.0f;
-        if (r < p && w < T && v < n) {
+        if (r < p && w < sd.T && v < sd.n) {
             int64_t slot = head + w;
-            if (slot >= T) slot -= T;
-            x = ring[slot * npad + v] - shift[v];
+            if (slot >= sd.T) slot -= sd.T;
+            x = sd.ring[slot * sd.npad + v] - sd.shift[v];
         }
-        XT[(int64_t)v * Kcap + r] = x;
+        sd.XT[(int64_t)v * Kcap + r] = x;
     }
 }
 
@@ -114,7 +119,7 @@ k_tc_stage_batch(const float* __restrict__ ring, int64_t T, const int64_t* __res
 // ---------------------------------------------------------------------------
 template <bool BF16>
 __global__ void __launch_bounds__(256)
-k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restrict__ opvars,
+k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t* __restrict__ opvars,
            int64_t rows, int nkb, uint16_t* __restrict__ ops)
 {
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
@@ -125,7 +130,8 @@ k_kr_build(const float* __restrict__ XT, int64_t Kcap, const uint64_t* __restric
         const int kb = e - row * nkb;
         const uint64_t w = opvars[row];
         const uint32_t vars = (uint32_t)w;
-        const int nf = (int)(w >> 32);
+        const int nf = (int)((w >> 32) & 0xffu);
+        const float* XT = sdesc[(int)(w >> 40)].XT;
         float p[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) p[t] = 1.0f;
@@ -337,7 +343,7 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const TcItem item = args.items[u / args.ksplit];
             const int split = u % args.ksplit;
             const UnitRange R = unit_range(args, split);
-            const TcOrder& od = args.ord[item.s];
+            const TcOrder& od = args.ord[item.stream * (kMaxOrder + 1) + item.s];
             const uint32_t ab = it & 1;
             // this warp's copy of the item's row tables
             int64_t* rowoff = s_rowoff[ew];
@@ -389,17 +395,22 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
-// S_s[e] += (double)(sum_k W[k][0][e]) for every order (window batches).
+// S += (double)(sum_k W[k][0][e]) for every (stream, order) segment (window batches).
 __global__ void __launch_bounds__(256)
-k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const TcAccArgs a)
+k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const TcAccSeg* __restrict__ segs,
+                int nsegs)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < wslice;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int s = 1;
-        while (s < a.d && e >= a.Eoff[s + 1]) ++s;
+        int lo = 0, hi = nsegs - 1;  // last segment with begin <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (segs[mid].begin <= e) lo = mid;
+            else hi = mid - 1;
+        }
         float din = 0.0f;
         for (int k = 0; k < ksplit; ++k) din += W[(int64_t)(2 * k) * wslice + e];
-        a.S[s][e - a.Eoff[s]] += f32_to_f64(din);
+        segs[lo].S[e - segs[lo].begin] += f32_to_f64(din);
     }
 }
 
@@ -412,7 +423,7 @@ inline int grid_for(int64_t work)
 cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, cudaStream_t st)
 {
     TcGemmArgs a{};
-    for (int s = 0; s <= kMaxOrder; ++s) a.ord[s] = plan.ord[s];
+    a.ord = plan.ord;
     a.items = plan.items;
     a.W = plan.W;
     a.wslice = plan.wslice;
@@ -424,6 +435,7 @@ cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, 
     a.status = plan.status;
     const int units = plan.nitems * plan.ksplit;
     const int grid = units < plan.sm_count ? units : plan.sm_count;
+    if (grid < 1) return cudaSuccess;
     if (plan.precision == 1)
         k_kr_gemm<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
                                                                 plan.mapB[2], a);
@@ -438,10 +450,10 @@ cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
     const int nkb = nsamples / 8;
     const int64_t work = plan.oprows * nkb;
     if (plan.precision == 1)
-        k_kr_build<true><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
+        k_kr_build<true><<<grid_for(work), 256, 0, st>>>(plan.sdesc, plan.Kcap, plan.opvars, plan.oprows,
                                                          nkb, plan.ops);
     else
-        k_kr_build<false><<<grid_for(work), 256, 0, st>>>(plan.XT, plan.Kcap, plan.opvars, plan.oprows,
+        k_kr_build<false><<<grid_for(work), 256, 0, st>>>(plan.sdesc, plan.Kcap, plan.opvars, plan.oprows,
                                                           nkb, plan.ops);
     return cudaGetLastError();
 }
@@ -499,133 +511,167 @@ double item_chunk_cost(int nrows)
 
 }  // namespace
 
-int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const UpdateArgs& upd,
-                   const int64_t* Eoff, int d, int n, int b, int npad, int64_t T, int p,
-                   int sm_count, int precision, int* status, const DevAlloc& alloc)
+int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
+                   int precision, int* status, const DevAlloc& alloc)
 {
-    (void)n;
     (void)b;
-    (void)upd;
     plan.precision = precision;
-    plan.npad = npad;
-    plan.T = T;
+    plan.nstreams = (int)streams.size();
     plan.p = p;
     plan.P = (p + KC - 1) / KC * KC;
-    plan.nbatch = (int)((T + p - 1) / p);
     plan.Kcap = 2 * (int64_t)plan.P;
     plan.status = status;
     plan.sm_count = sm_count;
+    if (plan.nstreams < 1 || plan.nstreams > (1 << 20)) return (int)cudaErrorInvalidValue;
 
-    cudaError_t e = alloc(sizeof(float) * (size_t)npad * plan.Kcap, (void**)&plan.XT);
+    // per-stream staging buffers and descriptors
+    std::vector<TcStreamDesc> sdesc(plan.nstreams);
+    plan.nbatch = 0;
+    plan.nbatch_stream.assign(plan.nstreams, 0);
+    for (int i = 0; i < plan.nstreams; ++i) {
+        const TcPlanStream& S = streams[i];
+        TcStreamDesc& sd = sdesc[i];
+        cudaError_t e = alloc(sizeof(float) * (size_t)S.npad * plan.Kcap, (void**)&sd.XT);
+        if (e != cudaSuccess) return (int)e;
+        e = cudaMemset(sd.XT, 0, sizeof(float) * (size_t)S.npad * plan.Kcap);
+        if (e != cudaSuccess) return (int)e;
+        sd.ring = S.ring;
+        sd.head = S.head;
+        sd.shift = S.shift;
+        sd.status = S.status;
+        sd.T = S.T;
+        sd.xoff = S.xoff;
+        sd.n = S.n;
+        sd.npad = S.npad;
+        plan.npad_max = std::max(plan.npad_max, S.npad);
+        plan.nbatch_stream[i] = (int)((S.T + p - 1) / p);
+        plan.nbatch = std::max(plan.nbatch, plan.nbatch_stream[i]);
+    }
+    cudaError_t e = alloc(sizeof(TcStreamDesc) * sdesc.size(), (void**)&plan.sdesc);
     if (e != cudaSuccess) return (int)e;
-    e = cudaMemset(plan.XT, 0, sizeof(float) * (size_t)npad * plan.Kcap);
+    e = cudaMemcpy(plan.sdesc, sdesc.data(), sizeof(TcStreamDesc) * sdesc.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return (int)e;
 
-    // operand sets: key (factors, grouped?) -> first row; singles and the
-    // empty product have one ordering
-    std::map<std::pair<int, int>, int64_t> setoff;
+    // operand sets per stream: key (factors, grouped?) -> first row; singles
+    // and the empty product have one ordering
     std::vector<uint64_t> opvars;
-    auto add_set = [&](int k, int grouped, const std::vector<uint32_t>& vars) -> int64_t {
-        const std::pair<int, int> key(k, k <= 1 ? 0 : grouped);
-        auto it = setoff.find(key);
-        if (it != setoff.end()) return it->second;
-        const int64_t off = (int64_t)opvars.size();
-        for (uint32_t v : vars) opvars.push_back((uint64_t)v | ((uint64_t)k << 32));
-        // pad each set to a multiple of 8 rows so boxes of later sets stay aligned
-        while (opvars.size() % 8) opvars.push_back(0);
-        setoff[key] = off;
-        return off;
-    };
-
     std::vector<TcItem> items;
+    std::vector<TcOrder> ord((size_t)plan.nstreams * (kMaxOrder + 1));
+    plan.wbase.assign(plan.nstreams, 0);
+    int64_t wtot = 0;
     double useful = 0, issued = 0;
-    for (int s = 1; s <= d; ++s) {
-        const UpdateTables& t = tables[s];
-        const OrderTables& ot = upd.ord[s];
-        TcOrder& o = plan.ord[s];
-        o.rowoff = ot.rowoff;
-        o.coloff = ot.coloff;
-        o.woff = Eoff[s];
-        const int64_t loff = add_set(t.h, 1, t.rowvar);
-        const int64_t roff = add_set(t.sh, 0, t.colvar);
-        const int nbar = (int)t.colstart.size();
-        const int ncols = (int)t.colvar.size();
-        std::vector<int32_t> colmin(t.rowvar.size());
-        for (int m = 0; m < nbar; ++m)
-            for (int r = t.rowstart[m]; r < t.rowstart[m + 1]; ++r) colmin[r] = t.colstart[m];
-        int32_t* dcm = nullptr;
-        e = alloc(sizeof(int32_t) * std::max<size_t>(colmin.size(), 1), (void**)&dcm);
-        if (e != cudaSuccess) return (int)e;
-        e = cudaMemcpy(dcm, colmin.data(), sizeof(int32_t) * colmin.size(), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return (int)e;
-        o.rowcolmin = dcm;
-
-        // row ranges: groups larger than NMAX rows are split; consecutive small
-        // groups are merged (invalid pairs are masked) while that lowers the
-        // modelled cost
-        struct Range { int r0, r1, c0; };
-        std::vector<Range> ranges;
-        for (int m = 0; m < nbar; ++m) {
-            const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
-            if (r1 <= r0 || t.colstart[m] >= ncols) continue;
-            for (int r = r0; r < r1; r += NMAX) ranges.push_back({r, std::min(r1, r + NMAX), t.colstart[m]});
-        }
-        auto cost = [&](const Range& R) {
-            const int span = ncols - R.c0;
-            return ((span + TM - 1) / TM) * item_chunk_cost(R.r1 - R.r0);
+    for (int i = 0; i < plan.nstreams; ++i) {
+        const TcPlanStream& S = streams[i];
+        std::map<std::pair<int, int>, int64_t> setoff;
+        auto add_set = [&](int k, int grouped, const std::vector<uint32_t>& vars) -> int64_t {
+            const std::pair<int, int> key(k, k <= 1 ? 0 : grouped);
+            auto it = setoff.find(key);
+            if (it != setoff.end()) return it->second;
+            const int64_t off = (int64_t)opvars.size();
+            for (uint32_t v : vars)
+                opvars.push_back((uint64_t)v | ((uint64_t)k << 32) | ((uint64_t)i << 40));
+            setoff[key] = off;
+            return off;
         };
-        std::vector<Range> merged;
-        for (const Range& R : ranges) {
-            if (!merged.empty()) {
-                Range& L = merged.back();
-                if (L.r1 == R.r0 && R.r1 - L.r0 <= NMAX) {
-                    Range M{L.r0, R.r1, L.c0};
-                    if (cost(M) <= cost(L) + cost(R)) {
-                        L = M;
-                        continue;
+        plan.wbase[i] = wtot;
+        for (int s = 1; s <= S.d; ++s) {
+            const UpdateTables& t = (*S.tables)[s];
+            const OrderTables& ot = S.upd->ord[s];
+            TcOrder& o = ord[(size_t)i * (kMaxOrder + 1) + s];
+            o.rowoff = ot.rowoff;
+            o.coloff = ot.coloff;
+            o.woff = wtot + S.Eoff[s];
+            const int64_t loff = add_set(t.h, 1, t.rowvar);
+            const int64_t roff = add_set(t.sh, 0, t.colvar);
+            const int nbar = (int)t.colstart.size();
+            const int ncols = (int)t.colvar.size();
+            std::vector<int32_t> colmin(t.rowvar.size());
+            for (int m = 0; m < nbar; ++m)
+                for (int r = t.rowstart[m]; r < t.rowstart[m + 1]; ++r) colmin[r] = t.colstart[m];
+            int32_t* dcm = nullptr;
+            e = alloc(sizeof(int32_t) * std::max<size_t>(colmin.size(), 1), (void**)&dcm);
+            if (e != cudaSuccess) return (int)e;
+            e = cudaMemcpy(dcm, colmin.data(), sizeof(int32_t) * colmin.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return (int)e;
+            o.rowcolmin = dcm;
+
+            // row ranges: groups larger than NMAX rows are split; consecutive small
+            // groups are merged (invalid pairs are masked) while that lowers the
+            // modelled cost
+            struct Range { int r0, r1, c0; };
+            std::vector<Range> ranges;
+            for (int m = 0; m < nbar; ++m) {
+                const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
+                if (r1 <= r0 || t.colstart[m] >= ncols) continue;
+                for (int r = r0; r < r1; r += NMAX) ranges.push_back({r, std::min(r1, r + NMAX), t.colstart[m]});
+            }
+            auto cost = [&](const Range& R) {
+                const int span = ncols - R.c0;
+                return ((span + TM - 1) / TM) * item_chunk_cost(R.r1 - R.r0);
+            };
+            std::vector<Range> merged;
+            for (const Range& R : ranges) {
+                if (!merged.empty()) {
+                    Range& L = merged.back();
+                    if (L.r1 == R.r0 && R.r1 - L.r0 <= NMAX) {
+                        Range M{L.r0, R.r1, L.c0};
+                        if (cost(M) <= cost(L) + cost(R)) {
+                            L = M;
+                            continue;
+                        }
                     }
                 }
+                merged.push_back(R);
             }
-            merged.push_back(R);
-        }
-        for (const Range& R : merged) {
-            for (int c = R.c0; c < ncols; c += TM) {
-                TcItem it{};
-                it.s = s;
-                it.row0 = R.r0;
-                it.nrows = R.r1 - R.r0;
-                it.col0 = c;
-                it.ncols = std::min(TM, ncols - c);
-                it.brow = (int32_t)(loff + R.r0);
-                it.acol = (int32_t)(roff + c);
-                it.bbox = b_box_rows(it.nrows);
-                items.push_back(it);
-                issued += 3.0 * TM * ((it.nrows + 15) & ~15);
+            for (const Range& R : merged) {
+                for (int c = R.c0; c < ncols; c += TM) {
+                    TcItem it{};
+                    it.s = s;
+                    it.row0 = R.r0;
+                    it.nrows = R.r1 - R.r0;
+                    it.col0 = c;
+                    it.ncols = std::min(TM, ncols - c);
+                    it.brow = (int32_t)(loff + R.r0);
+                    it.acol = (int32_t)(roff + c);
+                    it.bbox = b_box_rows(it.nrows);
+                    it.stream = i;
+                    items.push_back(it);
+                    issued += 3.0 * TM * ((it.nrows + 15) & ~15);
+                }
+                for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, ncols - colmin[r]);
             }
-            for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, ncols - colmin[r]);
         }
+        wtot += S.Eoff[S.d + 1];
     }
-    // larger items first
+    plan.wslice = wtot;
+    // larger items first, then round-robin over the persistent CTAs
     std::stable_sort(items.begin(), items.end(),
                      [](const TcItem& x, const TcItem& y) { return x.nrows > y.nrows; });
     plan.useful_macs_per_sample = useful;
     plan.issued_macs_per_sample = issued;
     plan.nitems = (int)items.size();
-    // K-splits: a few units per persistent CTA, at least 2 chunks per split
+
+    // K-splits: a few units per persistent CTA, at least 2 chunks per split,
+    // the workspace (2 x ksplit x wslice floats) within 256 MB
     const int chunks = plan.P / KC;
-    const int target = 3 * sm_count;
-    int ks = (target + plan.nitems - 1) / std::max(1, plan.nitems);
-    ks = std::max(1, std::min(ks, std::max(1, chunks / 2)));
-    plan.ksplit = ks;
+    int64_t kmem = ((int64_t)256 << 20) / std::max<int64_t>(1, 8 * plan.wslice);
+    plan.ksplit_max = (int)std::max<int64_t>(1, std::min<int64_t>(kmem, std::max(1, chunks / 2)));
+    int ks = (3 * sm_count + plan.nitems - 1) / std::max(1, plan.nitems);
+    plan.ksplit = std::max(1, std::min(ks, plan.ksplit_max));
 
     e = alloc(sizeof(TcItem) * std::max<size_t>(items.size(), 1), (void**)&plan.items);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return (int)e;
+    e = alloc(sizeof(TcOrder) * ord.size(), (void**)&plan.ord);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaMemcpy(plan.ord, ord.data(), sizeof(TcOrder) * ord.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return (int)e;
 
     // operand array and its tensor maps
     plan.oprows = (int64_t)opvars.size();
-    if (plan.oprows * (plan.Kcap / 8) >= ((int64_t)1 << 31)) return (int)cudaErrorInvalidValue;
+    if (plan.oprows * (plan.Kcap / 8) >= ((int64_t)1 << 31) || plan.oprows >= ((int64_t)1 << 31))
+        return (int)cudaErrorInvalidValue;
     e = alloc(sizeof(uint64_t) * opvars.size(), (void**)&plan.opvars);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.opvars, opvars.data(), sizeof(uint64_t) * opvars.size(), cudaMemcpyHostToDevice);
@@ -637,16 +683,15 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
     if (e != cudaSuccess) return (int)e;
     int rc = encode_operand_map(&plan.mapA, plan.ops, plan.oprows, plan.Kcap, TM);
     if (rc) return rc;
-    for (int i = 0; i < 3; ++i) {
-        rc = encode_operand_map(&plan.mapB[i], plan.ops, plan.oprows, plan.Kcap, 32 << i);
+    for (int k = 0; k < 3; ++k) {
+        rc = encode_operand_map(&plan.mapB[k], plan.ops, plan.oprows, plan.Kcap, 32 << k);
         if (rc) return rc;
     }
 
-    // workspace
-    plan.wslice = Eoff[d + 1];
-    e = alloc(sizeof(float) * 2 * (size_t)plan.ksplit * plan.wslice, (void**)&plan.W);
+    // workspace for the largest K-split the autotuner may pick
+    e = alloc(sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice, (void**)&plan.W);
     if (e != cudaSuccess) return (int)e;
-    e = cudaMemset(plan.W, 0, sizeof(float) * 2 * (size_t)plan.ksplit * plan.wslice);
+    e = cudaMemset(plan.W, 0, sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice);
     if (e != cudaSuccess) return (int)e;
 
     e = cudaFuncSetAttribute(k_kr_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
@@ -657,14 +702,12 @@ int tc_plan_create(TcPlan& plan, const std::vector<UpdateTables>& tables, const 
     return 0;
 }
 
-cudaError_t tc_stage_push(const TcPlan& plan, const float* x_in, int64_t ld_in, const float* x_out,
-                          int64_t ld_out, float* ring, const int64_t* head, int p, int n,
-                          const float* shift, cudaStream_t st)
+cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
+                          cudaStream_t st)
 {
     if (p > plan.p) return cudaErrorInvalidValue;
-    const dim3 grid((plan.P + 31) / 32, (plan.npad + 31) / 32);
-    k_tc_stage_push<<<grid, 256, 0, st>>>(x_in, ld_in, x_out, ld_out, ring, plan.T, head, p, plan.P, n,
-                                          plan.npad, shift, plan.XT, plan.Kcap, plan.status);
+    const dim3 grid((plan.P + 31) / 32, (plan.npad_max + 31) / 32, plan.nstreams);
+    k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_build(plan, 2 * plan.P, st);
@@ -675,11 +718,10 @@ cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st)
     return launch_gemm(plan, plan.P / KC, plan.P / KC, plan.P, st);
 }
 
-cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const int64_t* head, int q,
-                                   int n, const float* shift, cudaStream_t st)
+cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
 {
-    k_tc_stage_batch<<<grid_for((int64_t)plan.npad * plan.P), 256, 0, st>>>(
-        ring, plan.T, head, q, plan.p, plan.P, n, plan.npad, shift, plan.XT, plan.Kcap);
+    const int gx = std::max(1, std::min(64, (plan.npad_max * plan.P + 255) / 256));
+    k_tc_stage_batch<<<dim3(gx, plan.nstreams), 256, 0, st>>>(plan.sdesc, q, plan.p, plan.P, plan.Kcap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_build(plan, plan.P, st);
@@ -687,10 +729,44 @@ cudaError_t tc_update_window_batch(const TcPlan& plan, const float* ring, const 
     return launch_gemm(plan, plan.P / KC, 0, 0, st);
 }
 
-cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccArgs& a, cudaStream_t st)
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, cudaStream_t st)
 {
-    k_tc_accumulate<<<grid_for(plan.wslice), 256, 0, st>>>(plan.W, plan.wslice, plan.ksplit, a);
+    k_tc_accumulate<<<grid_for(plan.wslice), 256, 0, st>>>(plan.W, plan.wslice, plan.ksplit, segs_dev, nsegs);
     return cudaGetLastError();
+}
+
+int tc_autotune(TcPlan& plan, int reps, cudaStream_t st, double* best_ms)
+{
+    const int chunks = plan.P / KC;
+    int best = plan.ksplit;
+    double best_t = 1e30;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return -(int)cudaErrorUnknown;
+    for (int ks = 1; ks <= plan.ksplit_max && ks <= chunks; ks *= 2) {
+        plan.ksplit = ks;
+        cudaError_t e = launch_gemm(plan, chunks, chunks, plan.P, st);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm(plan, chunks, chunks, plan.P, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return -(int)e;
+        }
+        if (ms < best_t) {
+            best_t = ms;
+            best = ks;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan.ksplit = best;
+    if (best_ms) *best_ms = best_t / std::max(1, reps);
+    return best;
 }
 
 }  // namespace cw

@@ -1,0 +1,153 @@
+"""Batches of independent windows (uneven n, d, T) advanced with one launch per
+phase: every window of a batch matches the oracle within the mixed-form
+bounds, matches a standalone handle on the same data, survives CUDA-graph
+capture and replay, and the K-split autotuner keeps the results."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1701_06446_gb300 import CumWin, CumWinBatch, CumwinError
+from paper_1701_06446_gb300.streams import Stream, batched_streams
+
+pytestmark = pytest.mark.gpu
+
+MIXED_BOUND = {1: 2e-5, 2: 5e-5, 3: 5e-4, 4: 2e-3, 5: 5e-3}
+
+
+def rel_fro(got, ref):
+    return np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+
+
+def make_batch_data(specs, p, steps, seed):
+    data = []
+    for k, (n, d, T) in enumerate(specs):
+        rng = np.random.default_rng(seed + k)
+        A = rng.standard_normal((n, n)) / np.sqrt(n)
+        X = (rng.gamma(2.0, size=(T + steps * p, n)) @ A + 0.3).astype(np.float32)
+        data.append(X)
+    return data
+
+
+SPECS = [(3, 3, 512), (17, 4, 1024), (8, 2, 256), (33, 4, 512), (64, 3, 768), (5, 5, 512), (12, 4, 2048),
+         (40, 3, 256), (1, 4, 512), (70, 4, 512)]
+
+
+def test_batch_matches_oracle_and_standalone_handles():
+    b, p, steps = 4, 64, 3
+    data = make_batch_data(SPECS, p, steps, 100)
+    ns, ds, Ts = zip(*SPECS)
+    with CumWinBatch(ns, ds, Ts, b, p, "bf16") as B:
+        B.fill([torch.from_numpy(X[:T]).cuda() for X, (n, d, T) in zip(data, SPECS)])
+        for k in range(steps):
+            B.push(B.pack([torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda()
+                           for X, (n, d, T) in zip(data, SPECS)]))
+        fro, nu = B.norms()
+        for i, (X, (n, d, T)) in enumerate(zip(data, SPECS)):
+            Xw = X[steps * p: steps * p + T]
+            ref = oracle.cumulants(Xw, d, b)
+            with CumWin(n, d, b, T, p, "bf16") as h:
+                h.fill(torch.from_numpy(X[:T]).cuda())
+                for k in range(steps):
+                    h.push(torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda())
+                for s in range(1, d + 1):
+                    got = B.cumulants(i, s).cpu().numpy()
+                    assert rel_fro(got, ref[s - 1]) <= MIXED_BOUND[s], (i, s, rel_fro(got, ref[s - 1]))
+                    assert rel_fro(got, h.cumulants(s).cpu().numpy()) <= MIXED_BOUND[s]
+                hf, hn = h.norms()
+            assert np.allclose(fro[i, :d], hf, rtol=1e-4)
+            assert np.all(np.isnan(fro[i, d:]))
+
+
+def test_batch_graph_replay_matches_eager():
+    b, p = 4, 64
+    specs = SPECS[:6]
+    data = make_batch_data(specs, p, 8, 200)
+    ns, ds, Ts = zip(*specs)
+    with CumWinBatch(ns, ds, Ts, b, p, "bf16") as eager:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            cap = CumWinBatch(ns, ds, Ts, b, p, "bf16")
+        firsts = [torch.from_numpy(X[:T]).cuda() for X, (n, d, T) in zip(data, specs)]
+        eager.fill(firsts)
+        with torch.cuda.stream(s):
+            cap.fill(firsts)
+        torch.cuda.synchronize()
+        packs = [eager.pack([torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda()
+                             for X, (n, d, T) in zip(data, specs)]) for k in range(8)]
+        buf = packs[0].clone()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                cap.push(buf)
+        torch.cuda.synchronize()
+        for k in range(8):
+            buf.copy_(packs[k])
+            g.replay()
+            eager.push(packs[k])
+        torch.cuda.synchronize()
+        for i, (n, d, T) in enumerate(specs):
+            for order in range(1, d + 1):
+                with torch.cuda.stream(s):
+                    a = cap.cumulants(i, order)
+                torch.cuda.synchronize()
+                assert torch.equal(eager.cumulants(i, order), a)
+        with torch.cuda.stream(s):
+            cap.close()
+
+
+def test_many_streams_workload_sampled():
+    """64 streams drawn like the 512-stream workload (n in 8..64, d in {3,4},
+    T in {2^12, 2^14}, Gaussian or t(4)), b=4, p=256: two shifts, sampled
+    tuples of every window against the oracle."""
+    params = batched_streams(seed=4, count=64)
+    b, p = 4, 256
+    ns = [q["n"] for q in params]
+    ds = [q["d"] for q in params]
+    Ts = [q["T"] for q in params]
+    streams = [Stream(q["kind"], q["n"], q["seed"]) for q in params]
+    with CumWinBatch(ns, ds, Ts, b, p, "bf16") as B:
+        B.fill([torch.from_numpy(st.rows(0, T)).cuda() for st, T in zip(streams, Ts)])
+        for k in range(2):
+            B.push(B.pack([torch.from_numpy(st.rows(T + k * p, T + (k + 1) * p)).cuda()
+                           for st, T in zip(streams, Ts)]))
+        for i in range(0, 64, 7):
+            st, n, d, T = streams[i], ns[i], ds[i], Ts[i]
+            Xw = st.rows(2 * p, 2 * p + T)
+            cen = oracle.center(Xw)
+            for s in range(1, d + 1):
+                tup = oracle.sample_sorted_tuples(n, s, 150, seed=i * 10 + s)
+                idx = np.array([oracle.storage_index(n, b, t) for t in tup])
+                ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
+                got = B.cumulants(i, s).cpu().numpy()[idx]
+                assert rel_fro(got, ref) <= 3 * MIXED_BOUND[s], (i, s, rel_fro(got, ref))
+
+
+def test_autotune_keeps_results():
+    n, d, b, T, p = 30, 4, 3, 4096, 512
+    rng = np.random.default_rng(3)
+    X = rng.standard_t(6, size=(T + 4 * p, n)).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        h.push(Xd[T:T + p])
+        ks = h.tune(reps=3)
+        assert ks >= 1
+        for k in range(1, 4):
+            h.push(Xd[T + k * p: T + (k + 1) * p])
+        ref = oracle.cumulants(X[4 * p:], d, b)
+        for s in range(1, d + 1):
+            assert rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) <= MIXED_BOUND[s]
+        h.recompute()  # in/out sums still cancel after a change of K-split? recompute restores
+        for s in range(1, d + 1):
+            assert rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) <= MIXED_BOUND[s]
+
+
+def test_batch_argument_errors():
+    with pytest.raises(CumwinError):
+        CumWinBatch([4, 5], [3, 3], [64, 64], 2, 8, "fp64")
+    with pytest.raises(CumwinError):
+        CumWinBatch([4, 0], [3, 3], [64, 64], 2, 8, "bf16")
+    with CumWinBatch([4, 5], [3, 2], [64, 80], 2, 8, "bf16") as B:
+        with pytest.raises(CumwinError):
+            B.push(torch.zeros(B.offsets[-1], device="cuda"))  # push before fill
