@@ -286,12 +286,35 @@ def norms(X, d: int) -> tuple[np.ndarray, np.ndarray]:
 # gradient of L = sum_s w_s ||C_s||_F^2 (orders 1..4), closed form
 # ----------------------------------------------------------------------------
 
-def full_central_moments(Y: np.ndarray, s: int) -> np.ndarray:
-    """Full central-moment tensor mu_s = (1/T) sum_t y_t^{(x)s} (plain einsum)."""
-    T = Y.shape[0]
-    letters = "ijklmnop"[:s]
-    spec = ",".join("t" + c for c in letters) + "->" + letters
-    return np.einsum(spec, *([Y] * s), optimize=True) / T
+def _kr(Y: np.ndarray, k: int) -> np.ndarray:
+    """Row-wise Kronecker power: row t holds y_t (x) ... (x) y_t (k factors), first slowest."""
+    out = np.ones((Y.shape[0], 1))
+    for _ in range(k):
+        out = (out[:, :, None] * Y[:, None, :]).reshape(Y.shape[0], -1)
+    return out
+
+
+def full_central_moments(Y: np.ndarray, s: int, chunk: int = 512) -> np.ndarray:
+    """Full central-moment tensor mu_s = (1/T) sum_t y_t^{(x)s}, as the product of
+    the Kronecker powers of orders floor(s/2) and ceil(s/2), summed over row chunks."""
+    T, n = Y.shape
+    s1 = s // 2
+    acc = np.zeros((n ** s1, n ** (s - s1)))
+    for t0 in range(0, T, chunk):
+        Yc = Y[t0:t0 + chunk]
+        acc += _kr(Yc, s1).T @ _kr(Yc, s - s1)
+    return (acc / T).reshape((n,) * s)
+
+
+def _contract_rows(Y: np.ndarray, Cfull: np.ndarray, chunk: int = 512) -> np.ndarray:
+    """out[t, a] = sum_{i2..is} C[a, i2..is] y_{t,i2} ... y_{t,is} (row chunks)."""
+    T, n = Y.shape
+    k = Cfull.ndim - 1
+    Cm = Cfull.reshape(n, n ** k)
+    out = np.empty((T, n))
+    for t0 in range(0, T, chunk):
+        out[t0:t0 + chunk] = _kr(Y[t0:t0 + chunk], k) @ Cm.T
+    return out
 
 
 def full_cumulants_closed_form(X, d: int) -> list[np.ndarray]:
@@ -307,8 +330,8 @@ def full_cumulants_closed_form(X, d: int) -> list[np.ndarray]:
     if d >= 4:
         m2 = out[1]
         m4 = full_central_moments(Y, 4)
-        pair = (np.einsum("ij,kl->ijkl", m2, m2) + np.einsum("ik,jl->ijkl", m2, m2)
-                + np.einsum("il,jk->ijkl", m2, m2))
+        pair = (m2[:, :, None, None] * m2[None, None, :, :] + m2[:, None, :, None] * m2[None, :, None, :]
+                + m2[:, None, None, :] * m2[None, :, :, None])
         out.append(m4 - pair)
     return out
 
@@ -342,11 +365,10 @@ def grad(X, w) -> np.ndarray:
     if d >= 2 and w[2]:
         g += 2.0 * w[2] * (2.0 / T) * (Y @ C[1])
     if d >= 3 and w[3]:
-        g += 2.0 * w[3] * (3.0 / T) * np.einsum("ajk,tj,tk->ta", C[2], Y, Y, optimize=True)
+        g += 2.0 * w[3] * (3.0 / T) * _contract_rows(Y, C[2])
     if d >= 4 and w[4]:
-        D = np.einsum("ijkl,kl->ij", C[3], C[1])
-        g += 2.0 * w[4] * ((4.0 / T) * np.einsum("ajkl,tj,tk,tl->ta", C[3], Y, Y, Y, optimize=True)
-                           - (12.0 / T) * (Y @ D))
+        D = (C[3].reshape(n * n, n * n) @ C[1].reshape(n * n)).reshape(n, n)
+        g += 2.0 * w[4] * ((4.0 / T) * _contract_rows(Y, C[3]) - (12.0 / T) * (Y @ D))
     g = g - g.mean(axis=0, keepdims=True)
     if d >= 1 and w[1]:
         g += 2.0 * w[1] * mu[None, :] / T
