@@ -21,4 +21,34 @@ __device__ __forceinline__ double f32_to_f64(float x)
     return __longlong_as_double((long long)(sign | (e64 << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
+// Sum the K-split partials of one workspace element: slice 2k holds the
+// entering samples' partial k, slice 2k+1 the leaving samples' (stride
+// `wslice` floats).  Loads are issued in groups of four so that several are
+// in flight; the additions run in slice order, so every caller gets the same
+// FP32 sums for the same partials.
+__device__ __forceinline__ void sum_partials(const float* __restrict__ w, int64_t wslice, int ksplit,
+                                             float& din, float& dout)
+{
+    din = 0.0f;
+    dout = 0.0f;
+    int k = 0;
+    for (; k + 4 <= ksplit; k += 4) {
+        float vi[4], vo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vi[j] = w[(int64_t)(2 * (k + j)) * wslice];
+            vo[j] = w[(int64_t)(2 * (k + j) + 1) * wslice];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            din += vi[j];
+            dout += vo[j];
+        }
+    }
+    for (; k < ksplit; ++k) {
+        din += w[(int64_t)(2 * k) * wslice];
+        dout += w[(int64_t)(2 * k + 1) * wslice];
+    }
+}
+
 }  // namespace cw

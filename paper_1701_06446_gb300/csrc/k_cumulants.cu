@@ -111,12 +111,8 @@ __global__ void __launch_bounds__(NT) k_cumulants(const CumArgs* __restrict__ ar
         const int64_t e = blk * bs + off;
         double acc = Ss[e];
         if (a.accum) {
-            float din = 0.0f, dout = 0.0f;
-            const float* w = a.W + a.woff + e;
-            for (int k = 0; k < a.ksplit; ++k) {
-                din += w[(int64_t)(2 * k) * a.wslice];
-                dout += w[(int64_t)(2 * k + 1) * a.wslice];
-            }
+            float din, dout;
+            sum_partials(a.W + a.woff + e, a.wslice, a.ksplit, din, dout);
             acc += f32_to_f64(din) - f32_to_f64(dout);
             Ss[e] = acc;
         }
@@ -159,7 +155,15 @@ __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance)
     if (s >= a.d) return;
     double z = 0.0;
     const double* part = a.normpart + (int64_t)s * a.parts;
-    for (int q = lane; q < a.parts; q += 32) z += part[q];
+    int q = lane;
+    for (; q + 96 < a.parts; q += 128) {  // four loads in flight, added in index order
+        const double v0 = part[q], v1 = part[q + 32], v2 = part[q + 64], v3 = part[q + 96];
+        z += v0;
+        z += v1;
+        z += v2;
+        z += v3;
+    }
+    for (; q < a.parts; q += 32) z += part[q];
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
     if (lane == 0) a.fro2[s] = z;
 }

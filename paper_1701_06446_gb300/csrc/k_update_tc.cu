@@ -409,7 +409,15 @@ k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const T
             else hi = mid - 1;
         }
         float din = 0.0f;
-        for (int k = 0; k < ksplit; ++k) din += W[(int64_t)(2 * k) * wslice + e];
+        int k = 0;
+        for (; k + 4 <= ksplit; k += 4) {  // four loads in flight, added in slice order
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = W[(int64_t)(2 * (k + j)) * wslice + e];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) din += v[j];
+        }
+        for (; k < ksplit; ++k) din += W[(int64_t)(2 * k) * wslice + e];
         segs[lo].S[e - segs[lo].begin] += f32_to_f64(din);
     }
 }
@@ -656,8 +664,11 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     const int chunks = plan.P / KC;
     int64_t kmem = ((int64_t)256 << 20) / std::max<int64_t>(1, 8 * plan.wslice);
     plan.ksplit_max = (int)std::max<int64_t>(1, std::min<int64_t>(kmem, std::max(1, chunks / 2)));
-    int ks = (3 * sm_count + plan.nitems - 1) / std::max(1, plan.nitems);
-    plan.ksplit = std::max(1, std::min(ks, plan.ksplit_max));
+    // default: the largest power of two keeping about three units per CTA
+    // (powers of two divide the chunk count, so no split is left empty)
+    int ks = 1;
+    while (2 * ks <= plan.ksplit_max && (int64_t)plan.nitems * 2 * ks <= 3LL * sm_count) ks *= 2;
+    plan.ksplit = ks;
 
     e = alloc(sizeof(TcItem) * std::max<size_t>(items.size(), 1), (void**)&plan.items);
     if (e != cudaSuccess) return (int)e;
