@@ -49,12 +49,14 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def algorithmic_flops(W) -> dict:
-    """Flops of one shift: update 2 * (2p) * E_s per order (one product per
-    multiply-add), recovery 2 * (2^{s-1} - 1) * E_s (one multiply-add per
-    subset term)."""
+def algorithmic_flops(W, fifo: bool = False) -> dict:
+    """Flops of one shift: update 2 * K * E_s per order (one product per
+    multiply-add) with K = 2p samples (entering and leaving), or K = p when
+    the leaving batch's sums come from the batch-sum FIFO; recovery
+    2 * (2^{s-1} - 1) * E_s (one multiply-add per subset term)."""
     from paper_1701_06446_gb300 import layout_size
-    upd = sum(2.0 * 2 * W.p * layout_size(W.n, W.b, s) for s in range(1, W.d + 1))
+    K = W.p if fifo else 2 * W.p
+    upd = sum(2.0 * K * layout_size(W.n, W.b, s) for s in range(1, W.d + 1))
     rec = sum(2.0 * (2 ** (s - 1) - 1) * layout_size(W.n, W.b, s) for s in range(2, W.d + 1))
     return {"update": upd, "recovery": rec}
 
@@ -296,7 +298,8 @@ def run_ours(args, W, rank: int, world: int):
     if rank != 0:
         h.close()
         return
-    flops = algorithmic_flops(W)
+    fifo = bool(h.fifo)
+    flops = algorithmic_flops(W, fifo)
     peaks, peak_kind = _peaks()
     upd_ms = timing["update_ms"] / max(timing["shifts"], 1)
     rec_ms = timing["cumulant_ms"] / max(timing["shifts"], 1)
@@ -315,8 +318,9 @@ def run_ours(args, W, rank: int, world: int):
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_kind": f"{peak_kind} bf16 sustained (of measured)",
                 "traffic": None, "avg_launch_ms": upd_ms,
-                "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x 2p x E_s summed over "
-                              f"orders); the tensor pipe issues 3x (hi*hi + hi*lo + lo*hi)"}
+                "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x K x E_s summed over "
+                              f"orders, K = {'p: entering samples; leaving sums from the FIFO' if fifo else '2p'}); "
+                              f"the tensor pipe issues 3x (hi*hi + hi*lo + lo*hi)"}
     cpu = None
     fp64_form = None
     if precision != "fp64" and args.fp64_steps > 0:
@@ -331,7 +335,7 @@ def run_ours(args, W, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if precision == "fp64" else f"{precision}x3+f32acc+f64sum",
-        "data": "synthetic", "config": dict(config_of(W, precision), ksplit=ksplit),
+        "data": "synthetic", "config": dict(config_of(W, precision), ksplit=ksplit, fifo=fifo),
         "samples_per_s": value * W.p,
         "tflops": flops["update"] / (ms_per_step * 1e-3) / 1e12,
         "stage_ms": stg_ms, "update_ms": upd_ms, "recovery_ms": rec_ms,

@@ -116,8 +116,22 @@ int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx);
  * momentsupdate in Algorithm 2); the ring buffer is still advanced with x_in.
  * Requires 1 <= p <= T and a prior cumulant fill.  Errors: EINVAL, ESTATE.
  * Allocates nothing and does not synchronise (capturable into a CUDA graph).
+ *
+ * Mixed forms with T a multiple of the nominal p: the handle keeps a FIFO of
+ * the T/p batch sums (FP32, sum_s E_s each), the alternative scheme of
+ * Section 2.4, filled by cumwin_fill / cumwin_recompute.  A shift of exactly
+ * p rows with x_out_dev == NULL then subtracts the leaving batch's stored sum
+ * instead of recomputing it (half the tensor-core work); the result is bitwise
+ * the one of the recomputing form.  Any other shift (x_out_dev != NULL or
+ * fewer rows) recomputes X_(-) and retires the FIFO until the next fill or
+ * recompute.
  */
 int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p, int64_t ld);
+
+/* 1 when the next shift of the nominal p rows (x_out_dev == NULL) will use
+ * the batch-sum FIFO of cumwin_push, 0 when it recomputes X_(-) (FP64 form,
+ * T not a multiple of p, no room for the FIFO, or it was retired), EINVAL. */
+int cumwin_fifo(cumwin_t h);
 
 /*
  * As cumwin_push with X_(+) in HOST memory (pinned memory gives an
@@ -234,6 +248,10 @@ int cumwin_batch_norms(cumwin_batch_t B, double* fro_host, double* nu_host);
 
 /* Autotune the batch's update GEMM (as cumwin_tune). */
 int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out);
+
+/* 1 when the batch's shifts use the batch-sum FIFO (every T[i] a multiple of
+ * p and room for it, see cumwin_push), 0 otherwise, EINVAL. */
+int cumwin_batch_fifo(cumwin_batch_t B);
 
 /* Sticky device status over all windows (synchronises). */
 int cumwin_batch_status(cumwin_batch_t B);

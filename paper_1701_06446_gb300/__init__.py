@@ -212,6 +212,13 @@ class CumWin:
         check(self.lib.cumwin_tune(self._h, reps, ctypes.byref(ks)), "cumwin_tune")
         return ks.value
 
+    @property
+    def fifo(self) -> bool:
+        """True when the next nominal shift uses the batch-sum FIFO (see cumwin_push)."""
+        r = int(self.lib.cumwin_fifo(self._h))
+        check(min(r, 0), "cumwin_fifo")
+        return r == 1
+
     def status(self) -> int:
         self._sync_stream()
         return int(self.lib.cumwin_status(self._h))
@@ -305,6 +312,13 @@ class CumWinBatch:
         ks = ctypes.c_int()
         check(self.lib.cumwin_batch_tune(self._h, reps, ctypes.byref(ks)), "cumwin_batch_tune")
         return ks.value
+
+    @property
+    def fifo(self) -> bool:
+        """True when the batch's shifts use the batch-sum FIFO."""
+        r = int(self.lib.cumwin_batch_fifo(self._h))
+        check(min(r, 0), "cumwin_batch_fifo")
+        return r == 1
 
     def status(self) -> int:
         return int(self.lib.cumwin_batch_status(self._h))

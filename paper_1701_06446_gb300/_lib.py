@@ -39,6 +39,7 @@ SIGNATURES = {
     "cumwin_get_timing": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "cumwin_block_norm2_noalloc": (c_int, [c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "cumwin_tune": (c_int, [c_vp, c_int, c_vp]),
+    "cumwin_fifo": (c_int, [c_vp]),
     "cumwin_batch_create": (c_int, [c_int, c_vp, c_vp, c_vp, c_int, c_int, c_int, c_vp, _handle_p]),
     "cumwin_batch_destroy": (c_int, [c_vp]),
     "cumwin_batch_fill": (c_int, [c_vp, c_vp]),
@@ -47,6 +48,7 @@ SIGNATURES = {
     "cumwin_batch_cumulants": (c_int, [c_vp, c_int, c_int, c_vp]),
     "cumwin_batch_norms": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_batch_tune": (c_int, [c_vp, c_int, c_vp]),
+    "cumwin_batch_fifo": (c_int, [c_vp]),
     "cumwin_batch_status": (c_int, [c_vp]),
     "cumwin_layout_size": (c_i64, [c_int, c_int, c_int]),
     "cumwin_block_rank": (c_i64, [c_int, c_int, c_int, c_vp]),

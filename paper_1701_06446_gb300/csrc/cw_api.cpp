@@ -75,6 +75,14 @@ struct Arena {
 
 void cw::set_last_error(const std::string& msg) { g_last_error = msg; }
 
+// Fused recovery of orders 1..dfused (see FusedRecovery); dfused = 0 when the
+// device cannot run the cooperative launch, and one launch per order is used.
+struct FusedPlan {
+    FusedRecovery f{};
+    int dfused = 0, grid = 0;
+    size_t smem = 0;
+};
+
 struct cumwin_s {
     int n = 0, d = 0, b = 0, nbar = 0, npad = 0, prec = 0;
     int64_t T = 0;
@@ -83,6 +91,7 @@ struct cumwin_s {
     int device = 0, sm_count = 0;
     int64_t* head = nullptr;  // device: ring slot of the oldest sample
     bool filled = false;
+    bool fifo_valid = false;  // the batch-sum FIFO matches the window (mixed forms)
     Arena mem;
 
     float* ring = nullptr;   // [T][npad] raw samples
@@ -103,10 +112,12 @@ struct cumwin_s {
     TcPlan tc_own{};
     TcPlan* tc = nullptr;
 
-    // recovery: host arguments per order, device copies [2][order] (accumulate off / on)
+    // recovery: host arguments per order, device copies [kAccModes][order]
+    // (no workspace / stacked in-out workspace / FIFO)
     CumArgs cum[kMaxOrder + 1]{};
     CumArgs* cum_dev = nullptr;
     CumLaunch cum_launch[kMaxOrder + 1] = {};
+    FusedPlan fused;
     int parts = 0;  // norm partial slots per order
     double* normpart = nullptr;
     double* fro2 = nullptr;
@@ -158,6 +169,7 @@ struct cumwin_s {
 
 struct cumwin_batch_s {
     int nwin = 0, b = 0, p = 0, prec = 0, dmax = 0;
+    bool fifo = false;  // regular pushes use the batch-sum FIFO
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     bool filled = false;
@@ -166,8 +178,9 @@ struct cumwin_batch_s {
     Arena mem;
     TcPlan tc{};
     int* status = nullptr;
-    CumArgs* cum_dev = nullptr;  // [2][kMaxOrder + 1][nwin]
+    CumArgs* cum_dev = nullptr;  // [kAccModes][kMaxOrder + 1][nwin]
     CumLaunch cum_launch[kMaxOrder + 1] = {};
+    FusedPlan fused;
     NormArgs* norm_dev = nullptr;
     double* fro2 = nullptr;      // [nwin][dmax]
     TcAccSeg* segs = nullptr;
@@ -338,6 +351,12 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         for (int u = 0; u < ct.nsub && u < 128; ++u) a.mask[u] = ct.masks[u];
         a.W = nullptr;
         a.accum = 0;
+        a.bR = (int32_t)ipow(b, s - split_rows(s));
+        if (precision != CUMWIN_FP64) {
+            int32_t* wb = nullptr;
+            CW_TRY(h->upload(&wb, build_w_blocks(h->ut[s], n, b)));
+            a.wblk = wb;
+        }
         h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
     }
     CW_TRY(h->alloc(&h->fro2, d));
@@ -357,7 +376,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         ps.shift = h->shift;
         ps.status = h->status;
         ps.xoff = 0;
-        int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status,
+        int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status, true,
                                 [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
         if (rc != 0) {
             g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
@@ -369,28 +388,34 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
 }
 
 // Norm partial slots and the device copies of the recovery arguments of a
-// window: `parts` slots per order, workspace slice `wbase` of plan `tc`.
-int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int64_t wbase)
+// window: `parts` slots per order, stream `index` of plan `tc`.
+int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int index)
 {
     h->parts = parts;
     CW_TRY(h->alloc(&h->normpart, (size_t)parts * h->d));
     CW_TRY(cudaMemset(h->normpart, 0, sizeof(double) * (size_t)parts * h->d));
-    CumArgs arr[2][kMaxOrder + 1] = {};
+    CumArgs arr[kAccModes][kMaxOrder + 1] = {};
     for (int s = 1; s <= h->d; ++s) {
         CumArgs& a = h->cum[s];
         a.normpart = h->normpart + (size_t)(s - 1) * parts;
         if (tc != nullptr) {
             a.W = tc->W;
             a.wslice = tc->wslice;
-            a.woff = wbase + h->Eoff[s];
+            a.woff = tc->wbase[index] + h->Eoff[s];
             a.ksplit = tc->ksplit;
+            if (tc->fifo != nullptr) {
+                a.fifo = tc->fifo + tc->fbase[index] + h->Eoff[s];
+                a.fstride = h->Eoff[h->d + 1];
+                a.head = h->head;
+                a.p = h->p;
+            }
         }
-        arr[0][s] = a;
-        arr[1][s] = a;
-        arr[0][s].accum = 0;
-        arr[1][s].accum = 1;
+        for (int m = 0; m < kAccModes; ++m) {
+            arr[m][s] = a;
+            arr[m][s].accum = m;
+        }
     }
-    CW_TRY(h->mem.upload(&h->cum_dev, &arr[0][0], 2 * (kMaxOrder + 1)));
+    CW_TRY(h->mem.upload(&h->cum_dev, &arr[0][0], kAccModes * (kMaxOrder + 1)));
     NormArgs na{};
     na.normpart = h->normpart;
     na.fro2 = h->fro2;
@@ -402,15 +427,89 @@ int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int64_t wbase)
     return CUMWIN_OK;
 }
 
-// Recovery of C_1..C_d and norms.  accum: fold the tensor-core workspace of
-// the shift into the sums first (mixed forms, after a push).
-int run_cumulants(cumwin_t h, int64_t advance, bool accum = false)
+// Work units of the fused recovery over the windows `wins` (shared b), the
+// barrier state and the norm partials; leaves fp.dfused = 0 when the device
+// cannot run it.
+int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm_count,
+                const NormArgs* norm_dev, int* status, Arena& mem)
 {
-    for (int s = 1; s <= h->d; ++s)
-        CW_TRY(launch_cumulants(s, h->cum_dev + (accum ? kMaxOrder + 1 : 0) + s, 1, h->cum_launch[s],
-                                h->stream));
-    CW_TRY(launch_norm_final(h->norm_dev, 1, advance, h->stream));
-    h->launches += h->d + 1;
+    int dmax = 0, device = 0, coop = 0;
+    for (const cumwin_s* h : wins) dmax = std::max(dmax, h->d);
+    CW_TRY(cudaGetDevice(&device));
+    CW_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    fp.dfused = 0;
+    if (!coop) return CUMWIN_OK;
+    const int df = std::min(dmax, kFusedMax);
+    const int nwin = (int)wins.size();
+    FusedRecovery& f = fp.f;
+    f.nwin = nwin;
+    std::vector<int64_t> ustart((size_t)(kFusedMax + 1) * (nwin + 1), 0);
+    int64_t utot = 0;
+    for (int s = 1; s <= df; ++s) {
+        int64_t nbmax = 0;
+        for (const cumwin_s* h : wins)
+            if (s <= h->d) nbmax = std::max<int64_t>(nbmax, n_sorted(h->nbar, s));
+        const CumLaunch L = plan_cumulants(s, (int)ipow(b, s), nbmax, sm_count);
+        f.slots[s] = L.slots;
+        f.gy[s] = L.gy;
+        f.upoff[s] = utot;
+        int64_t* us = &ustart[(size_t)s * (nwin + 1)];
+        for (int w = 0; w < nwin; ++w) {
+            const cumwin_s* h = wins[w];
+            const int64_t nb = s <= h->d ? n_sorted(h->nbar, s) : 0;
+            us[w + 1] = us[w] + (nb + L.slots - 1) / L.slots * L.gy;
+        }
+        utot += us[nwin];
+    }
+    fp.smem = fused_smem_bytes(f, df);
+    fp.grid = fused_grid(df, fp.smem, sm_count);
+    if (fp.grid < 1) return CUMWIN_OK;
+    int64_t* dus = nullptr;
+    CW_TRY(mem.upload(&dus, ustart));
+    f.ustart = dus;
+    CW_TRY(mem.alloc(&f.upart, (size_t)std::max<int64_t>(utot, 1)));
+    CW_TRY(mem.alloc(&f.bar, 2));
+    CW_TRY(cudaMemset(f.bar, 0, 2 * sizeof(unsigned)));
+    f.norm = norm_dev;
+    f.status = status;
+    fp.dfused = df;
+    return CUMWIN_OK;
+}
+
+// Recovery of orders 1..d and norms of the windows of `fp` / `cum_dev`
+// ([mode][order][nwin]); accum: how the tensor-core workspace of the shift is
+// folded into the sums first (CumArgs::accum; 0 = it is not).  Returns the
+// number of launches through *launches.
+int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_launch, const NormArgs* norm_dev,
+            int nwin, int d, int64_t advance, int accum, cudaStream_t st, int64_t* launches)
+{
+    const CumArgs* args = cum_dev + (size_t)accum * (kMaxOrder + 1) * nwin;
+    int s0 = 1;
+    if (fp.dfused > 0) {
+        FusedRecovery f = fp.f;
+        f.args = args;
+        f.advance = advance;
+        f.advance_heads = d <= fp.dfused && advance != 0;
+        CW_TRY(launch_recover_fused(f, fp.dfused, fp.grid, fp.smem, st));
+        *launches += 1;
+        s0 = fp.dfused + 1;
+    }
+    for (int s = s0; s <= d; ++s) {
+        CW_TRY(launch_cumulants(s, args + (size_t)s * nwin, nwin, cum_launch[s], st));
+        *launches += 1;
+    }
+    if (s0 <= d) {
+        CW_TRY(launch_norm_final(norm_dev, nwin, advance, s0, st));
+        *launches += 1;
+    }
+    return CUMWIN_OK;
+}
+
+int run_cumulants(cumwin_t h, int64_t advance, int accum = 0)
+{
+    const int rc = recover(h->fused, h->cum_dev, h->cum_launch, h->norm_dev, 1, h->d, advance, accum, h->stream,
+                           &h->launches);
+    if (rc) return rc;
     if (h->mark(3) != nullptr) h->timed++;
     return CUMWIN_OK;
 }
@@ -418,9 +517,26 @@ int run_cumulants(cumwin_t h, int64_t advance, bool accum = false)
 std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcPlan& tc)
 {
     std::vector<TcAccSeg> segs;
-    for (size_t i = 0; i < wins.size(); ++i)
-        for (int s = 1; s <= wins[i]->d; ++s)
-            segs.push_back({wins[i]->S[s], tc.wbase[i] + wins[i]->Eoff[s]});
+    for (size_t i = 0; i < wins.size(); ++i) {
+        const cumwin_s* h = wins[i];
+        for (int s = 1; s <= h->d; ++s) {
+            TcAccSeg g{};
+            g.S = h->S[s];
+            g.wblk = h->cum[s].wblk;
+            g.begin = tc.wbase[i] + h->Eoff[s];
+            g.E = h->E[s];
+            g.bs = (int32_t)ipow(h->b, s);
+            g.bR = h->cum[s].bR;
+            g.head = h->head;
+            g.p = h->p;
+            if (tc.fifo != nullptr) {
+                g.fifo = tc.fifo + tc.fbase[i] + h->Eoff[s];
+                g.fstride = h->Eoff[h->d + 1];
+                g.nslots = (int32_t)(h->T / h->p);
+            }
+            segs.push_back(g);
+        }
+    }
     return segs;
 }
 
@@ -436,17 +552,23 @@ int update_window(cumwin_t h)
     } else {
         for (int q = 0; q < h->tc->nbatch; ++q) {
             CW_TRY(tc_update_window_batch(*h->tc, q, h->stream));
-            CW_TRY(launch_tc_accumulate(*h->tc, h->segs, h->nsegs, h->stream));
+            CW_TRY(launch_tc_accumulate(*h->tc, h->segs, h->nsegs, q, h->stream));
         }
         h->launches += 4LL * h->tc->nbatch;
+        h->fifo_valid = h->tc->fifo != nullptr;
     }
     h->mark(2);
     return CUMWIN_OK;
 }
 
 // One shift: stage X_(+) / X_(-), move X_(+) into the ring, update the sums.
-int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld)
+// *accum: how the recovery folds the shift's workspace in (CumArgs::accum).
+// A shift of the nominal p with the leaving rows taken from the ring uses the
+// batch-sum FIFO when there is one; any other shift recomputes the leaving
+// half and retires the FIFO until the next fill or recompute.
+int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld, int* accum)
 {
+    *accum = 0;
     h->mark(0);
     if (h->prec == CUMWIN_FP64) {
         CW_TRY(launch_stage(x_in, ld, x_out, ld, h->ring, h->T, h->head, p, h->n, h->npad,
@@ -455,9 +577,12 @@ int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_
         CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, 2 * (int64_t)p, p,
                                  h->shift, h->stream));
     } else {
-        CW_TRY(tc_stage_push(*h->tc, x_in, x_out, ld, p, h->stream));
+        const bool fifo = h->tc->fifo != nullptr && h->fifo_valid && x_out == nullptr && p == h->p;
+        if (!fifo) h->fifo_valid = false;
+        CW_TRY(tc_stage_push(*h->tc, x_in, x_out, ld, p, !fifo, h->stream));
         h->mark(1);
-        CW_TRY(tc_gemm_push(*h->tc, h->stream));
+        CW_TRY(tc_gemm_push(*h->tc, !fifo, h->stream));
+        *accum = fifo ? 2 : 1;
     }
     h->launches += 2 + (h->prec != CUMWIN_FP64);
     h->mark(2);
@@ -563,7 +688,10 @@ int cumwin_selftest_tables(int n, int b, int s)
     // 1. update tables: every stored element produced exactly once, at the
     //    storage index of its (row vars ++ col vars) multi-index.
     UpdateTables t = build_update_tables(n, b, s);
-    std::vector<int> hits(E, 0);
+    std::vector<int> hits(E, 0), whits(E, 0);
+    const std::vector<int64_t> roww = build_w_rows(t);
+    const std::vector<int32_t> wblk = build_w_blocks(t, n, b);
+    const int64_t bsh = ipow(b, t.sh);
     const int ncols = (int)t.colvar.size();
     for (int m = 0; m < nbar; ++m) {
         for (int r = t.rowstart[m]; r < t.rowstart[m + 1]; ++r) {
@@ -580,11 +708,17 @@ int cumwin_selftest_tables(int n, int b, int s)
                 const int64_t got = t.rowoff[r] + t.coloff[c];
                 if (got != want || got < 0 || got >= E) return 2;
                 hits[got]++;
+                // workspace slot: the row form (epilogue) and the block form
+                // (recovery) agree, and the slots cover [0, E) once
+                const int64_t w = roww[r] + c;
+                const int64_t wb = wblk[2 * rk] + (off / bsh) * wblk[2 * rk + 1] + off % bsh;
+                if (w != wb || w < 0 || w >= E) return 6;
+                whits[w]++;
             }
         }
     }
     for (int64_t e = 0; e < E; ++e)
-        if (hits[e] != 1) return 3;
+        if (hits[e] != 1 || whits[e] != 1) return 3;
     // 2. cumulant tables: sub-block lookups of a synthetic symmetric tensor
     //    f(i) = prod_k (i_k + 1.5) return f of the sub-multi-index.
     if (s >= 2) {
@@ -675,6 +809,7 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         if (ks >= 1 && ks <= h->tc->ksplit_max) h->tc->ksplit = ks;
     }
     if (rc == CUMWIN_OK) rc = window_finish(h, parts, h->tc, 0);
+    if (rc == CUMWIN_OK) rc = fused_setup(h->fused, {h}, b, h->sm_count, h->norm_dev, h->status, h->mem);
     if (rc == CUMWIN_OK && h->tc != nullptr) {
         std::vector<TcAccSeg> segs = acc_segments({h}, *h->tc);
         h->nsegs = (int)segs.size();
@@ -731,9 +866,16 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
         g_last_error = "the mixed forms accept shifts of at most the nominal p given at create";
         return CUMWIN_EINVAL;
     }
-    int rc = update_push(h, x_in_dev, x_out_dev, p, ld);
+    int accum = 0;
+    int rc = update_push(h, x_in_dev, x_out_dev, p, ld, &accum);
     if (rc) return rc;
-    return run_cumulants(h, p, h->prec != CUMWIN_FP64);
+    return run_cumulants(h, p, accum);
+}
+
+int cumwin_fifo(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    return h->tc != nullptr && h->tc->fifo != nullptr && h->fifo_valid ? 1 : 0;
 }
 
 int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld)
@@ -923,16 +1065,16 @@ int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
         if (ksplit_out) *ksplit_out = 0;
         return CUMWIN_OK;  // nothing to tune in the FP64 form
     }
-    const int ks = tc_autotune(*h->tc, reps, h->stream, nullptr);
+    const bool leaving = !(h->tc->fifo != nullptr && h->fifo_valid);
+    const int ks = tc_autotune(*h->tc, reps, leaving, h->stream, nullptr);
     if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
     for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
-    CumArgs arr[2][kMaxOrder + 1] = {};
-    for (int s = 1; s <= h->d; ++s) {
-        arr[0][s] = h->cum[s];
-        arr[1][s] = h->cum[s];
-        arr[0][s].accum = 0;
-        arr[1][s].accum = 1;
-    }
+    CumArgs arr[kAccModes][kMaxOrder + 1] = {};
+    for (int s = 1; s <= h->d; ++s)
+        for (int m = 0; m < kAccModes; ++m) {
+            arr[m][s] = h->cum[s];
+            arr[m][s].accum = m;
+        }
     CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0], sizeof(arr), cudaMemcpyHostToDevice));
     tune_cache_put(plan_signature(*h->tc, {h}, h->device), ks);
     if (ksplit_out) *ksplit_out = ks;
@@ -1053,7 +1195,7 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     cudaError_t e0 = B->mem.alloc(&B->status, 1);
     if (e0 != cudaSuccess) return bail(fail_cuda(e0, "alloc"));
     cudaMemset(B->status, 0, sizeof(int));
-    int rc = tc_plan_create(B->tc, ps, b, p, B->sm_count, precision, B->status,
+    int rc = tc_plan_create(B->tc, ps, b, p, B->sm_count, precision, B->status, true,
                             [&](size_t bytes, void** q) { return B->mem.alloc((char**)q, bytes); });
     if (rc != 0) {
         g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
@@ -1070,7 +1212,8 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
         B->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), nb, B->sm_count);
         parts = std::max(parts, B->cum_launch[s].gx * B->cum_launch[s].gy);
     }
-    std::vector<CumArgs> arr((size_t)2 * (kMaxOrder + 1) * nwin);
+    B->fifo = B->tc.fifo != nullptr;
+    std::vector<CumArgs> arr((size_t)kAccModes * (kMaxOrder + 1) * nwin);
     std::vector<NormArgs> na(nwin);
     cudaError_t e = B->mem.alloc(&B->fro2, (size_t)nwin * B->dmax);
     if (e != cudaSuccess) return bail(fail_cuda(e, "alloc"));
@@ -1078,10 +1221,10 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
         cumwin_s* h = B->wins[i];
         h->fro2 = B->fro2 + (size_t)i * B->dmax;
         h->tc = &B->tc;
-        rc = window_finish(h, parts, &B->tc, B->tc.wbase[i]);
+        rc = window_finish(h, parts, &B->tc, i);
         if (rc) return bail(rc);
         for (int s = 1; s <= B->dmax; ++s) {
-            for (int acc = 0; acc < 2; ++acc) {
+            for (int acc = 0; acc < kAccModes; ++acc) {
                 CumArgs a{};
                 if (s <= h->d) {
                     a = h->cum[s];
@@ -1099,6 +1242,10 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     }
     e = B->mem.upload(&B->cum_dev, arr);
     if (e == cudaSuccess) e = B->mem.upload(&B->norm_dev, na);
+    if (e == cudaSuccess) {
+        rc = fused_setup(B->fused, B->wins, b, B->sm_count, B->norm_dev, B->status, B->mem);
+        if (rc) return bail(rc);
+    }
     std::vector<TcAccSeg> segs = acc_segments(B->wins, B->tc);
     B->nsegs = (int)segs.size();
     if (e == cudaSuccess) e = B->mem.upload(&B->segs, segs);
@@ -1114,13 +1261,11 @@ int64_t cumwin_batch_offset(cumwin_batch_t B, int window)
     return B->xoff[window];
 }
 
-static int batch_recover(cumwin_batch_t B, int64_t advance, bool accum)
+static int batch_recover(cumwin_batch_t B, int64_t advance, int accum)
 {
-    for (int s = 1; s <= B->dmax; ++s)
-        CW_TRY(launch_cumulants(s, B->cum_dev + ((size_t)(accum ? 1 : 0) * (kMaxOrder + 1) + s) * B->nwin,
-                                B->nwin, B->cum_launch[s], B->stream));
-    CW_TRY(launch_norm_final(B->norm_dev, B->nwin, advance, B->stream));
-    return CUMWIN_OK;
+    int64_t launches = 0;
+    return recover(B->fused, B->cum_dev, B->cum_launch, B->norm_dev, B->nwin, B->dmax, advance, accum,
+                   B->stream, &launches);
 }
 
 int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev)
@@ -1136,9 +1281,9 @@ int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev)
     }
     for (int q = 0; q < B->tc.nbatch; ++q) {
         CW_TRY(tc_update_window_batch(B->tc, q, B->stream));
-        CW_TRY(launch_tc_accumulate(B->tc, B->segs, B->nsegs, B->stream));
+        CW_TRY(launch_tc_accumulate(B->tc, B->segs, B->nsegs, q, B->stream));
     }
-    const int rc = batch_recover(B, 0, false);
+    const int rc = batch_recover(B, 0, 0);
     if (rc) return rc;
     for (cumwin_s* h : B->wins) h->filled = true;
     B->filled = true;
@@ -1149,9 +1294,9 @@ int cumwin_batch_push(cumwin_batch_t B, const float* x_dev)
 {
     if (B == nullptr || x_dev == nullptr) return CUMWIN_EINVAL;
     if (!B->filled) return CUMWIN_ESTATE;
-    CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, B->stream));
-    CW_TRY(tc_gemm_push(B->tc, B->stream));
-    return batch_recover(B, B->p, true);
+    CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, !B->fifo, B->stream));
+    CW_TRY(tc_gemm_push(B->tc, !B->fifo, B->stream));
+    return batch_recover(B, B->p, B->fifo ? 2 : 1);
 }
 
 int cumwin_batch_cumulants(cumwin_batch_t B, int window, int order, double* out_dev)
@@ -1197,9 +1342,9 @@ int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out)
 {
     if (B == nullptr || reps < 1) return CUMWIN_EINVAL;
     if (!B->filled) return CUMWIN_ESTATE;
-    const int ks = tc_autotune(B->tc, reps, B->stream, nullptr);
+    const int ks = tc_autotune(B->tc, reps, !B->fifo, B->stream, nullptr);
     if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
-    std::vector<CumArgs> arr((size_t)2 * (kMaxOrder + 1) * B->nwin);
+    std::vector<CumArgs> arr((size_t)kAccModes * (kMaxOrder + 1) * B->nwin);
     CW_TRY(cudaMemcpy(arr.data(), B->cum_dev, sizeof(CumArgs) * arr.size(), cudaMemcpyDeviceToHost));
     for (CumArgs& a : arr) a.ksplit = ks;
     CW_TRY(cudaMemcpy(B->cum_dev, arr.data(), sizeof(CumArgs) * arr.size(), cudaMemcpyHostToDevice));
@@ -1208,6 +1353,12 @@ int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out)
     tune_cache_put(plan_signature(B->tc, B->wins, B->wins[0]->device), ks);
     if (ksplit_out) *ksplit_out = ks;
     return CUMWIN_OK;
+}
+
+int cumwin_batch_fifo(cumwin_batch_t B)
+{
+    if (B == nullptr) return CUMWIN_EINVAL;
+    return B->fifo ? 1 : 0;
 }
 
 int cumwin_batch_status(cumwin_batch_t B)

@@ -51,4 +51,21 @@ __device__ __forceinline__ void sum_partials(const float* __restrict__ w, int64_
     }
 }
 
+// The entering half only (slices 2k): the same additions in the same order as
+// the `din` of sum_partials.
+__device__ __forceinline__ float sum_in_partials(const float* __restrict__ w, int64_t wslice, int ksplit)
+{
+    float din = 0.0f;
+    int k = 0;
+    for (; k + 4 <= ksplit; k += 4) {
+        float vi[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vi[j] = w[(int64_t)(2 * (k + j)) * wslice];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) din += vi[j];
+    }
+    for (; k < ksplit; ++k) din += w[(int64_t)(2 * k) * wslice];
+    return din;
+}
+
 }  // namespace cw

@@ -52,6 +52,8 @@ struct UpdTile {
 // For a sorted block j every sub-tuple j_A is sorted, hence a stored block;
 // subrank holds (rank(j_A), rank(j_rest)) for each block and each subset.
 // ---------------------------------------------------------------------------
+constexpr int kAccModes = 3;  // CumArgs::accum values
+
 struct CumArgs {
     double* S[kMaxOrder + 1];        // running sums per order (moments = S * invT)
     const double* C[kMaxOrder + 1];  // cumulants per order (order 1 about the shift)
@@ -65,10 +67,18 @@ struct CumArgs {
     int32_t s, b, bs, nsub;
     uint8_t mask[128];               // subset bitmasks over the s positions
     // tensor-core form: before recovering C_s, fold the FP32 tile sums of the
-    // shift into S_s:  S += (double)(sum_k W[k][0]) - (double)(sum_k W[k][1])
+    // shift into S_s: S += (double)D_in - (double)D_out with D_in = sum_k W[k][0],
+    // read at the element's workspace slot wblk[2 blk] + aL * wblk[2 blk + 1] + aR
+    // (in-block offset a = aL * bR + aR).  accum 1: D_out = sum_k W[k][1];
+    // accum 2: D_out = the element's entry (storage order) in slot head / p of
+    // the batch-sum FIFO, which then takes D_in.
     const float* W;                  // [ksplit][2][wslice]
-    int64_t wslice, woff;
-    int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = fold it in
+    const int32_t* wblk;             // [nblocks][2] (build_w_blocks)
+    float* fifo;                     // this order's FIFO in slot 0 (accum 2)
+    const int64_t* head;             // ring head (accum 2)
+    int64_t wslice, woff, fstride;
+    int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = stacked in/out, 2 = FIFO
+    int32_t bR, p;                   // b^(s - h); shift size (accum 2)
 };
 
 // Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
@@ -124,9 +134,34 @@ struct NormArgs {
     int64_t T;
     int32_t parts, d;
 };
-// Also advances each ring head by `advance` rows (mod T): the head lives in
-// device memory so that a captured shift can be replayed.
-cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, cudaStream_t st);
+// Orders s >= s_from only.  Also advances each ring head by `advance` rows
+// (mod T): the head lives in device memory so that a captured shift can be
+// replayed.
+cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, int s_from,
+                              cudaStream_t st);
+
+// Orders 1..dfused (dfused <= kFusedMax) of every window in one cooperative
+// launch with a grid barrier between orders; one norm partial per work unit
+// (a group of blocks of one window, or a 256-offset slice of one block), the
+// norms of those orders reduced at the end, and the ring heads advanced when
+// no higher order follows.
+constexpr int kFusedMax = 4;
+struct FusedRecovery {
+    const CumArgs* args;     // args[s * nwin + w], one accumulate mode
+    const int64_t* ustart;   // [(kFusedMax + 1)][nwin + 1] first work unit of each window, per order
+    double* upart;           // norm partial of each work unit; order s from upoff[s]
+    const NormArgs* norm;    // [nwin]
+    unsigned* bar;           // grid barrier state [2] (arrivals, generation), zero at creation
+    int* status;
+    int64_t upoff[kFusedMax + 1];
+    int64_t advance;
+    int32_t nwin, advance_heads;
+    int32_t slots[kFusedMax + 1], gy[kFusedMax + 1];
+};
+size_t fused_smem_bytes(const FusedRecovery& f, int dfused);
+// Resident CTAs for the cooperative launch (0: not possible).
+int fused_grid(int dfused, size_t smem, int sm_count);
+cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_zero(double* p, int64_t count, cudaStream_t st);
 cudaError_t launch_add_shift(const double* C1, const float* shift, int n, int npad, double* out,
                              cudaStream_t st);

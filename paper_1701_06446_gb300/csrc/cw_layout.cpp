@@ -103,12 +103,14 @@ UpdateTables build_update_tables(int n, int b, int s)
     const int64_t nleft = (int64_t)left.size() / h;
     t.rowstart.assign(nbar + 1, 0);
     std::vector<int> full(s), vars(kMaxOrder);
+    t.leftrow.assign(nleft, 0);
     for (int m = 0; m < nbar; ++m) {
         t.rowstart[m] = (int32_t)t.rowvar.size();
         const int64_t off_m = off_first_below(m);
         for (int64_t q = 0; q < nleft; ++q) {
             const int* jl = &left[q * h];
             if (jl[h - 1] != m) continue;
+            t.leftrow[q] = (int32_t)t.rowvar.size();
             for (int k = 0; k < h; ++k) full[k] = jl[k];
             for (int k = h; k < s; ++k) full[k] = m;
             const int64_t P = rank_sorted(full.data(), s, nbar);
@@ -148,6 +150,56 @@ UpdateTables build_update_tables(int n, int b, int s)
         for (int m = 0; m < nbar; ++m) t.colstart[m] = (int32_t)(off_first_below(m) * bsh);
     }
     return t;
+}
+
+// Workspace order of the order-s update: group m is a dense
+// rows_m x (ncols - colstart[m]) block, row-major, the groups one after the
+// other.  Each GEMM output (r, c) has exactly one slot, so the workspace has
+// E_s elements, and a row's outputs are contiguous.
+static std::vector<int64_t> group_bases(const UpdateTables& t)
+{
+    const int nbar = (int)t.colstart.size();
+    const int64_t ncols = (int64_t)t.colvar.size();
+    std::vector<int64_t> gbase(nbar + 1, 0);
+    for (int m = 0; m < nbar; ++m)
+        gbase[m + 1] = gbase[m] + (int64_t)(t.rowstart[m + 1] - t.rowstart[m]) * (ncols - t.colstart[m]);
+    return gbase;
+}
+
+std::vector<int64_t> build_w_rows(const UpdateTables& t)
+{
+    const int nbar = (int)t.colstart.size();
+    const int64_t ncols = (int64_t)t.colvar.size();
+    const std::vector<int64_t> gbase = group_bases(t);
+    std::vector<int64_t> roww(t.rowvar.size());
+    for (int m = 0; m < nbar; ++m) {
+        const int64_t width = ncols - t.colstart[m];
+        for (int r = t.rowstart[m]; r < t.rowstart[m + 1]; ++r)
+            roww[r] = gbase[m] + (int64_t)(r - t.rowstart[m]) * width - t.colstart[m];
+    }
+    return roww;
+}
+
+std::vector<int32_t> build_w_blocks(const UpdateTables& t, int n, int b)
+{
+    const int nbar = (n + b - 1) / b;
+    const int s = t.s, h = t.h, sh = t.sh;
+    const int64_t ncols = (int64_t)t.colvar.size();
+    const int64_t bsh = ipow(b, sh);
+    const std::vector<int64_t> gbase = group_bases(t);
+    const std::vector<int> blocks = enumerate_sorted(nbar, s);
+    const int64_t nb = (int64_t)blocks.size() / s;
+    std::vector<int32_t> out((size_t)nb * 2);
+    for (int64_t q = 0; q < nb; ++q) {
+        const int* j = &blocks[q * s];
+        const int m = j[h - 1];
+        const int64_t r0 = t.leftrow[rank_sorted(j, h, nbar)];
+        const int64_t c0 = sh == 0 ? 0 : rank_sorted(j + h, sh, nbar) * bsh;
+        const int64_t width = ncols - t.colstart[m];
+        out[2 * q] = (int32_t)(gbase[m] + (r0 - t.rowstart[m]) * width + (c0 - t.colstart[m]));
+        out[2 * q + 1] = (int32_t)width;
+    }
+    return out;
 }
 
 CumTables build_cum_tables(int n, int b, int s)

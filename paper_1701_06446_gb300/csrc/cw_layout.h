@@ -28,8 +28,18 @@ struct UpdateTables {
     std::vector<int64_t> rowoff, coloff;
     std::vector<int32_t> rowstart;  // [nbar + 1] rows of group m
     std::vector<int32_t> colstart;  // [nbar] first column of group m
+    std::vector<int32_t> leftrow;   // [sorted h-tuples, lexicographic] first row of the tuple
 };
 UpdateTables build_update_tables(int n, int b, int s);
+
+// Workspace ("GEMM") order of the order-s update outputs: group m of the
+// update is a dense row-major block of rows_m x (ncols - colstart[m]) slots.
+// Slot of output (r, c) = roww[r] + c.
+std::vector<int64_t> build_w_rows(const UpdateTables& t);
+// Per sorted block j of order s (lexicographic rank): {slot of its in-block
+// offset 0, row stride}; in-block offset a = aL * b^sh + aR lives at
+// slot + aL * stride + aR.
+std::vector<int32_t> build_w_blocks(const UpdateTables& t, int n, int b);
 
 // Tables of the order-s cumulant recovery (see CumArgs in cw_internal.h).
 struct CumTables {

@@ -7,8 +7,9 @@
 // (h indices, "rows") the MMA N side (up to kTcNmax rows).
 //
 // Per shift, for all streams at once (one launch per phase):
-//   1. k_tc_stage_push: X_(+) and X_(-), minus the shift vector, transposed to
-//      [variable][sample] (FP32), zero-padded to P samples each.
+//   1. k_tc_stage_push: X_(+) (and X_(-) when the leaving samples are
+//      recomputed), minus the shift vector, transposed to [variable][sample]
+//      (FP32), zero-padded to P samples each.
 //   2. k_kr_build: every distinct Khatri-Rao operand row (the products of its
 //      variables over the staged samples) is formed once in FP32, split into
 //      bf16 hi + lo and written with the samples contiguous, so that a TMA box
@@ -19,11 +20,17 @@
 //      ring, an MMA warp issues hi*hi + hi*lo + lo*hi per 16-sample step into
 //      one of two TMEM accumulator sets (entering samples into D_in, leaving
 //      samples into D_out), and four epilogue warps store the FP32 tiles into
-//      a workspace W[split][in/out] while the next unit's MMAs run.
+//      a workspace W[split][in/out] while the next unit's MMAs run.  The
+//      workspace is in GEMM order (each row's outputs contiguous, see
+//      build_w_rows), so the stores are whole 128-byte lines.
 //   4. the recovery kernel of each order folds the workspace into the FP64
-//      sums: S += (double)(sum_k D_in,k) - (double)(sum_k D_out,k), the FP32
-//      sums over splits taken in a fixed order, so that a batch's sum is
-//      bitwise the same when it enters and when it leaves the window.
+//      sums: S += (double)(sum_k D_in,k) - (double)(D_out), the FP32 sums over
+//      splits taken in a fixed order.  D_out is either recomputed from the
+//      leaving samples (stacked form) or, when T is a multiple of p, read from
+//      a FIFO that keeps each batch's FP32 sum from when it entered (the
+//      batch-moment variant of Section 2.4; the leaving half of the GEMM is
+//      then skipped).  Either way a batch's sum is bitwise the same when it
+//      enters and when it leaves the window.
 #pragma once
 
 #include <cstdint>
@@ -63,14 +70,15 @@ struct TcItem {
     int32_t acol;   // TMA row coordinate of col0 in the operand array
     int32_t bbox;   // rows of the B tile box (32, 64 or 128)
     int32_t stream; // index of the stream
-    int32_t pad0, pad1, pad2;
+    int32_t fast;   // all rows in one group: slot(row0 + k, c) = wrow0 + k * wwidth + c
+    int32_t wwidth; // row stride of the group in the workspace (fast items)
+    int32_t wrow0;  // workspace slot of (row0, column 0) (fast items)
 };
 
 // Per (stream, order) tables of the epilogue (device array [stream][kMaxOrder + 1]).
 struct TcOrder {
-    const int64_t* rowoff;
+    const int64_t* roww;       // workspace slot of (row r, column 0): slot(r, c) = roww[r] + c
     const int32_t* rowcolmin;  // first valid column of each row (its group's start)
-    const int64_t* coloff;
     int64_t woff;              // offset of this (stream, order) in one workspace slice
 };
 
@@ -118,6 +126,11 @@ struct TcPlan {
     int64_t wslice = 0;
     std::vector<int64_t> wbase;    // per stream: offset of the stream in a workspace slice
     std::vector<int> nbatch_stream;
+    // batch-sum FIFO (null when some T is not a multiple of p, or it does not
+    // fit): stream i keeps T_i / p slots of its E_i = sum_s E_s FP32 sums in
+    // storage order at fifo + fbase[i] + slot * E_i
+    float* fifo = nullptr;
+    std::vector<int64_t> fbase;
     int* status = nullptr;
     double useful_macs_per_sample = 0, issued_macs_per_sample = 0;
 };
@@ -125,16 +138,19 @@ struct TcPlan {
 using DevAlloc = std::function<cudaError_t(size_t, void**)>;
 
 // Returns 0 or a cudaError_t code.
+// `fifo`: allocate the batch-sum FIFO when every T is a multiple of p and it
+// takes at most a quarter of the free device memory.
 int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
-                   int precision, int* status, const DevAlloc& alloc);
+                   int precision, int* status, bool fifo, const DevAlloc& alloc);
 
 // Staging + operand build for all streams (2 launches).  Stream i reads its
-// X_(+) at xin + xoff_i (row stride ld, or n_i when ld < 0) and, when xout is
-// not null, its X_(-) at xout + xoff_i; otherwise from its ring buffer.
+// X_(+) at xin + xoff_i (row stride ld, or n_i when ld < 0).  With `leaving`,
+// X_(-) is staged too: from xout + xoff_i when xout is not null, else from the
+// ring buffer.
 cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
-                          cudaStream_t st);
-// The GEMM units of a shift (1 launch).
-cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st);
+                          bool leaving, cudaStream_t st);
+// The GEMM units of a shift (1 launch); `leaving` adds the X_(-) half.
+cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, cudaStream_t st);
 
 // Batch q (window order, p samples) of every stream's ring buffer: stage, build
 // and GEMM with no leaving segment (3 launches); streams with fewer batches
@@ -142,16 +158,26 @@ cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st);
 // launch_tc_accumulate.
 cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st);
 
-// S += (double)sum_k W[k][0] for every (stream, order) segment.
+// Batch q of a window's sums, one (stream, order) segment: S += (double)D_in
+// with D_in = sum_k W[k][0] at the element's workspace slot, and, with a FIFO,
+// D_in is kept in slot (head / p + q) mod nslots of the stream's FIFO.
 struct TcAccSeg {
     double* S;
-    int64_t begin;  // first element of the segment in a workspace slice
+    const int32_t* wblk;   // build_w_blocks of the order
+    float* fifo;           // FIFO of the order in slot 0, or null
+    const int64_t* head;   // ring head of the stream
+    int64_t begin;         // first element of the segment in a workspace slice
+    int64_t E;             // elements of the segment
+    int64_t fstride;       // FIFO slot stride (floats)
+    int32_t bs, bR;        // b^s, b^(s - h)
+    int32_t p, nslots;
 };
-cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs,
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, int q,
                                  cudaStream_t st);
 
 // Time the GEMM for each candidate K-split on the data currently staged and
 // keep the fastest; returns the chosen K-split (or a negative cudaError_t).
-int tc_autotune(TcPlan& plan, int reps, cudaStream_t st, double* best_ms);
+// `leaving`: time the shape with the X_(-) half.
+int tc_autotune(TcPlan& plan, int reps, bool leaving, cudaStream_t st, double* best_ms);
 
 }  // namespace cw

@@ -13,13 +13,21 @@
 // For a sorted block j every sub-tuple j_A is sorted, so each operand is a
 // stored block whose rank comes from a per-block table, and its in-block
 // offset follows from the element's own in-block digits because diagonal
-// blocks are stored whole.  The kernel is specialised per order: the subset
+// blocks are stored whole.  The code is specialised per order: the subset
 // masks are compile-time constants, each thread owns one in-block offset and
-// computes its per-subset operand offsets once, and the per-block operand
-// bases (rank * b^|A|) are staged in shared memory for a group of blocks.
-// The same pass accumulates multiplicity * C^2 (Algorithm 5 with k = 2) into
-// one partial per CTA; a second kernel adds the partials of each order in a
-// fixed order.
+// computes its per-subset operand offsets once; the per-block sub-block ranks
+// come from a table all threads of a block read together.  The same pass
+// accumulates multiplicity * C^2 (Algorithm 5 with k = 2).
+//
+// Two launch forms share that per-group routine:
+//   * k_recover_fused: orders 1..min(d, 4) in one cooperative launch, a grid
+//     barrier between orders (order s reads C_1..C_{s-1}), norm partials per
+//     work unit, and the norms reduced at the end; the small orders cost a
+//     barrier each instead of a launch each.
+//   * k_cumulants<S>: one launch per order above 4, one norm partial per CTA,
+//     reduced by k_norm_final.
+#include <algorithm>
+
 #include "cw_device.cuh"
 #include "cw_internal.h"
 
@@ -28,131 +36,319 @@ namespace cw {
 namespace {
 
 constexpr int NT = 256;
+constexpr long long kBarrierLimit = 1LL << 32;  // clock cycles (~2 s)
 
 // Subset t (0 <= t < 2^{S-1} - 1) holds position 0 and the positions of the
 // set bits of t shifted by one: mask = 2t + 1 (the host tables use this order).
 template <int S>
 struct Subsets {
     static constexpr int N = (1 << (S - 1)) - 1;
+    static constexpr int ND = N > 0 ? N : 1;
 };
 
 __host__ __device__ constexpr int popc_c(unsigned x) { return x ? (int)(x & 1u) + popc_c(x >> 1) : 0; }
 
-template <int S>
-__global__ void __launch_bounds__(NT) k_cumulants(const CumArgs* __restrict__ args, int slots)
+__device__ __forceinline__ int ipow_c(int b, int k)
 {
-    constexpr int NS = Subsets<S>::N;
-    const CumArgs& a = args[blockIdx.z];  // one window per blockIdx.z
-    if (a.E == 0) return;                 // this window has no order S
-    extern __shared__ int sbase[];  // [slots][NS][2]: rank(j_A) * b^|A|, rank(j_rest) * b^|rest|
-    const int b = a.b, bs = a.bs;
-    int bp[kMaxOrder + 1];
-    bp[0] = 1;
-#pragma unroll
-    for (int k = 1; k <= kMaxOrder; ++k) bp[k] = bp[k - 1] * b;
-
-    // this thread's slot and in-block offset
-    int slot, off;
-    if (slots == 1) {
-        slot = 0;
-        off = blockIdx.y * NT + threadIdx.x;
-    } else {
-        slot = threadIdx.x / bs;
-        off = threadIdx.x - slot * bs;
-    }
-    const bool tvalid = slot < slots && off < bs;
-    int dig[S];
-    {
-        int rem = off;
-#pragma unroll
-        for (int k = S - 1; k >= 0; --k) {
-            const int q = rem / b;
-            dig[k] = rem - q * b;
-            rem = q;
-        }
-    }
-    int offA[NS > 0 ? NS : 1], offR[NS > 0 ? NS : 1];
-#pragma unroll
-    for (int t = 0; t < NS; ++t) {
-        const unsigned mask = 2u * t + 1u;
-        int oa = 0, orr = 0;
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            if ((mask >> k) & 1u) oa = oa * b + dig[k];
-            else orr = orr * b + dig[k];
-        }
-        offA[t] = oa;
-        offR[t] = orr;
-    }
-
-    double* __restrict__ Ss = a.S[S];
-    double local = 0.0;
-    const int64_t nblocks = a.E / bs;
-    const int64_t ngroups = (nblocks + slots - 1) / slots;
-    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int64_t blk0 = grp * slots;
-        if (NS > 0) {
-            __syncthreads();
-            constexpr int NSD = NS > 0 ? NS : 1;
-            for (int i = threadIdx.x; i < slots * NS; i += NT) {
-                const int64_t blk = blk0 + i / NSD;
-                const int t = i - (i / NSD) * NSD;
-                if (blk < nblocks) {
-                    const int32_t* sr = a.subrank + ((size_t)blk * NS + t) * 2;
-                    const int la = __popc(2u * t + 1u), lr = S - la;
-                    sbase[2 * i] = sr[0] * bp[la];
-                    sbase[2 * i + 1] = sr[1] * bp[lr];
-                }
-            }
-            __syncthreads();
-        }
-        const int64_t blk = blk0 + slot;
-        if (!tvalid || blk >= nblocks) continue;
-        const int64_t e = blk * bs + off;
-        double acc = Ss[e];
-        if (a.accum) {
-            float din, dout;
-            sum_partials(a.W + a.woff + e, a.wslice, a.ksplit, din, dout);
-            acc += f32_to_f64(din) - f32_to_f64(dout);
-            Ss[e] = acc;
-        }
-        const int* sb = sbase + 2 * slot * NS;
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-            const int la = popc_c(2u * t + 1u), lr = S - la;
-            const double cA = a.C[la][sb[2 * t] + offA[t]];
-            const double sR = a.S[lr][sb[2 * t + 1] + offR[t]];
-            acc = fma(-cA, sR, acc);
-        }
-        const double c = acc * a.invT;
-        a.Cout[e] = c;
-        if (S == 1) {
-            const double x = c + (double)a.shift[e];
-            local = fma(x, x, local);
-        } else {
-            local = fma(a.mult[blk] * c, c, local);
-        }
-    }
-    // deterministic CTA reduction
-    __shared__ double red[NT];
-    __syncthreads();
-    red[threadIdx.x] = local;
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    int r = 1;
+    for (int i = 0; i < k; ++i) r *= b;
+    return r;
 }
 
-// One CTA per window, one warp per order: lanes add strided partials, then a
-// fixed shuffle tree.  Also advances the window's ring head.
-__global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance)
+// Per-thread constants of one in-block offset of order S.  Up to order 4 the
+// in-block offsets of both factors of every subset are kept; above, only the
+// digits, and each subset's offsets are formed when it is used (integer work
+// is cheap next to the FP64 multiply-add it feeds).
+constexpr int kKeepOffsets = 4;
+template <int S>
+struct Elem {
+    static constexpr int NO = S <= kKeepOffsets ? Subsets<S>::ND : 1;
+    int slot, off;
+    bool valid;
+    int dig[S];
+    int offA[NO], offR[NO];  // in-block offsets of the two factors (S <= kKeepOffsets)
+    int offL, offRw;         // workspace: in-block row / column
+};
+
+template <int S>
+__device__ __forceinline__ void subset_offsets(const Elem<S>& c, int b, int t, int& oa, int& orr)
+{
+    if constexpr (S <= kKeepOffsets) {
+        oa = c.offA[t];
+        orr = c.offR[t];
+    } else {
+        const unsigned mask = 2u * t + 1u;
+        oa = 0;
+        orr = 0;
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            if ((mask >> k) & 1u) oa = oa * b + c.dig[k];
+            else orr = orr * b + c.dig[k];
+        }
+    }
+}
+
+// Thread -> (slot, in-block offset): `slots` blocks per CTA when b^S < NT,
+// else slice y of NT offsets of one block.
+template <int S>
+__device__ __forceinline__ Elem<S> make_elem(int b, int bs, int bR, int slots, int y)
+{
+    Elem<S> c;
+    if (slots == 1) {
+        c.slot = 0;
+        c.off = y * NT + (int)threadIdx.x;
+    } else {
+        c.slot = (int)threadIdx.x / bs;
+        c.off = (int)threadIdx.x - c.slot * bs;
+    }
+    c.valid = c.slot < slots && c.off < bs;
+    int rem = c.off;
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+        const int q = rem / b;
+        c.dig[k] = rem - q * b;
+        rem = q;
+    }
+    if constexpr (S <= kKeepOffsets) {
+#pragma unroll
+        for (int t = 0; t < Subsets<S>::N; ++t) {
+            const unsigned mask = 2u * t + 1u;
+            int oa = 0, orr = 0;
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                if ((mask >> k) & 1u) oa = oa * b + c.dig[k];
+                else orr = orr * b + c.dig[k];
+            }
+            c.offA[t] = oa;
+            c.offR[t] = orr;
+        }
+    }
+    c.offL = c.off / bR;
+    c.offRw = c.off - c.offL * bR;
+    return c;
+}
+
+// The element of thread `c` in block `blk`: fold the shift's workspace into
+// S_S, recover C_S and add multiplicity * C^2 to `local`.  No shared memory
+// and no CTA synchronisation: the per-block sub-block ranks come from a table
+// whose rows all threads of a block read together (L1 broadcast).
+template <int S>
+__device__ __forceinline__ void recover_elem(const CumArgs& a, const Elem<S>& c, int64_t blk, int64_t fslot,
+                                             double& local)
+{
+    constexpr int NS = Subsets<S>::N;
+    constexpr int ND = Subsets<S>::ND;
+    const int b = a.b;
+    const int64_t e = blk * a.bs + c.off;
+    double* Ss = a.S[S];
+    // 1. independent loads: the sum and the workspace
+    double acc = Ss[e];
+    float din = 0.0f, dout = 0.0f;
+    float* fptr = nullptr;
+    if (a.accum) {
+        const int2 wb = *reinterpret_cast<const int2*>(a.wblk + 2 * blk);
+        const int64_t w = (int64_t)wb.x + (int64_t)c.offL * wb.y + c.offRw;
+        if (a.accum == 1) {
+            sum_partials(a.W + a.woff + w, a.wslice, a.ksplit, din, dout);
+        } else {
+            din = sum_in_partials(a.W + a.woff + w, a.wslice, a.ksplit);
+            fptr = a.fifo + fslot * a.fstride + e;  // FIFO in storage order: coalesced
+            dout = *fptr;
+        }
+    }
+    if (a.accum) {
+        acc += f32_to_f64(din) - f32_to_f64(dout);
+        Ss[e] = acc;
+        if (fptr != nullptr) *fptr = din;
+    }
+    // 2. the subsets: sub-block ranks (rank(j_A), rank(j_rest)) of the block,
+    //    one gather per factor, one FP64 multiply-add
+    const int32_t* sr = a.subrank + (size_t)blk * NS * 2;
+#pragma unroll(S <= 4 ? NS : 4)
+    for (int t = 0; t < NS; ++t) {
+        const int2 q = *reinterpret_cast<const int2*>(sr + 2 * t);
+        const int la = __popc(2u * t + 1u), lr = S - la;
+        int oa, orr;
+        subset_offsets<S>(c, b, t, oa, orr);
+        const double cA = a.C[la][q.x * ipow_c(b, la) + oa];
+        const double sR = a.S[lr][q.y * ipow_c(b, lr) + orr];
+        acc = fma(-cA, sR, acc);
+    }
+    const double cv = acc * a.invT;
+    a.Cout[e] = cv;
+    if (S == 1) {
+        const double x = cv + (double)a.shift[e];
+        local = fma(x, x, local);
+    } else {
+        local = fma(a.mult[blk] * cv, cv, local);
+    }
+}
+
+// Deterministic CTA sum (fixed shuffle tree per warp, warps in order).
+__device__ __forceinline__ double cta_sum(double v, double* red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double z = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < NT / 32; ++w) z += red[w];
+    return z;  // valid in thread 0
+}
+
+template <int S>
+__global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__ args, int slots)
+{
+    const CumArgs& a = args[blockIdx.z];  // one window per blockIdx.z
+    if (a.E == 0) return;                 // this window has no order S
+    __shared__ double red[NT / 32];
+    const Elem<S> c = make_elem<S>(a.b, a.bs, a.bR, slots, blockIdx.y);
+    const int64_t fslot = a.accum == 2 ? *a.head / a.p : 0;
+    const int64_t nblocks = a.E / a.bs;
+    double local = 0.0;
+    if (c.valid)
+        for (int64_t blk = (int64_t)blockIdx.x * slots + c.slot; blk < nblocks; blk += (int64_t)gridDim.x * slots)
+            recover_elem<S>(a, c, blk, fslot, local);
+    const double z = cta_sum(local, red);
+    if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = z;
+}
+
+// Grid barrier of a cooperative launch: the last CTA to arrive resets the
+// count and bumps the generation the others wait on.  Bounded: a CTA that
+// waits too long records kStatusTimeout and goes on.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kBarrierLimit) {
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Window of work unit u of an order: last w with ustart[w] <= u.
+__device__ __forceinline__ int unit_window(const int64_t* ustart, int nwin, int64_t u)
+{
+    int lo = 0, hi = nwin - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ustart[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One order of the fused recovery.  Units go round-robin over the CTAs; a
+// CTA's units of one window are consecutive, so it sums them per thread and
+// reduces once per window ("run"): the run's sum goes to the slot of its first
+// unit and the other units of the run hold zero, so that every unit slot is
+// written and the window's norm is the sum of its unit slots.
+template <int S>
+__device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red)
+{
+    const int slots = f.slots[S], gy = f.gy[S];
+    const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
+    const int64_t total = us[f.nwin];
+    double* part = f.upart + f.upoff[S];
+    int cur = -1;
+    int64_t first = 0;
+    double local = 0.0;
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int w = unit_window(us, f.nwin, u);
+        if (w != cur) {
+            if (cur >= 0) {
+                const double z = cta_sum(local, red);
+                if (threadIdx.x == 0) part[first] = z;
+            }
+            cur = w;
+            first = u;
+            local = 0.0;
+        } else if (threadIdx.x == 0) {
+            part[u] = 0.0;
+        }
+        const CumArgs& a = f.args[(int64_t)S * f.nwin + w];
+        const int64_t ul = u - us[w];
+        const int64_t grp = ul / gy;
+        const int y = (int)(ul - grp * gy);
+        const Elem<S> c = make_elem<S>(a.b, a.bs, a.bR, slots, y);
+        const int64_t fslot = a.accum == 2 ? *a.head / a.p : 0;
+        const int64_t blk = grp * slots + c.slot;
+        if (c.valid && blk < a.E / a.bs) recover_elem<S>(a, c, blk, fslot, local);
+    }
+    if (cur >= 0) {
+        const double z = cta_sum(local, red);
+        if (threadIdx.x == 0) part[first] = z;
+    }
+}
+
+// Orders 1..DF of every window, cooperative launch (all CTAs resident).
+template <int DF>
+__global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__ FusedRecovery f)
+{
+    __shared__ double red[NT / 32];
+    fused_order<1>(f, red);
+    if (DF >= 2) {
+        grid_barrier(f.bar, f.status);
+        fused_order<(DF >= 2 ? 2 : 1)>(f, red);
+    }
+    if (DF >= 3) {
+        grid_barrier(f.bar, f.status);
+        fused_order<(DF >= 3 ? 3 : 1)>(f, red);
+    }
+    if (DF >= 4) {
+        grid_barrier(f.bar, f.status);
+        fused_order<(DF >= 4 ? 4 : 1)>(f, red);
+    }
+    grid_barrier(f.bar, f.status);
+    // norms: one warp per (window, order), partials of the order's units of
+    // the window added lane-strided, then a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+    for (int64_t it = gw; it < (int64_t)f.nwin * DF; it += nwarps) {
+        const int w = (int)(it / DF), s = (int)(it - (it / DF) * DF) + 1;
+        const NormArgs& na = f.norm[w];
+        if (s > na.d) continue;
+        const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
+        const double* part = f.upart + f.upoff[s];
+        double z = 0.0;
+        for (int64_t q = us[w] + lane; q < us[w + 1]; q += 32) z += part[q];
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (lane == 0) na.fro2[s - 1] = z;
+    }
+    // every CTA read the ring heads (FIFO slots) before the last barrier
+    if (f.advance_heads)
+        for (int w = blockIdx.x * NT + threadIdx.x; w < f.nwin; w += gridDim.x * NT) {
+            const NormArgs& na = f.norm[w];
+            *na.head = (*na.head + f.advance) % na.T;
+        }
+}
+
+// One CTA per window, one warp per order s >= s_from: lanes add strided
+// partials, then a fixed shuffle tree.  Also advances the window's ring head.
+__global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance, int s_from)
 {
     const NormArgs& a = args[blockIdx.x];
     const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
     if (threadIdx.x == 0 && advance != 0) *a.head = (*a.head + advance) % a.T;
-    if (s >= a.d) return;
+    if (s >= a.d || s + 1 < s_from) return;
     double z = 0.0;
     const double* part = a.normpart + (int64_t)s * a.parts;
     int q = lane;
@@ -171,10 +367,24 @@ __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance)
 template <int S>
 cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cudaStream_t st)
 {
-    constexpr int NS = Subsets<S>::N;
-    const size_t smem = (size_t)L.slots * (NS > 0 ? NS : 1) * 2 * sizeof(int);
-    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots);
+    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, 0, st>>>(args, L.slots);
     return cudaGetLastError();
+}
+
+template <int DF>
+cudaError_t launch_fused_df(const FusedRecovery& f, int grid, size_t smem, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_recover_fused<DF>, f);
 }
 
 }  // namespace
@@ -218,9 +428,37 @@ cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const Cum
     }
 }
 
-cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, cudaStream_t st)
+size_t fused_smem_bytes(const FusedRecovery&, int) { return 0; }
+
+int fused_grid(int dfused, size_t smem, int sm_count)
 {
-    k_norm_final<<<nwin, 32 * kMaxOrder, 0, st>>>(args_dev, advance);
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (dfused) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover_fused<1>, NT, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover_fused<2>, NT, smem); break;
+    case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover_fused<3>, NT, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_recover_fused<4>, NT, smem); break;
+    default: break;
+    }
+    if (e != cudaSuccess || per_sm < 1) return 0;
+    return std::min(per_sm, 4) * sm_count;
+}
+
+cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st)
+{
+    switch (dfused) {
+    case 1: return launch_fused_df<1>(f, grid, smem, st);
+    case 2: return launch_fused_df<2>(f, grid, smem, st);
+    case 3: return launch_fused_df<3>(f, grid, smem, st);
+    case 4: return launch_fused_df<4>(f, grid, smem, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, int s_from, cudaStream_t st)
+{
+    k_norm_final<<<nwin, 32 * kMaxOrder, 0, st>>>(args_dev, advance, s_from);
     return cudaGetLastError();
 }
 

@@ -39,14 +39,15 @@ constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 // ---------------------------------------------------------------------------
 // staging: shifted samples, transposed to [variable][sample]
 // ---------------------------------------------------------------------------
-// Samples [0, P) of the K axis hold X_(+), [P, 2P) hold X_(-), zero beyond p.
+// Samples [0, P) of the K axis hold X_(+), [P, 2P) hold X_(-) (when
+// `leaving`), zero beyond p.
 // Each CTA (blockIdx.z = stream) moves a tile of 32 samples x 32 variables
 // through shared memory so that both the row-major reads and the
 // variable-major writes are coalesced; the thread that reads X_(-) from a ring
 // slot also writes X_(+) into it.
 __global__ void __launch_bounds__(256)
 k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict__ xin_base,
-                const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap)
+                const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap, int leaving)
 {
     __shared__ float tin[32][33], tout[32][33];
     const TcStreamDesc sd = sdesc[blockIdx.z];
@@ -65,9 +66,11 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
             int64_t slot = head + r;
             if (slot >= sd.T) slot -= sd.T;
             const float raw_in = v < sd.n ? x_in[(int64_t)r * ld + v] : 0.0f;
-            float raw_out;
-            if (x_out != nullptr) raw_out = v < sd.n ? x_out[(int64_t)r * ld + v] : 0.0f;
-            else raw_out = sd.ring[slot * sd.npad + v];
+            float raw_out = 0.0f;
+            if (leaving) {
+                if (x_out != nullptr) raw_out = v < sd.n ? x_out[(int64_t)r * ld + v] : 0.0f;
+                else raw_out = sd.ring[slot * sd.npad + v];
+            }
             sd.ring[slot * sd.npad + v] = raw_in;
             badv |= !isfinite(raw_in);
             if (v < sd.n) {
@@ -83,7 +86,7 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
         const int v = v0 + vv, r = r0 + tx;
         if (v < sd.npad && r < P) {
             sd.XT[(int64_t)v * Kcap + r] = tin[tx][vv];
-            sd.XT[(int64_t)v * Kcap + P + r] = tout[tx][vv];
+            if (leaving) sd.XT[(int64_t)v * Kcap + P + r] = tout[tx][vv];
         }
     }
     if (badv) atomicOr(sd.status, kStatusNonFinite);
@@ -214,7 +217,7 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_final;
     __shared__ uint32_t s_tbase;
     __shared__ int s_abort;
-    __shared__ int64_t s_rowoff[4][NMAX];    // one copy per epilogue warp
+    __shared__ int64_t s_roww[4][NMAX];      // one copy per epilogue warp
     __shared__ int32_t s_rowcolmin[4][NMAX];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -345,16 +348,18 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const UnitRange R = unit_range(args, split);
             const TcOrder& od = args.ord[item.stream * (kMaxOrder + 1) + item.s];
             const uint32_t ab = it & 1;
-            // this warp's copy of the item's row tables
-            int64_t* rowoff = s_rowoff[ew];
+            // this warp's copy of the row tables of an item that spans groups
+            int64_t* roww = s_roww[ew];
             int32_t* rowcolmin = s_rowcolmin[ew];
-            __syncwarp();
-            for (int r = lane; r < NMAX; r += 32) {
-                const bool v = r < item.nrows;
-                rowoff[r] = v ? od.rowoff[item.row0 + r] : 0;
-                rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
+            if (!item.fast) {
+                __syncwarp();
+                for (int r = lane; r < NMAX; r += 32) {
+                    const bool v = r < item.nrows;
+                    roww[r] = v ? od.roww[item.row0 + r] : 0;
+                    rowcolmin[r] = v ? od.rowcolmin[item.row0 + r] : INT_MAX;
+                }
+                __syncwarp();
             }
-            __syncwarp();
             const bool ok = mbar_wait(&bar_accfull[ab], (it >> 1) & 1, kWaitLimit);
             if (!ok || *(volatile int*)&s_abort) {
                 if (!ok && lane == 0) atomicOr(args.status, kStatusTimeout);
@@ -365,23 +370,43 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             const int i = 32 * quarter + lane;
             const bool ivalid = i < item.ncols;
             const int cglob = item.col0 + i;
-            const int64_t co = ivalid ? od.coloff[cglob] : 0;
             float* Win = args.W + (int64_t)(2 * split) * args.wslice + od.woff;
             float* Wout = Win + args.wslice;
             const int NB = (item.nrows + 15) & ~15;
-            for (int jb = 0; jb < NB; jb += 16) {
-                uint32_t d0[16], d1[16];
+            // 32 rows per round: two TMEM loads per accumulator, one wait, then
+            // one coalesced 128-byte store per row (lanes = consecutive slots)
+            for (int jb = 0; jb < NB; jb += 32) {
+                const bool two = jb + 16 < NB;  // warp-uniform
+                uint32_t d0[32], d1[32];
                 const uint32_t ta = tbase + ab * 256u + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
-                if (R.nplus > 0) tmem_ld16(ta, d0);
-                if (R.nminus > 0) tmem_ld16(ta + (uint32_t)NMAX, d1);
+                if (R.nplus > 0) {
+                    tmem_ld16p(ta, d0);
+                    if (two) tmem_ld16p(ta + 16u, d0 + 16);
+                }
+                if (R.nminus > 0) {
+                    tmem_ld16p(ta + (uint32_t)NMAX, d1);
+                    if (two) tmem_ld16p(ta + (uint32_t)NMAX + 16u, d1 + 16);
+                }
                 tmem_ld_wait();
+                if (item.fast) {
+                    const int64_t w0 = (int64_t)item.wrow0 + (int64_t)jb * item.wwidth + cglob;
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int r = jb + t;
-                    if (ivalid && r < item.nrows && cglob >= rowcolmin[r]) {
-                        const int64_t e = rowoff[r] + co;
-                        Win[e] = R.nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
-                        if (args.nminus > 0) Wout[e] = R.nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
+                    for (int t = 0; t < 32; ++t) {
+                        if (ivalid && jb + t < item.nrows) {
+                            const int64_t e = w0 + (int64_t)t * item.wwidth;
+                            Win[e] = R.nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
+                            if (args.nminus > 0) Wout[e] = R.nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) {
+                        const int r = jb + t;
+                        if (ivalid && r < item.nrows && cglob >= rowcolmin[r]) {
+                            const int64_t e = roww[r] + cglob;
+                            Win[e] = R.nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
+                            if (args.nminus > 0) Wout[e] = R.nminus > 0 ? __uint_as_float(d1[t]) : 0.0f;
+                        }
                     }
                 }
             }
@@ -395,10 +420,15 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
-// S += (double)(sum_k W[k][0][e]) for every (stream, order) segment (window batches).
+// Batch q of the window: S += (double)D_in for every (stream, order) segment,
+// D_in = sum_k W[k][0] at the element's workspace slot; with a FIFO, D_in is
+// also kept (storage order) in slot (head / p + q) mod nslots, the batch's slot
+// from then on.
+// Threads run over storage elements (e) so the FP64 sums are read and
+// written contiguously.
 __global__ void __launch_bounds__(256)
 k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const TcAccSeg* __restrict__ segs,
-                int nsegs)
+                int nsegs, int q)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < wslice;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -408,17 +438,18 @@ k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const T
             if (segs[mid].begin <= e) lo = mid;
             else hi = mid - 1;
         }
-        float din = 0.0f;
-        int k = 0;
-        for (; k + 4 <= ksplit; k += 4) {  // four loads in flight, added in slice order
-            float v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = W[(int64_t)(2 * (k + j)) * wslice + e];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) din += v[j];
+        const TcAccSeg& g = segs[lo];
+        const int64_t el = e - g.begin;
+        if (el >= g.E) continue;
+        const int32_t blk = (int32_t)(el / g.bs), a = (int32_t)(el - (int64_t)blk * g.bs);
+        const int32_t aL = a / g.bR, aR = a - aL * g.bR;
+        const int64_t slot = (int64_t)g.wblk[2 * blk] + (int64_t)aL * g.wblk[2 * blk + 1] + aR;
+        const float din = sum_in_partials(W + g.begin + slot, wslice, ksplit);
+        g.S[el] += f32_to_f64(din);
+        if (g.fifo != nullptr && q < g.nslots) {
+            const int64_t f = (*g.head / g.p + q) % g.nslots;
+            g.fifo[f * g.fstride + el] = din;
         }
-        for (; k < ksplit; ++k) din += W[(int64_t)(2 * k) * wslice + e];
-        segs[lo].S[e - segs[lo].begin] += f32_to_f64(din);
     }
 }
 
@@ -520,7 +551,7 @@ double item_chunk_cost(int nrows)
 }  // namespace
 
 int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
-                   int precision, int* status, const DevAlloc& alloc)
+                   int precision, int* status, bool fifo, const DevAlloc& alloc)
 {
     (void)b;
     plan.precision = precision;
@@ -586,9 +617,16 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
             const UpdateTables& t = (*S.tables)[s];
             const OrderTables& ot = S.upd->ord[s];
             TcOrder& o = ord[(size_t)i * (kMaxOrder + 1) + s];
-            o.rowoff = ot.rowoff;
-            o.coloff = ot.coloff;
             o.woff = wtot + S.Eoff[s];
+            const std::vector<int64_t> roww = build_w_rows(t);
+            {
+                int64_t* dw = nullptr;
+                e = alloc(sizeof(int64_t) * std::max<size_t>(roww.size(), 1), (void**)&dw);
+                if (e != cudaSuccess) return (int)e;
+                e = cudaMemcpy(dw, roww.data(), sizeof(int64_t) * roww.size(), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return (int)e;
+                o.roww = dw;
+            }
             const int64_t loff = add_set(t.h, 1, t.rowvar);
             const int64_t roff = add_set(t.sh, 0, t.colvar);
             const int nbar = (int)t.colstart.size();
@@ -643,6 +681,12 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
                     it.acol = (int32_t)(roff + c);
                     it.bbox = b_box_rows(it.nrows);
                     it.stream = i;
+                    // rows of one group: the slots of a row follow from the first row's
+                    const int m0 = (int)(std::upper_bound(t.rowstart.begin(), t.rowstart.end(), R.r0) -
+                                         t.rowstart.begin()) - 1;
+                    it.fast = R.r1 <= t.rowstart[m0 + 1] ? 1 : 0;
+                    it.wwidth = (int32_t)(ncols - t.colstart[m0]);
+                    it.wrow0 = (int32_t)roww[R.r0];
                     items.push_back(it);
                     issued += 3.0 * TM * ((it.nrows + 15) & ~15);
                 }
@@ -705,6 +749,26 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     e = cudaMemset(plan.W, 0, sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice);
     if (e != cudaSuccess) return (int)e;
 
+    // batch-sum FIFO: T_i / p slots of every stream's sums (workspace order)
+    plan.fbase.assign(plan.nstreams, 0);
+    if (fifo) {
+        bool ok = true;
+        int64_t ftot = 0;
+        for (int i = 0; i < plan.nstreams; ++i) {
+            if (streams[i].T % p != 0) ok = false;
+            plan.fbase[i] = ftot;
+            ftot += streams[i].T / p * streams[i].Eoff[streams[i].d + 1];
+        }
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) ok = false;
+        if (ok && (size_t)ftot * sizeof(float) <= free_b / 4) {
+            e = alloc(sizeof(float) * (size_t)std::max<int64_t>(ftot, 1), (void**)&plan.fifo);
+            if (e != cudaSuccess) return (int)e;
+            e = cudaMemset(plan.fifo, 0, sizeof(float) * (size_t)std::max<int64_t>(ftot, 1));
+            if (e != cudaSuccess) return (int)e;
+        }
+    }
+
     e = cudaFuncSetAttribute(k_kr_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
     if (e != cudaSuccess) return (int)e;
     e = cudaFuncSetAttribute(k_kr_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM);
@@ -714,19 +778,19 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
 }
 
 cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
-                          cudaStream_t st)
+                          bool leaving, cudaStream_t st)
 {
     if (p > plan.p) return cudaErrorInvalidValue;
     const dim3 grid((plan.P + 31) / 32, (plan.npad_max + 31) / 32, plan.nstreams);
-    k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap);
+    k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap, leaving ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_build(plan, 2 * plan.P, st);
+    return launch_build(plan, (leaving ? 2 : 1) * plan.P, st);
 }
 
-cudaError_t tc_gemm_push(const TcPlan& plan, cudaStream_t st)
+cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, cudaStream_t st)
 {
-    return launch_gemm(plan, plan.P / KC, plan.P / KC, plan.P, st);
+    return launch_gemm(plan, plan.P / KC, leaving ? plan.P / KC : 0, plan.P, st);
 }
 
 cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
@@ -740,15 +804,17 @@ cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
     return launch_gemm(plan, plan.P / KC, 0, 0, st);
 }
 
-cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, cudaStream_t st)
+cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, int q,
+                                 cudaStream_t st)
 {
-    k_tc_accumulate<<<grid_for(plan.wslice), 256, 0, st>>>(plan.W, plan.wslice, plan.ksplit, segs_dev, nsegs);
+    k_tc_accumulate<<<grid_for(plan.wslice), 256, 0, st>>>(plan.W, plan.wslice, plan.ksplit, segs_dev, nsegs, q);
     return cudaGetLastError();
 }
 
-int tc_autotune(TcPlan& plan, int reps, cudaStream_t st, double* best_ms)
+int tc_autotune(TcPlan& plan, int reps, bool leaving, cudaStream_t st, double* best_ms)
 {
     const int chunks = plan.P / KC;
+    const int mchunks = leaving ? chunks : 0;
     int best = plan.ksplit;
     double best_t = 1e30;
     cudaEvent_t e0, e1;
@@ -756,9 +822,9 @@ int tc_autotune(TcPlan& plan, int reps, cudaStream_t st, double* best_ms)
         return -(int)cudaErrorUnknown;
     for (int ks = 1; ks <= plan.ksplit_max && ks <= chunks; ks *= 2) {
         plan.ksplit = ks;
-        cudaError_t e = launch_gemm(plan, chunks, chunks, plan.P, st);  // warm-up
+        cudaError_t e = launch_gemm(plan, chunks, mchunks, plan.P, st);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm(plan, chunks, chunks, plan.P, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm(plan, chunks, mchunks, plan.P, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

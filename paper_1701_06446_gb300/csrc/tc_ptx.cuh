@@ -157,6 +157,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+// 16 consecutive columns into r[0..15] (pointer form for sub-ranges of a larger array).
+__device__ __forceinline__ void tmem_ld16p(uint32_t taddr, uint32_t* r)
+{
+    tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(r));
+}
+
 __device__ __forceinline__ void tmem_ld_wait()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

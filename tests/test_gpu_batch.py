@@ -33,11 +33,14 @@ SPECS = [(3, 3, 512), (17, 4, 1024), (8, 2, 256), (33, 4, 512), (64, 3, 768), (5
          (40, 3, 256), (1, 4, 512), (70, 4, 512)]
 
 
-def test_batch_matches_oracle_and_standalone_handles():
-    b, p, steps = 4, 64, 3
+@pytest.mark.parametrize("p", [64, 96])
+def test_batch_matches_oracle_and_standalone_handles(p):
+    """p = 64 divides every T (batch-sum FIFO); p = 96 does not (leaving rows recomputed)."""
+    b, steps = 4, 3
     data = make_batch_data(SPECS, p, steps, 100)
     ns, ds, Ts = zip(*SPECS)
     with CumWinBatch(ns, ds, Ts, b, p, "bf16") as B:
+        assert B.fifo == all(T % p == 0 for T in Ts)
         B.fill([torch.from_numpy(X[:T]).cuda() for X, (n, d, T) in zip(data, SPECS)])
         for k in range(steps):
             B.push(B.pack([torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda()

@@ -100,6 +100,60 @@ def test_mixed_sliding_equals_recompute_exactly():
             assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
 
 
+def test_fifo_matches_recomputing_form_bitwise():
+    """The batch-sum FIFO (Section 2.4's alternative scheme) subtracts the stored
+    FP32 sum of the leaving batch; recomputing X_(-) (caller-supplied leaving rows)
+    gives the same FP32 sum, so both handles hold bitwise equal moments."""
+    n, d, b, T, p = 13, 4, 3, 1024, 128
+    rng = np.random.default_rng(21)
+    X = (rng.standard_t(6, size=(T + 20 * p, n)) + 1.5).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as fifo, CumWin(n, d, b, T, p, "bf16") as rec:
+        fifo.fill(Xd[:T])
+        rec.fill(Xd[:T])
+        assert fifo.fifo and rec.fifo
+        for w in range(20):
+            fifo.push(Xd[T + w * p: T + (w + 1) * p])
+            rec.push(Xd[T + w * p: T + (w + 1) * p], Xd[w * p: (w + 1) * p])
+        assert fifo.fifo and not rec.fifo
+        for s in range(1, d + 1):
+            assert torch.equal(fifo.moments(s), rec.moments(s)), s
+            assert torch.equal(fifo.cumulants(s), rec.cumulants(s)), s
+        check_bounds(errors_vs_oracle(fifo, X[20 * p: 20 * p + T]))
+
+
+def test_fifo_retired_by_short_shift_and_restored_by_recompute():
+    n, d, b, T, p = 10, 4, 4, 768, 96
+    rng = np.random.default_rng(22)
+    X = (rng.gamma(3.0, size=(T + 30 * p, n)) - 1.0).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        assert h.fifo
+        pos = T
+        for w in range(3):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        h.push(Xd[pos: pos + 37])  # fewer rows than p: X_(-) recomputed, FIFO retired
+        pos += 37
+        assert not h.fifo
+        for w in range(4):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        check_bounds(errors_vs_oracle(h, X[pos - T: pos]))
+        h.recompute()  # head is no longer a multiple of p; the FIFO slots follow it
+        assert h.fifo
+        for w in range(2 * T // p + 3):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        assert h.fifo
+        check_bounds(errors_vs_oracle(h, X[pos - T: pos]))
+        slide = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        h.recompute()
+        for s in range(1, d + 1):
+            assert rel_fro(slide[s - 1], h.moments(s).cpu().numpy()) <= 1e-13, s
+
+
 def test_mixed_vs_fp64_form_n60():
     """n=60, d=4, b=3, T=2^15, p=2^10: the mixed form against the FP64 GPU form
     (every element) and against the oracle (sampled tuples)."""
