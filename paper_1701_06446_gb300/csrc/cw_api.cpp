@@ -461,15 +461,34 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
         }
         utot += us[nwin];
     }
+    // fold segments: (window, order) with the order's stored elements
+    std::vector<int64_t> abeg(1, 0);
+    std::vector<int32_t> aarg;
+    for (int pass = 0; pass < 2; ++pass) {  // orders <= 3 first, then order 4
+        for (int w = 0; w < nwin; ++w)
+            for (int s = 1; s <= std::min(df, wins[w]->d); ++s) {
+                if ((s == 4) != (pass == 1)) continue;
+                aarg.push_back(s * nwin + w);
+                abeg.push_back(abeg.back() + wins[w]->E[s]);
+            }
+        if (pass == 0) f.nseg_lo = (int32_t)aarg.size();
+    }
+    f.nseg = (int32_t)aarg.size();
     fp.smem = fused_smem_bytes(f, df);
     fp.grid = fused_grid(df, fp.smem, sm_count);
     if (fp.grid < 1) return CUMWIN_OK;
     int64_t* dus = nullptr;
     CW_TRY(mem.upload(&dus, ustart));
     f.ustart = dus;
+    int64_t* dab = nullptr;
+    int32_t* daa = nullptr;
+    CW_TRY(mem.upload(&dab, abeg));
+    CW_TRY(mem.upload(&daa, aarg));
+    f.abeg = dab;
+    f.aarg = daa;
     CW_TRY(mem.alloc(&f.upart, (size_t)std::max<int64_t>(utot, 1)));
-    CW_TRY(mem.alloc(&f.bar, 2));
-    CW_TRY(cudaMemset(f.bar, 0, 2 * sizeof(unsigned)));
+    CW_TRY(mem.alloc(&f.bar, kBarrierWords));
+    CW_TRY(cudaMemset(f.bar, 0, kBarrierWords * sizeof(unsigned)));
     f.norm = norm_dev;
     f.status = status;
     fp.dfused = df;
@@ -490,6 +509,7 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
         f.args = args;
         f.advance = advance;
         f.advance_heads = d <= fp.dfused && advance != 0;
+        f.fold = accum != 0;
         CW_TRY(launch_recover_fused(f, fp.dfused, fp.grid, fp.smem, st));
         *launches += 1;
         s0 = fp.dfused + 1;

@@ -141,21 +141,24 @@ cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advanc
                               cudaStream_t st);
 
 // Orders 1..dfused (dfused <= kFusedMax) of every window in one cooperative
-// launch with a grid barrier between orders; one norm partial per work unit
+// launch (grid barriers between its phases); one norm partial per work unit
 // (a group of blocks of one window, or a 256-offset slice of one block), the
 // norms of those orders reduced at the end, and the ring heads advanced when
 // no higher order follows.
 constexpr int kFusedMax = 4;
+constexpr int kBarrierWords = 2;  // one 64-bit arrival counter
 struct FusedRecovery {
     const CumArgs* args;     // args[s * nwin + w], one accumulate mode
     const int64_t* ustart;   // [(kFusedMax + 1)][nwin + 1] first work unit of each window, per order
     double* upart;           // norm partial of each work unit; order s from upoff[s]
     const NormArgs* norm;    // [nwin]
-    unsigned* bar;           // grid barrier state [2] (arrivals, generation), zero at creation
+    unsigned* bar;           // grid barrier state [kBarrierWords], zero at creation
     int* status;
+    const int64_t* abeg;     // [nseg + 1] first stored element of each (window, order) segment:
+    const int32_t* aarg;     // [nseg] its index into args; orders <= 3 first (nseg_lo), then order 4
     int64_t upoff[kFusedMax + 1];
     int64_t advance;
-    int32_t nwin, advance_heads;
+    int32_t nwin, advance_heads, nseg, nseg_lo, fold;
     int32_t slots[kFusedMax + 1], gy[kFusedMax + 1];
 };
 size_t fused_smem_bytes(const FusedRecovery& f, int dfused);

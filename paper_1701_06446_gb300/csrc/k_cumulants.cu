@@ -20,10 +20,11 @@
 // accumulates multiplicity * C^2 (Algorithm 5 with k = 2).
 //
 // Two launch forms share that per-group routine:
-//   * k_recover_fused: orders 1..min(d, 4) in one cooperative launch, a grid
-//     barrier between orders (order s reads C_1..C_{s-1}), norm partials per
-//     work unit, and the norms reduced at the end; the small orders cost a
-//     barrier each instead of a launch each.
+//   * k_recover_fused: orders 1..min(d, 4) in one cooperative launch: every
+//     sum takes the shift's workspace first, then orders 1-3 run together (a
+//     higher order recomputes the C_1 / C_2 factors it needs from the sums
+//     instead of waiting for them), a grid barrier, order 4, a grid barrier
+//     and the norms; norm partials per work unit.
 //   * k_cumulants<S>: one launch per order above 4, one norm partial per CTA,
 //     reduced by k_norm_final.
 #include <algorithm>
@@ -128,41 +129,85 @@ __device__ __forceinline__ Elem<S> make_elem(int b, int bs, int bR, int slots, i
     return c;
 }
 
-// The element of thread `c` in block `blk`: fold the shift's workspace into
-// S_S, recover C_S and add multiplicity * C^2 to `local`.  No shared memory
-// and no CTA synchronisation: the per-block sub-block ranks come from a table
-// whose rows all threads of a block read together (L1 broadcast).
-template <int S>
-__device__ __forceinline__ void recover_elem(const CumArgs& a, const Elem<S>& c, int64_t blk, int64_t fslot,
-                                             double& local)
+// FIFO slot of the batch that leaves with this shift: head / p.
+__device__ __forceinline__ int64_t fifo_slot(const CumArgs& a)
+{
+    const int64_t hd = *a.head;
+    return hd < ((int64_t)1 << 31) ? (int64_t)((unsigned)hd / (unsigned)a.p) : hd / a.p;
+}
+
+// Fold the shift's workspace into one element e of S_s (block blk, in-block
+// offset off): S += (double)D_in - (double)D_out (CumArgs::accum).  Split in
+// a load half and a store half so that callers can keep several elements'
+// loads in flight.
+struct FoldVal {
+    double* sp;    // the sum
+    float* fptr;   // FIFO entry (accum 2) or null
+    double s;
+    float din, dout;
+};
+
+__device__ __forceinline__ FoldVal fold_load(const CumArgs& a, int64_t blk, int off, int64_t e, int64_t fslot)
+{
+    FoldVal v;
+    const int offL = off / a.bR, offRw = off - (off / a.bR) * a.bR;
+    const int2 wb = *reinterpret_cast<const int2*>(a.wblk + 2 * blk);
+    const int64_t w = (int64_t)wb.x + (int64_t)offL * wb.y + offRw;
+    v.fptr = nullptr;
+    if (a.accum == 1) {
+        sum_partials(a.W + a.woff + w, a.wslice, a.ksplit, v.din, v.dout);
+    } else {
+        v.din = sum_in_partials(a.W + a.woff + w, a.wslice, a.ksplit);
+        v.fptr = a.fifo + fslot * a.fstride + e;  // FIFO in storage order: coalesced
+        v.dout = *v.fptr;
+    }
+    v.sp = a.S[a.s] + e;
+    v.s = *v.sp;
+    return v;
+}
+
+__device__ __forceinline__ void fold_store(const FoldVal& v)
+{
+    *v.sp = v.s + (f32_to_f64(v.din) - f32_to_f64(v.dout));
+    if (v.fptr != nullptr) *v.fptr = v.din;
+}
+
+__device__ __forceinline__ void fold_elem(const CumArgs& a, int64_t blk, int off, int64_t e, int64_t fslot)
+{
+    fold_store(fold_load(a, blk, off, e, fslot));
+}
+
+// C_2 at storage index x of order 2, from the (folded) sums: what the order-2
+// element computes, operation for operation, with C_1 = S_1 / T.
+__device__ __forceinline__ double c2_from_sums(const CumArgs& a2, int64_t x)
+{
+    const int b = a2.b, bb = b * b;
+    const int64_t blk = x / bb;
+    const int off = (int)(x - blk * bb);
+    const int2 q = *reinterpret_cast<const int2*>(a2.subrank + 2 * blk);  // ranks of (j0), (j1)
+    const double cA = a2.S[1][(int64_t)q.x * b + off / b] * a2.invT;
+    const double sR = a2.S[1][(int64_t)q.y * b + off % b];
+    return fma(-cA, sR, a2.S[2][x]) * a2.invT;
+}
+
+// The element of thread `c` in block `blk`: optionally fold the shift's
+// workspace into S_S first (FOLD), recover C_S and add multiplicity * C^2 to
+// `local`.  Factors C_k with k <= OTF are recomputed from the sums instead of
+// read (k = 1: S_1 / T; k = 2: c2_from_sums with the order-2 tables of `a2`),
+// which lets orders 1-3 run without a grid barrier between them.  No shared
+// memory and no CTA synchronisation: the per-block sub-block ranks come from a
+// table whose rows all threads of a block read together (L1 broadcast).
+template <int S, bool FOLD, int OTF>
+__device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2, const Elem<S>& c, int64_t blk,
+                                             int64_t fslot, double& local)
 {
     constexpr int NS = Subsets<S>::N;
-    constexpr int ND = Subsets<S>::ND;
     const int b = a.b;
     const int64_t e = blk * a.bs + c.off;
-    double* Ss = a.S[S];
-    // 1. independent loads: the sum and the workspace
-    double acc = Ss[e];
-    float din = 0.0f, dout = 0.0f;
-    float* fptr = nullptr;
-    if (a.accum) {
-        const int2 wb = *reinterpret_cast<const int2*>(a.wblk + 2 * blk);
-        const int64_t w = (int64_t)wb.x + (int64_t)c.offL * wb.y + c.offRw;
-        if (a.accum == 1) {
-            sum_partials(a.W + a.woff + w, a.wslice, a.ksplit, din, dout);
-        } else {
-            din = sum_in_partials(a.W + a.woff + w, a.wslice, a.ksplit);
-            fptr = a.fifo + fslot * a.fstride + e;  // FIFO in storage order: coalesced
-            dout = *fptr;
-        }
-    }
-    if (a.accum) {
-        acc += f32_to_f64(din) - f32_to_f64(dout);
-        Ss[e] = acc;
-        if (fptr != nullptr) *fptr = din;
-    }
-    // 2. the subsets: sub-block ranks (rank(j_A), rank(j_rest)) of the block,
-    //    one gather per factor, one FP64 multiply-add
+    if (FOLD && a.accum) fold_elem(a, blk, c.off, e, fslot);
+    double acc = a.S[S][e];
+    // the subsets: sub-block ranks (rank(j_A), rank(j_rest)) of the block, one
+    // gather per factor, one FP64 multiply-add
     const int32_t* sr = a.subrank + (size_t)blk * NS * 2;
 #pragma unroll(S <= 4 ? NS : 4)
     for (int t = 0; t < NS; ++t) {
@@ -170,8 +215,12 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const Elem<S>& c,
         const int la = __popc(2u * t + 1u), lr = S - la;
         int oa, orr;
         subset_offsets<S>(c, b, t, oa, orr);
-        const double cA = a.C[la][q.x * ipow_c(b, la) + oa];
-        const double sR = a.S[lr][q.y * ipow_c(b, lr) + orr];
+        const int64_t ia = (int64_t)q.x * ipow_c(b, la) + oa;
+        double cA;
+        if (OTF >= 1 && la == 1) cA = a.S[1][ia] * a.invT;
+        else if (OTF >= 2 && la == 2) cA = c2_from_sums(*a2, ia);
+        else cA = a.C[la][ia];
+        const double sR = a.S[lr][(int64_t)q.y * ipow_c(b, lr) + orr];
         acc = fma(-cA, sR, acc);
     }
     const double cv = acc * a.invT;
@@ -204,41 +253,71 @@ __global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__
     if (a.E == 0) return;                 // this window has no order S
     __shared__ double red[NT / 32];
     const Elem<S> c = make_elem<S>(a.b, a.bs, a.bR, slots, blockIdx.y);
-    const int64_t fslot = a.accum == 2 ? *a.head / a.p : 0;
+    const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
     const int64_t nblocks = a.E / a.bs;
     double local = 0.0;
     if (c.valid)
         for (int64_t blk = (int64_t)blockIdx.x * slots + c.slot; blk < nblocks; blk += (int64_t)gridDim.x * slots)
-            recover_elem<S>(a, c, blk, fslot, local);
+            recover_elem<S, true, 0>(a, nullptr, c, blk, fslot, local);
     const double z = cta_sum(local, red);
     if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = z;
 }
 
-// Grid barrier of a cooperative launch: the last CTA to arrive resets the
-// count and bumps the generation the others wait on.  Bounded: a CTA that
-// waits too long records kStatusTimeout and goes on.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, int* status)
+// Grid barrier of a cooperative launch over one 64-bit arrival counter that
+// only grows: every barrier adds gridDim.x, so between launches it is a
+// multiple of gridDim.x, and barrier k of a launch completes when it reaches
+// base + (k + 1) * gridDim.x, base being the counter at the launch's start
+// rounded down to a multiple of gridDim.x (no CTA can pass barrier 0 before
+// all have read it).  Arrivals release, waits acquire; a wait that takes too
+// long records kStatusTimeout and goes on.
+__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.add.release.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+struct GridBarrier {
+    unsigned long long* ctr;
+    unsigned long long base;
+    unsigned k;
+};
+
+__device__ __forceinline__ GridBarrier grid_barrier_init(unsigned* state, unsigned long long* s_base)
+{
+    GridBarrier g;
+    g.ctr = reinterpret_cast<unsigned long long*>(state);
+    if (threadIdx.x == 0) {
+        const unsigned long long v = ld_acquire(g.ctr);
+        *s_base = v - v % gridDim.x;
+    }
+    __syncthreads();
+    g.base = *s_base;
+    g.k = 0;
+    return g;
+}
+
+__device__ __forceinline__ void grid_barrier(GridBarrier& g, int* status)
 {
     __syncthreads();
+    ++g.k;
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*gen == g) {
-                if (clock64() - t0 > kBarrierLimit) {
-                    atomicOr(status, kStatusTimeout);
-                    break;
-                }
+        const unsigned long long target = g.base + (unsigned long long)g.k * gridDim.x;
+        atom_add_release(g.ctr, 1ull);
+        const long long t0 = clock64();
+        while (ld_acquire(g.ctr) < target) {
+            if (clock64() - t0 > kBarrierLimit) {
+                atomicOr(status, kStatusTimeout);
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
 }
@@ -255,22 +334,25 @@ __device__ __forceinline__ int unit_window(const int64_t* ustart, int nwin, int6
     return lo;
 }
 
-// One order of the fused recovery.  Units go round-robin over the CTAs; a
-// CTA's units of one window are consecutive, so it sums them per thread and
-// reduces once per window ("run"): the run's sum goes to the slot of its first
-// unit and the other units of the run hold zero, so that every unit slot is
-// written and the window's norm is the sum of its unit slots.
-template <int S>
-__device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red)
+// One order of the fused recovery (the sums already folded).  Units go
+// round-robin over the CTAs, starting `rot` CTAs further on so that the small
+// orders land on different CTAs; a CTA's units of one window are consecutive,
+// so it sums them per thread and reduces once per window ("run"): the run's
+// sum goes to the slot of its first unit and the other units of the run hold
+// zero, so that every unit slot is written and the window's norm is the sum of
+// its unit slots.
+template <int S, int OTF>
+__device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red, int64_t rot)
 {
     const int slots = f.slots[S], gy = f.gy[S];
     const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
     const int64_t total = us[f.nwin];
     double* part = f.upart + f.upoff[S];
+    const int64_t G = gridDim.x;
     int cur = -1;
     int64_t first = 0;
     double local = 0.0;
-    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+    for (int64_t u = ((int64_t)blockIdx.x + G - rot % G) % G; u < total; u += G) {
         const int w = unit_window(us, f.nwin, u);
         if (w != cur) {
             if (cur >= 0) {
@@ -284,17 +366,49 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red)
             part[u] = 0.0;
         }
         const CumArgs& a = f.args[(int64_t)S * f.nwin + w];
+        const CumArgs* a2 = OTF >= 2 ? &f.args[(int64_t)2 * f.nwin + w] : nullptr;
         const int64_t ul = u - us[w];
         const int64_t grp = ul / gy;
         const int y = (int)(ul - grp * gy);
         const Elem<S> c = make_elem<S>(a.b, a.bs, a.bR, slots, y);
-        const int64_t fslot = a.accum == 2 ? *a.head / a.p : 0;
         const int64_t blk = grp * slots + c.slot;
-        if (c.valid && blk < a.E / a.bs) recover_elem<S>(a, c, blk, fslot, local);
+        if (c.valid && blk < a.E / a.bs) recover_elem<S, false, OTF>(a, a2, c, blk, 0, local);
     }
     if (cur >= 0) {
         const double z = cta_sum(local, red);
         if (threadIdx.x == 0) part[first] = z;
+    }
+}
+
+// Fold the shift's workspace into the sums of the (window, order) segments
+// [seg0, seg1): one thread per stored element, four elements per thread in
+// flight (their loads issued before any of their stores).
+__device__ __forceinline__ void fused_fold(const FusedRecovery& f, int seg0, int seg1)
+{
+    const int64_t g0 = f.abeg[seg0], g1 = f.abeg[seg1];
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    for (int64_t base = g0 + (int64_t)blockIdx.x * NT + threadIdx.x; base < g1; base += 4 * stride) {
+        FoldVal v[4];
+        bool ok[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t g = base + k * stride;
+            ok[k] = g < g1;
+            if (!ok[k]) continue;
+            int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (f.abeg[mid] <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            const CumArgs& a = f.args[f.aarg[lo]];
+            const int e = (int)(g - f.abeg[lo]);  // E_s < 2^31
+            const int blk = e / a.bs;
+            v[k] = fold_load(a, blk, e - blk * a.bs, e, a.accum == 2 ? fifo_slot(a) : 0);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (ok[k]) fold_store(v[k]);
     }
 }
 
@@ -303,20 +417,31 @@ template <int DF>
 __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__ FusedRecovery f)
 {
     __shared__ double red[NT / 32];
-    fused_order<1>(f, red);
+    __shared__ unsigned long long s_base;
+    GridBarrier gb = grid_barrier_init(f.bar, &s_base);
+    // 1. the sums of orders 1..min(DF, 3) take the shift's workspace
+    if (f.fold) {
+        fused_fold(f, 0, f.nseg_lo);
+        grid_barrier(gb, f.status);
+    }
+    // 2. orders 1..min(DF, 3): C_1, C_2 recomputed from the sums where a higher
+    //    order needs them, so no barrier between these orders; meanwhile the
+    //    order-4 sums take their workspace (nothing reads them before step 3)
+    if (f.fold) fused_fold(f, f.nseg_lo, f.nseg);
+    int64_t rot = 0;
+    fused_order<1, 0>(f, red, rot);
+    rot += f.ustart[1 * (f.nwin + 1) + f.nwin];
     if (DF >= 2) {
-        grid_barrier(f.bar, f.status);
-        fused_order<(DF >= 2 ? 2 : 1)>(f, red);
+        fused_order<(DF >= 2 ? 2 : 1), 1>(f, red, rot);
+        rot += f.ustart[2 * (f.nwin + 1) + f.nwin];
     }
-    if (DF >= 3) {
-        grid_barrier(f.bar, f.status);
-        fused_order<(DF >= 3 ? 3 : 1)>(f, red);
-    }
+    if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2>(f, red, rot);
+    // 3. order 4 reads the stored C_1..C_3
     if (DF >= 4) {
-        grid_barrier(f.bar, f.status);
-        fused_order<(DF >= 4 ? 4 : 1)>(f, red);
+        grid_barrier(gb, f.status);
+        fused_order<(DF >= 4 ? 4 : 1), 0>(f, red, 0);
     }
-    grid_barrier(f.bar, f.status);
+    grid_barrier(gb, f.status);
     // norms: one warp per (window, order), partials of the order's units of
     // the window added lane-strided, then a fixed shuffle tree
     const int lane = threadIdx.x & 31;
