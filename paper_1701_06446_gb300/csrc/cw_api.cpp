@@ -81,6 +81,7 @@ struct FusedPlan {
     FusedRecovery f{};
     int dfused = 0, grid = 0;
     size_t smem = 0;
+    int64_t emax[kMaxOrder + 1] = {};  // largest E_s over the windows
 };
 
 struct cumwin_s {
@@ -352,6 +353,9 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         a.W = nullptr;
         a.accum = 0;
         a.bR = (int32_t)ipow(b, s - split_rows(s));
+        // the top order's sums follow the workspace order in the mixed forms,
+        // so that folding a shift into them is one coalesced pass
+        a.sgemm = precision != CUMWIN_FP64 && s == d;
         if (precision != CUMWIN_FP64) {
             int32_t* wb = nullptr;
             CW_TRY(h->upload(&wb, build_w_blocks(h->ut[s], n, b)));
@@ -434,7 +438,10 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
                 const NormArgs* norm_dev, int* status, Arena& mem)
 {
     int dmax = 0, device = 0, coop = 0;
-    for (const cumwin_s* h : wins) dmax = std::max(dmax, h->d);
+    for (const cumwin_s* h : wins) {
+        dmax = std::max(dmax, h->d);
+        for (int s = 1; s <= h->d; ++s) fp.emax[s] = std::max(fp.emax[s], h->E[s]);
+    }
     CW_TRY(cudaGetDevice(&device));
     CW_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
     fp.dfused = 0;
@@ -500,7 +507,7 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
 // folded into the sums first (CumArgs::accum; 0 = it is not).  Returns the
 // number of launches through *launches.
 int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_launch, const NormArgs* norm_dev,
-            int nwin, int d, int64_t advance, int accum, cudaStream_t st, int64_t* launches)
+            int nwin, int d, int64_t advance, int accum, int sm_count, cudaStream_t st, int64_t* launches)
 {
     const CumArgs* args = cum_dev + (size_t)accum * (kMaxOrder + 1) * nwin;
     int s0 = 1;
@@ -515,6 +522,10 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
         s0 = fp.dfused + 1;
     }
     for (int s = s0; s <= d; ++s) {
+        if (accum != 0) {  // windows whose top order is s fold it in one linear pass first
+            CW_TRY(launch_fold_linear(args + (size_t)s * nwin, nwin, fp.emax[s], sm_count, st));
+            *launches += 1;
+        }
         CW_TRY(launch_cumulants(s, args + (size_t)s * nwin, nwin, cum_launch[s], st));
         *launches += 1;
     }
@@ -527,8 +538,8 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
 
 int run_cumulants(cumwin_t h, int64_t advance, int accum = 0)
 {
-    const int rc = recover(h->fused, h->cum_dev, h->cum_launch, h->norm_dev, 1, h->d, advance, accum, h->stream,
-                           &h->launches);
+    const int rc = recover(h->fused, h->cum_dev, h->cum_launch, h->norm_dev, 1, h->d, advance, accum,
+                           h->sm_count, h->stream, &h->launches);
     if (rc) return rc;
     if (h->mark(3) != nullptr) h->timed++;
     return CUMWIN_OK;
@@ -549,6 +560,7 @@ std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcP
             g.bR = h->cum[s].bR;
             g.head = h->head;
             g.p = h->p;
+            g.sgemm = h->cum[s].sgemm;
             if (tc.fifo != nullptr) {
                 g.fifo = tc.fifo + tc.fbase[i] + h->Eoff[s];
                 g.fstride = h->Eoff[h->d + 1];
@@ -924,7 +936,10 @@ int cumwin_moments(cumwin_t h, int order, double* out_dev)
 {
     if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
-    CW_TRY(launch_scale(h->S[order], 1.0 / (double)h->T, h->E[order], out_dev, h->stream));
+    if (h->cum[order].sgemm)  // kept in workspace order: gather back to the block layout
+        CW_TRY(launch_gather_sums(h->cum_dev + order, h->E[order], 1.0 / (double)h->T, out_dev, h->stream));
+    else
+        CW_TRY(launch_scale(h->S[order], 1.0 / (double)h->T, h->E[order], out_dev, h->stream));
     return CUMWIN_OK;
 }
 
@@ -1285,7 +1300,7 @@ static int batch_recover(cumwin_batch_t B, int64_t advance, int accum)
 {
     int64_t launches = 0;
     return recover(B->fused, B->cum_dev, B->cum_launch, B->norm_dev, B->nwin, B->dmax, advance, accum,
-                   B->stream, &launches);
+                   B->sm_count, B->stream, &launches);
 }
 
 int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev)

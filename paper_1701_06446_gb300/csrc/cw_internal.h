@@ -70,8 +70,8 @@ struct CumArgs {
     // shift into S_s: S += (double)D_in - (double)D_out with D_in = sum_k W[k][0],
     // read at the element's workspace slot wblk[2 blk] + aL * wblk[2 blk + 1] + aR
     // (in-block offset a = aL * bR + aR).  accum 1: D_out = sum_k W[k][1];
-    // accum 2: D_out = the element's entry (storage order) in slot head / p of
-    // the batch-sum FIFO, which then takes D_in.
+    // accum 2: D_out = the element's entry in slot head / p of the batch-sum
+    // FIFO (workspace order), which then takes D_in.
     const float* W;                  // [ksplit][2][wslice]
     const int32_t* wblk;             // [nblocks][2] (build_w_blocks)
     float* fifo;                     // this order's FIFO in slot 0 (accum 2)
@@ -79,6 +79,7 @@ struct CumArgs {
     int64_t wslice, woff, fstride;
     int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = stacked in/out, 2 = FIFO
     int32_t bR, p;                   // b^(s - h); shift size (accum 2)
+    int32_t sgemm;                   // S_s kept in workspace order (the top order of the mixed forms)
 };
 
 // Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
@@ -125,6 +126,11 @@ CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count);
 // Recovery of order s for nwin windows at once (args_dev[w] for window w;
 // windows without order s have E = 0).
 cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const CumLaunch& L, cudaStream_t st);
+// Fold of the workspace into sums kept in workspace order (args with sgemm),
+// one linear pass per window; others are skipped.
+cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st);
+// out = S_s * scale in storage order for sums kept in workspace order.
+cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale, double* out, cudaStream_t st);
 
 // Norm reduction of one window: partials of order s at normpart[(s-1)*parts ..].
 struct NormArgs {

@@ -128,7 +128,7 @@ struct TcPlan {
     std::vector<int> nbatch_stream;
     // batch-sum FIFO (null when some T is not a multiple of p, or it does not
     // fit): stream i keeps T_i / p slots of its E_i = sum_s E_s FP32 sums in
-    // storage order at fifo + fbase[i] + slot * E_i
+    // workspace order at fifo + fbase[i] + slot * E_i
     float* fifo = nullptr;
     std::vector<int64_t> fbase;
     int* status = nullptr;
@@ -171,6 +171,7 @@ struct TcAccSeg {
     int64_t fstride;       // FIFO slot stride (floats)
     int32_t bs, bR;        // b^s, b^(s - h)
     int32_t p, nslots;
+    int32_t sgemm, pad;    // S in workspace order
 };
 cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, int q,
                                  cudaStream_t st);

@@ -147,23 +147,36 @@ struct FoldVal {
     float din, dout;
 };
 
-__device__ __forceinline__ FoldVal fold_load(const CumArgs& a, int64_t blk, int off, int64_t e, int64_t fslot)
+// Workspace slot of (block blk, in-block offset off) of an order.
+__device__ __forceinline__ int64_t wslot(const CumArgs& a, int64_t blk, int off)
 {
-    FoldVal v;
     const int offL = off / a.bR, offRw = off - (off / a.bR) * a.bR;
     const int2 wb = *reinterpret_cast<const int2*>(a.wblk + 2 * blk);
-    const int64_t w = (int64_t)wb.x + (int64_t)offL * wb.y + offRw;
+    return (int64_t)wb.x + (int64_t)offL * wb.y + offRw;
+}
+
+// Load half of the fold of the element at workspace slot w whose sum lives
+// at S_s[si] (si = w when the order's sums are in workspace order).
+__device__ __forceinline__ FoldVal fold_load_at(const CumArgs& a, int64_t w, int64_t si, int64_t fslot)
+{
+    FoldVal v;
     v.fptr = nullptr;
     if (a.accum == 1) {
         sum_partials(a.W + a.woff + w, a.wslice, a.ksplit, v.din, v.dout);
     } else {
         v.din = sum_in_partials(a.W + a.woff + w, a.wslice, a.ksplit);
-        v.fptr = a.fifo + fslot * a.fstride + e;  // FIFO in storage order: coalesced
+        v.fptr = a.fifo + fslot * a.fstride + w;  // FIFO in workspace order
         v.dout = *v.fptr;
     }
-    v.sp = a.S[a.s] + e;
+    v.sp = a.S[a.s] + si;
     v.s = *v.sp;
     return v;
+}
+
+__device__ __forceinline__ FoldVal fold_load(const CumArgs& a, int64_t blk, int off, int64_t e, int64_t fslot)
+{
+    const int64_t w = wslot(a, blk, off);
+    return fold_load_at(a, w, a.sgemm ? w : e, fslot);
 }
 
 __device__ __forceinline__ void fold_store(const FoldVal& v)
@@ -204,8 +217,8 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2
     constexpr int NS = Subsets<S>::N;
     const int b = a.b;
     const int64_t e = blk * a.bs + c.off;
-    if (FOLD && a.accum) fold_elem(a, blk, c.off, e, fslot);
-    double acc = a.S[S][e];
+    if (FOLD && a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
+    double acc = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
     // the subsets: sub-block ranks (rank(j_A), rank(j_rest)) of the block, one
     // gather per factor, one FP64 multiply-add
     const int32_t* sr = a.subrank + (size_t)blk * NS * 2;
@@ -381,34 +394,28 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red,
 }
 
 // Fold the shift's workspace into the sums of the (window, order) segments
-// [seg0, seg1): one thread per stored element, four elements per thread in
-// flight (their loads issued before any of their stores).
+// [seg0, seg1): one thread per stored element.  A segment whose sums are in
+// workspace order (the top order) is one linear pass over its slots, every
+// access coalesced; the others go through the per-block slot table.
 __device__ __forceinline__ void fused_fold(const FusedRecovery& f, int seg0, int seg1)
 {
     const int64_t g0 = f.abeg[seg0], g1 = f.abeg[seg1];
-    const int64_t stride = (int64_t)gridDim.x * NT;
-    for (int64_t base = g0 + (int64_t)blockIdx.x * NT + threadIdx.x; base < g1; base += 4 * stride) {
-        FoldVal v[4];
-        bool ok[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t g = base + k * stride;
-            ok[k] = g < g1;
-            if (!ok[k]) continue;
-            int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (f.abeg[mid] <= g) lo = mid;
-                else hi = mid - 1;
-            }
-            const CumArgs& a = f.args[f.aarg[lo]];
-            const int e = (int)(g - f.abeg[lo]);  // E_s < 2^31
-            const int blk = e / a.bs;
-            v[k] = fold_load(a, blk, e - blk * a.bs, e, a.accum == 2 ? fifo_slot(a) : 0);
+    for (int64_t g = g0 + (int64_t)blockIdx.x * NT + threadIdx.x; g < g1; g += (int64_t)gridDim.x * NT) {
+        int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (f.abeg[mid] <= g) lo = mid;
+            else hi = mid - 1;
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (ok[k]) fold_store(v[k]);
+        const CumArgs& a = f.args[f.aarg[lo]];
+        const int e = (int)(g - f.abeg[lo]);  // E_s < 2^31
+        const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
+        if (a.sgemm) {
+            fold_store(fold_load_at(a, e, e, fslot));
+        } else {
+            const int blk = e / a.bs;
+            fold_store(fold_load(a, blk, e - blk * a.bs, e, fslot));
+        }
     }
 }
 
@@ -464,6 +471,28 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
             const NormArgs& na = f.norm[w];
             *na.head = (*na.head + f.advance) % na.T;
         }
+}
+
+// Fold of orders whose sums are in workspace order (the top order of windows
+// whose recovery is not fused): one linear coalesced pass per window.
+__global__ void __launch_bounds__(NT) k_fold_linear(const CumArgs* __restrict__ args)
+{
+    const CumArgs& a = args[blockIdx.y];
+    if (a.E == 0 || !a.accum || !a.sgemm) return;
+    const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
+    for (int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x; w < a.E; w += (int64_t)gridDim.x * NT)
+        fold_store(fold_load_at(a, w, w, fslot));
+}
+
+// out[e] = S_s[slot(e)] * scale: the sums of an order kept in workspace order,
+// back in storage order.
+__global__ void __launch_bounds__(NT) k_gather_sums(const CumArgs* __restrict__ args, double scale, double* out)
+{
+    const CumArgs& a = *args;
+    for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < a.E; e += (int64_t)gridDim.x * NT) {
+        const int64_t blk = e / a.bs;
+        out[e] = a.S[a.s][wslot(a, blk, (int)(e - blk * a.bs))] * scale;
+    }
 }
 
 // One CTA per window, one warp per order s >= s_from: lanes add strided
@@ -579,6 +608,22 @@ cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, s
     case 4: return launch_fused_df<4>(f, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st)
+{
+    const int64_t need = (maxE + NT - 1) / NT;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(need, 8LL * sm_count));
+    k_fold_linear<<<dim3(gx, nwin), NT, 0, st>>>(args_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale, double* out, cudaStream_t st)
+{
+    const int64_t need = (E + NT - 1) / NT;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(need, 16384));
+    k_gather_sums<<<gx, NT, 0, st>>>(args_dev, scale, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_norm_final(const NormArgs* args_dev, int nwin, int64_t advance, int s_from, cudaStream_t st)

@@ -50,6 +50,7 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
                 const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap, int leaving)
 {
     __shared__ float tin[32][33], tout[32][33];
+    grid_dep_launch();  // the operand build may launch now; it waits for this grid
     const TcStreamDesc sd = sdesc[blockIdx.z];
     const int r0 = blockIdx.x * 32, v0 = blockIdx.y * 32;
     if (v0 >= sd.npad) return;
@@ -97,6 +98,7 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
 __global__ void __launch_bounds__(256)
 k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, int64_t Kcap)
 {
+    grid_dep_launch();
     const TcStreamDesc sd = sdesc[blockIdx.y];
     const int64_t head = *sd.head;
     const int64_t total = (int64_t)sd.npad * P;
@@ -126,6 +128,8 @@ k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t*
            int64_t rows, int nkb, uint16_t* __restrict__ ops)
 {
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
+    grid_dep_launch();  // the GEMM may launch now; its TMA warp waits for this grid
+    grid_dep_wait();    // the staged samples come from the previous kernel
     const int total = (int)(rows * nkb);
     const int64_t part = rows * Kcap;  // elements of one part
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -254,6 +258,7 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            grid_dep_wait();  // the operands come from the previous kernel
             uint32_t g = 0;
             bool stop = false;
             for (int u = blockIdx.x; u < nunits && !stop; u += gridDim.x) {
@@ -422,8 +427,8 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
 // Batch q of the window: S += (double)D_in for every (stream, order) segment,
 // D_in = sum_k W[k][0] at the element's workspace slot; with a FIFO, D_in is
-// also kept (storage order) in slot (head / p + q) mod nslots, the batch's slot
-// from then on.
+// also kept (workspace order) in slot (head / p + q) mod nslots, the batch's
+// slot from then on.  Sums kept in workspace order are indexed by the slot.
 // Threads run over storage elements (e) so the FP64 sums are read and
 // written contiguously.
 __global__ void __launch_bounds__(256)
@@ -441,16 +446,35 @@ k_tc_accumulate(const float* __restrict__ W, int64_t wslice, int ksplit, const T
         const TcAccSeg& g = segs[lo];
         const int64_t el = e - g.begin;
         if (el >= g.E) continue;
-        const int32_t blk = (int32_t)(el / g.bs), a = (int32_t)(el - (int64_t)blk * g.bs);
-        const int32_t aL = a / g.bR, aR = a - aL * g.bR;
-        const int64_t slot = (int64_t)g.wblk[2 * blk] + (int64_t)aL * g.wblk[2 * blk + 1] + aR;
+        int64_t slot = el;  // sums in workspace order: element = slot
+        if (!g.sgemm) {
+            const int32_t blk = (int32_t)(el / g.bs), a = (int32_t)(el - (int64_t)blk * g.bs);
+            const int32_t aL = a / g.bR, aR = a - aL * g.bR;
+            slot = (int64_t)g.wblk[2 * blk] + (int64_t)aL * g.wblk[2 * blk + 1] + aR;
+        }
         const float din = sum_in_partials(W + g.begin + slot, wslice, ksplit);
         g.S[el] += f32_to_f64(din);
         if (g.fifo != nullptr && q < g.nslots) {
             const int64_t f = (*g.head / g.p + q) % g.nslots;
-            g.fifo[f * g.fstride + el] = din;
+            g.fifo[f * g.fstride + slot] = din;
         }
     }
+}
+
+// Launch configuration with programmatic stream serialization: the kernel may
+// start while the previous one on the stream runs (it waits with
+// grid_dep_wait before reading what that one wrote).
+void pdl_config(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&attr)[1], dim3 grid, dim3 block, size_t smem,
+                cudaStream_t st)
+{
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
 }
 
 inline int grid_for(int64_t work)
@@ -475,26 +499,26 @@ cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, 
     const int units = plan.nitems * plan.ksplit;
     const int grid = units < plan.sm_count ? units : plan.sm_count;
     if (grid < 1) return cudaSuccess;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    pdl_config(cfg, attr, dim3(grid), dim3(GEMM_THREADS), GEMM_SMEM, st);
     if (plan.precision == 1)
-        k_kr_gemm<true><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
-                                                                plan.mapB[2], a);
-    else
-        k_kr_gemm<false><<<grid, GEMM_THREADS, GEMM_SMEM, st>>>(plan.mapA, plan.mapB[0], plan.mapB[1],
-                                                                 plan.mapB[2], a);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, k_kr_gemm<true>, plan.mapA, plan.mapB[0], plan.mapB[1], plan.mapB[2], a);
+    return cudaLaunchKernelEx(&cfg, k_kr_gemm<false>, plan.mapA, plan.mapB[0], plan.mapB[1], plan.mapB[2], a);
 }
 
 cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
 {
     const int nkb = nsamples / 8;
     const int64_t work = plan.oprows * nkb;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    pdl_config(cfg, attr, dim3(grid_for(work)), dim3(256), 0, st);
     if (plan.precision == 1)
-        k_kr_build<true><<<grid_for(work), 256, 0, st>>>(plan.sdesc, plan.Kcap, plan.opvars, plan.oprows,
-                                                         nkb, plan.ops);
-    else
-        k_kr_build<false><<<grid_for(work), 256, 0, st>>>(plan.sdesc, plan.Kcap, plan.opvars, plan.oprows,
-                                                          nkb, plan.ops);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, k_kr_build<true>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
+                                  (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops);
+    return cudaLaunchKernelEx(&cfg, k_kr_build<false>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
+                              (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops);
 }
 
 // --------------------------------------------------------------------------
