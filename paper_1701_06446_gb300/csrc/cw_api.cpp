@@ -288,7 +288,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             g_last_error = "a moment tensor of this size (2^31 stored elements or more) is not supported";
             return CUMWIN_EINVAL;
         }
-        h->Eoff[s + 1] = h->Eoff[s] + h->E[s];
+        h->Eoff[s + 1] = h->Eoff[s] + (h->E[s] + 3) / 4 * 4;  // orders start on 16-byte boundaries
         CW_TRY(h->alloc(&h->S[s], h->E[s]));
         CW_TRY(h->alloc(&h->C[s], h->E[s]));
         CW_TRY(cudaMemset(h->S[s], 0, sizeof(double) * h->E[s]));
@@ -471,14 +471,21 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
     // fold segments: (window, order) with the order's stored elements
     std::vector<int64_t> abeg(1, 0);
     std::vector<int32_t> aarg;
-    for (int pass = 0; pass < 2; ++pass) {  // orders <= 3 first, then order 4
+    // the order-4 sums kept in workspace order (windows whose top order is 4)
+    // are folded alongside orders 1-3 (vector pass); every other segment first
+    for (int pass = 0; pass < 2; ++pass) {
         for (int w = 0; w < nwin; ++w)
             for (int s = 1; s <= std::min(df, wins[w]->d); ++s) {
-                if ((s == 4) != (pass == 1)) continue;
+                const bool late = s == 4 && wins[w]->cum[s].sgemm;
+                if (late != (pass == 1)) continue;
                 aarg.push_back(s * nwin + w);
-                abeg.push_back(abeg.back() + wins[w]->E[s]);
+                // order-4 segments start at multiples of four (vector fold)
+                abeg.push_back(abeg.back() + (pass == 1 ? (wins[w]->E[s] + 3) / 4 * 4 : wins[w]->E[s]));
             }
-        if (pass == 0) f.nseg_lo = (int32_t)aarg.size();
+        if (pass == 0) {
+            f.nseg_lo = (int32_t)aarg.size();
+            abeg.back() = (abeg.back() + 3) / 4 * 4;  // the order-4 range starts at a multiple of four
+        }
     }
     f.nseg = (int32_t)aarg.size();
     fp.smem = fused_smem_bytes(f, df);

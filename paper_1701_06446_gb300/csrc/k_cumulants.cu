@@ -355,17 +355,18 @@ __device__ __forceinline__ int unit_window(const int64_t* ustart, int nwin, int6
 // zero, so that every unit slot is written and the window's norm is the sum of
 // its unit slots.
 template <int S, int OTF>
-__device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red, int64_t rot)
+__device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArgs* sargs, double* red, int64_t rot,
+                                            int cta, int ncta)
 {
     const int slots = f.slots[S], gy = f.gy[S];
     const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
     const int64_t total = us[f.nwin];
     double* part = f.upart + f.upoff[S];
-    const int64_t G = gridDim.x;
+    const int64_t G = ncta;  // CTAs [0, ncta) of the grid take part, this one as `cta`
     int cur = -1;
     int64_t first = 0;
     double local = 0.0;
-    for (int64_t u = ((int64_t)blockIdx.x + G - rot % G) % G; u < total; u += G) {
+    for (int64_t u = ((int64_t)cta + G - rot % G) % G; u < total; u += G) {
         const int w = unit_window(us, f.nwin, u);
         if (w != cur) {
             if (cur >= 0) {
@@ -378,8 +379,9 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red,
         } else if (threadIdx.x == 0) {
             part[u] = 0.0;
         }
-        const CumArgs& a = f.args[(int64_t)S * f.nwin + w];
-        const CumArgs* a2 = OTF >= 2 ? &f.args[(int64_t)2 * f.nwin + w] : nullptr;
+        // a single window's arguments come from the shared-memory copy
+        const CumArgs& a = sargs != nullptr ? sargs[S] : f.args[(int64_t)S * f.nwin + w];
+        const CumArgs* a2 = OTF < 2 ? nullptr : sargs != nullptr ? &sargs[2] : &f.args[(int64_t)2 * f.nwin + w];
         const int64_t ul = u - us[w];
         const int64_t grp = ul / gy;
         const int y = (int)(ul - grp * gy);
@@ -393,29 +395,145 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, double* red,
     }
 }
 
+// What the fold of one (window, order) segment needs, resolved once per
+// launch (pointers with the FIFO slot applied), so that a thread's first
+// data load does not wait on a chain of argument loads.
+struct FoldSeg {
+    const float* W;       // workspace of the order (slice 0)
+    float* fifo;          // FIFO of the order at this shift's slot, or null
+    double* S;
+    const int32_t* wblk;
+    int64_t wslice;
+    int32_t E, bs, bR, ksplit, accum, sgemm;
+};
+
+constexpr int kFoldSegSmem = 32;  // segments resolved into shared memory (single windows)
+
+__device__ __forceinline__ FoldSeg fold_seg(const CumArgs& a)
+{
+    FoldSeg g;
+    g.W = a.W + a.woff;
+    g.fifo = a.accum == 2 ? a.fifo + fifo_slot(a) * a.fstride : nullptr;
+    g.S = a.S[a.s];
+    g.wblk = a.wblk;
+    g.wslice = a.wslice;
+    g.E = (int32_t)a.E;
+    g.bs = a.bs;
+    g.bR = a.bR;
+    g.ksplit = a.ksplit;
+    g.accum = a.accum;
+    g.sgemm = a.sgemm;
+    return g;
+}
+
+// One element's fold in two halves: loads, then stores.
+struct FoldPend {
+    double* sp;
+    float* fp;  // FIFO entry or null
+    double s;
+    float din, dout;
+};
+
+__device__ __forceinline__ FoldPend fold_seg_load(const FoldSeg& g, int e)
+{
+    int64_t w = e;  // sums in workspace order: element = slot
+    if (!g.sgemm) {
+        const int blk = e / g.bs, off = e - (e / g.bs) * g.bs;
+        const int offL = off / g.bR, offRw = off - (off / g.bR) * g.bR;
+        const int2 wb = *reinterpret_cast<const int2*>(g.wblk + 2 * blk);
+        w = (int64_t)wb.x + (int64_t)offL * wb.y + offRw;
+    }
+    FoldPend v;
+    v.fp = nullptr;
+    if (g.fifo == nullptr) {
+        sum_partials(g.W + w, g.wslice, g.ksplit, v.din, v.dout);
+    } else {
+        v.din = sum_in_partials(g.W + w, g.wslice, g.ksplit);
+        v.fp = g.fifo + w;
+        v.dout = *v.fp;
+    }
+    v.sp = g.S + (g.sgemm ? w : (int64_t)e);
+    v.s = *v.sp;
+    return v;
+}
+
+__device__ __forceinline__ void fold_commit(const FoldPend& v)
+{
+    *v.sp = v.s + (f32_to_f64(v.din) - f32_to_f64(v.dout));
+    if (v.fp != nullptr) *v.fp = v.din;
+}
+
 // Fold the shift's workspace into the sums of the (window, order) segments
 // [seg0, seg1): one thread per stored element.  A segment whose sums are in
-// workspace order (the top order) is one linear pass over its slots, every
-// access coalesced; the others go through the per-block slot table.
-__device__ __forceinline__ void fused_fold(const FusedRecovery& f, int seg0, int seg1)
+// workspace order (the top order) is a linear pass over its slots, every
+// access coalesced; the others go through the per-block slot table.  With few
+// segments their descriptors come from shared memory (`sg`, resolved at the
+// start of the launch), otherwise from the argument array.
+__device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1, int64_t t0,
+                                           int64_t nthreads)
 {
     const int64_t g0 = f.abeg[seg0], g1 = f.abeg[seg1];
-    for (int64_t g = g0 + (int64_t)blockIdx.x * NT + threadIdx.x; g < g1; g += (int64_t)gridDim.x * NT) {
+    for (int64_t g = g0 + t0; g < g1; g += nthreads) {
         int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (f.abeg[mid] <= g) lo = mid;
             else hi = mid - 1;
         }
-        const CumArgs& a = f.args[f.aarg[lo]];
         const int e = (int)(g - f.abeg[lo]);  // E_s < 2^31
-        const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
-        if (a.sgemm) {
-            fold_store(fold_load_at(a, e, e, fslot));
-        } else {
-            const int blk = e / a.bs;
-            fold_store(fold_load(a, blk, e - blk * a.bs, e, fslot));
+        const FoldSeg gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
+        if (e < gs.E) fold_commit(fold_seg_load(gs, e));  // segments may end in padding
+    }
+}
+
+// Fold of segments whose sums are in workspace order (the order-4 range):
+// four consecutive slots per thread with 16-byte loads and stores (workspace
+// orders, FIFO slots and sums start on 16-byte boundaries; the segments are
+// padded to multiples of four in this index space).  The FP32 partials of a
+// slot are added in slice order, as in sum_partials / sum_in_partials.
+__device__ __forceinline__ void fused_fold_quads(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1,
+                                                 int64_t t0, int64_t nthreads)
+{
+    const int64_t q0 = f.abeg[seg0] >> 2, q1 = f.abeg[seg1] >> 2;
+    for (int64_t q = q0 + t0; q < q1; q += nthreads) {
+        const int64_t g = q << 2;
+        int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (f.abeg[mid] <= g) lo = mid;
+            else hi = mid - 1;
         }
+        const FoldSeg gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
+        const int e0 = (int)(g - f.abeg[lo]);
+        if (e0 + 4 > gs.E) {  // ragged end of the segment
+            for (int e = e0; e < gs.E; ++e) fold_commit(fold_seg_load(gs, e));
+            continue;
+        }
+        float4 din = make_float4(0.f, 0.f, 0.f, 0.f), dout = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float* w = gs.W + e0;
+        if (gs.fifo == nullptr) {
+            for (int k = 0; k < gs.ksplit; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(w + (int64_t)(2 * k) * gs.wslice);
+                const float4 b = *reinterpret_cast<const float4*>(w + (int64_t)(2 * k + 1) * gs.wslice);
+                din.x += a.x; din.y += a.y; din.z += a.z; din.w += a.w;
+                dout.x += b.x; dout.y += b.y; dout.z += b.z; dout.w += b.w;
+            }
+        } else {
+            for (int k = 0; k < gs.ksplit; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(w + (int64_t)(2 * k) * gs.wslice);
+                din.x += a.x; din.y += a.y; din.z += a.z; din.w += a.w;
+            }
+            dout = *reinterpret_cast<const float4*>(gs.fifo + e0);
+        }
+        double2* sp = reinterpret_cast<double2*>(gs.S + e0);
+        double2 s01 = sp[0], s23 = sp[1];
+        s01.x += f32_to_f64(din.x) - f32_to_f64(dout.x);
+        s01.y += f32_to_f64(din.y) - f32_to_f64(dout.y);
+        s23.x += f32_to_f64(din.z) - f32_to_f64(dout.z);
+        s23.y += f32_to_f64(din.w) - f32_to_f64(dout.w);
+        sp[0] = s01;
+        sp[1] = s23;
+        if (gs.fifo != nullptr) *reinterpret_cast<float4*>(gs.fifo + e0) = din;
     }
 }
 
@@ -425,45 +543,68 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
 {
     __shared__ double red[NT / 32];
     __shared__ unsigned long long s_base;
-    GridBarrier gb = grid_barrier_init(f.bar, &s_base);
+    __shared__ FoldSeg s_seg[kFoldSegSmem];
+    __shared__ CumArgs s_args[DF + 1];
+    const bool seg_smem = f.fold && f.nseg <= kFoldSegSmem;
+    if (seg_smem && (int)threadIdx.x < f.nseg) s_seg[threadIdx.x] = fold_seg(f.args[f.aarg[threadIdx.x]]);
+    if (f.nwin == 1) {  // one window: its arguments of orders 1..DF, copied once
+        constexpr int words = (int)(sizeof(CumArgs) / sizeof(int));
+        static_assert(sizeof(CumArgs) % sizeof(int) == 0, "CumArgs copied as words");
+        for (int i = threadIdx.x; i < DF * words; i += NT) {
+            const int o = i / words + 1, k = i - (i / words) * words;
+            reinterpret_cast<int*>(&s_args[o])[k] = reinterpret_cast<const int*>(&f.args[o])[k];
+        }
+    }
+    GridBarrier gb = grid_barrier_init(f.bar, &s_base);  // synchronises the CTA
+    const FoldSeg* sg = seg_smem ? s_seg : nullptr;
+    const CumArgs* sargs = f.nwin == 1 ? s_args : nullptr;
     // 1. the sums of orders 1..min(DF, 3) take the shift's workspace
     if (f.fold) {
-        fused_fold(f, 0, f.nseg_lo);
+        fused_fold(f, sg, 0, f.nseg_lo, (int64_t)blockIdx.x * NT + threadIdx.x, (int64_t)gridDim.x * NT);
         grid_barrier(gb, f.status);
     }
     // 2. orders 1..min(DF, 3): C_1, C_2 recomputed from the sums where a higher
-    //    order needs them, so no barrier between these orders; meanwhile the
-    //    order-4 sums take their workspace (nothing reads them before step 3)
-    if (f.fold) fused_fold(f, f.nseg_lo, f.nseg);
-    int64_t rot = 0;
-    fused_order<1, 0>(f, red, rot);
-    rot += f.ustart[1 * (f.nwin + 1) + f.nwin];
-    if (DF >= 2) {
-        fused_order<(DF >= 2 ? 2 : 1), 1>(f, red, rot);
-        rot += f.ustart[2 * (f.nwin + 1) + f.nwin];
+    //    order needs them, so no barrier between these orders.  When the
+    //    order-4 sums still take their workspace (nothing reads them before
+    //    step 3), the first n13 CTAs take the small orders and the others that
+    //    fold, so the latency-bound small orders overlap the memory-bound fold.
+    const int G = gridDim.x;
+    int64_t u13 = 0;
+    for (int k = 1; k <= (DF < 3 ? DF : 3); ++k) u13 += f.ustart[(int64_t)k * (f.nwin + 1) + f.nwin];
+    const bool split = f.fold && f.nseg > f.nseg_lo && G > 1;
+    const int n13 = split ? (int)(u13 < G / 2 ? (u13 > 0 ? u13 : 1) : G / 2) : G;
+    if ((int)blockIdx.x >= n13) {
+        fused_fold_quads(f, sg, f.nseg_lo, f.nseg, (int64_t)(blockIdx.x - n13) * NT + threadIdx.x,
+                         (int64_t)(G - n13) * NT);
+    } else {
+        int64_t rot = 0;
+        fused_order<1, 0>(f, sargs, red, rot, blockIdx.x, n13);
+        rot += f.ustart[1 * (f.nwin + 1) + f.nwin];
+        if (DF >= 2) {
+            fused_order<(DF >= 2 ? 2 : 1), 1>(f, sargs, red, rot, blockIdx.x, n13);
+            rot += f.ustart[2 * (f.nwin + 1) + f.nwin];
+        }
+        if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2>(f, sargs, red, rot, blockIdx.x, n13);
     }
-    if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2>(f, red, rot);
     // 3. order 4 reads the stored C_1..C_3
     if (DF >= 4) {
         grid_barrier(gb, f.status);
-        fused_order<(DF >= 4 ? 4 : 1), 0>(f, red, 0);
+        fused_order<(DF >= 4 ? 4 : 1), 0>(f, sargs, red, 0, blockIdx.x, G);
     }
     grid_barrier(gb, f.status);
-    // norms: one warp per (window, order), partials of the order's units of
-    // the window added lane-strided, then a fixed shuffle tree
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-    for (int64_t it = gw; it < (int64_t)f.nwin * DF; it += nwarps) {
+    // norms: one CTA per (window, order), the partials of the order's units of
+    // the window added thread-strided, then the fixed CTA tree
+    for (int64_t it = blockIdx.x; it < (int64_t)f.nwin * DF; it += G) {
         const int w = (int)(it / DF), s = (int)(it - (it / DF) * DF) + 1;
         const NormArgs& na = f.norm[w];
-        if (s > na.d) continue;
-        const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
-        const double* part = f.upart + f.upoff[s];
         double z = 0.0;
-        for (int64_t q = us[w] + lane; q < us[w + 1]; q += 32) z += part[q];
-        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-        if (lane == 0) na.fro2[s - 1] = z;
+        if (s <= na.d) {
+            const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
+            const double* part = f.upart + f.upoff[s];
+            for (int64_t q = us[w] + threadIdx.x; q < us[w + 1]; q += NT) z += part[q];
+        }
+        z = cta_sum(z, red);
+        if (threadIdx.x == 0 && s <= na.d) na.fro2[s - 1] = z;
     }
     // every CTA read the ring heads (FIFO slots) before the last barrier
     if (f.advance_heads)

@@ -181,3 +181,71 @@ def batched_streams(seed: int = 4, count: int = 512):
     kind = np.where(rng.integers(0, 2, size=count) == 0, "gauss", "t4")
     return [dict(n=int(n[i]), d=int(d[i]), T=int(T[i]), b=4, p=256, kind=str(kind[i]),
                  seed=seed * 100003 + i) for i in range(count)]
+
+
+# ----------------------------------------------------------------------------
+# the paper's illustration stream (Section 4.2) at full scale, drawn on the GPU
+# ----------------------------------------------------------------------------
+
+def student_t_cdf_even(x, nu: int):
+    """CDF of Student's t with an even number of degrees of freedom nu, in
+    closed form: with s = x / sqrt(nu + x^2),
+    F(x) = 1/2 + (s/2) * sum_{k < nu/2} C(2k, k) / 4^k * (1 - s^2)^k.
+    Works on numpy arrays and torch tensors alike (elementwise)."""
+    if nu <= 0 or nu % 2:
+        raise ValueError("nu must be a positive even integer")
+    s = x / (nu + x * x) ** 0.5
+    c = 1.0 - s * s
+    term = s * 0.0 + 1.0
+    acc = term
+    for k in range(1, nu // 2):
+        term = term * c * (2 * k - 1) / (2 * k)
+        acc = acc + term
+    return 0.5 + 0.5 * s * acc
+
+
+class GaussThenTCopulaGPU:
+    """The stream of Section 4.2 drawn on a CUDA device with torch: the first
+    `first` samples are N(0, S); every later sample comes from a t-copula with
+    nu degrees of freedom and the correlation of S, with the Gaussian marginals
+    N(0, S_ii) of the first part (x_i = sqrt(S_ii) * Phi^{-1}(F_nu(w_i)),
+    w = z / sqrt(g / nu), z ~ N(0, corr(S)), g ~ chi^2_nu).  S = A A^T / n with
+    A ~ N(0, 1)^{n x n}.  Seeded with torch.Generator; rows are produced in
+    order, `take(k)` returns the next k rows (k x n, float32, on the device)."""
+
+    def __init__(self, n: int, first: int, seed: int, nu: int = 10, device="cuda"):
+        import torch
+        self.torch = torch
+        self.n, self.first, self.nu, self.pos = n, first, nu, 0
+        self.dev = torch.device(device)
+        self.gen = torch.Generator(device=self.dev)
+        self.gen.manual_seed(seed)
+        A = torch.randn(n, n, generator=self.gen, device=self.dev, dtype=torch.float64)
+        S = A @ A.T / n
+        self.sd = torch.sqrt(torch.diag(S))
+        R = S / self.sd[:, None] / self.sd[None, :]
+        self.L = torch.linalg.cholesky(S)
+        self.LR = torch.linalg.cholesky(R)
+
+    def take(self, k: int):
+        torch = self.torch
+        out = torch.empty(k, self.n, device=self.dev, dtype=torch.float32)
+        done = 0
+        while done < k:
+            m = min(k - done, 1 << 18)
+            z = torch.randn(m, self.n, generator=self.gen, device=self.dev, dtype=torch.float64)
+            gauss = self.pos + done < self.first
+            if gauss:
+                m = min(m, self.first - (self.pos + done))
+                x = z[:m] @ self.L.T
+            else:
+                # chi^2_nu as a sum of nu squared standard normals (one seeded generator)
+                c = torch.randn(m, self.nu, generator=self.gen, device=self.dev, dtype=torch.float64)
+                chi = (c * c).sum(dim=1)
+                w = (z[:m] @ self.LR.T) / torch.sqrt(chi / self.nu)[:, None]
+                u = student_t_cdf_even(w, self.nu).clamp(1e-300, 1.0 - 1e-16)
+                x = torch.special.ndtri(u) * self.sd[None, :]
+            out[done:done + m] = x.to(torch.float32)
+            done += m
+        self.pos += k
+        return out
