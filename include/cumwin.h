@@ -164,6 +164,25 @@ int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host);
 /* Squared norms ||C_s||_F^2, s = 1..d, as d doubles in device memory (no sync). */
 int cumwin_norms_device(cumwin_t h, double* fro2_dev);
 
+/*
+ * Entry-wise k-norms of the current cumulants (Eq. me and Algorithm 5 with a
+ * general k >= 1): out_host[s-1] = (sum over all n^s entries |C_s[i]|^k)^(1/k),
+ * s = 1..d, each stored block weighted by its multiplicity s!/prod r_l!
+ * (Section 4.1); k = 2 gives cumwin_norms.  Order 1 is the mean (not the
+ * shifted mean of the mixed forms).  The partial sums are added in a fixed
+ * order (deterministic).  Synchronises.  Errors: EINVAL (k < 1), ESTATE.
+ */
+int cumwin_norms_k(cumwin_t h, double k, double* out_host);
+
+/*
+ * Univariate diagnostics of the current window (the quantities of Fig. 1 of
+ * Section 4.2): per variable i, the skewness C_3[iii] / C_2[ii]^(3/2) and the
+ * excess kurtosis C_4[iiii] / C_2[ii]^2 of its marginal, n doubles each (NaN
+ * where the order is above d or C_2[ii] = 0).  Either pointer may be NULL.
+ * Synchronises.  Errors: EINVAL, ESTATE.
+ */
+int cumwin_marginals(cumwin_t h, double* skew_host, double* kurt_host);
+
 /* Recompute the moment sums from the window held in the ring buffer (the
  * "simple recalculation" the update is compared against in Section 3.2), then
  * the cumulants and norms. */

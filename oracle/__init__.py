@@ -282,6 +282,22 @@ def norms(X, d: int) -> tuple[np.ndarray, np.ndarray]:
     return fro, nu
 
 
+def norms_k(X, d: int, k: float) -> np.ndarray:
+    """Entry-wise k-norms (sum over all n^s index tuples of |C[i]|^k)^(1/k), s = 1..d
+    (Eq. me with a general k, Algorithm 5); each sorted tuple is evaluated once and
+    counted once per distinct permutation."""
+    X = _as_f64(X)
+    n = X.shape[1]
+    cen = center(X)
+    out = np.zeros(d)
+    for s in range(1, d + 1):
+        tup = np.array(list(itertools.combinations_with_replacement(range(n), s)), dtype=np.int32)
+        vals = cumulant_tuples(X, tup, centred=cen)
+        cnt = np.array([tuple_permutations(t) for t in tup], dtype=np.float64)
+        out[s - 1] = float(np.sum(cnt * np.abs(vals) ** k)) ** (1.0 / k)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # gradient of L = sum_s w_s ||C_s||_F^2 (orders 1..4), closed form
 # ----------------------------------------------------------------------------

@@ -212,6 +212,21 @@ class CumWin:
         check(self.lib.cumwin_tune(self._h, reps, ctypes.byref(ks)), "cumwin_tune")
         return ks.value
 
+    def norms_k(self, k: float) -> np.ndarray:
+        """Entry-wise k-norms ||C_s||_k, s = 1..d (Algorithm 5 with a general k >= 1)."""
+        out = np.zeros(self.d)
+        self._sync_stream()
+        check(self.lib.cumwin_norms_k(self._h, ctypes.c_double(k), out.ctypes.data), "cumwin_norms_k")
+        return out
+
+    def marginals(self):
+        """Per-variable skewness and excess kurtosis of the window (NaN above order d)."""
+        sk = np.zeros(self.n)
+        ku = np.zeros(self.n)
+        self._sync_stream()
+        check(self.lib.cumwin_marginals(self._h, sk.ctypes.data, ku.ctypes.data), "cumwin_marginals")
+        return sk, ku
+
     @property
     def fifo(self) -> bool:
         """True when the next nominal shift uses the batch-sum FIFO (see cumwin_push)."""

@@ -16,6 +16,7 @@ _lib = None
 
 c_int, c_i64, c_vp, c_dp, c_fp = (ctypes.c_int, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float))
+c_double = ctypes.c_double
 _handle_p = ctypes.POINTER(c_vp)
 
 # name -> (restype, argtypes)
@@ -40,6 +41,8 @@ SIGNATURES = {
     "cumwin_block_norm2_noalloc": (c_int, [c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "cumwin_tune": (c_int, [c_vp, c_int, c_vp]),
     "cumwin_fifo": (c_int, [c_vp]),
+    "cumwin_norms_k": (c_int, [c_vp, c_double, c_vp]),
+    "cumwin_marginals": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_batch_create": (c_int, [c_int, c_vp, c_vp, c_vp, c_int, c_int, c_int, c_vp, _handle_p]),
     "cumwin_batch_destroy": (c_int, [c_vp]),
     "cumwin_batch_fill": (c_int, [c_vp, c_vp]),

@@ -968,6 +968,71 @@ int cumwin_norms_device(cumwin_t h, double* fro2_dev)
     return CUMWIN_OK;
 }
 
+int cumwin_norms_k(cumwin_t h, double k, double* out_host)
+{
+    if (h == nullptr || out_host == nullptr || !(k >= 1.0) || !std::isfinite(k)) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    constexpr int kParts = 512;
+    double* parts = nullptr;
+    CW_TRY(cudaMallocAsync((void**)&parts, sizeof(double) * kParts * h->d, h->stream));
+    for (int s = 1; s <= h->d; ++s) {
+        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kParts, (h->E[s] + 255) / 256));
+        const cudaError_t e = launch_knorm(h->cum_dev + s, h->E[s], k, parts + (size_t)(s - 1) * kParts, np,
+                                           h->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(parts, h->stream);
+            return fail_cuda(e, "cumwin_norms_k");
+        }
+    }
+    std::vector<double> host((size_t)kParts * h->d, 0.0);
+    CW_TRY(cudaMemcpyAsync(host.data(), parts, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
+    CW_TRY(cudaFreeAsync(parts, h->stream));
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    for (int s = 1; s <= h->d; ++s) {
+        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kParts, (h->E[s] + 255) / 256));
+        double z = 0.0;
+        for (int q = 0; q < np; ++q) z += host[(size_t)(s - 1) * kParts + q];
+        out_host[s - 1] = std::pow(z, 1.0 / k);
+    }
+    return CUMWIN_OK;
+}
+
+int cumwin_marginals(cumwin_t h, double* skew_host, double* kurt_host)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    const int n = h->n, dm = std::min(h->d, 4);
+    std::vector<double> diag((size_t)(dm + 1) * n, NAN);
+    if (dm >= 2) {
+        std::vector<int64_t> idx((size_t)(dm - 1) * n);
+        for (int s = 2; s <= dm; ++s)
+            for (int i = 0; i < n; ++i) {
+                int v[kMaxOrder];
+                for (int q = 0; q < s; ++q) v[q] = i;
+                idx[(size_t)(s - 2) * n + i] = element_index_impl(n, h->b, s, v);
+            }
+        int64_t* didx = nullptr;
+        double* dout = nullptr;
+        CW_TRY(cudaMallocAsync((void**)&didx, sizeof(int64_t) * idx.size(), h->stream));
+        CW_TRY(cudaMallocAsync((void**)&dout, sizeof(double) * idx.size(), h->stream));
+        CW_TRY(cudaMemcpyAsync(didx, idx.data(), sizeof(int64_t) * idx.size(), cudaMemcpyHostToDevice, h->stream));
+        for (int s = 2; s <= dm; ++s)
+            CW_TRY(launch_gather_idx(h->C[s], didx + (size_t)(s - 2) * n, n, dout + (size_t)(s - 2) * n, h->stream));
+        CW_TRY(cudaMemcpyAsync(diag.data() + 2 * (size_t)n, dout, sizeof(double) * idx.size(), cudaMemcpyDeviceToHost,
+                               h->stream));
+        CW_TRY(cudaFreeAsync(didx, h->stream));
+        CW_TRY(cudaFreeAsync(dout, h->stream));
+        CW_TRY(cudaStreamSynchronize(h->stream));
+    }
+    for (int i = 0; i < n; ++i) {
+        const double v2 = diag[2 * (size_t)n + i];
+        const bool ok = dm >= 2 && v2 > 0.0;
+        if (skew_host) skew_host[i] = ok && dm >= 3 ? diag[3 * (size_t)n + i] / std::pow(v2, 1.5) : NAN;
+        if (kurt_host) kurt_host[i] = ok && dm >= 4 ? diag[4 * (size_t)n + i] / (v2 * v2) : NAN;
+    }
+    return CUMWIN_OK;
+}
+
 static void nu_from_fro(const double* fro, int d, double* nu)
 {
     for (int s = 1; s <= d; ++s)

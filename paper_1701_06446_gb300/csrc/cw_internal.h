@@ -129,6 +129,10 @@ cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const Cum
 // Fold of the workspace into sums kept in workspace order (args with sgemm),
 // one linear pass per window; others are skipped.
 cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st);
+// Per-CTA partials of sum multiplicity * |C_s|^k (nparts CTAs).
+cudaError_t launch_knorm(const CumArgs* args_dev, int64_t E, double k, double* partials, int nparts, cudaStream_t st);
+// out[i] = src[idx[i]], i < n.
+cudaError_t launch_gather_idx(const double* src, const int64_t* idx, int n, double* out, cudaStream_t st);
 // out = S_s * scale in storage order for sums kept in workspace order.
 cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale, double* out, cudaStream_t st);
 

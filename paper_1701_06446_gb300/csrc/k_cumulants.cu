@@ -636,6 +636,29 @@ __global__ void __launch_bounds__(NT) k_gather_sums(const CumArgs* __restrict__ 
     }
 }
 
+// Entry-wise k-norm partials of C_s (Algorithm 5 with a general k): each
+// CTA adds multiplicity * |c|^k over a strided share of the stored elements
+// (order 1: |C_1 + shift|^k) and reduces it in a fixed order.
+__global__ void __launch_bounds__(NT) k_knorm(const CumArgs* __restrict__ args, double k, double* partials)
+{
+    __shared__ double red[NT / 32];
+    const CumArgs& a = *args;
+    double local = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < a.E; e += (int64_t)gridDim.x * NT) {
+        double c = a.Cout[e];
+        if (a.s == 1) c += (double)a.shift[e];
+        local += (a.s == 1 ? 1.0 : a.mult[e / a.bs]) * pow(fabs(c), k);
+    }
+    const double z = cta_sum(local, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = z;
+}
+
+__global__ void k_gather_idx(const double* __restrict__ src, const int64_t* __restrict__ idx, int n, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = src[idx[i]];
+}
+
 // One CTA per window, one warp per order s >= s_from: lanes add strided
 // partials, then a fixed shuffle tree.  Also advances the window's ring head.
 __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance, int s_from)
@@ -749,6 +772,18 @@ cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, s
     case 4: return launch_fused_df<4>(f, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_knorm(const CumArgs* args_dev, int64_t E, double k, double* partials, int nparts, cudaStream_t st)
+{
+    k_knorm<<<nparts, NT, 0, st>>>(args_dev, k, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_idx(const double* src, const int64_t* idx, int n, double* out, cudaStream_t st)
+{
+    k_gather_idx<<<(n + NT - 1) / NT, NT, 0, st>>>(src, idx, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st)

@@ -241,3 +241,34 @@ def test_call_sequence_and_argument_errors():
             h.push(torch.zeros(51, 3, device="cuda"))
         fro, nu = h.norms()
         assert fro[1] == 0.0 and np.isnan(nu[2])  # constant window: nu is 0/0
+
+
+@pytest.mark.parametrize("k", [1.0, 2.0, 3.5])
+def test_k_norms_and_marginals(k):
+    """Algorithm 5 with a general k against the oracle's k-norms; the per-variable
+    skewness and excess kurtosis against scipy's biased estimators."""
+    from scipy import stats
+    n, d, b, T, p = 7, 4, 3, 300, 50
+    rng = np.random.default_rng(17)
+    X = (rng.gamma(2.0, size=(T + 2 * p, n)) @ rng.standard_normal((n, n)) + 1.0).astype(np.float32)
+    Xd = dev(X)
+    Xw = X[2 * p:].astype(np.float64)
+    want = oracle.norms_k(Xw, d, k)
+    for precision, tol in (("fp64", 1e-10), ("bf16", 5e-3)):
+        with CumWin(n, d, b, T, p, precision) as h:
+            h.fill(Xd[:T])
+            h.push(Xd[T:T + p])
+            h.push(Xd[T + p:])
+            got = h.norms_k(k)
+            np.testing.assert_allclose(got, want, rtol=tol)
+            if k == 2.0:
+                np.testing.assert_allclose(got, h.norms()[0], rtol=1e-12)
+            sk, ku = h.marginals()
+            np.testing.assert_allclose(sk, stats.skew(Xw, axis=0, bias=True), rtol=tol, atol=tol)
+            np.testing.assert_allclose(ku, stats.kurtosis(Xw, axis=0, fisher=True, bias=True), rtol=tol, atol=tol)
+    with CumWin(n, 2, b, T, p, "fp64") as h2:
+        h2.fill(Xd[:T])
+        sk, ku = h2.marginals()
+        assert np.all(np.isnan(sk)) and np.all(np.isnan(ku))
+        with pytest.raises(CumwinError):
+            h2.norms_k(0.5)

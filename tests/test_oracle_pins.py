@@ -267,6 +267,27 @@ def test_norm_block_weighted_equals_full_tensor():
     assert abs(nu[3] - fro[3] / fro[1] ** 2) < 1e-14 and np.isnan(nu[0])
 
 
+@pytest.mark.parametrize("k", [1.0, 1.5, 3.0, 4.0])
+def test_k_norms_equal_the_full_tensor_sums(k):
+    """Eq. me with a general k: the permutation-weighted sum over sorted tuples
+    equals the entry-wise sum over the full tensor (expanded from the blocks),
+    k = 2 is the Frobenius norm, and a single variable gives |kappa_s|."""
+    rng = np.random.default_rng(81)
+    n, b = 4, 3
+    X = rng.gamma(2.0, size=(300, n)) @ rng.standard_normal((n, n))
+    C = oracle.cumulants(X, 4, b)
+    got = oracle.norms_k(X, 4, k)
+    for s in range(1, 5):
+        full = oracle.to_full(C[s - 1], n, b, s)
+        want = float(np.sum(np.abs(full) ** k)) ** (1.0 / k)
+        assert abs(got[s - 1] - want) <= 1e-12 * want
+    fro, _ = oracle.norms(X, 4)
+    np.testing.assert_allclose(oracle.norms_k(X, 4, 2.0), fro, rtol=1e-13)
+    x = rng.exponential(size=(500, 1))
+    cum = [float(oracle.cumulants(x, 4, 1)[s - 1][0]) for s in range(1, 5)]
+    np.testing.assert_allclose(oracle.norms_k(x, 4, k), np.abs(cum), rtol=1e-13)
+
+
 # ----------------------------------------------------------------------------
 # statistical behaviour
 # ----------------------------------------------------------------------------
