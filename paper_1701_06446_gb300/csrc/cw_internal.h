@@ -121,6 +121,7 @@ cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int nti
 // Launch shape of the recovery kernel of one order (see plan_cumulants).
 struct CumLaunch {
     int slots, gx, gy;
+    int bpow1;  // b^(s-1)
 };
 CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count);
 // Recovery of order s for nwin windows at once (args_dev[w] for window w;

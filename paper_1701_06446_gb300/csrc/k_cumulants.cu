@@ -49,7 +49,7 @@ struct Subsets {
 
 __host__ __device__ constexpr int popc_c(unsigned x) { return x ? (int)(x & 1u) + popc_c(x >> 1) : 0; }
 
-__device__ __forceinline__ int ipow_c(int b, int k)
+__host__ __device__ __forceinline__ int ipow_c(int b, int k)
 {
     int r = 1;
     for (int i = 0; i < k; ++i) r *= b;
@@ -259,6 +259,55 @@ __device__ __forceinline__ double cta_sum(double v, double* red)
     return z;  // valid in thread 0
 }
 
+// Orders whose per-thread subset offsets are kept in shared memory (packed
+// 16 + 16 bits): 2^{S-1} - 1 of them per thread would not fit in registers,
+// and forming them per element costs as much integer work as the FP64 work
+// they feed.  Above this order they are formed per element.
+constexpr int kSmemOffsetsMax = 6;
+
+// Order S >= 5 with the subset offsets of each thread's in-block offset in
+// shared memory (computed once) and the sub-block bases (rank * b^|A|) of the
+// CTA's blocks staged per group: per subset two shared loads, two gathers and
+// one FP64 multiply-add.
+template <int S>
+__device__ __forceinline__ void recover_group_smem(const CumArgs& a, const Elem<S>& c, int64_t grp, int slots,
+                                                   int64_t fslot, const int* offs, int* sbase, double& local)
+{
+    constexpr int NS = Subsets<S>::N;
+    const int b = a.b;
+    const int64_t nblocks = a.E / a.bs;
+    const int64_t blk0 = grp * slots;
+    __syncthreads();
+    for (int i = threadIdx.x; i < slots * NS; i += NT) {
+        const int64_t blk = blk0 + i / NS;
+        const int t = i - (i / NS) * NS;
+        if (blk < nblocks) {
+            const int2 q = *reinterpret_cast<const int2*>(a.subrank + ((size_t)blk * NS + t) * 2);
+            const int la = __popc(2u * t + 1u);
+            sbase[2 * i] = q.x * ipow_c(b, la);
+            sbase[2 * i + 1] = q.y * ipow_c(b, S - la);
+        }
+    }
+    __syncthreads();
+    const int64_t blk = blk0 + c.slot;
+    if (!c.valid || blk >= nblocks) return;
+    const int64_t e = blk * a.bs + c.off;
+    if (a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
+    double acc = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
+    const int* sb = sbase + 2 * c.slot * NS;
+#pragma unroll 4
+    for (int t = 0; t < NS; ++t) {
+        const int la = __popc(2u * t + 1u), lr = S - la;
+        const int packed = offs[t * NT + threadIdx.x];
+        const double cA = a.C[la][sb[2 * t] + (packed >> 16)];
+        const double sR = a.S[lr][sb[2 * t + 1] + (packed & 0xffff)];
+        acc = fma(-cA, sR, acc);
+    }
+    const double cv = acc * a.invT;
+    a.Cout[e] = cv;
+    local = fma(a.mult[blk] * cv, cv, local);
+}
+
 template <int S>
 __global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__ args, int slots)
 {
@@ -269,9 +318,26 @@ __global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__
     const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
     const int64_t nblocks = a.E / a.bs;
     double local = 0.0;
-    if (c.valid)
-        for (int64_t blk = (int64_t)blockIdx.x * slots + c.slot; blk < nblocks; blk += (int64_t)gridDim.x * slots)
-            recover_elem<S, true, 0>(a, nullptr, c, blk, fslot, local);
+    bool smem_path = false;
+    if constexpr (S > kKeepOffsets && S <= kSmemOffsetsMax) smem_path = ipow_c(a.b, S - 1) <= 0xffff;
+    if (smem_path) {
+        constexpr int NS = Subsets<S>::N;
+        extern __shared__ int dyn[];  // [NS][NT] packed offsets, then [slots][NS][2] bases
+        int* offs = dyn;
+        int* sbase = dyn + NS * NT;
+        for (int t = 0; t < NS; ++t) {
+            int oa, orr;
+            subset_offsets<S>(c, a.b, t, oa, orr);
+            offs[t * NT + threadIdx.x] = (oa << 16) | orr;  // both < b^{S-1} <= 2^16
+        }
+        const int64_t ngroups = (nblocks + slots - 1) / slots;
+        for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x)
+            recover_group_smem<S>(a, c, grp, slots, fslot, offs, sbase, local);
+    } else {
+        if (c.valid)
+            for (int64_t blk = (int64_t)blockIdx.x * slots + c.slot; blk < nblocks; blk += (int64_t)gridDim.x * slots)
+                recover_elem<S, true, 0>(a, nullptr, c, blk, fslot, local);
+    }
     const double z = cta_sum(local, red);
     if (threadIdx.x == 0) a.normpart[blockIdx.y * gridDim.x + blockIdx.x] = z;
 }
@@ -685,7 +751,18 @@ __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance,
 template <int S>
 cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cudaStream_t st)
 {
-    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, 0, st>>>(args, L.slots);
+    size_t smem = 0;
+    if (S > kKeepOffsets && S <= kSmemOffsetsMax && L.bpow1 <= 0xffff) {  // the kernel takes the same branch
+        constexpr int NS = Subsets<S>::N;
+        smem = sizeof(int) * ((size_t)NS * NT + (size_t)L.slots * NS * 2);
+        static size_t opted = 48 * 1024;  // above 48 KB needs the opt-in (raised once per size)
+        if (smem > opted) {
+            cudaError_t e = cudaFuncSetAttribute(k_cumulants<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            opted = smem;
+        }
+    }
+    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots);
     return cudaGetLastError();
 }
 
@@ -713,6 +790,9 @@ cudaError_t launch_fused_df(const FusedRecovery& f, int grid, size_t smem, cudaS
 CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count)
 {
     CumLaunch L{};
+    int b = 1;
+    while (ipow_c(b, s) < bs) ++b;  // bs = b^s
+    L.bpow1 = ipow_c(b, s - 1);
     const int ns = (1 << (s - 1)) - 1;
     if (bs >= NT) {
         L.slots = 1;
