@@ -413,13 +413,14 @@ __device__ __forceinline__ int unit_window(const int64_t* ustart, int nwin, int6
     return lo;
 }
 
-// One order of the fused recovery (the sums already folded).  Units go
-// round-robin over the CTAs, starting `rot` CTAs further on so that the small
-// orders land on different CTAs; a CTA's units of one window are consecutive,
-// so it sums them per thread and reduces once per window ("run"): the run's
-// sum goes to the slot of its first unit and the other units of the run hold
-// zero, so that every unit slot is written and the window's norm is the sum of
-// its unit slots.
+// One order of the fused recovery (the sums already folded).  CTAs [0, ncta)
+// take part, this one as `cta`; each takes a contiguous chunk of the order's
+// work units (chunks rotated by `rot`, so that the small orders land on
+// different CTAs).  A CTA's units of one window are consecutive, so it sums
+// them per thread and reduces once per window ("run"): the run's sum goes to
+// the slot of its first unit and the other units of the run hold zero, so
+// that every unit slot is written and the window's norm is the sum of its
+// unit slots.
 template <int S, int OTF>
 __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArgs* sargs, double* red, int64_t rot,
                                             int cta, int ncta)
@@ -427,38 +428,43 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArg
     const int slots = f.slots[S], gy = f.gy[S];
     const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
     const int64_t total = us[f.nwin];
+    const int64_t per = (total + ncta - 1) / ncta;
+    const int64_t chunk = ((int64_t)cta + ncta - rot % ncta) % ncta;
+    const int64_t u0 = min(total, chunk * per), u1 = min(total, u0 + per);
+    if (u0 >= u1) return;  // uniform over the CTA
     double* part = f.upart + f.upoff[S];
-    const int64_t G = ncta;  // CTAs [0, ncta) of the grid take part, this one as `cta`
-    int cur = -1;
-    int64_t first = 0;
+    int w = unit_window(us, f.nwin, u0);
+    const CumArgs* ap = sargs != nullptr ? &sargs[S] : &f.args[(int64_t)S * f.nwin + w];
+    const CumArgs* a2 = OTF < 2 ? nullptr : sargs != nullptr ? &sargs[2] : &f.args[(int64_t)2 * f.nwin + w];
+    int64_t nblocks = ap->E / ap->bs;
+    Elem<S> c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, 0);
+    int64_t first = u0;
     double local = 0.0;
-    for (int64_t u = ((int64_t)cta + G - rot % G) % G; u < total; u += G) {
-        const int w = unit_window(us, f.nwin, u);
-        if (w != cur) {
-            if (cur >= 0) {
-                const double z = cta_sum(local, red);
-                if (threadIdx.x == 0) part[first] = z;
-            }
-            cur = w;
+    for (int64_t u = u0; u < u1; ++u) {
+        if (u >= us[w + 1]) {  // the next window with units: close the run
+            const double z = cta_sum(local, red);
+            if (threadIdx.x == 0) part[first] = z;
             first = u;
             local = 0.0;
-        } else if (threadIdx.x == 0) {
+            while (u >= us[w + 1]) ++w;
+            ap = &f.args[(int64_t)S * f.nwin + w];  // several windows: no shared copy
+            if (OTF >= 2) a2 = &f.args[(int64_t)2 * f.nwin + w];
+            nblocks = ap->E / ap->bs;
+            if (gy == 1) c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, 0);
+        } else if (u != first && threadIdx.x == 0) {
             part[u] = 0.0;
         }
-        // a single window's arguments come from the shared-memory copy
-        const CumArgs& a = sargs != nullptr ? sargs[S] : f.args[(int64_t)S * f.nwin + w];
-        const CumArgs* a2 = OTF < 2 ? nullptr : sargs != nullptr ? &sargs[2] : &f.args[(int64_t)2 * f.nwin + w];
         const int64_t ul = u - us[w];
-        const int64_t grp = ul / gy;
-        const int y = (int)(ul - grp * gy);
-        const Elem<S> c = make_elem<S>(a.b, a.bs, a.bR, slots, y);
+        int64_t grp = ul;
+        if (gy > 1) {
+            grp = ul / gy;
+            c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, (int)(ul - grp * gy));
+        }
         const int64_t blk = grp * slots + c.slot;
-        if (c.valid && blk < a.E / a.bs) recover_elem<S, false, OTF>(a, a2, c, blk, 0, local);
+        if (c.valid && blk < nblocks) recover_elem<S, false, OTF>(*ap, a2, c, blk, 0, local);
     }
-    if (cur >= 0) {
-        const double z = cta_sum(local, red);
-        if (threadIdx.x == 0) part[first] = z;
-    }
+    const double z = cta_sum(local, red);
+    if (threadIdx.x == 0) part[first] = z;
 }
 
 // What the fold of one (window, order) segment needs, resolved once per
@@ -535,19 +541,27 @@ __device__ __forceinline__ void fold_commit(const FoldPend& v)
 // access coalesced; the others go through the per-block slot table.  With few
 // segments their descriptors come from shared memory (`sg`, resolved at the
 // start of the launch), otherwise from the argument array.
-__device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1, int64_t t0,
-                                           int64_t nthreads)
+__device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1, int cta,
+                                           int ncta)
 {
     const int64_t g0 = f.abeg[seg0], g1 = f.abeg[seg1];
-    for (int64_t g = g0 + t0; g < g1; g += nthreads) {
-        int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (f.abeg[mid] <= g) lo = mid;
-            else hi = mid - 1;
+    const int64_t per = ((g1 - g0 + ncta - 1) / ncta + NT - 1) / NT * NT;  // contiguous chunk per CTA
+    const int64_t c0 = min(g1, g0 + cta * per), c1 = min(g1, c0 + per);
+    int64_t g = c0 + threadIdx.x;
+    if (g >= c1) return;
+    int seg = seg0, hi = seg1 - 1;  // last segment with abeg <= g
+    while (seg < hi) {
+        const int mid = (seg + hi + 1) >> 1;
+        if (f.abeg[mid] <= g) seg = mid;
+        else hi = mid - 1;
+    }
+    FoldSeg gs = sg != nullptr ? sg[seg] : fold_seg(f.args[f.aarg[seg]]);
+    for (; g < c1; g += NT) {
+        if (g >= f.abeg[seg + 1]) {  // the thread's next segment (monotone)
+            while (g >= f.abeg[seg + 1]) ++seg;
+            gs = sg != nullptr ? sg[seg] : fold_seg(f.args[f.aarg[seg]]);
         }
-        const int e = (int)(g - f.abeg[lo]);  // E_s < 2^31
-        const FoldSeg gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
+        const int e = (int)(g - f.abeg[seg]);  // E_s < 2^31
         if (e < gs.E) fold_commit(fold_seg_load(gs, e));  // segments may end in padding
     }
 }
@@ -558,18 +572,26 @@ __device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg
 // padded to multiples of four in this index space).  The FP32 partials of a
 // slot are added in slice order, as in sum_partials / sum_in_partials.
 __device__ __forceinline__ void fused_fold_quads(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1,
-                                                 int64_t t0, int64_t nthreads)
+                                                 int cta, int ncta)
 {
     const int64_t q0 = f.abeg[seg0] >> 2, q1 = f.abeg[seg1] >> 2;
-    for (int64_t q = q0 + t0; q < q1; q += nthreads) {
+    const int64_t per = ((q1 - q0 + ncta - 1) / ncta + NT - 1) / NT * NT;  // contiguous chunk per CTA
+    const int64_t c0 = min(q1, q0 + cta * per), c1 = min(q1, c0 + per);
+    int64_t q = c0 + threadIdx.x;
+    if (q >= c1) return;
+    int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= 4q
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (f.abeg[mid] <= (q << 2)) lo = mid;
+        else hi = mid - 1;
+    }
+    FoldSeg gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
+    for (; q < c1; q += NT) {
         const int64_t g = q << 2;
-        int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= g
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (f.abeg[mid] <= g) lo = mid;
-            else hi = mid - 1;
+        if (g >= f.abeg[lo + 1]) {  // the thread's next segment (monotone)
+            while (g >= f.abeg[lo + 1]) ++lo;
+            gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
         }
-        const FoldSeg gs = sg != nullptr ? sg[lo] : fold_seg(f.args[f.aarg[lo]]);
         const int e0 = (int)(g - f.abeg[lo]);
         if (e0 + 4 > gs.E) {  // ragged end of the segment
             for (int e = e0; e < gs.E; ++e) fold_commit(fold_seg_load(gs, e));
@@ -626,7 +648,7 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
     const CumArgs* sargs = f.nwin == 1 ? s_args : nullptr;
     // 1. the sums of orders 1..min(DF, 3) take the shift's workspace
     if (f.fold) {
-        fused_fold(f, sg, 0, f.nseg_lo, (int64_t)blockIdx.x * NT + threadIdx.x, (int64_t)gridDim.x * NT);
+        fused_fold(f, sg, 0, f.nseg_lo, blockIdx.x, gridDim.x);
         grid_barrier(gb, f.status);
     }
     // 2. orders 1..min(DF, 3): C_1, C_2 recomputed from the sums where a higher
@@ -640,8 +662,7 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
     const bool split = f.fold && f.nseg > f.nseg_lo && G > 1;
     const int n13 = split ? (int)(u13 < G / 2 ? (u13 > 0 ? u13 : 1) : G / 2) : G;
     if ((int)blockIdx.x >= n13) {
-        fused_fold_quads(f, sg, f.nseg_lo, f.nseg, (int64_t)(blockIdx.x - n13) * NT + threadIdx.x,
-                         (int64_t)(G - n13) * NT);
+        fused_fold_quads(f, sg, f.nseg_lo, f.nseg, blockIdx.x - n13, G - n13);
     } else {
         int64_t rot = 0;
         fused_order<1, 0>(f, sargs, red, rot, blockIdx.x, n13);
