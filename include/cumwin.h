@@ -125,8 +125,39 @@ int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx);
  * the one of the recomputing form.  Any other shift (x_out_dev != NULL or
  * fewer rows) recomputes X_(-) and retires the FIFO until the next fill or
  * recompute.
+ *
+ * Pipelined shifts (mixed forms): the recovery of C_1..C_d and of the norms
+ * runs on a stream owned by the handle, ordered after the shift's moment
+ * update by an event, so that the next push's staging and tensor-core update
+ * overlap it (the two alternate between two update workspaces).  Every other
+ * entry point of the handle first makes the handle's stream wait for it, so
+ * results read through the API are always those of the last push; work the
+ * caller queues on the stream itself (e.g. a timing event after the push)
+ * needs cumwin_join first.  A push issued under stream capture, or with
+ * phase timing on, runs the recovery on the handle's stream.
  */
 int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p, int64_t ld);
+
+/* Make the handle's stream wait (on the device; the host does not block) for
+ * the recovery of the last pipelined push.  Always succeeds on a valid handle. */
+int cumwin_join(cumwin_t h);
+
+/*
+ * Enqueue copies of the squared norms ||C_s||_F^2, s = 1..d (d doubles, into
+ * fro2_out) and of the sticky device status (one int, into status_out) of the
+ * window as it stands after the calls issued so far.  Either pointer may be
+ * NULL, not both; each may be device memory or host memory (pinned for an
+ * asynchronous copy).  After a pipelined push the copies run on the recovery
+ * stream behind that push's recovery, so they do not hold back the next
+ * push; otherwise on the handle's stream.  The values are in place once the
+ * handle's stream has been synchronised after cumwin_join (or the device has
+ * been synchronised).  Nothing is allocated; the host does not block.
+ */
+int cumwin_norms_enqueue(cumwin_t h, double* fro2_out, int* status_out);
+
+/* Turn pipelined shifts (cumwin_push) on (enable != 0, the default) or off.
+ * Results are bitwise the same either way. */
+int cumwin_set_pipeline(cumwin_t h, int enable);
 
 /* 1 when the next shift of the nominal p rows (x_out_dev == NULL) will use
  * the batch-sum FIFO of cumwin_push, 0 when it recomputes X_(-) (FP64 form,

@@ -122,6 +122,16 @@ class CumWin:
         check(self.lib.cumwin_push(self._h, _dev_ptr(x_in, torch.float32, "x_in"), out_ptr, p,
                                    x_in.stride(0)), "cumwin_push")
 
+    def join(self):
+        """Make the current stream wait (on the device) for the last pipelined push."""
+        self._sync_stream()
+        check(self.lib.cumwin_join(self._h), "cumwin_join")
+
+    def set_pipeline(self, enable: bool):
+        """Overlap each push's recovery with the next push's update (the default) or not."""
+        self._sync_stream()
+        check(self.lib.cumwin_set_pipeline(self._h, int(bool(enable))), "cumwin_set_pipeline")
+
     def push_host(self, x_in):
         """Shift with X_(+) in host memory (numpy array or CPU tensor, pinned if possible)."""
         if isinstance(x_in, torch.Tensor):
@@ -174,6 +184,21 @@ class CumWin:
         check(self.lib.cumwin_norms_device(self._h, _dev_ptr(out, torch.float64, "out")),
               "cumwin_norms_device")
         return out
+
+    def norms_enqueue(self, fro2_out: torch.Tensor, status_out: torch.Tensor | None = None):
+        """Enqueue copies of ||C_s||^2 (d float64) and of the device status (int32)
+        into the given tensors (pinned CPU or CUDA), behind the last push's
+        recovery; valid after ``join()`` and a synchronisation (see cumwin_norms_enqueue)."""
+        def ptr(t, dtype, count, what):
+            if t.dtype != dtype or not t.is_contiguous() or t.numel() < count:
+                raise ValueError(f"{what} must be a contiguous {dtype} tensor of at least {count} elements")
+            if not t.is_cuda and not t.is_pinned():
+                raise ValueError(f"{what} must be a CUDA tensor or pinned host memory")
+            return ctypes.c_void_p(t.data_ptr())
+        sp = ptr(status_out, torch.int32, 1, "status_out") if status_out is not None else None
+        self._sync_stream()
+        check(self.lib.cumwin_norms_enqueue(self._h, ptr(fro2_out, torch.float64, self.d, "fro2_out"), sp),
+              "cumwin_norms_enqueue")
 
     def recompute(self):
         self._sync_stream()

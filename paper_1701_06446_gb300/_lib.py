@@ -41,6 +41,9 @@ SIGNATURES = {
     "cumwin_block_norm2_noalloc": (c_int, [c_int, c_int, c_int, c_vp, c_vp, c_vp]),
     "cumwin_tune": (c_int, [c_vp, c_int, c_vp]),
     "cumwin_fifo": (c_int, [c_vp]),
+    "cumwin_join": (c_int, [c_vp]),
+    "cumwin_norms_enqueue": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_set_pipeline": (c_int, [c_vp, c_int]),
     "cumwin_norms_k": (c_int, [c_vp, c_double, c_vp]),
     "cumwin_marginals": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_batch_create": (c_int, [c_int, c_vp, c_vp, c_vp, c_int, c_int, c_int, c_vp, _handle_p]),

@@ -90,7 +90,9 @@ struct cumwin_s {
     int p = 1;  // nominal shift size (batch of the mixed-form FP32 sums)
     cudaStream_t stream = nullptr;
     int device = 0, sm_count = 0;
-    int64_t* head = nullptr;  // device: ring slot of the oldest sample
+    int64_t* head = nullptr;      // device: ring slot of the oldest sample, as the staging sees it
+    int64_t* head_rec = nullptr;  // device: the same, as the recovery sees it (FIFO slots); the two
+                                  // advance once per shift each, in their own kernels
     bool filled = false;
     bool fifo_valid = false;  // the batch-sum FIFO matches the window (mixed forms)
     Arena mem;
@@ -113,8 +115,9 @@ struct cumwin_s {
     TcPlan tc_own{};
     TcPlan* tc = nullptr;
 
-    // recovery: host arguments per order, device copies [kAccModes][order]
-    // (no workspace / stacked in-out workspace / FIFO)
+    // recovery: host arguments per order, device copies
+    // [workspace parity][kAccModes][order] (accumulate modes: no workspace /
+    // stacked in-out workspace / FIFO)
     CumArgs cum[kMaxOrder + 1]{};
     CumArgs* cum_dev = nullptr;
     CumLaunch cum_launch[kMaxOrder + 1] = {};
@@ -143,6 +146,20 @@ struct cumwin_s {
         float* Gc = nullptr;              // [nu][n]
     } grad;
 
+    // Pipelined shifts (mixed forms, single handles): the recovery of a shift
+    // runs on `rstream`, so that the staging, operand build and GEMM of the
+    // next shift (on the handle's stream) overlap it.  Shifts alternate
+    // between two workspaces (parity); ev_rec[q] marks the end of the last
+    // recovery that read workspace q, pend[q] that the handle's stream has
+    // not waited for it yet.
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t ev_gemm = nullptr;
+    cudaEvent_t ev_rec[2] = {nullptr, nullptr};
+    bool pend[2] = {false, false};
+    int par = 0;
+    int last = 0;          // workspace of the last pipelined push
+    bool pipeline = true;  // cumwin_set_pipeline
+
     // kernel timing (cumwin_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev;  // 4 per timed shift: start, staged, updated, recovered
@@ -157,13 +174,23 @@ struct cumwin_s {
         mem.release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         ev.clear();
+        if (rstream != nullptr) {
+            cudaStreamSynchronize(rstream);
+            cudaStreamDestroy(rstream);
+            rstream = nullptr;
+        }
+        for (cudaEvent_t* e : {&ev_gemm, &ev_rec[0], &ev_rec[1]})
+            if (*e != nullptr) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
+            }
     }
     // event slot k of the current timed shift, or null when not timing
-    cudaEvent_t mark(int k)
+    cudaEvent_t mark(int k, cudaStream_t on = nullptr)
     {
         if (!timing || timed * 4 + k >= (int64_t)ev.size()) return nullptr;
         cudaEvent_t e = ev[timed * 4 + k];
-        cudaEventRecord(e, stream);
+        cudaEventRecord(e, on != nullptr ? on : stream);
         return e;
     }
 };
@@ -280,6 +307,8 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     CW_TRY(cudaMemset(h->status, 0, sizeof(int)));
     CW_TRY(h->alloc(&h->head, 1));
     CW_TRY(cudaMemset(h->head, 0, sizeof(int64_t)));
+    CW_TRY(h->alloc(&h->head_rec, 1));
+    CW_TRY(cudaMemset(h->head_rec, 0, sizeof(int64_t)));
     CW_TRY(cudaMemset(h->ring, 0, sizeof(float) * (size_t)T * npad));
     h->Eoff[1] = 0;
     for (int s = 1; s <= d; ++s) {
@@ -380,7 +409,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         ps.shift = h->shift;
         ps.status = h->status;
         ps.xoff = 0;
-        int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status, true,
+        int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status, true, true,
                                 [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
         if (rc != 0) {
             g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
@@ -398,7 +427,7 @@ int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int index)
     h->parts = parts;
     CW_TRY(h->alloc(&h->normpart, (size_t)parts * h->d));
     CW_TRY(cudaMemset(h->normpart, 0, sizeof(double) * (size_t)parts * h->d));
-    CumArgs arr[kAccModes][kMaxOrder + 1] = {};
+    CumArgs arr[2][kAccModes][kMaxOrder + 1] = {};  // [workspace parity][accumulate mode][order]
     for (int s = 1; s <= h->d; ++s) {
         CumArgs& a = h->cum[s];
         a.normpart = h->normpart + (size_t)(s - 1) * parts;
@@ -410,20 +439,23 @@ int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int index)
             if (tc->fifo != nullptr) {
                 a.fifo = tc->fifo + tc->fbase[index] + h->Eoff[s];
                 a.fstride = h->Eoff[h->d + 1];
-                a.head = h->head;
+                a.head = h->head_rec;
                 a.p = h->p;
             }
         }
-        for (int m = 0; m < kAccModes; ++m) {
-            arr[m][s] = a;
-            arr[m][s].accum = m;
-        }
+        for (int q = 0; q < 2; ++q)
+            for (int m = 0; m < kAccModes; ++m) {
+                arr[q][m][s] = a;
+                arr[q][m][s].accum = m;
+                if (q == 1 && tc != nullptr && tc->W2 != nullptr) arr[q][m][s].W = tc->W2;
+            }
     }
-    CW_TRY(h->mem.upload(&h->cum_dev, &arr[0][0], kAccModes * (kMaxOrder + 1)));
+    CW_TRY(h->mem.upload(&h->cum_dev, &arr[0][0][0], 2 * kAccModes * (kMaxOrder + 1)));
     NormArgs na{};
     na.normpart = h->normpart;
     na.fro2 = h->fro2;
-    na.head = h->head;
+    na.head = h->head_rec;
+    na.head_stage = h->prec == CUMWIN_FP64 ? h->head : nullptr;  // mixed forms: the build advances it
     na.T = h->T;
     na.parts = parts;
     na.d = h->d;
@@ -433,9 +465,11 @@ int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int index)
 
 // Work units of the fused recovery over the windows `wins` (shared b), the
 // barrier state and the norm partials; leaves fp.dfused = 0 when the device
-// cannot run it.
+// cannot run it.  per_sm: CTAs per SM of its grid.  A single window takes 3,
+// which leaves room on each SM for a CTA of the next shift's GEMM (pipelined
+// shifts) and measured no slower than 4 alone; batches take 4.
 int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm_count,
-                const NormArgs* norm_dev, int* status, Arena& mem)
+                const NormArgs* norm_dev, int* status, Arena& mem, int per_sm)
 {
     int dmax = 0, device = 0, coop = 0;
     for (const cumwin_s* h : wins) {
@@ -489,7 +523,7 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
     }
     f.nseg = (int32_t)aarg.size();
     fp.smem = fused_smem_bytes(f, df);
-    fp.grid = fused_grid(df, fp.smem, sm_count);
+    fp.grid = fused_grid(df, fp.smem, sm_count, per_sm);
     if (fp.grid < 1) return CUMWIN_OK;
     int64_t* dus = nullptr;
     CW_TRY(mem.upload(&dus, ustart));
@@ -543,13 +577,49 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
     return CUMWIN_OK;
 }
 
-int run_cumulants(cumwin_t h, int64_t advance, int accum = 0)
+int run_cumulants(cumwin_t h, int64_t advance, int accum = 0, int parity = 0, cudaStream_t on = nullptr)
 {
-    const int rc = recover(h->fused, h->cum_dev, h->cum_launch, h->norm_dev, 1, h->d, advance, accum,
-                           h->sm_count, h->stream, &h->launches);
+    cudaStream_t st = on != nullptr ? on : h->stream;
+    const int rc = recover(h->fused, h->cum_dev + (size_t)parity * kAccModes * (kMaxOrder + 1), h->cum_launch,
+                           h->norm_dev, 1, h->d, advance, accum, h->sm_count, st, &h->launches);
     if (rc) return rc;
-    if (h->mark(3) != nullptr) h->timed++;
+    if (h->mark(3, st) != nullptr) h->timed++;
     return CUMWIN_OK;
+}
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// The handle's stream waits for the recoveries still running on the
+// recovery stream (no host synchronisation).  Under stream capture the wait
+// becomes an external-event node of the graph and the recoveries stay
+// pending for the eager work that follows the capture.
+cudaError_t wait_recovery(cumwin_t h, int q)
+{
+    if (!h->pend[q]) return cudaSuccess;
+    if (capturing(h->stream)) return cudaStreamWaitEvent(h->stream, h->ev_rec[q], cudaEventWaitExternal);
+    const cudaError_t e = cudaStreamWaitEvent(h->stream, h->ev_rec[q], 0);
+    if (e == cudaSuccess) h->pend[q] = false;
+    return e;
+}
+
+cudaError_t join(cumwin_t h)
+{
+    for (int q = 0; q < 2; ++q) {
+        const cudaError_t e = wait_recovery(h, q);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Shifts overlap the recovery of the previous one in the mixed forms, unless
+// switched off, timed phase by phase, or captured into a graph.
+bool pipelined(cumwin_t h)
+{
+    return h->pipeline && h->rstream != nullptr && !h->timing && !capturing(h->stream);
 }
 
 std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcPlan& tc)
@@ -565,7 +635,7 @@ std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcP
             g.E = h->E[s];
             g.bs = (int32_t)ipow(h->b, s);
             g.bR = h->cum[s].bR;
-            g.head = h->head;
+            g.head = h->head_rec;
             g.p = h->p;
             g.sgemm = h->cum[s].sgemm;
             if (tc.fifo != nullptr) {
@@ -605,7 +675,7 @@ int update_window(cumwin_t h)
 // A shift of the nominal p with the leaving rows taken from the ring uses the
 // batch-sum FIFO when there is one; any other shift recomputes the leaving
 // half and retires the FIFO until the next fill or recompute.
-int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld, int* accum)
+int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_t ld, int* accum, int parity)
 {
     *accum = 0;
     h->mark(0);
@@ -620,7 +690,7 @@ int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_
         if (!fifo) h->fifo_valid = false;
         CW_TRY(tc_stage_push(*h->tc, x_in, x_out, ld, p, !fifo, h->stream));
         h->mark(1);
-        CW_TRY(tc_gemm_push(*h->tc, !fifo, h->stream));
+        CW_TRY(tc_gemm_push(*h->tc, !fifo, parity, h->stream));
         *accum = fifo ? 2 : 1;
     }
     h->launches += 2 + (h->prec != CUMWIN_FP64);
@@ -638,6 +708,7 @@ int fill_prepare(cumwin_t h, const float* X_dev, int64_t ldx)
 {
     CW_TRY(launch_fill_ring(X_dev, ldx, h->ring, h->T, h->n, h->npad, h->status, h->stream));
     CW_TRY(cudaMemsetAsync(h->head, 0, sizeof(int64_t), h->stream));
+    CW_TRY(cudaMemsetAsync(h->head_rec, 0, sizeof(int64_t), h->stream));
     if (h->prec != CUMWIN_FP64)
         CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
     return zero_sums(h);
@@ -848,7 +919,14 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
         if (ks >= 1 && ks <= h->tc->ksplit_max) h->tc->ksplit = ks;
     }
     if (rc == CUMWIN_OK) rc = window_finish(h, parts, h->tc, 0);
-    if (rc == CUMWIN_OK) rc = fused_setup(h->fused, {h}, b, h->sm_count, h->norm_dev, h->status, h->mem);
+    if (rc == CUMWIN_OK) rc = fused_setup(h->fused, {h}, b, h->sm_count, h->norm_dev, h->status, h->mem, 3);
+    if (rc == CUMWIN_OK && h->tc != nullptr) {  // the recovery stream of pipelined shifts
+        cudaError_t e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_gemm, cudaEventDisableTiming);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+            e = cudaEventCreateWithFlags(&h->ev_rec[q], cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = fail_cuda(e, "create");
+    }
     if (rc == CUMWIN_OK && h->tc != nullptr) {
         std::vector<TcAccSeg> segs = acc_segments({h}, *h->tc);
         h->nsegs = (int)segs.size();
@@ -887,6 +965,7 @@ int cumwin_set_stream(cumwin_t h, void* cuda_stream)
 int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx)
 {
     if (h == nullptr || X_dev == nullptr || ldx < h->n) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
     int rc = fill_prepare(h, X_dev, ldx);
     if (rc) return rc;
     rc = update_window(h);
@@ -906,9 +985,58 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
         return CUMWIN_EINVAL;
     }
     int accum = 0;
-    int rc = update_push(h, x_in_dev, x_out_dev, p, ld, &accum);
+    const bool pipe = pipelined(h);
+    const int q = pipe ? h->par : 0;
+    CW_TRY(wait_recovery(h, q));  // the recovery that last read workspace q
+    int rc = update_push(h, x_in_dev, x_out_dev, p, ld, &accum, q);
     if (rc) return rc;
-    return run_cumulants(h, p, accum);
+    if (!pipe) {
+        CW_TRY(join(h));
+        return run_cumulants(h, p, accum);
+    }
+    // the recovery of this shift on the recovery stream, after its GEMM
+    CW_TRY(cudaEventRecord(h->ev_gemm, h->stream));
+    CW_TRY(cudaStreamWaitEvent(h->rstream, h->ev_gemm, 0));
+    rc = run_cumulants(h, p, accum, q, h->rstream);
+    if (rc) return rc;
+    CW_TRY(cudaEventRecord(h->ev_rec[q], h->rstream));
+    h->pend[q] = true;
+    h->last = q;
+    h->par ^= 1;
+    return CUMWIN_OK;
+}
+
+int cumwin_norms_enqueue(cumwin_t h, double* fro2_out, int* status_out)
+{
+    if (h == nullptr || (fro2_out == nullptr && status_out == nullptr)) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    // behind the last pipelined recovery on the recovery stream (and counted
+    // in its event, so that cumwin_join covers the copies), else on the
+    // handle's stream
+    const bool behind = h->pend[h->last] && !capturing(h->stream);
+    cudaStream_t st = behind ? h->rstream : h->stream;
+    if (!behind) CW_TRY(join(h));
+    if (fro2_out != nullptr)
+        CW_TRY(cudaMemcpyAsync(fro2_out, h->fro2, sizeof(double) * h->d, cudaMemcpyDefault, st));
+    if (status_out != nullptr)
+        CW_TRY(cudaMemcpyAsync(status_out, h->status, sizeof(int), cudaMemcpyDefault, st));
+    if (behind) CW_TRY(cudaEventRecord(h->ev_rec[h->last], h->rstream));
+    return CUMWIN_OK;
+}
+
+int cumwin_join(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
+    return CUMWIN_OK;
+}
+
+int cumwin_set_pipeline(cumwin_t h, int enable)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
+    h->pipeline = enable != 0;
+    return CUMWIN_OK;
 }
 
 int cumwin_fifo(cumwin_t h)
@@ -930,6 +1058,7 @@ int cumwin_cumulants(cumwin_t h, int order, double* out_dev)
 {
     if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     if (order == 1) {
         CW_TRY(launch_add_shift(h->C[1], h->shift, h->n, h->npad, out_dev, h->stream));
     } else {
@@ -943,6 +1072,7 @@ int cumwin_moments(cumwin_t h, int order, double* out_dev)
 {
     if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     if (h->cum[order].sgemm)  // kept in workspace order: gather back to the block layout
         CW_TRY(launch_gather_sums(h->cum_dev + order, h->E[order], 1.0 / (double)h->T, out_dev, h->stream));
     else
@@ -953,6 +1083,7 @@ int cumwin_moments(cumwin_t h, int order, double* out_dev)
 int cumwin_shift(cumwin_t h, float* shift_host)
 {
     if (h == nullptr || shift_host == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
     CW_TRY(cudaMemcpyAsync(shift_host, h->shift, sizeof(float) * h->n, cudaMemcpyDeviceToHost,
                            h->stream));
     CW_TRY(cudaStreamSynchronize(h->stream));
@@ -963,6 +1094,7 @@ int cumwin_norms_device(cumwin_t h, double* fro2_dev)
 {
     if (h == nullptr || fro2_dev == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     CW_TRY(cudaMemcpyAsync(fro2_dev, h->fro2, sizeof(double) * h->d, cudaMemcpyDeviceToDevice,
                            h->stream));
     return CUMWIN_OK;
@@ -972,6 +1104,7 @@ int cumwin_norms_k(cumwin_t h, double k, double* out_host)
 {
     if (h == nullptr || out_host == nullptr || !(k >= 1.0) || !std::isfinite(k)) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     constexpr int kParts = 512;
     double* parts = nullptr;
     CW_TRY(cudaMallocAsync((void**)&parts, sizeof(double) * kParts * h->d, h->stream));
@@ -1001,6 +1134,7 @@ int cumwin_marginals(cumwin_t h, double* skew_host, double* kurt_host)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     const int n = h->n, dm = std::min(h->d, 4);
     std::vector<double> diag((size_t)(dm + 1) * n, NAN);
     if (dm >= 2) {
@@ -1043,6 +1177,7 @@ int cumwin_norms(cumwin_t h, double* fro_host, double* nu_host)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     double z[kMaxOrder];
     int st = 0;
     CW_TRY(cudaMemcpyAsync(z, h->fro2, sizeof(double) * h->d, cudaMemcpyDeviceToHost, h->stream));
@@ -1062,6 +1197,7 @@ int cumwin_recompute(cumwin_t h)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     int rc = zero_sums(h);
     if (rc) return rc;
     rc = update_window(h);
@@ -1073,6 +1209,7 @@ int cumwin_window(cumwin_t h, float* out_dev)
 {
     if (h == nullptr || out_dev == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     CW_TRY(launch_window_copy(h->ring, h->T, h->head, h->n, h->npad, out_dev, h->stream));
     return CUMWIN_OK;
 }
@@ -1081,6 +1218,7 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
 {
     if (h == nullptr || w_host == nullptr || dX_dev == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     const int n = h->n, d = h->d;
     auto& g = h->grad;
     if (!g.ready) {
@@ -1168,6 +1306,7 @@ int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
 {
     if (h == nullptr || reps < 1) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
     if (h->tc == nullptr) {
         if (ksplit_out) *ksplit_out = 0;
         return CUMWIN_OK;  // nothing to tune in the FP64 form
@@ -1176,13 +1315,15 @@ int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
     const int ks = tc_autotune(*h->tc, reps, leaving, h->stream, nullptr);
     if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
     for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
-    CumArgs arr[kAccModes][kMaxOrder + 1] = {};
+    CumArgs arr[2][kAccModes][kMaxOrder + 1] = {};
     for (int s = 1; s <= h->d; ++s)
-        for (int m = 0; m < kAccModes; ++m) {
-            arr[m][s] = h->cum[s];
-            arr[m][s].accum = m;
-        }
-    CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0], sizeof(arr), cudaMemcpyHostToDevice));
+        for (int q = 0; q < 2; ++q)
+            for (int m = 0; m < kAccModes; ++m) {
+                arr[q][m][s] = h->cum[s];
+                arr[q][m][s].accum = m;
+                if (q == 1 && h->tc->W2 != nullptr) arr[q][m][s].W = h->tc->W2;
+            }
+    CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0][0], sizeof(arr), cudaMemcpyHostToDevice));
     tune_cache_put(plan_signature(*h->tc, {h}, h->device), ks);
     if (ksplit_out) *ksplit_out = ks;
     return CUMWIN_OK;
@@ -1191,6 +1332,7 @@ int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
 int cumwin_set_timing(cumwin_t h, int enable)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
     h->timing = enable != 0;
     h->timed = 0;
     h->launches = 0;
@@ -1205,6 +1347,7 @@ int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* c
                       int64_t* shifts, int64_t* launches)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
     CW_TRY(cudaStreamSynchronize(h->stream));
     double a = 0.0, u = 0.0, c = 0.0;
     for (int64_t k = 0; k < h->timed; ++k) {
@@ -1227,6 +1370,7 @@ int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* c
 int cumwin_status(cumwin_t h)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
     int st = 0;
     CW_TRY(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CW_TRY(cudaStreamSynchronize(h->stream));
@@ -1302,7 +1446,7 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     cudaError_t e0 = B->mem.alloc(&B->status, 1);
     if (e0 != cudaSuccess) return bail(fail_cuda(e0, "alloc"));
     cudaMemset(B->status, 0, sizeof(int));
-    int rc = tc_plan_create(B->tc, ps, b, p, B->sm_count, precision, B->status, true,
+    int rc = tc_plan_create(B->tc, ps, b, p, B->sm_count, precision, B->status, true, false,
                             [&](size_t bytes, void** q) { return B->mem.alloc((char**)q, bytes); });
     if (rc != 0) {
         g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
@@ -1342,7 +1486,8 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
         }
         na[i].normpart = h->normpart;
         na[i].fro2 = h->fro2;
-        na[i].head = h->head;
+        na[i].head = h->head_rec;
+        na[i].head_stage = nullptr;  // the operand build advances it
         na[i].T = h->T;
         na[i].parts = parts;
         na[i].d = h->d;
@@ -1350,7 +1495,7 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     e = B->mem.upload(&B->cum_dev, arr);
     if (e == cudaSuccess) e = B->mem.upload(&B->norm_dev, na);
     if (e == cudaSuccess) {
-        rc = fused_setup(B->fused, B->wins, b, B->sm_count, B->norm_dev, B->status, B->mem);
+        rc = fused_setup(B->fused, B->wins, b, B->sm_count, B->norm_dev, B->status, B->mem, 4);
         if (rc) return bail(rc);
     }
     std::vector<TcAccSeg> segs = acc_segments(B->wins, B->tc);
@@ -1402,7 +1547,7 @@ int cumwin_batch_push(cumwin_batch_t B, const float* x_dev)
     if (B == nullptr || x_dev == nullptr) return CUMWIN_EINVAL;
     if (!B->filled) return CUMWIN_ESTATE;
     CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, !B->fifo, B->stream));
-    CW_TRY(tc_gemm_push(B->tc, !B->fifo, B->stream));
+    CW_TRY(tc_gemm_push(B->tc, !B->fifo, 0, B->stream));
     return batch_recover(B, B->p, B->fifo ? 2 : 1);
 }
 

@@ -140,8 +140,9 @@ cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale,
 // Norm reduction of one window: partials of order s at normpart[(s-1)*parts ..].
 struct NormArgs {
     const double* normpart;
-    double* fro2;      // [d]
-    int64_t* head;     // ring head, advanced by `advance` rows (mod T)
+    double* fro2;         // [d]
+    int64_t* head;        // ring head of the recovery (FIFO slots), advanced by `advance` rows (mod T)
+    int64_t* head_stage;  // ring head of the staging, advanced too when not null (FP64 form)
     int64_t T;
     int32_t parts, d;
 };
@@ -173,8 +174,8 @@ struct FusedRecovery {
     int32_t slots[kFusedMax + 1], gy[kFusedMax + 1];
 };
 size_t fused_smem_bytes(const FusedRecovery& f, int dfused);
-// Resident CTAs for the cooperative launch (0: not possible).
-int fused_grid(int dfused, size_t smem, int sm_count);
+// Resident CTAs for the cooperative launch, at most per_sm_max per SM (0: not possible).
+int fused_grid(int dfused, size_t smem, int sm_count, int per_sm_max);
 cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_zero(double* p, int64_t count, cudaStream_t st);
 cudaError_t launch_add_shift(const double* C1, const float* shift, int n, int npad, double* out,

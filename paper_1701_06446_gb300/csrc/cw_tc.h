@@ -51,7 +51,7 @@ constexpr int kTcStages = 3;   // TMA / MMA pipeline depth (64 KB per stage)
 // Per-stream state the staging / build kernels read (device array).
 struct TcStreamDesc {
     float* ring;
-    const int64_t* head;
+    int64_t* head;      // ring head of the staging (advanced by the operand build of a shift)
     const float* shift;
     float* XT;          // [npad][Kcap]
     int* status;
@@ -101,7 +101,7 @@ struct TcPlanStream {
     int d, n, npad;
     int64_t T;
     float* ring;
-    const int64_t* head;
+    int64_t* head;
     const float* shift;
     int* status;
     int64_t xoff;
@@ -123,6 +123,7 @@ struct TcPlan {
     int nitems = 0, ksplit = 1, ksplit_max = 1;
     TcOrder* ord = nullptr;        // device [nstreams][kMaxOrder + 1]
     float* W = nullptr;
+    float* W2 = nullptr;           // second workspace (shifts alternate) or null
     int64_t wslice = 0;
     std::vector<int64_t> wbase;    // per stream: offset of the stream in a workspace slice
     std::vector<int> nbatch_stream;
@@ -139,9 +140,11 @@ using DevAlloc = std::function<cudaError_t(size_t, void**)>;
 
 // Returns 0 or a cudaError_t code.
 // `fifo`: allocate the batch-sum FIFO when every T is a multiple of p and it
-// takes at most a quarter of the free device memory.
+// takes at most a quarter of the free device memory.  `double_w`: a second
+// workspace, so that the GEMM of a shift can run while the recovery of the
+// previous shift still reads the first.
 int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
-                   int precision, int* status, bool fifo, const DevAlloc& alloc);
+                   int precision, int* status, bool fifo, bool double_w, const DevAlloc& alloc);
 
 // Staging + operand build for all streams (2 launches).  Stream i reads its
 // X_(+) at xin + xoff_i (row stride ld, or n_i when ld < 0).  With `leaving`,
@@ -149,8 +152,9 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
 // ring buffer.
 cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
                           bool leaving, cudaStream_t st);
-// The GEMM units of a shift (1 launch); `leaving` adds the X_(-) half.
-cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, cudaStream_t st);
+// The GEMM units of a shift (1 launch); `leaving` adds the X_(-) half;
+// `parity` 1 writes the second workspace when there is one.
+cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, int parity, cudaStream_t st);
 
 // Batch q (window order, p samples) of every stream's ring buffer: stage, build
 // and GEMM with no leaving segment (3 launches); streams with fewer batches

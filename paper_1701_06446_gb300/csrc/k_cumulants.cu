@@ -698,6 +698,7 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
         for (int w = blockIdx.x * NT + threadIdx.x; w < f.nwin; w += gridDim.x * NT) {
             const NormArgs& na = f.norm[w];
             *na.head = (*na.head + f.advance) % na.T;
+            if (na.head_stage != nullptr) *na.head_stage = (*na.head_stage + f.advance) % na.T;
         }
 }
 
@@ -752,7 +753,10 @@ __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance,
 {
     const NormArgs& a = args[blockIdx.x];
     const int lane = threadIdx.x & 31, s = threadIdx.x >> 5;
-    if (threadIdx.x == 0 && advance != 0) *a.head = (*a.head + advance) % a.T;
+    if (threadIdx.x == 0 && advance != 0) {
+        *a.head = (*a.head + advance) % a.T;
+        if (a.head_stage != nullptr) *a.head_stage = (*a.head_stage + advance) % a.T;
+    }
     if (s >= a.d || s + 1 < s_from) return;
     double z = 0.0;
     const double* part = a.normpart + (int64_t)s * a.parts;
@@ -849,7 +853,7 @@ cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const Cum
 
 size_t fused_smem_bytes(const FusedRecovery&, int) { return 0; }
 
-int fused_grid(int dfused, size_t smem, int sm_count)
+int fused_grid(int dfused, size_t smem, int sm_count, int per_sm_max)
 {
     int per_sm = 0;
     cudaError_t e = cudaErrorInvalidValue;
@@ -861,7 +865,7 @@ int fused_grid(int dfused, size_t smem, int sm_count)
     default: break;
     }
     if (e != cudaSuccess || per_sm < 1) return 0;
-    return std::min(per_sm, 4) * sm_count;
+    return std::min(per_sm, per_sm_max) * sm_count;
 }
 
 cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st)

@@ -125,11 +125,18 @@ k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, in
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t* __restrict__ opvars,
-           int64_t rows, int nkb, uint16_t* __restrict__ ops)
+           int64_t rows, int nkb, uint16_t* __restrict__ ops, int nstreams, int64_t advance)
 {
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
     grid_dep_launch();  // the GEMM may launch now; its TMA warp waits for this grid
     grid_dep_wait();    // the staged samples come from the previous kernel
+    // the staging of this shift is complete: its ring heads move on (the
+    // recovery keeps its own head, so it may still run on another stream)
+    if (advance != 0 && blockIdx.x == 0)
+        for (int i = threadIdx.x; i < nstreams; i += blockDim.x) {
+            int64_t* hp = sdesc[i].head;
+            *hp = (*hp + advance) % sdesc[i].T;
+        }
     const int total = (int)(rows * nkb);
     const int64_t part = rows * Kcap;  // elements of one part
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -483,12 +490,12 @@ inline int grid_for(int64_t work)
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, 16384));
 }
 
-cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, cudaStream_t st)
+cudaError_t launch_gemm(const TcPlan& plan, float* W, int nplus, int nminus, int minus_k, cudaStream_t st)
 {
     TcGemmArgs a{};
     a.ord = plan.ord;
     a.items = plan.items;
-    a.W = plan.W;
+    a.W = W;
     a.wslice = plan.wslice;
     a.nitems = plan.nitems;
     a.ksplit = plan.ksplit;
@@ -507,7 +514,7 @@ cudaError_t launch_gemm(const TcPlan& plan, int nplus, int nminus, int minus_k, 
     return cudaLaunchKernelEx(&cfg, k_kr_gemm<false>, plan.mapA, plan.mapB[0], plan.mapB[1], plan.mapB[2], a);
 }
 
-cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
+cudaError_t launch_build(const TcPlan& plan, int nsamples, int64_t advance, cudaStream_t st)
 {
     const int nkb = nsamples / 8;
     const int64_t work = plan.oprows * nkb;
@@ -516,9 +523,9 @@ cudaError_t launch_build(const TcPlan& plan, int nsamples, cudaStream_t st)
     pdl_config(cfg, attr, dim3(grid_for(work)), dim3(256), 0, st);
     if (plan.precision == 1)
         return cudaLaunchKernelEx(&cfg, k_kr_build<true>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
-                                  (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops);
+                                  (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance);
     return cudaLaunchKernelEx(&cfg, k_kr_build<false>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
-                              (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops);
+                              (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance);
 }
 
 // --------------------------------------------------------------------------
@@ -575,7 +582,7 @@ double item_chunk_cost(int nrows)
 }  // namespace
 
 int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b, int p, int sm_count,
-                   int precision, int* status, bool fifo, const DevAlloc& alloc)
+                   int precision, int* status, bool fifo, bool double_w, const DevAlloc& alloc)
 {
     (void)b;
     plan.precision = precision;
@@ -774,6 +781,12 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     if (e != cudaSuccess) return (int)e;
     e = cudaMemset(plan.W, 0, sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice);
     if (e != cudaSuccess) return (int)e;
+    if (double_w) {  // a second workspace: the GEMM of one shift while the recovery of the last reads the first
+        e = alloc(sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice, (void**)&plan.W2);
+        if (e != cudaSuccess) return (int)e;
+        e = cudaMemset(plan.W2, 0, sizeof(float) * 2 * (size_t)plan.ksplit_max * plan.wslice);
+        if (e != cudaSuccess) return (int)e;
+    }
 
     // batch-sum FIFO: T_i / p slots of every stream's sums (workspace order)
     plan.fbase.assign(plan.nstreams, 0);
@@ -811,12 +824,13 @@ cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xou
     k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap, leaving ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_build(plan, (leaving ? 2 : 1) * plan.P, st);
+    return launch_build(plan, (leaving ? 2 : 1) * plan.P, p, st);
 }
 
-cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, cudaStream_t st)
+cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, int parity, cudaStream_t st)
 {
-    return launch_gemm(plan, plan.P / KC, leaving ? plan.P / KC : 0, plan.P, st);
+    float* W = parity != 0 && plan.W2 != nullptr ? plan.W2 : plan.W;
+    return launch_gemm(plan, W, plan.P / KC, leaving ? plan.P / KC : 0, plan.P, st);
 }
 
 cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
@@ -825,9 +839,9 @@ cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
     k_tc_stage_batch<<<dim3(gx, plan.nstreams), 256, 0, st>>>(plan.sdesc, q, plan.p, plan.P, plan.Kcap);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_build(plan, plan.P, st);
+    e = launch_build(plan, plan.P, 0, st);
     if (e != cudaSuccess) return e;
-    return launch_gemm(plan, plan.P / KC, 0, 0, st);
+    return launch_gemm(plan, plan.W, plan.P / KC, 0, 0, st);
 }
 
 cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, int q,
@@ -849,9 +863,10 @@ int tc_autotune(TcPlan& plan, int reps, bool leaving, cudaStream_t st, double* b
     std::vector<double> times;
     for (int ks = 1; ks <= plan.ksplit_max && ks <= chunks; ks *= 2) {
         plan.ksplit = ks;
-        cudaError_t e = launch_gemm(plan, chunks, mchunks, plan.P, st);  // warm-up
+        cudaError_t e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm(plan, chunks, mchunks, plan.P, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -234,3 +234,89 @@ def test_fp16_form_reports_not_supported():
     with pytest.raises(CumwinError) as ei:
         CumWin(4, 3, 2, 64, 8, "fp16")
     assert ei.value.code == -7
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fifo_T", [512, 500])
+def test_pipelined_pushes_match_serial_bitwise(fifo_T):
+    """Pushes whose recovery overlaps the next push (two workspaces, an event
+    per workspace) give bitwise the results of the serial order, with and
+    without the batch-sum FIFO, and interleaved with reads of the results."""
+    n, d, b, p = 24, 4, 3, 64
+    T = fifo_T
+    rng = np.random.default_rng(21)
+    X = dev(rng.standard_normal((T + 16 * p, n)).astype(np.float32))
+    with CumWin(n, d, b, T, p, "bf16") as pip, CumWin(n, d, b, T, p, "bf16") as ser:
+        ser.set_pipeline(False)
+        pip.fill(X[:T])
+        ser.fill(X[:T])
+        assert pip.fifo == (T % p == 0)
+        for w in range(16):
+            x = X[T + w * p: T + (w + 1) * p]
+            pip.push(x)
+            ser.push(x)
+            if w % 5 == 4:  # a read between pushes joins the pending recovery
+                assert np.array_equal(pip.norms()[0], ser.norms()[0])
+        pip.join()
+        torch.cuda.synchronize()
+        for k in range(1, d + 1):
+            assert torch.equal(pip.cumulants(k), ser.cumulants(k))
+        assert np.array_equal(pip.norms()[0], ser.norms()[0])
+
+
+@pytest.mark.gpu
+def test_graph_capture_after_pipelined_pushes():
+    """A push captured into a graph right after eager pipelined pushes waits
+    for their recovery (an external-event node) and replays bitwise like eager
+    pushes."""
+    n, d, b, T, p = 20, 4, 4, 512, 64
+    rng = np.random.default_rng(22)
+    Xd = dev(rng.standard_normal((T + 16 * p, n)).astype(np.float32))
+    with CumWin(n, d, b, T, p, "bf16") as eager, CumWin(n, d, b, T, p, "bf16") as cap:
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            eager.fill(Xd[:T])
+            cap.fill(Xd[:T])
+            for w in range(3):  # leave a pipelined recovery pending on `cap`
+                eager.push(Xd[T + w * p: T + (w + 1) * p])
+                cap.push(Xd[T + w * p: T + (w + 1) * p])
+            buf = torch.empty(p, n, device="cuda")
+            buf.copy_(Xd[T + 3 * p: T + 4 * p])
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                cap.push(buf)
+            for w in range(3, 12):
+                buf.copy_(Xd[T + w * p: T + (w + 1) * p])
+                g.replay()
+                eager.push(Xd[T + w * p: T + (w + 1) * p])
+            for k in range(1, d + 1):
+                assert torch.equal(eager.cumulants(k), cap.cumulants(k))
+        torch.cuda.synchronize()
+
+
+@pytest.mark.gpu
+def test_norms_enqueue_per_push_matches_serial():
+    """Per-push copies of the squared norms and of the status into pinned
+    host memory, enqueued behind each pipelined recovery, equal bitwise the
+    norms a serial handle reports after the same pushes."""
+    n, d, b, T, p = 24, 4, 3, 512, 64
+    K = 10
+    rng = np.random.default_rng(23)
+    X = dev(rng.standard_normal((T + K * p, n)).astype(np.float32))
+    out = torch.zeros(K, d, dtype=torch.float64).pin_memory()
+    st = torch.full((K,), -1, dtype=torch.int32).pin_memory()
+    ref = torch.zeros(K, d, dtype=torch.float64, device="cuda")
+    with CumWin(n, d, b, T, p, "bf16") as pip, CumWin(n, d, b, T, p, "bf16") as ser:
+        ser.set_pipeline(False)
+        pip.fill(X[:T])
+        ser.fill(X[:T])
+        for w in range(K):
+            x = X[T + w * p: T + (w + 1) * p]
+            pip.push(x)
+            pip.norms_enqueue(out[w], st[w:w + 1])
+            ser.push(x)
+            ser.norms_device(ref[w])
+        pip.join()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref.cpu())
+        assert torch.equal(st, torch.zeros(K, dtype=torch.int32))
