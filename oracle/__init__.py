@@ -257,6 +257,52 @@ def sample_sorted_tuples(n: int, s: int, count: int, seed: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# moments -> cumulants (Algorithms 3-4), from given moment tensors
+# ----------------------------------------------------------------------------
+
+def set_partitions(items):
+    """All set partitions of the list `items` (each a list of blocks): the
+    first item either forms a block of its own or joins one block of a
+    partition of the rest."""
+    items = list(items)
+    if not items:
+        yield []
+        return
+    first, rest = items[0], items[1:]
+    for part in set_partitions(rest):
+        yield [[first]] + part
+        for k in range(len(part)):
+            yield part[:k] + [[first] + part[k]] + part[k + 1:]
+
+
+def moms2cums_tuples(M, n: int, b: int, tuples) -> np.ndarray:
+    """Cumulants at index tuples (all of one order s) from moment tensors, by
+    Algorithms 3-4: C_s(i) = M_s(i) - A(i), A(i) the sum over the set
+    partitions of the s positions into at least two parts of the product of
+    the lower-order cumulants at the parts' sub-tuples, those computed the
+    same way (memoised).  M[k-1] is M_k in the block layout.  Orders >= 2 do
+    not depend on the point the moments are taken about; C_1 = M_1 does."""
+    memo = {}
+
+    def cum(t):
+        if t in memo:
+            return memo[t]
+        s = len(t)
+        val = float(M[s - 1][storage_index(n, b, t)])
+        for part in set_partitions(range(s)):
+            if len(part) < 2:
+                continue
+            prod = 1.0
+            for blk in part:
+                prod *= cum(tuple(sorted(t[k] for k in blk)))
+            val -= prod
+        memo[t] = val
+        return val
+
+    return np.array([cum(tuple(sorted(int(x) for x in row))) for row in np.asarray(tuples)])
+
+
+# ----------------------------------------------------------------------------
 # norms and the non-Gaussianity estimator (Eqs. me, mef)
 # ----------------------------------------------------------------------------
 

@@ -104,6 +104,8 @@ struct cumwin_s {
     int* status = nullptr;
     double* S[kMaxOrder + 1] = {};
     double* C[kMaxOrder + 1] = {};
+    float2* C2[kMaxOrder + 1] = {};  // two-word copies of the orders below d (mixed forms, d >= 4)
+    float2* S2[kMaxOrder + 1] = {};
     int64_t E[kMaxOrder + 1] = {};
     int64_t Eoff[kMaxOrder + 2] = {};  // offsets of the orders in one concatenated index space
 
@@ -361,13 +363,28 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     if (precision == CUMWIN_FP64) CW_TRY(h->upload(&h->tiles, tiles));
 
     // cumulant recovery tables (norm partials and workspace pointers are set later)
+    for (int k = 1; k < d; ++k)
+        if (h->E[k] >= ((int64_t)1 << 32)) {  // the recovery indexes the lower orders in 32 bits
+            g_last_error = "orders below d must hold fewer than 2^32 stored elements";
+            return CUMWIN_ENOTSUP;
+        }
+    const bool twoword = precision != CUMWIN_FP64 && d >= kTwoWordMinOrder;
+    if (twoword)
+        for (int k = 1; k < d; ++k) {
+            CW_TRY(h->alloc(&h->C2[k], (size_t)h->E[k]));
+            CW_TRY(h->alloc(&h->S2[k], (size_t)h->E[k]));
+        }
     for (int s = 1; s <= d; ++s) {
         CumTables ct = build_cum_tables(n, b, s);
         CumArgs& a = h->cum[s];
         for (int k = 1; k <= d; ++k) {
             a.S[k] = h->S[k];
             a.C[k] = h->C[k];
+            a.C2[k] = h->C2[k];
+            a.S2[k] = h->S2[k];
         }
+        a.split = twoword && s < d;
+        a.twoword = twoword && s >= kTwoWordMinOrder;
         a.Cout = h->C[s];
         CW_TRY(h->upload((int32_t**)&a.subrank, ct.subrank));
         CW_TRY(h->upload((double**)&a.mult, ct.mult));
@@ -563,6 +580,13 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
         s0 = fp.dfused + 1;
     }
     for (int s = s0; s <= d; ++s) {
+        if (s == kTwoWordMinOrder) {  // two-word copies of the lower orders for the orders from here on
+            const int s_hi = kTwoWordMinOrder - 1;
+            int64_t maxE = 1;
+            for (int k = 1; k <= s_hi; ++k) maxE = std::max(maxE, fp.emax[k]);
+            CW_TRY(launch_split(args, nwin, s_hi, maxE, sm_count, st));
+            *launches += 1;
+        }
         if (accum != 0) {  // windows whose top order is s fold it in one linear pass first
             CW_TRY(launch_fold_linear(args + (size_t)s * nwin, nwin, fp.emax[s], sm_count, st));
             *launches += 1;

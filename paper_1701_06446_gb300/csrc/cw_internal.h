@@ -80,7 +80,16 @@ struct CumArgs {
     int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = stacked in/out, 2 = FIFO
     int32_t bR, p;                   // b^(s - h); shift size (accum 2)
     int32_t sgemm;                   // S_s kept in workspace order (the top order of the mixed forms)
+    // Mixed forms with d >= kTwoWordMinOrder: the orders below d also keep
+    // C_k and S_k as two-word FP32 values (hi + lo, written by their own
+    // recovery: `split`), and orders >= kTwoWordMinOrder form the products of
+    // their subset sum in that two-word arithmetic (`twoword`), leaving only
+    // the final subtraction from S_s, the scaling and the norm on the FP64 pipe.
+    float2* C2[kMaxOrder + 1];
+    float2* S2[kMaxOrder + 1];
+    int32_t split, twoword;
 };
+constexpr int kTwoWordMinOrder = 5;
 
 // Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
 // trailing indices, seeding, compaction over sorted tuples, and dL/dX.
@@ -132,6 +141,10 @@ cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const Cum
 cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st);
 // Per-CTA partials of sum multiplicity * |C_s|^k (nparts CTAs).
 cudaError_t launch_knorm(const CumArgs* args_dev, int64_t E, double k, double* partials, int nparts, cudaStream_t st);
+// Two-word copies (CumArgs::C2 / S2) of orders 1..s_hi of the windows whose
+// arguments are args_dev[order * nwin + window] (those with `split` set);
+// maxE = the largest of their E.
+cudaError_t launch_split(const CumArgs* args_dev, int nwin, int s_hi, int64_t maxE, int sm_count, cudaStream_t st);
 // out[i] = src[idx[i]], i < n.
 cudaError_t launch_gather_idx(const double* src, const int64_t* idx, int n, double* out, cudaStream_t st);
 // out = S_s * scale in storage order for sums kept in workspace order.

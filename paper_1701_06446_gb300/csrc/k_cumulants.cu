@@ -190,6 +190,36 @@ __device__ __forceinline__ void fold_elem(const CumArgs& a, int64_t blk, int off
     fold_store(fold_load(a, blk, off, e, fslot));
 }
 
+// Two-word FP32 arithmetic for the subset sums of the mixed forms (a value
+// is hi + lo).  The product of two such values uses Dekker's exact product
+// (the rounding error of hi*hi recovered with one fused multiply-add, after
+// Dekker 1971) plus the two cross terms; the running sum uses Knuth's
+// two-sum for the high words and adds the errors into the low word.  Every
+// operation is an explicitly rounded intrinsic, so the compiler cannot
+// contract or reorder them.  The relative error of a sum of m products is
+// about m * 2^-46 of the sum of the products' magnitudes, far below the
+// error of the sums being recovered, at a few FP32 operations per product
+// instead of one FP64 multiply-add on this GPU's narrow FP64 pipe.
+__device__ __forceinline__ void tw_acc_prod(float& hi, float& lo, float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float s = __fadd_rn(hi, p);
+    const float v = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+    hi = s;
+}
+
+// hi = x rounded to FP32, lo = the rest rounded to FP32.
+__device__ __forceinline__ float2 tw_split(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - f32_to_f64(h)));
+}
+
 // C_2 at storage index x of order 2, from the (folded) sums: what the order-2
 // element computes, operation for operation, with C_1 = S_1 / T.
 __device__ __forceinline__ double c2_from_sums(const CumArgs& a2, int64_t x)
@@ -218,26 +248,47 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2
     const int b = a.b;
     const int64_t e = blk * a.bs + c.off;
     if (FOLD && a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
-    double acc = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
+    const double sv = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
     // the subsets: sub-block ranks (rank(j_A), rank(j_rest)) of the block, one
-    // gather per factor, one FP64 multiply-add
+    // gather per factor, one multiply-add
     const int32_t* sr = a.subrank + (size_t)blk * NS * 2;
+    double cv;
+    if (S >= kTwoWordMinOrder && a.twoword) {
+        float hi = 0.0f, lo = 0.0f;
 #pragma unroll(S <= 4 ? NS : 4)
-    for (int t = 0; t < NS; ++t) {
-        const int2 q = *reinterpret_cast<const int2*>(sr + 2 * t);
-        const int la = __popc(2u * t + 1u), lr = S - la;
-        int oa, orr;
-        subset_offsets<S>(c, b, t, oa, orr);
-        const int64_t ia = (int64_t)q.x * ipow_c(b, la) + oa;
-        double cA;
-        if (OTF >= 1 && la == 1) cA = a.S[1][ia] * a.invT;
-        else if (OTF >= 2 && la == 2) cA = c2_from_sums(*a2, ia);
-        else cA = a.C[la][ia];
-        const double sR = a.S[lr][(int64_t)q.y * ipow_c(b, lr) + orr];
-        acc = fma(-cA, sR, acc);
+        for (int t = 0; t < NS; ++t) {
+            const int2 q = *reinterpret_cast<const int2*>(sr + 2 * t);
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            int oa, orr;
+            subset_offsets<S>(c, b, t, oa, orr);
+            const float2 cA = a.C2[la][(unsigned)q.x * (unsigned)ipow_c(b, la) + (unsigned)oa];
+            const float2 sR = a.S2[lr][(unsigned)q.y * (unsigned)ipow_c(b, lr) + (unsigned)orr];
+            tw_acc_prod(hi, lo, cA, sR);
+        }
+        cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
+    } else {
+        double acc = sv;
+#pragma unroll(S <= 4 ? NS : 4)
+        for (int t = 0; t < NS; ++t) {
+            const int2 q = *reinterpret_cast<const int2*>(sr + 2 * t);
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            int oa, orr;
+            subset_offsets<S>(c, b, t, oa, orr);
+            const unsigned ia = (unsigned)q.x * (unsigned)ipow_c(b, la) + (unsigned)oa;
+            double cA;
+            if (OTF >= 1 && la == 1) cA = a.S[1][ia] * a.invT;
+            else if (OTF >= 2 && la == 2) cA = c2_from_sums(*a2, ia);
+            else cA = a.C[la][ia];
+            const double sR = a.S[lr][(unsigned)q.y * (unsigned)ipow_c(b, lr) + (unsigned)orr];
+            acc = fma(-cA, sR, acc);
+        }
+        cv = acc * a.invT;
     }
-    const double cv = acc * a.invT;
     a.Cout[e] = cv;
+    if (S >= kTwoWordMinOrder && a.split) {  // the two-word copies the next orders read
+        a.C2[S][e] = tw_split(cv);
+        a.S2[S][e] = tw_split(sv);
+    }
     if (S == 1) {
         const double x = cv + (double)a.shift[e];
         local = fma(x, x, local);
@@ -293,18 +344,37 @@ __device__ __forceinline__ void recover_group_smem(const CumArgs& a, const Elem<
     if (!c.valid || blk >= nblocks) return;
     const int64_t e = blk * a.bs + c.off;
     if (a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
-    double acc = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
+    const double sv = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
     const int* sb = sbase + 2 * c.slot * NS;
+    double cv;
+    if (a.twoword) {
+        float hi = 0.0f, lo = 0.0f;
 #pragma unroll 4
-    for (int t = 0; t < NS; ++t) {
-        const int la = __popc(2u * t + 1u), lr = S - la;
-        const int packed = offs[t * NT + threadIdx.x];
-        const double cA = a.C[la][sb[2 * t] + (packed >> 16)];
-        const double sR = a.S[lr][sb[2 * t + 1] + (packed & 0xffff)];
-        acc = fma(-cA, sR, acc);
+        for (int t = 0; t < NS; ++t) {
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            const int packed = offs[t * NT + threadIdx.x];
+            const float2 cA = a.C2[la][sb[2 * t] + (packed >> 16)];
+            const float2 sR = a.S2[lr][sb[2 * t + 1] + (packed & 0xffff)];
+            tw_acc_prod(hi, lo, cA, sR);
+        }
+        cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
+    } else {
+        double acc = sv;
+#pragma unroll 4
+        for (int t = 0; t < NS; ++t) {
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            const int packed = offs[t * NT + threadIdx.x];
+            const double cA = a.C[la][sb[2 * t] + (packed >> 16)];
+            const double sR = a.S[lr][sb[2 * t + 1] + (packed & 0xffff)];
+            acc = fma(-cA, sR, acc);
+        }
+        cv = acc * a.invT;
     }
-    const double cv = acc * a.invT;
     a.Cout[e] = cv;
+    if (a.split) {
+        a.C2[S][e] = tw_split(cv);
+        a.S2[S][e] = tw_split(sv);
+    }
     local = fma(a.mult[blk] * cv, cv, local);
 }
 
@@ -713,6 +783,19 @@ __global__ void __launch_bounds__(NT) k_fold_linear(const CumArgs* __restrict__ 
         fold_store(fold_load_at(a, w, w, fslot));
 }
 
+// Two-word copies of C_k and S_k for the orders k <= s_hi recovered below
+// kTwoWordMinOrder (the higher orders write theirs as they go); blockIdx.y =
+// k - 1, blockIdx.z = window.
+__global__ void __launch_bounds__(NT) k_split(const CumArgs* __restrict__ args)
+{
+    const CumArgs& a = args[(int64_t)(blockIdx.y + 1) * gridDim.z + blockIdx.z];
+    if (!a.split) return;
+    for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < a.E; e += (int64_t)gridDim.x * NT) {
+        a.C2[a.s][e] = tw_split(a.Cout[e]);
+        a.S2[a.s][e] = tw_split(a.S[a.s][e]);
+    }
+}
+
 // out[e] = S_s[slot(e)] * scale: the sums of an order kept in workspace order,
 // back in storage order.
 __global__ void __launch_bounds__(NT) k_gather_sums(const CumArgs* __restrict__ args, double scale, double* out)
@@ -877,6 +960,14 @@ cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, s
     case 4: return launch_fused_df<4>(f, grid, smem, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_split(const CumArgs* args_dev, int nwin, int s_hi, int64_t maxE, int sm_count, cudaStream_t st)
+{
+    const int64_t need = (maxE + NT - 1) / NT;
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(need, 4LL * sm_count));
+    k_split<<<dim3(gx, s_hi, nwin), NT, 0, st>>>(args_dev);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_knorm(const CumArgs* args_dev, int64_t E, double k, double* partials, int nparts, cudaStream_t st)

@@ -320,3 +320,31 @@ def test_norms_enqueue_per_push_matches_serial():
         torch.cuda.synchronize()
         assert torch.equal(out, ref.cpu())
         assert torch.equal(st, torch.zeros(K, dtype=torch.int32))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,d,b", [(20, 4, 4), (22, 4, 3), (10, 6, 2), (9, 5, 4)])
+def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b):
+    """The recovery alone (orders >= 4 form their subset sums in two-word FP32
+    arithmetic, the final subtraction in FP64): the cumulants of a mixed-form
+    window against Algorithms 3-4 evaluated by the oracle in FP64 on that
+    window's own moments, so that the update's rounding is not in the
+    comparison."""
+    T, p = 384, 64
+    rng = np.random.default_rng(31 + n + d)
+    X = rng.standard_normal((T + 4 * p, n)) + 0.3 * rng.exponential(1.0, (T + 4 * p, n))
+    Xd = dev(X.astype(np.float32))
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        for w in range(4):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        M = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        errs = {}
+        for s in range(2, d + 1):
+            C = h.cumulants(s).cpu().numpy()
+            tup = oracle.sample_sorted_tuples(n, s, 150, seed=s)
+            idx = np.array([oracle.storage_index(n, b, t) for t in tup])
+            ref = oracle.moms2cums_tuples(M, n, b, tup)
+            errs[s] = rel_fro(C[idx], ref)
+        print("recovery-only errors", errs)
+        assert max(errs.values()) < 1e-10

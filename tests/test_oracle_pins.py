@@ -356,3 +356,37 @@ def test_storage_index_agrees_with_enumerated_layout():
         for e in np.nonzero(keep)[0]:
             g = oracle.storage_index(n, b, idx[e])
             assert np.array_equal(np.sort(idx[g]), np.sort(idx[e]))
+
+
+# ----------------------------------------------------------------------------
+# moments -> cumulants (Algorithms 3-4)
+# ----------------------------------------------------------------------------
+
+def test_set_partitions_are_the_bell_numbers_of_eq_n1():
+    with open(os.path.join(GOLDEN, "eq_n1_counts.json")) as f:
+        gold = json.load(f)
+    for d, bell in gold["bell"].items():
+        parts = list(oracle.set_partitions(range(int(d))))
+        assert len(parts) == bell
+        seen = set()
+        for p in parts:  # each a partition of 0..d-1, no duplicates
+            assert sorted(x for blk in p for x in blk) == list(range(int(d)))
+            key = frozenset(frozenset(blk) for blk in p)
+            assert key not in seen
+            seen.add(key)
+
+
+@pytest.mark.parametrize("seed,n,T,D", [(5, 2, 9, 5), (6, 3, 11, 4), (7, 1, 8, 6)])
+def test_moms2cums_matches_cgf_on_integer_windows(seed, n, T, D):
+    """Algorithms 3-4 on the window's raw moments give the exact cumulants of
+    the cumulant-generating function."""
+    rng = np.random.default_rng(seed)
+    X = rng.integers(-3, 4, size=(T, n)).astype(np.float64)
+    kappa = cgf_cumulants(X.astype(np.int64), D)
+    b = 2
+    M = oracle.moments(X, D, b)
+    for s in range(1, D + 1):
+        tup = np.array(list(itertools.combinations_with_replacement(range(n), s)), dtype=np.int32)
+        got = oracle.moms2cums_tuples(M, n, b, tup)
+        want = np.array([float(kappa[tuple(int(np.sum(t == i)) for i in range(n))]) for t in tup])
+        assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(want).max()))
