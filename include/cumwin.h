@@ -243,6 +243,11 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev);
  * synchronises and returns the summed event times in milliseconds, the number
  * of timed shifts and the number of kernels the library launched since timing
  * was enabled.  Enabling resets the counters.  Not for use inside stream capture.
+ * enable == 2 records no event between the staging and the update (an event
+ * there separates the operand build from the GEMM, which otherwise launch
+ * chained); the staging time is then reported inside update_ms and stage_ms
+ * is 0.  Timed pushes run their recovery on the handle's stream (no
+ * pipelining), so that the three intervals follow each other.
  */
 int cumwin_set_timing(cumwin_t h, int enable);
 int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* cumulant_ms,

@@ -219,8 +219,12 @@ class CumWin:
         check(self.lib.cumwin_grad(self._h, wa.ctypes.data, out.data_ptr()), "cumwin_grad")
         return out
 
-    def set_timing(self, enable: bool = True):
-        check(self.lib.cumwin_set_timing(self._h, int(bool(enable))), "cumwin_set_timing")
+    def set_timing(self, enable=True):
+        """Phase timing of later shifts (see cumwin_set_timing): True / 1 splits each
+        shift into staging, update and recovery; 2 leaves the staging inside the
+        update (no event between the operand build and the GEMM)."""
+        level = int(enable) if not isinstance(enable, bool) else int(enable)
+        check(self.lib.cumwin_set_timing(self._h, level), "cumwin_set_timing")
 
     def get_timing(self) -> dict:
         a, u, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -164,6 +164,7 @@ struct cumwin_s {
 
     // kernel timing (cumwin_set_timing)
     bool timing = false;
+    bool coarse = false;          // no event between staging and update (cumwin_set_timing 2)
     std::vector<cudaEvent_t> ev;  // 4 per timed shift: start, staged, updated, recovered
     int64_t timed = 0, launches = 0;
 
@@ -190,7 +191,7 @@ struct cumwin_s {
     // event slot k of the current timed shift, or null when not timing
     cudaEvent_t mark(int k, cudaStream_t on = nullptr)
     {
-        if (!timing || timed * 4 + k >= (int64_t)ev.size()) return nullptr;
+        if (!timing || timed * 4 + k >= (int64_t)ev.size() || (coarse && k == 1)) return nullptr;
         cudaEvent_t e = ev[timed * 4 + k];
         cudaEventRecord(e, on != nullptr ? on : stream);
         return e;
@@ -1358,6 +1359,7 @@ int cumwin_set_timing(cumwin_t h, int enable)
     if (h == nullptr) return CUMWIN_EINVAL;
     CW_TRY(join(h));
     h->timing = enable != 0;
+    h->coarse = enable == 2;
     h->timed = 0;
     h->launches = 0;
     if (h->timing && h->ev.empty()) {
@@ -1376,8 +1378,12 @@ int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* c
     double a = 0.0, u = 0.0, c = 0.0;
     for (int64_t k = 0; k < h->timed; ++k) {
         float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-        CW_TRY(cudaEventElapsedTime(&t0, h->ev[4 * k], h->ev[4 * k + 1]));
-        CW_TRY(cudaEventElapsedTime(&t1, h->ev[4 * k + 1], h->ev[4 * k + 2]));
+        if (h->coarse) {  // staging counted in the update
+            CW_TRY(cudaEventElapsedTime(&t1, h->ev[4 * k], h->ev[4 * k + 2]));
+        } else {
+            CW_TRY(cudaEventElapsedTime(&t0, h->ev[4 * k], h->ev[4 * k + 1]));
+            CW_TRY(cudaEventElapsedTime(&t1, h->ev[4 * k + 1], h->ev[4 * k + 2]));
+        }
         CW_TRY(cudaEventElapsedTime(&t2, h->ev[4 * k + 2], h->ev[4 * k + 3]));
         a += t0;
         u += t1;
