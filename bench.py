@@ -67,7 +67,9 @@ def algorithmic_flops(W, fifo: bool = False) -> dict:
 
 # DRAM bytes (read + write) per launch of the recovery from one ncu capture of the current
 # kernel (see profiles/), by workload; None where no capture of the current kernel exists.
-RECOVERY_TRAFFIC = {}
+RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 12996864}
+# the same for the GEMM (k_kr_gemm)
+GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15838976}
 
 
 class ClockSampler:
@@ -357,7 +359,8 @@ def run_ours(args, W, rank: int, world: int):
         roof_gemm = {"kernel": "k_kr_gemm", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_kind": f"{peak_kind} bf16 sustained (of measured)",
-                     "traffic": None, "avg_launch_ms": upd_ms, "share_of_step": upd_ms / ms_per_step,
+                     "traffic": GEMM_TRAFFIC.get(W.name), "avg_launch_ms": upd_ms,
+                     "share_of_step": upd_ms / ms_per_step,
                      "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x K x E_s summed over "
                                    f"orders, K = {'p: entering samples; leaving sums from the FIFO' if fifo else '2p'}); "
                                    f"the tensor pipe issues 3x (hi*hi + hi*lo + lo*hi)"}
