@@ -317,69 +317,79 @@ __device__ __forceinline__ double cta_sum(double v, double* red)
 constexpr int kSmemOffsetsMax = 6;
 
 // Order S >= 5 with the subset offsets of each thread's in-block offset in
-// shared memory (computed once) and the sub-block bases (rank * b^|A|) of the
-// CTA's blocks staged per group: per subset two shared loads, two gathers and
-// one FP64 multiply-add.
+// shared memory (computed once, packed 16 + 16 bits) and, per subset of each
+// block of a batch of groups, the addresses of its two sub-blocks (the
+// operand arrays of the form: two-word copies, or the FP64 arrays), staged
+// once per batch: per subset three shared loads, two gathers and the
+// multiply-add.  `ptrs` holds [gb][slots][NS] address pairs.
 template <int S>
-__device__ __forceinline__ void recover_group_smem(const CumArgs& a, const Elem<S>& c, int64_t grp, int slots,
-                                                   int64_t fslot, const int* offs, int* sbase, double& local)
+__device__ __forceinline__ void recover_groups_smem(const CumArgs& a, const Elem<S>& c, int64_t g0, int64_t gstride,
+                                                    int gb, int slots, int64_t fslot, const int* offs,
+                                                    ulonglong2* ptrs, double& local)
 {
     constexpr int NS = Subsets<S>::N;
     const int b = a.b;
     const int64_t nblocks = a.E / a.bs;
-    const int64_t blk0 = grp * slots;
-    __syncthreads();
-    for (int i = threadIdx.x; i < slots * NS; i += NT) {
-        const int64_t blk = blk0 + i / NS;
-        const int t = i - (i / NS) * NS;
-        if (blk < nblocks) {
+    const int64_t ngroups = (nblocks + slots - 1) / slots;
+    const bool tw = a.twoword != 0;
+    __syncthreads();  // the previous batch's readers are done
+    for (int i = threadIdx.x; i < gb * slots * NS; i += NT) {
+        const int jg = i / (slots * NS), r = i - jg * (slots * NS);
+        const int sl = r / NS, t = r - sl * NS;
+        const int64_t grp = g0 + jg * gstride, blk = grp * slots + sl;
+        if (grp < ngroups && blk < nblocks) {
             const int2 q = *reinterpret_cast<const int2*>(a.subrank + ((size_t)blk * NS + t) * 2);
-            const int la = __popc(2u * t + 1u);
-            sbase[2 * i] = q.x * ipow_c(b, la);
-            sbase[2 * i + 1] = q.y * ipow_c(b, S - la);
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            const char* ca = tw ? (const char*)a.C2[la] : (const char*)a.C[la];
+            const char* sr = tw ? (const char*)a.S2[lr] : (const char*)a.S[lr];
+            ptrs[i] = make_ulonglong2((unsigned long long)(ca + (size_t)q.x * ipow_c(b, la) * 8),
+                                      (unsigned long long)(sr + (size_t)q.y * ipow_c(b, lr) * 8));
         }
     }
     __syncthreads();
-    const int64_t blk = blk0 + c.slot;
-    if (!c.valid || blk >= nblocks) return;
-    const int64_t e = blk * a.bs + c.off;
-    if (a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
-    const double sv = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
-    const int* sb = sbase + 2 * c.slot * NS;
-    double cv;
-    if (a.twoword) {
-        float hi = 0.0f, lo = 0.0f;
+    for (int jg = 0; jg < gb; ++jg) {
+        const int64_t grp = g0 + jg * gstride;
+        if (grp >= ngroups) break;
+        const int64_t blk = grp * slots + c.slot;
+        if (!c.valid || blk >= nblocks) continue;
+        const int64_t e = blk * a.bs + c.off;
+        if (a.accum && !a.sgemm) fold_elem(a, blk, c.off, e, fslot);
+        const double sv = a.S[S][a.sgemm ? wslot(a, blk, c.off) : e];
+        const ulonglong2* pp = ptrs + (jg * slots + c.slot) * NS;
+        double cv;
+        if (tw) {
+            float hi = 0.0f, lo = 0.0f;
 #pragma unroll 4
-        for (int t = 0; t < NS; ++t) {
-            const int la = __popc(2u * t + 1u), lr = S - la;
-            const int packed = offs[t * NT + threadIdx.x];
-            const float2 cA = a.C2[la][sb[2 * t] + (packed >> 16)];
-            const float2 sR = a.S2[lr][sb[2 * t + 1] + (packed & 0xffff)];
-            tw_acc_prod(hi, lo, cA, sR);
-        }
-        cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
-    } else {
-        double acc = sv;
+            for (int t = 0; t < NS; ++t) {
+                const ulonglong2 pr = pp[t];
+                const int packed = offs[t * NT + threadIdx.x];
+                const float2 cA = reinterpret_cast<const float2*>(pr.x)[packed >> 16];
+                const float2 sR = reinterpret_cast<const float2*>(pr.y)[packed & 0xffff];
+                tw_acc_prod(hi, lo, cA, sR);
+            }
+            cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
+        } else {
+            double acc = sv;
 #pragma unroll 4
-        for (int t = 0; t < NS; ++t) {
-            const int la = __popc(2u * t + 1u), lr = S - la;
-            const int packed = offs[t * NT + threadIdx.x];
-            const double cA = a.C[la][sb[2 * t] + (packed >> 16)];
-            const double sR = a.S[lr][sb[2 * t + 1] + (packed & 0xffff)];
-            acc = fma(-cA, sR, acc);
+            for (int t = 0; t < NS; ++t) {
+                const ulonglong2 pr = pp[t];
+                const int packed = offs[t * NT + threadIdx.x];
+                acc = fma(-reinterpret_cast<const double*>(pr.x)[packed >> 16],
+                          reinterpret_cast<const double*>(pr.y)[packed & 0xffff], acc);
+            }
+            cv = acc * a.invT;
         }
-        cv = acc * a.invT;
+        a.Cout[e] = cv;
+        if (a.split) {
+            a.C2[S][e] = tw_split(cv);
+            a.S2[S][e] = tw_split(sv);
+        }
+        local = fma(a.mult[blk] * cv, cv, local);
     }
-    a.Cout[e] = cv;
-    if (a.split) {
-        a.C2[S][e] = tw_split(cv);
-        a.S2[S][e] = tw_split(sv);
-    }
-    local = fma(a.mult[blk] * cv, cv, local);
 }
 
 template <int S>
-__global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__ args, int slots)
+__global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__ args, int slots, int gb)
 {
     const CumArgs& a = args[blockIdx.z];  // one window per blockIdx.z
     if (a.E == 0) return;                 // this window has no order S
@@ -392,17 +402,17 @@ __global__ void __launch_bounds__(NT, 4) k_cumulants(const CumArgs* __restrict__
     if constexpr (S > kKeepOffsets && S <= kSmemOffsetsMax) smem_path = ipow_c(a.b, S - 1) <= 0xffff;
     if (smem_path) {
         constexpr int NS = Subsets<S>::N;
-        extern __shared__ int dyn[];  // [NS][NT] packed offsets, then [slots][NS][2] bases
-        int* offs = dyn;
-        int* sbase = dyn + NS * NT;
+        extern __shared__ ulonglong2 dyn[];  // [gb][slots][NS] address pairs, then [NS][NT] offsets
+        ulonglong2* ptrs = dyn;
+        int* offs = reinterpret_cast<int*>(dyn + (size_t)gb * slots * NS);
         for (int t = 0; t < NS; ++t) {
             int oa, orr;
             subset_offsets<S>(c, a.b, t, oa, orr);
             offs[t * NT + threadIdx.x] = (oa << 16) | orr;  // both < b^{S-1} <= 2^16
         }
         const int64_t ngroups = (nblocks + slots - 1) / slots;
-        for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x)
-            recover_group_smem<S>(a, c, grp, slots, fslot, offs, sbase, local);
+        for (int64_t g0 = blockIdx.x; g0 < ngroups; g0 += (int64_t)gridDim.x * gb)
+            recover_groups_smem<S>(a, c, g0, gridDim.x, gb, slots, fslot, offs, ptrs, local);
     } else {
         if (c.valid)
             for (int64_t blk = (int64_t)blockIdx.x * slots + c.slot; blk < nblocks; blk += (int64_t)gridDim.x * slots)
@@ -860,9 +870,13 @@ template <int S>
 cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cudaStream_t st)
 {
     size_t smem = 0;
+    int gb = 1;
     if (S > kKeepOffsets && S <= kSmemOffsetsMax && L.bpow1 <= 0xffff) {  // the kernel takes the same branch
         constexpr int NS = Subsets<S>::N;
-        smem = sizeof(int) * ((size_t)NS * NT + (size_t)L.slots * NS * 2);
+        // groups whose operand addresses are staged together: up to 8, within 16 KB
+        const size_t per = sizeof(ulonglong2) * (size_t)L.slots * NS;
+        gb = (int)std::max<size_t>(1, std::min<size_t>(8, (16 * 1024) / per));
+        smem = per * gb + sizeof(int) * (size_t)NS * NT;
         static size_t opted = 48 * 1024;  // above 48 KB needs the opt-in (raised once per size)
         if (smem > opted) {
             cudaError_t e = cudaFuncSetAttribute(k_cumulants<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -870,7 +884,7 @@ cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cuda
             opted = smem;
         }
     }
-    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots);
+    k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots, gb);
     return cudaGetLastError();
 }
 

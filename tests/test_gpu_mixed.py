@@ -348,3 +348,32 @@ def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b):
             errs[s] = rel_fro(C[idx], ref)
         print("recovery-only errors", errs)
         assert max(errs.values()) < 1e-10
+
+
+@pytest.mark.gpu
+def test_phase_timing_levels():
+    """Timing level 1 splits a shift into staging, update and recovery; level 2
+    keeps the staging inside the update (no event between the operand build
+    and the GEMM); both count the library's launches and leave the results
+    bitwise unchanged."""
+    n, d, b, T, p = 24, 4, 3, 512, 64
+    rng = np.random.default_rng(41)
+    X = dev(rng.standard_normal((T + 8 * p, n)).astype(np.float32))
+    with CumWin(n, d, b, T, p, "bf16") as h, CumWin(n, d, b, T, p, "bf16") as ref:
+        h.fill(X[:T])
+        ref.fill(X[:T])
+        for level, w0 in ((1, 0), (2, 4)):
+            h.set_timing(level)
+            for w in range(w0, w0 + 4):
+                h.push(X[T + w * p: T + (w + 1) * p])
+                ref.push(X[T + w * p: T + (w + 1) * p])
+            t = h.get_timing()
+            h.set_timing(False)
+            assert t["shifts"] == 4 and t["launches"] >= 16
+            assert t["update_ms"] > 0 and t["cumulant_ms"] > 0
+            if level == 1:
+                assert t["stage_ms"] > 0
+            else:
+                assert t["stage_ms"] == 0
+        for k in range(1, d + 1):
+            assert torch.equal(h.cumulants(k), ref.cumulants(k))
