@@ -67,9 +67,9 @@ def algorithmic_flops(W, fifo: bool = False) -> dict:
 
 # DRAM bytes (read + write) per launch of the recovery from one ncu capture of the current
 # kernel (see profiles/), by workload; None where no capture of the current kernel exists.
-RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 12996864}
+RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 12997376}
 # the same for the GEMM (k_kr_gemm)
-GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15838976}
+GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15818240}
 
 
 class ClockSampler:
@@ -374,6 +374,9 @@ def run_ours(args, W, rank: int, world: int):
                     "share_of_step": rec_ms / ms_per_step,
                     "per_launch": f"{flops['recovery_launch']:.4g} algorithmic FP64 flops (per stored element "
                                   f"of order s: 2(2^(s-1)-1) subset recursion + 1 scaling + 2 norm + 2 fold)"}
+        if W.d >= 5:
+            roof_rec["note"] = ("orders >= 5 form their subset products in two-word FP32 arithmetic on the "
+                                "FMA pipe, so these FP64-class flops can run faster than the FP64 pipe's peak")
         # the roofline line is the dominant kernel's; the other is kept beside it
         if rec_ms >= upd_ms:
             roof, roof_other = roof_rec, roof_gemm

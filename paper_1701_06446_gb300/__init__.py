@@ -187,13 +187,12 @@ class CumWin:
 
     def norms_enqueue(self, fro2_out: torch.Tensor, status_out: torch.Tensor | None = None):
         """Enqueue copies of ||C_s||^2 (d float64) and of the device status (int32)
-        into the given tensors (pinned CPU or CUDA), behind the last push's
+        into the given tensors (CUDA, or host memory: pinned for an asynchronous
+        copy, pageable makes the copy synchronous), behind the last push's
         recovery; valid after ``join()`` and a synchronisation (see cumwin_norms_enqueue)."""
         def ptr(t, dtype, count, what):
             if t.dtype != dtype or not t.is_contiguous() or t.numel() < count:
                 raise ValueError(f"{what} must be a contiguous {dtype} tensor of at least {count} elements")
-            if not t.is_cuda and not t.is_pinned():
-                raise ValueError(f"{what} must be a CUDA tensor or pinned host memory")
             return ctypes.c_void_p(t.data_ptr())
         sp = ptr(status_out, torch.int32, 1, "status_out") if status_out is not None else None
         self._sync_stream()

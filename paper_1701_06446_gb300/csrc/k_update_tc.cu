@@ -215,8 +215,11 @@ __device__ __forceinline__ UnitRange unit_range(const TcGemmArgs& args, int spli
     return r;
 }
 
+// The bound of 4 CTAs per SM only caps the registers at 80 (shared memory allows
+// one CTA per SM): the GEMM of the next shift then fits on an SM beside the three
+// CTAs of the previous shift's recovery.
 template <bool BF16>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 4)
 k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB32,
           const __grid_constant__ CUtensorMap mapB64, const __grid_constant__ CUtensorMap mapB128,
           const TcGemmArgs args)
@@ -385,25 +388,18 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             float* Win = args.W + (int64_t)(2 * split) * args.wslice + od.woff;
             float* Wout = Win + args.wslice;
             const int NB = (item.nrows + 15) & ~15;
-            // 32 rows per round: two TMEM loads per accumulator, one wait, then
-            // one coalesced 128-byte store per row (lanes = consecutive slots)
-            for (int jb = 0; jb < NB; jb += 32) {
-                const bool two = jb + 16 < NB;  // warp-uniform
-                uint32_t d0[32], d1[32];
+            // 16 rows per round: one TMEM load per accumulator, one wait, then
+            // one coalesced 64-byte store per row (lanes = consecutive slots)
+            for (int jb = 0; jb < NB; jb += 16) {
+                uint32_t d0[16], d1[16];
                 const uint32_t ta = tbase + ab * 256u + ((uint32_t)(32 * quarter) << 16) + (uint32_t)jb;
-                if (R.nplus > 0) {
-                    tmem_ld16p(ta, d0);
-                    if (two) tmem_ld16p(ta + 16u, d0 + 16);
-                }
-                if (R.nminus > 0) {
-                    tmem_ld16p(ta + (uint32_t)NMAX, d1);
-                    if (two) tmem_ld16p(ta + (uint32_t)NMAX + 16u, d1 + 16);
-                }
+                if (R.nplus > 0) tmem_ld16p(ta, d0);
+                if (R.nminus > 0) tmem_ld16p(ta + (uint32_t)NMAX, d1);
                 tmem_ld_wait();
                 if (item.fast) {
                     const int64_t w0 = (int64_t)item.wrow0 + (int64_t)jb * item.wwidth + cglob;
 #pragma unroll
-                    for (int t = 0; t < 32; ++t) {
+                    for (int t = 0; t < 16; ++t) {
                         if (ivalid && jb + t < item.nrows) {
                             const int64_t e = w0 + (int64_t)t * item.wwidth;
                             Win[e] = R.nplus > 0 ? __uint_as_float(d0[t]) : 0.0f;
@@ -412,7 +408,7 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                     }
                 } else {
 #pragma unroll
-                    for (int t = 0; t < 32; ++t) {
+                    for (int t = 0; t < 16; ++t) {
                         const int r = jb + t;
                         if (ivalid && r < item.nrows && cglob >= rowcolmin[r]) {
                             const int64_t e = roww[r] + cglob;
