@@ -2,11 +2,32 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include <cuda_runtime.h>
 
 namespace cw {
+
+// Raise a kernel's dynamic shared memory limit to `bytes` on the current
+// device; done once per (kernel, device) and size, under a lock, so that
+// launches on several devices or threads each get the opt-in.
+inline cudaError_t smem_opt_in(const void* func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = done[{func, dev}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 constexpr int kMaxOrder = 8;
 constexpr int kMaxN = 256;

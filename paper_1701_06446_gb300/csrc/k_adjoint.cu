@@ -221,13 +221,8 @@ cudaError_t launch_grad_x(const float* ring, int64_t T, const int64_t* head, int
                           cudaStream_t st)
 {
     const size_t smem = sizeof(float) * ((size_t)AT * npad + AT * AU + (size_t)AU * n);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_grad_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(float) * (AT * kMaxN + AT * AU + AU * kMaxN)));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = smem_opt_in((const void*)k_grad_x, sizeof(float) * (AT * kMaxN + AT * AU + AU * kMaxN));
+    if (e != cudaSuccess) return e;
     k_grad_x<<<(int)((T + AT - 1) / AT), NT, smem, st>>>(ring, T, head, n, npad, shift, uvars, unf, nu, Gc, dX);
     return cudaGetLastError();
 }

@@ -877,11 +877,9 @@ cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cuda
         const size_t per = sizeof(ulonglong2) * (size_t)L.slots * NS;
         gb = (int)std::max<size_t>(1, std::min<size_t>(8, (16 * 1024) / per));
         smem = per * gb + sizeof(int) * (size_t)NS * NT;
-        static size_t opted = 48 * 1024;  // above 48 KB needs the opt-in (raised once per size)
-        if (smem > opted) {
-            cudaError_t e = cudaFuncSetAttribute(k_cumulants<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 48 * 1024) {  // above 48 KB needs the opt-in
+            cudaError_t e = smem_opt_in((const void*)k_cumulants<S>, smem);
             if (e != cudaSuccess) return e;
-            opted = smem;
         }
     }
     k_cumulants<S><<<dim3(L.gx, L.gy, nwin), NT, smem, st>>>(args, L.slots, gb);

@@ -113,13 +113,8 @@ cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int nti
 {
     if (ntiles <= 0 || K <= 0) return cudaSuccess;
     const size_t smem = sizeof(double) * ((size_t)KC * a.npad + KC * TM + KC * TN);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_update_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(double) * ((size_t)KC * kMaxN + KC * TM + KC * TN)));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = smem_opt_in((const void*)k_update_f64, sizeof(double) * ((size_t)KC * kMaxN + KC * TM + KC * TN));
+    if (e != cudaSuccess) return e;
     k_update_f64<<<ntiles, NT, smem, st>>>(a, tiles, rows, K, npos, shift);
     return cudaGetLastError();
 }
