@@ -219,6 +219,16 @@ int cumwin_marginals(cumwin_t h, double* skew_host, double* kurt_host);
  * the cumulants and norms. */
 int cumwin_recompute(cumwin_t h);
 
+/* Mixed forms: re-fix the shift vector at the current window's column means
+ * (FP32-rounded) and recompute the moment sums, the batch-sum FIFO, the
+ * cumulants and the norms about it.  The moments are accumulated about that
+ * vector, so when the stream's mean has drifted far from the one of the first
+ * window, the raw-moment cancellation (and with it the split form's error)
+ * grows; this call removes it at the cost of one recomputation.  Cumulants of
+ * order >= 2 do not depend on the shift.  In the FP64 form (no shift) it is
+ * cumwin_recompute.  Asynchronous; errors: EINVAL, ESTATE. */
+int cumwin_recenter(cumwin_t h);
+
 /* Copy the current window, oldest sample first, T x n FP32 row-major (ld = n). */
 int cumwin_window(cumwin_t h, float* out_dev);
 

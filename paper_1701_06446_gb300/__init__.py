@@ -203,6 +203,11 @@ class CumWin:
         self._sync_stream()
         check(self.lib.cumwin_recompute(self._h), "cumwin_recompute")
 
+    def recenter(self):
+        """Re-fix the shift at the window's column means and recompute about it (cumwin_recenter)."""
+        self._sync_stream()
+        check(self.lib.cumwin_recenter(self._h), "cumwin_recenter")
+
     def window(self) -> torch.Tensor:
         out = torch.empty(self.T, self.n, dtype=torch.float32, device=self.device)
         self._sync_stream()

@@ -33,6 +33,7 @@ SIGNATURES = {
     "cumwin_norms": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_norms_device": (c_int, [c_vp, c_vp]),
     "cumwin_recompute": (c_int, [c_vp]),
+    "cumwin_recenter": (c_int, [c_vp]),
     "cumwin_window": (c_int, [c_vp, c_vp]),
     "cumwin_grad": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_status": (c_int, [c_vp]),

@@ -1230,6 +1230,20 @@ int cumwin_recompute(cumwin_t h)
     return run_cumulants(h, 0);
 }
 
+int cumwin_recenter(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
+    if (h->prec != CUMWIN_FP64)  // the new shift: the current window's column means
+        CW_TRY(launch_column_mean(h->ring, h->T, h->n, h->npad, h->shift, h->stream));
+    int rc = zero_sums(h);
+    if (rc) return rc;
+    rc = update_window(h);
+    if (rc) return rc;
+    return run_cumulants(h, 0);
+}
+
 int cumwin_window(cumwin_t h, float* out_dev)
 {
     if (h == nullptr || out_dev == nullptr) return CUMWIN_EINVAL;

@@ -377,3 +377,39 @@ def test_phase_timing_levels():
                 assert t["stage_ms"] == 0
         for k in range(1, d + 1):
             assert torch.equal(h.cumulants(k), ref.cumulants(k))
+
+
+@pytest.mark.gpu
+def test_recenter_after_mean_drift():
+    """A stream whose mean drifts far from the first window's: the sums about
+    the old shift carry a large raw-moment cancellation; re-centering at the
+    window's own means recomputes them about the new shift, which lowers the
+    error against the oracle, keeps the FIFO, and later pushes stay exact
+    against a fresh recomputation."""
+    n, d, b, T, p = 16, 4, 4, 1024, 128
+    rng = np.random.default_rng(51)
+    X = rng.standard_t(6, size=(T + 16 * p, n))
+    X[T:] += 6.0 + rng.standard_normal(n)  # the stream moves away from the first window's mean
+    X = X.astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "bf16") as h:
+        h.fill(Xd[:T])
+        for w in range(8):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        win = X[8 * p: 8 * p + T]
+        before = errors_vs_oracle(h, win)
+        h.recenter()
+        after = errors_vs_oracle(h, win)
+        print("error before / after re-centering", before, after)
+        for s in range(2, d + 1):
+            assert after[s] <= before[s], s
+        check_bounds(after)
+        assert h.fifo
+        for w in range(8, 16):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        slide = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        h.recompute()
+        fresh = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        for s in range(1, d + 1):
+            assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
+        check_bounds(errors_vs_oracle(h, X[16 * p: 16 * p + T]))
