@@ -31,6 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1701_06446_gb300 import ranks  # noqa: E402
 from paper_1701_06446_gb300.streams import WORKLOADS  # noqa: E402
 
 METRIC = "window updates/s and TFLOP/s vs tensor-core peak at stated error vs FP64 oracle"
@@ -229,7 +230,6 @@ def measure_fp64_form(W, stream, base: int, steps: int, dev) -> dict:
 
 def run_ours(args, W, rank: int, world: int):
     import torch
-    import torch.distributed as dist
     from paper_1701_06446_gb300 import CumWin
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -240,7 +240,7 @@ def run_ours(args, W, rank: int, world: int):
     nsteps = args.warmup + args.steps + split_steps
     e2e_steps = min(args.steps, 200)
     # each rank advances its own independent stretch of the stream
-    base = rank * (W.T + (nsteps + 2 * e2e_steps + 1) * W.p)
+    base = ranks.stream_base(rank, W.T, W.p, nsteps + 2 * e2e_steps)
     ksplit = None
     X = stream.rows(base, base + W.T + nsteps * W.p)
     Xd = torch.from_numpy(X).to(dev)
@@ -262,8 +262,7 @@ def run_ours(args, W, rank: int, world: int):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-    if world > 1:
-        dist.barrier()
+    ranks.barrier(world)
     torch.cuda.synchronize()
     sampler = ClockSampler(uuid) if rank == 0 else None
     # coarse library timing inside the timed region: the recovery's own interval (the
@@ -275,26 +274,21 @@ def run_ours(args, W, rank: int, world: int):
         h.push(batches[args.warmup + k])
         ends[k].record(st)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    ranks.barrier(world)
     clocks = sampler.stop() if sampler else None
     timing = h.get_timing()
     h.set_timing(False)
-    # the staging / GEMM split from an untimed pass with every phase event (same data again,
-    # L2 flushed before each shift)
+    # the staging / GEMM split from an untimed pass with every phase event (the next shifts
+    # of the stream, L2 flushed before each)
     h.set_timing(True)
     for k in range(split_steps):
         flush.zero_()
         h.push(batches[args.warmup + args.steps + k])
     timing_split = h.get_timing()
     h.set_timing(False)
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms = float(t.item())
+    step_ms = ranks.max_over_ranks([sum(s.elapsed_time(e) for s, e in zip(starts, ends))], dev, world)[0]
     ms_per_step = step_ms / args.steps
-    value = world * args.steps / (step_ms * 1e-3)
+    value = ranks.job_rate(world, args.steps, step_ms * 1e-3)
 
     # end-to-end through the C ABI with host buffers: H2D of X_(+) from pinned memory and D2H of
     # every step's squared norms and status inside the timed region.  Streaming form: each push's
@@ -306,8 +300,7 @@ def run_ours(args, W, rank: int, world: int):
     fro2_host = torch.zeros(e2e_steps, W.d, dtype=torch.float64).pin_memory()
     st_host = torch.full((e2e_steps,), -1, dtype=torch.int32).pin_memory()
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    ranks.barrier(world)
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         h.push_host(hb[k])
@@ -325,11 +318,9 @@ def run_ours(args, W, rank: int, world: int):
         h.push_host(hb[k])
         fro, nu = h.norms()
     t3 = time.perf_counter()
-    e2e_t = torch.tensor([t1 - t0, t3 - t2], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps / float(e2e_t[0].item())
-    e2e_sync_value = world * e2e_steps / float(e2e_t[1].item())
+    e2e_t = ranks.max_over_ranks([t1 - t0, t3 - t2], dev, world)
+    e2e_value = ranks.job_rate(world, e2e_steps, e2e_t[0])
+    e2e_sync_value = ranks.job_rate(world, e2e_steps, e2e_t[1])
     e2e_steps_total = 2 * e2e_steps
 
     # accuracy of the final window against the FP64 oracle (sampled tuples)
@@ -459,6 +450,8 @@ def run_batch(args, rank: int, world: int):
     steps = nsteps - args.warmup
     st0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     st1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ranks.barrier(world)
+    torch.cuda.synchronize()
     with torch.cuda.stream(cap_stream):
         for k in range(steps):
             buf.copy_(packs[args.warmup + k])
@@ -466,6 +459,7 @@ def run_batch(args, rank: int, world: int):
             g.replay()
             st1[k].record(cap_stream)
     torch.cuda.synchronize()
+    ranks.barrier(world)
     ms = [a.elapsed_time(z) for a, z in zip(st0, st1)]
     # latency over >= 1000 replays (inputs cycle through the same packs)
     reps = max(1000, steps)
@@ -505,8 +499,8 @@ def run_batch(args, rank: int, world: int):
                 e[str(s_)] = float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
             err[f"window{i}(n={ns[i]},d={ds[i]})"] = e
         B2.close()
-    mean_ms = statistics.mean(ms)
-    value = world * 512 * 1e3 / mean_ms
+    mean_ms = ranks.max_over_ranks([statistics.mean(ms)], dev, world)[0]
+    value = ranks.job_rate(world, 512, mean_ms * 1e-3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -544,8 +538,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank, world, local_rank = ranks.rank_env()
     if args.workload == BATCH_WORKLOAD:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the "
@@ -553,15 +546,12 @@ def main():
             return
         if world > 1:
             import torch
-            import torch.distributed as dist
-            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-            dist.init_process_group("nccl")
+            torch.cuda.set_device(local_rank)
+        ranks.init(world, "nccl")
         try:
             run_batch(args, rank, world)
         finally:
-            if world > 1:
-                import torch.distributed as dist
-                dist.destroy_process_group()
+            ranks.finish(world)
         return
     W = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -570,15 +560,12 @@ def main():
         return
     if world > 1:
         import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        dist.init_process_group("nccl")
+        torch.cuda.set_device(local_rank)
+    ranks.init(world, "nccl")
     try:
         run_ours(args, W, rank, world)
     finally:
-        if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        ranks.finish(world)
 
 
 if __name__ == "__main__":
