@@ -83,7 +83,8 @@ def test_bad_arguments_rejected_without_gpu():
     h = ctypes.c_void_p()
     # argument checks run before any CUDA call
     for args in [(0, 4, 2, 100, 10), (4, 0, 2, 100, 10), (4, 9, 2, 100, 10), (4, 4, 0, 100, 10),
-                 (4, 4, 2, 0, 1), (4, 4, 2, 100, 0), (4, 4, 2, 100, 101), (300, 2, 1, 10, 1)]:
+                 (4, 4, 2, 0, 1), (4, 4, 2, 100, 0), (4, 4, 2, 100, 101), (300, 2, 1, 10, 1),
+                 (257, 2, 8, 10, 1), (250, 2, 43, 10, 1)]:  # above 256 variables, also once padded
         assert lib.cumwin_create(*args, 0, None, ctypes.byref(h)) == _lib.CODES["EINVAL"]
     assert lib.cumwin_create(4, 4, 2, 100, 10, 7, None, ctypes.byref(h)) == _lib.CODES["EINVAL"]
     assert lib.cumwin_push(None, None, None, 1, 4) == _lib.CODES["EINVAL"]

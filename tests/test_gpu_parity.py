@@ -272,3 +272,53 @@ def test_k_norms_and_marginals(k):
         assert np.all(np.isnan(sk)) and np.all(np.isnan(ku))
         with pytest.raises(CumwinError):
             h2.norms_k(0.5)
+
+
+@pytest.mark.parametrize("n,precision", [(256, "fp64"), (255, "bf16"), (256, "bf16")])
+def test_maximum_number_of_variables(n, precision):
+    """n at the largest the layout takes (256 variables, padded or not), orders
+    1-3 with b = 8 (order 3: 3.06 M stored elements), FP64 and split forms,
+    sampled tuples against the oracle after shifts through the ring."""
+    d, b, T, p = 3, 8, 512, 64
+    rng = np.random.default_rng(61 + n)
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    X = (rng.gamma(2.0, size=(T + 4 * p, n)) @ A).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, precision) as h:
+        h.fill(Xd[:T])
+        for w in range(4):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        Xw = X[4 * p: 4 * p + T]
+        cen = oracle.center(Xw)
+        tol = TOL_FP64 if precision == "fp64" else {1: 2e-5, 2: 5e-5, 3: 5e-4}
+        for s in range(1, d + 1):
+            tup = oracle.sample_sorted_tuples(n, s, 300, seed=7 * s + n)
+            idx = np.array([oracle.storage_index(n, b, t) for t in tup])
+            ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
+            err = rel_fro(h.cumulants(s).cpu().numpy()[idx], ref)
+            assert err <= (tol if precision == "fp64" else tol[s]), (s, err)
+        assert np.array_equal(h.window().cpu().numpy(), Xw)
+
+
+@pytest.mark.parametrize("d,precision", [(1, "fp64"), (1, "bf16"), (2, "fp64"), (2, "bf16")])
+def test_lowest_orders(d, precision):
+    """d = 1 (means only) and d = 2 (covariance): no order above the split and no
+    nu; the recovery, norms and ring still follow the window."""
+    n, b, T, p = 11, 3, 96, 16
+    rng = np.random.default_rng(71 + d)
+    X = (rng.standard_normal((T + 5 * p, n)) * 2.0 + 1.0).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, precision) as h:
+        h.fill(Xd[:T])
+        for w in range(5):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        Xw = X[5 * p: 5 * p + T]
+        ref = oracle.cumulants(Xw, d, b)
+        tol = [TOL_FP64] * d if precision == "fp64" else [2e-5, 5e-5][:d]
+        for s in range(1, d + 1):
+            assert rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) <= tol[s - 1], s
+        fro, nu = h.norms()
+        ofro, _ = oracle.norms(Xw, d)
+        assert np.allclose(fro, ofro, rtol=max(tol), atol=0)
+        assert np.all(np.isnan(nu))
+        assert np.array_equal(h.window().cpu().numpy(), Xw)
