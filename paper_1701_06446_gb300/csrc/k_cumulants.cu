@@ -768,7 +768,16 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
         if (s <= na.d) {
             const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
             const double* part = f.upart + f.upoff[s];
-            for (int64_t q = us[w] + threadIdx.x; q < us[w + 1]; q += NT) z += part[q];
+            const int64_t q1 = us[w + 1];
+            int64_t q = us[w] + threadIdx.x;
+            for (; q + 3 * NT < q1; q += 4 * NT) {  // four loads in flight, added in index order
+                const double v0 = part[q], v1 = part[q + NT], v2 = part[q + 2 * NT], v3 = part[q + 3 * NT];
+                z += v0;
+                z += v1;
+                z += v2;
+                z += v3;
+            }
+            for (; q < q1; q += NT) z += part[q];
         }
         z = cta_sum(z, red);
         if (threadIdx.x == 0 && s <= na.d) na.fro2[s - 1] = z;
