@@ -749,7 +749,7 @@ int check_args(int n, int d, int b, int64_t T, int p, int precision)
     if ((int64_t)nbar * b > kMaxN) return CUMWIN_EINVAL;
     if (T > ((int64_t)1 << 40)) return CUMWIN_EINVAL;
     if (precision == CUMWIN_MIXED_FP16) {
-        g_last_error = "the FP16 split form is not available in this build";
+        g_last_error = "the FP16 split form is not implemented (use the BF16 split form)";
         return CUMWIN_ENOTSUP;
     }
     return CUMWIN_OK;
