@@ -94,7 +94,10 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
 /* Free all device state.  Synchronises the handle's stream first.  NULL is a no-op. */
 int cumwin_destroy(cumwin_t h);
 
-/* Change the stream later calls are issued on. */
+/* Change the stream later calls are issued on.  The new stream first waits
+ * (on the device) for the work issued so far on the old stream and for any
+ * pending pipelined recovery, so the handle's calls stay in order.  When either
+ * stream is being captured, ordering the two streams is left to the capturer. */
 int cumwin_set_stream(cumwin_t h, void* cuda_stream);
 
 /*

@@ -983,7 +983,21 @@ int cumwin_destroy(cumwin_t h)
 int cumwin_set_stream(cumwin_t h, void* cuda_stream)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
-    h->stream = (cudaStream_t)cuda_stream;
+    cudaStream_t next = (cudaStream_t)cuda_stream;
+    if (next == h->stream) return CUMWIN_OK;
+    // later work on the new stream follows everything issued so far on the old
+    // one and the pending recoveries.  When either stream is under capture the
+    // capturer orders the streams (a graph cannot wait on a temporary event).
+    if (!capturing(h->stream) && !capturing(next)) {
+        cudaEvent_t e = nullptr;
+        CW_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaError_t err = cudaEventRecord(e, h->stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(next, e, 0);
+        cudaEventDestroy(e);  // released once the wait is resolved
+        CW_TRY(err);
+    }
+    h->stream = next;
+    CW_TRY(join(h));
     return CUMWIN_OK;
 }
 

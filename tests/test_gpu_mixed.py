@@ -413,3 +413,70 @@ def test_recenter_after_mean_drift():
         for s in range(1, d + 1):
             assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
         check_bounds(errors_vs_oracle(h, X[16 * p: 16 * p + T]))
+
+
+@pytest.mark.gpu
+def test_pipelined_handle_under_a_random_call_sequence():
+    """A pipelined handle and a serial twin driven by the same seeded sequence
+    of calls (nominal, short and caller-supplied shifts, reads of every kind,
+    recomputation, re-centering, pipeline toggles, a switch to another stream)
+    hold bitwise equal results at every read."""
+    n, d, b, T, p = 14, 4, 3, 384, 48
+    rng = np.random.default_rng(81)
+    steps = 60
+    X = rng.standard_t(5, size=(T + steps * p, n)).astype(np.float32)
+    Xd = dev(X)
+    other = torch.cuda.Stream()
+    with CumWin(n, d, b, T, p, "bf16") as a, CumWin(n, d, b, T, p, "bf16") as ref:
+        ref.set_pipeline(False)
+        a.fill(Xd[:T])
+        ref.fill(Xd[:T])
+        pos = T  # next unread row of the stream
+        win0 = 0  # first row of the current window
+        for step in range(steps):
+            op = rng.choice(["push", "push", "push", "short", "xout", "read", "norms", "recompute",
+                             "recenter", "toggle", "stream"])
+            if op in ("push", "short", "xout"):
+                k = p if op != "short" else int(rng.integers(1, p))
+                if pos + k > X.shape[0]:
+                    continue
+                x = Xd[pos: pos + k]
+                if op == "xout":
+                    xo = Xd[win0: win0 + k]
+                    a.push(x, xo)
+                    ref.push(x, xo)
+                else:
+                    a.push(x)
+                    ref.push(x)
+                pos += k
+                win0 += k
+            elif op == "read":
+                s = int(rng.integers(1, d + 1))
+                assert torch.equal(a.cumulants(s), ref.cumulants(s)), (step, s)
+                assert torch.equal(a.moments(s), ref.moments(s)), (step, s)
+            elif op == "norms":
+                fa, na = a.norms()
+                fr, nr = ref.norms()
+                assert np.array_equal(fa, fr), step
+            elif op == "recompute":
+                a.recompute()
+                ref.recompute()
+            elif op == "recenter":
+                a.recenter()
+                ref.recenter()
+            elif op == "toggle":
+                a.set_pipeline(bool(rng.integers(0, 2)))
+            else:  # later calls on another stream, then back
+                with torch.cuda.stream(other):
+                    x = Xd[pos: pos + p] if pos + p <= X.shape[0] else None
+                    if x is not None:
+                        a.push(x)
+                        ref.push(x)
+                        pos += p
+                        win0 += p
+                    assert torch.equal(a.cumulants(d), ref.cumulants(d)), step
+        torch.cuda.synchronize()
+        for s in range(1, d + 1):
+            assert torch.equal(a.cumulants(s), ref.cumulants(s)), s
+        assert np.array_equal(a.window().cpu().numpy(), X[win0: win0 + T])
+        assert a.status() == 0
