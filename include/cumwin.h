@@ -170,7 +170,10 @@ int cumwin_fifo(cumwin_t h);
 /*
  * As cumwin_push with X_(+) in HOST memory (pinned memory gives an
  * asynchronous copy; pageable memory makes the copy synchronous).  The copy
- * goes to a device staging buffer owned by the handle.
+ * goes to one of two device staging buffers owned by the handle, on a copy
+ * stream of the handle, so that it overlaps the kernels of the previous
+ * pushes; the push waits for its copy, and a buffer is reused only after the
+ * push that read it.  Under stream capture the copy runs on the handle's stream.
  */
 int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld);
 

@@ -99,7 +99,7 @@ struct cumwin_s {
 
     float* ring = nullptr;   // [T][npad] raw samples
     float* stage = nullptr;  // [2T][npad] X_(+) then X_(-) (FP64 form)
-    float* hin = nullptr;    // [T][npad] device copy of host X_(+)
+    float* hin[2] = {};      // [T][npad] device copies of host X_(+), used by alternate pushes
     float* shift = nullptr;  // [npad]
     int* status = nullptr;
     double* S[kMaxOrder + 1] = {};
@@ -160,6 +160,15 @@ struct cumwin_s {
     bool pend[2] = {false, false};
     int par = 0;
     int last = 0;          // workspace of the last pipelined push
+    // cumwin_push_host: the host-to-device copy of a push runs on `cstream`
+    // into one of two buffers, overlapping the previous pushes' kernels;
+    // ev_h2d[q] marks the copy into buffer q, ev_staged[q] the push that last
+    // read it
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr};
+    cudaEvent_t ev_staged[2] = {nullptr, nullptr};
+    bool hin_pend[2] = {false, false};
+    int hq = 0;
     bool pipeline = true;  // cumwin_set_pipeline
 
     // kernel timing (cumwin_set_timing)
@@ -174,15 +183,16 @@ struct cumwin_s {
     cudaError_t upload(T** p, const std::vector<T>& v) { return mem.upload(p, v); }
     void release()
     {
+        for (cudaStream_t* q : {&rstream, &cstream})
+            if (*q != nullptr) {  // their work ends before the memory goes
+                cudaStreamSynchronize(*q);
+                cudaStreamDestroy(*q);
+                *q = nullptr;
+            }
         mem.release();
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         ev.clear();
-        if (rstream != nullptr) {
-            cudaStreamSynchronize(rstream);
-            cudaStreamDestroy(rstream);
-            rstream = nullptr;
-        }
-        for (cudaEvent_t* e : {&ev_gemm, &ev_rec[0], &ev_rec[1]})
+        for (cudaEvent_t* e : {&ev_gemm, &ev_rec[0], &ev_rec[1], &ev_h2d[0], &ev_h2d[1], &ev_staged[0], &ev_staged[1]})
             if (*e != nullptr) {
                 cudaEventDestroy(*e);
                 *e = nullptr;
@@ -303,7 +313,8 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     const int npad = h->npad;
     CW_TRY(h->alloc(&h->ring, (size_t)T * npad));
     if (precision == CUMWIN_FP64) CW_TRY(h->alloc(&h->stage, (size_t)2 * T * npad));
-    CW_TRY(h->alloc(&h->hin, (size_t)T * npad));
+    CW_TRY(h->alloc(&h->hin[0], (size_t)T * npad));
+    CW_TRY(h->alloc(&h->hin[1], (size_t)T * npad));
     CW_TRY(h->alloc(&h->shift, npad));
     CW_TRY(cudaMemset(h->shift, 0, sizeof(float) * npad));
     CW_TRY(h->alloc(&h->status, 1));
@@ -945,6 +956,14 @@ int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cu
     }
     if (rc == CUMWIN_OK) rc = window_finish(h, parts, h->tc, 0);
     if (rc == CUMWIN_OK) rc = fused_setup(h->fused, {h}, b, h->sm_count, h->norm_dev, h->status, h->mem, 3);
+    if (rc == CUMWIN_OK) {  // the copy stream of cumwin_push_host
+        cudaError_t e = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            e = cudaEventCreateWithFlags(&h->ev_h2d[q], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_staged[q], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) rc = fail_cuda(e, "create");
+    }
     if (rc == CUMWIN_OK && h->tc != nullptr) {  // the recovery stream of pipelined shifts
         cudaError_t e = cudaStreamCreateWithFlags(&h->rstream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_gemm, cudaEventDisableTiming);
@@ -1088,9 +1107,25 @@ int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld)
 {
     if (h == nullptr || x_in_host == nullptr || p < 1 || p > h->T || ld < h->n) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
-    CW_TRY(cudaMemcpy2DAsync(h->hin, sizeof(float) * h->npad, x_in_host, sizeof(float) * ld,
-                             sizeof(float) * h->n, p, cudaMemcpyHostToDevice, h->stream));
-    return cumwin_push(h, h->hin, nullptr, p, h->npad);
+    if (h->cstream == nullptr || capturing(h->stream)) {  // one stream: the copy, then the push
+        CW_TRY(cudaMemcpy2DAsync(h->hin[0], sizeof(float) * h->npad, x_in_host, sizeof(float) * ld,
+                                 sizeof(float) * h->n, p, cudaMemcpyHostToDevice, h->stream));
+        return cumwin_push(h, h->hin[0], nullptr, p, h->npad);
+    }
+    // the copy into buffer q waits for the push that last read it and overlaps
+    // the kernels of the pushes before; the push waits for the copy
+    const int q = h->hq;
+    if (h->hin_pend[q]) CW_TRY(cudaStreamWaitEvent(h->cstream, h->ev_staged[q], 0));
+    CW_TRY(cudaMemcpy2DAsync(h->hin[q], sizeof(float) * h->npad, x_in_host, sizeof(float) * ld,
+                             sizeof(float) * h->n, p, cudaMemcpyHostToDevice, h->cstream));
+    CW_TRY(cudaEventRecord(h->ev_h2d[q], h->cstream));
+    CW_TRY(cudaStreamWaitEvent(h->stream, h->ev_h2d[q], 0));
+    const int rc = cumwin_push(h, h->hin[q], nullptr, p, h->npad);
+    if (rc) return rc;
+    CW_TRY(cudaEventRecord(h->ev_staged[q], h->stream));  // after the push's staging read the buffer
+    h->hin_pend[q] = true;
+    h->hq = q ^ 1;
+    return CUMWIN_OK;
 }
 
 int cumwin_cumulants(cumwin_t h, int order, double* out_dev)

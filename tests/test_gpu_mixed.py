@@ -480,3 +480,28 @@ def test_pipelined_handle_under_a_random_call_sequence():
             assert torch.equal(a.cumulants(s), ref.cumulants(s)), s
         assert np.array_equal(a.window().cpu().numpy(), X[win0: win0 + T])
         assert a.status() == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["bf16", "fp64"])
+def test_push_host_matches_device_pushes(precision):
+    """Pushes from host memory (pinned and pageable; the copies overlap the
+    previous pushes' kernels through two staging buffers) equal pushes of the
+    same rows from device memory, bitwise, with reads interleaved."""
+    n, d, b, T, p = 12, 4, 3, 256, 32
+    rng = np.random.default_rng(91)
+    X = rng.standard_normal((T + 24 * p, n)).astype(np.float32)
+    Xd = dev(X)
+    pinned = torch.from_numpy(X).pin_memory()
+    with CumWin(n, d, b, T, p, precision) as hh, CumWin(n, d, b, T, p, precision) as hd:
+        hh.fill(Xd[:T])
+        hd.fill(Xd[:T])
+        for w in range(24):
+            rows = slice(T + w * p, T + (w + 1) * p)
+            hh.push_host(pinned[rows] if w % 3 else X[rows])
+            hd.push(Xd[rows])
+            if w % 7 == 6:
+                assert np.array_equal(hh.norms()[0], hd.norms()[0]), w
+        for s in range(1, d + 1):
+            assert torch.equal(hh.cumulants(s), hd.cumulants(s)), s
+        assert torch.equal(hh.window(), hd.window())
