@@ -181,6 +181,14 @@ int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld);
  * cumwin_layout_size(n, b, order) elements, into out_dev. */
 int cumwin_cumulants(cumwin_t h, int order, double* out_dev);
 
+/* Expand C_s (1 <= order <= d) of the current window into the full
+ * n^order tensor, row-major over (i_1, ..., i_order) with every permutation of
+ * a sorted index tuple holding the same value (the super-symmetric tensor the
+ * block layout of Section 2.3 stores once), FP64, n^order doubles into
+ * out_dev.  Order 1 includes the shift (it is the window mean).  Errors:
+ * EINVAL (also when n^order exceeds 2^36), ESTATE. */
+int cumwin_full(cumwin_t h, int order, double* out_dev);
+
 /* Copy the current moment tensor M_s about the shift vector, i.e. the moments
  * (Eq. 5) of x - shift; the shift is zero in the FP64 form.  Block layout. */
 int cumwin_moments(cumwin_t h, int order, double* out_dev);

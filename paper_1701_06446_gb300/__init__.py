@@ -157,6 +157,14 @@ class CumWin:
               "cumwin_cumulants")
         return out
 
+    def full(self, order: int) -> torch.Tensor:
+        """C_order as the full super-symmetric n^order tensor (cumwin_full)."""
+        self._order(order)
+        out = torch.empty((self.n,) * order, dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_full(self._h, order, _dev_ptr(out, torch.float64, "out")), "cumwin_full")
+        return out
+
     def moments(self, order: int) -> torch.Tensor:
         self._order(order)
         out = torch.empty(self.sizes[order - 1], dtype=torch.float64, device=self.device)

@@ -29,6 +29,7 @@ SIGNATURES = {
     "cumwin_push_host": (c_int, [c_vp, c_vp, c_int, c_i64]),
     "cumwin_cumulants": (c_int, [c_vp, c_int, c_vp]),
     "cumwin_moments": (c_int, [c_vp, c_int, c_vp]),
+    "cumwin_full": (c_int, [c_vp, c_int, c_vp]),
     "cumwin_shift": (c_int, [c_vp, c_vp]),
     "cumwin_norms": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_norms_device": (c_int, [c_vp, c_vp]),

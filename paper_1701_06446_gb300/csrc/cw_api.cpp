@@ -100,6 +100,7 @@ struct cumwin_s {
     float* ring = nullptr;   // [T][npad] raw samples
     float* stage = nullptr;  // [2T][npad] X_(+) then X_(-) (FP64 form)
     float* hin[2] = {};      // [T][npad] device copies of host X_(+), used by alternate pushes
+    int64_t* nst = nullptr;  // [nbar + 1][kMaxOrder + 1] sorted-tuple counts (full-tensor expansion)
     float* shift = nullptr;  // [npad]
     int* status = nullptr;
     double* S[kMaxOrder + 1] = {};
@@ -313,6 +314,12 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     const int npad = h->npad;
     CW_TRY(h->alloc(&h->ring, (size_t)T * npad));
     if (precision == CUMWIN_FP64) CW_TRY(h->alloc(&h->stage, (size_t)2 * T * npad));
+    {
+        std::vector<int64_t> nst((size_t)(nbar + 1) * (kMaxOrder + 1));
+        for (int v = 0; v <= nbar; ++v)
+            for (int r = 0; r <= kMaxOrder; ++r) nst[v * (kMaxOrder + 1) + r] = n_sorted(nbar - v, r);
+        CW_TRY(h->upload(&h->nst, nst));
+    }
     CW_TRY(h->alloc(&h->hin[0], (size_t)T * npad));
     CW_TRY(h->alloc(&h->hin[1], (size_t)T * npad));
     CW_TRY(h->alloc(&h->shift, npad));
@@ -1142,6 +1149,24 @@ int cumwin_cumulants(cumwin_t h, int order, double* out_dev)
     return CUMWIN_OK;
 }
 
+int cumwin_full(cumwin_t h, int order, double* out_dev)
+{
+    if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    int64_t nf = 1;
+    for (int s = 0; s < order; ++s) {
+        nf *= h->n;
+        if (nf > ((int64_t)1 << 36)) {
+            g_last_error = "the full tensor would hold more than 2^36 elements";
+            return CUMWIN_EINVAL;
+        }
+    }
+    CW_TRY(join(h));
+    CW_TRY(launch_expand(h->C[order], nf, order, h->n, h->b, h->nst, 1.0, order == 1 ? h->shift : nullptr, out_dev,
+                         h->stream));
+    return CUMWIN_OK;
+}
+
 int cumwin_moments(cumwin_t h, int order, double* out_dev)
 {
     if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
@@ -1326,10 +1351,7 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
             if (s < d) CW_TRY(h->alloc(&g.Mf[s], g.nf[s]));
         }
         CW_TRY(h->alloc(&g.C1true, n));
-        std::vector<int64_t> nst((size_t)(h->nbar + 1) * (kMaxOrder + 1));
-        for (int v = 0; v <= h->nbar; ++v)
-            for (int r = 0; r <= kMaxOrder; ++r) nst[v * (kMaxOrder + 1) + r] = n_sorted(h->nbar - v, r);
-        CW_TRY(h->upload(&g.nst, nst));
+        g.nst = h->nst;
         // sorted (s-1)-tuples of variables with their numbers of distinct orderings
         std::vector<uint32_t> uv;
         std::vector<float> um;

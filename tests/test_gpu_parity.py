@@ -5,6 +5,8 @@ oracle, element by element on windows the oracle recomputes in seconds, and on
 seeded samples of sorted tuples at the full workload sizes.  Integer-valued
 windows (exact products and sums) must match to 1e-12.
 """
+import itertools
+
 import numpy as np
 import pytest
 import torch
@@ -322,3 +324,31 @@ def test_lowest_orders(d, precision):
         assert np.allclose(fro, ofro, rtol=max(tol), atol=0)
         assert np.all(np.isnan(nu))
         assert np.array_equal(h.window().cpu().numpy(), Xw)
+
+
+@pytest.mark.parametrize("n,d,b,precision", [(7, 4, 3, "fp64"), (9, 3, 4, "bf16"), (5, 5, 2, "fp64")])
+def test_full_tensor_expansion(n, d, b, precision):
+    """cumwin_full expands the block layout into the full super-symmetric n^s
+    tensor: equal to the oracle's expansion of the same stored values, and to
+    the oracle's cumulants within the form's tolerance."""
+    T, p = 80, 10
+    rng = np.random.default_rng(101 + n)
+    X = (rng.standard_normal((T + 3 * p, n)) + 0.5).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, precision) as h:
+        h.fill(Xd[:T])
+        for w in range(3):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        Xw = X[3 * p: 3 * p + T]
+        ref = oracle.cumulants(Xw, d, b)
+        for s in range(1, d + 1):
+            full = h.full(s).cpu().numpy()
+            assert full.shape == (n,) * s
+            # every full index reads the stored element of its sorted tuple (a diagonal block
+            # also stores the unsorted in-block orders, which agree up to rounding)
+            blk = h.cumulants(s).cpu().numpy()
+            tup = list(itertools.product(range(n), repeat=s))
+            want = np.array([blk[oracle.storage_index(n, b, tuple(sorted(t)))] for t in tup]).reshape((n,) * s)
+            assert np.array_equal(full, want), s
+            tol = TOL_FP64 if precision == "fp64" else 5e-4
+            assert rel_fro(full, oracle.to_full(ref[s - 1], n, b, s)) <= tol, s
