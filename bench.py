@@ -73,6 +73,15 @@ RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 16044800}
 GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15818240}
 
 
+def device_uuid(dev):
+    """nvidia-smi's id of the torch device (its UUID), or None."""
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
 
@@ -258,14 +267,9 @@ def run_ours(args, W, rank: int, world: int):
     st = torch.cuda.current_stream(dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
     ranks.barrier(world)
     torch.cuda.synchronize()
-    sampler = ClockSampler(uuid) if rank == 0 else None
+    sampler = ClockSampler(device_uuid(dev)) if rank == 0 else None
     # coarse library timing inside the timed region: the recovery's own interval (the
     # dominant kernel) without an event between the operand build and the GEMM
     h.set_timing(2)
@@ -454,8 +458,10 @@ def run_batch(args, rank: int, world: int):
     steps = nsteps - args.warmup
     st0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     st1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    launches_per_shift = B.launches()  # the eager push before the capture launched the same kernels
     ranks.barrier(world)
     torch.cuda.synchronize()
+    sampler = ClockSampler(device_uuid(dev)) if rank == 0 else None
     with torch.cuda.stream(cap_stream):
         for k in range(steps):
             buf.copy_(packs[args.warmup + k])
@@ -464,6 +470,7 @@ def run_batch(args, rank: int, world: int):
             st1[k].record(cap_stream)
     torch.cuda.synchronize()
     ranks.barrier(world)
+    clocks = sampler.stop() if sampler else None
     ms = [a.elapsed_time(z) for a, z in zip(st0, st1)]
     # latency over >= 1000 replays (inputs cycle through the same packs)
     reps = max(1000, steps)
@@ -506,6 +513,32 @@ def run_batch(args, rank: int, world: int):
     mean_ms = ranks.max_over_ranks([statistics.mean(ms)], dev, world)[0]
     value = ranks.job_rate(world, 512, mean_ms * 1e-3)
     if rank == 0:
+        from paper_1701_06446_gb300 import layout_size
+        fifo = B.fifo
+        elems = sum(layout_size(n_, b, s_) for n_, d_ in zip(ns, ds) for s_ in range(1, d_ + 1))
+        # FP64 flops of the recovery per shift (as for one window: subset recursion, scaling, norm, fold)
+        rec_flops = sum((2.0 * (2 ** (s_ - 1) - 1) + 5.0) * layout_size(n_, b, s_)
+                        for n_, d_ in zip(ns, ds) for s_ in range(1, d_ + 1))
+        # bytes per stored element: FP64 sum read + write (16), cumulant write (8), the FP32 workspace
+        # write + read (8) and the FIFO slot read + write (8), or the leaving workspace's (8)
+        bpe = 40
+        peaks, peak_kind = _peaks()
+        t_s = mean_ms * 1e-3
+        whole = "one shift (the graph: staging, operand build, GEMM, fused recovery), timed as a whole"
+        roof = {"kernel": whole, "bound": "alu", "achieved": rec_flops / t_s / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": rec_flops / t_s / 1e12 / FP64_NOMINAL_TFLOPS,
+                "peak_kind": "nominal FP64 rate (the recovery's scarcest pipe)", "traffic": None,
+                "avg_launch_ms": mean_ms,
+                "per_launch": f"{rec_flops:.4g} algorithmic FP64 flops of the recovery (per stored element of "
+                              f"order s: 2(2^(s-1)-1) subset recursion + 1 scaling + 2 norm + 2 fold) over "
+                              f"{elems} stored elements"}
+        roof_hbm = {"kernel": whole, "bound": "hbm", "achieved": elems * bpe / t_s / 1e9,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": elems * bpe / t_s / 1e9 / peaks["hbm_gbs"], "peak_kind": f"{peak_kind} HBM copy",
+                    "traffic": None, "avg_launch_ms": mean_ms,
+                    "per_launch": f"{elems * bpe:.4g} algorithmic bytes ({bpe} per stored element: FP64 sum "
+                                  f"read + write, cumulant write, FP32 workspace and "
+                                  f"{'FIFO slot' if fifo else 'leaving workspace'} write + read)"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
@@ -521,6 +554,8 @@ def run_batch(args, rank: int, world: int):
                               for s_ in range(1, d_ + 1)) for n_, d_ in zip(ns, ds)))},
             "error_vs_oracle": {"metric": "relative Frobenius error per order on 100 sampled tuples",
                                 "windows": err},
+            "roofline": roof, "roofline_other": roof_hbm,
+            "gpu_launches": launches_per_shift * steps, "clocks": clocks,
             "setup_s": t_gen,
         }
         print(json.dumps(line), flush=True)

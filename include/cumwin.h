@@ -332,6 +332,11 @@ int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out);
  * p and room for it, see cumwin_push), 0 otherwise, EINVAL. */
 int cumwin_batch_fifo(cumwin_batch_t B);
 
+/* Kernels launched by the last cumwin_batch_push (staging, operand build,
+ * GEMM and the recovery's launches); 0 before the first push, EINVAL for a
+ * null handle.  Host bookkeeping only: it does not synchronise. */
+int64_t cumwin_batch_launches(cumwin_batch_t B);
+
 /* Sticky device status over all windows (synchronises). */
 int cumwin_batch_status(cumwin_batch_t B);
 

@@ -379,6 +379,12 @@ class CumWinBatch:
     def status(self) -> int:
         return int(self.lib.cumwin_batch_status(self._h))
 
+    def launches(self) -> int:
+        """Kernels launched by the last push."""
+        r = int(self.lib.cumwin_batch_launches(self._h))
+        check(min(r, 0), "cumwin_batch_launches")
+        return r
+
 
 class CumulantNormLoss(torch.autograd.Function):
     """L(X) = sum_s w[s] ||C_s(X)||_F^2 for a window X (T x n), with a hand-written adjoint.

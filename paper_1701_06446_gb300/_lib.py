@@ -58,6 +58,7 @@ SIGNATURES = {
     "cumwin_batch_tune": (c_int, [c_vp, c_int, c_vp]),
     "cumwin_batch_fifo": (c_int, [c_vp]),
     "cumwin_batch_status": (c_int, [c_vp]),
+    "cumwin_batch_launches": (c_i64, [c_vp]),
     "cumwin_layout_size": (c_i64, [c_int, c_int, c_int]),
     "cumwin_block_rank": (c_i64, [c_int, c_int, c_int, c_vp]),
     "cumwin_element_index": (c_i64, [c_int, c_int, c_int, c_vp]),

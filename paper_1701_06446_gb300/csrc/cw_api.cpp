@@ -227,6 +227,7 @@ struct cumwin_batch_s {
     double* fro2 = nullptr;      // [nwin][dmax]
     TcAccSeg* segs = nullptr;
     int nsegs = 0;
+    int64_t push_launches = 0;  // kernels the last cumwin_batch_push launched
 };
 
 namespace {
@@ -409,6 +410,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         CW_TRY(h->upload((double**)&a.mult, ct.mult));
         a.shift = h->shift;
         a.invT = 1.0 / (double)T;
+        a.tpow2 = (T & (T - 1)) == 0 ? 1 + (int32_t)__builtin_ctzll((unsigned long long)T) : 0;
         a.E = h->E[s];
         a.s = s;
         a.b = b;
@@ -1628,11 +1630,13 @@ int64_t cumwin_batch_offset(cumwin_batch_t B, int window)
     return B->xoff[window];
 }
 
-static int batch_recover(cumwin_batch_t B, int64_t advance, int accum)
+static int batch_recover(cumwin_batch_t B, int64_t advance, int accum, int64_t* launches = nullptr)
 {
-    int64_t launches = 0;
-    return recover(B->fused, B->cum_dev, B->cum_launch, B->norm_dev, B->nwin, B->dmax, advance, accum,
-                   B->sm_count, B->stream, &launches);
+    int64_t L = 0;
+    const int rc = recover(B->fused, B->cum_dev, B->cum_launch, B->norm_dev, B->nwin, B->dmax, advance, accum,
+                           B->sm_count, B->stream, &L);
+    if (launches != nullptr) *launches = L;
+    return rc;
 }
 
 int cumwin_batch_fill(cumwin_batch_t B, const float* const* X_dev)
@@ -1661,9 +1665,12 @@ int cumwin_batch_push(cumwin_batch_t B, const float* x_dev)
 {
     if (B == nullptr || x_dev == nullptr) return CUMWIN_EINVAL;
     if (!B->filled) return CUMWIN_ESTATE;
-    CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, !B->fifo, B->stream));
+    CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, !B->fifo, B->stream));  // staging + operand build
     CW_TRY(tc_gemm_push(B->tc, !B->fifo, 0, B->stream));
-    return batch_recover(B, B->p, B->fifo ? 2 : 1);
+    int64_t L = 0;
+    const int rc = batch_recover(B, B->p, B->fifo ? 2 : 1, &L);
+    B->push_launches = 3 + L;
+    return rc;
 }
 
 int cumwin_batch_cumulants(cumwin_batch_t B, int window, int order, double* out_dev)
@@ -1726,6 +1733,11 @@ int cumwin_batch_fifo(cumwin_batch_t B)
 {
     if (B == nullptr) return CUMWIN_EINVAL;
     return B->fifo ? 1 : 0;
+}
+
+int64_t cumwin_batch_launches(cumwin_batch_t B)
+{
+    return B == nullptr ? CUMWIN_EINVAL : B->push_launches;
 }
 
 int cumwin_batch_status(cumwin_batch_t B)

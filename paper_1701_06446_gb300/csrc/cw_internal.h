@@ -84,6 +84,7 @@ struct CumArgs {
     double* normpart;                // [gridDim.x] partial sums of mult * C^2
     const float* shift;              // order-1 norm uses C_1 + shift
     double invT;
+    int32_t tpow2;  // k + 1 when T = 2^k, 0 otherwise
     int64_t E;                       // stored elements of order s
     int32_t s, b, bs, nsub;
     uint8_t mask[128];               // subset bitmasks over the s positions

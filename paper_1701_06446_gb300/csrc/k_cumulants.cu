@@ -222,6 +222,21 @@ __device__ __forceinline__ float2 tw_split(double x)
 
 // C_2 at storage index x of order 2, from the (folded) sums: what the order-2
 // element computes, operation for operation, with C_1 = S_1 / T.
+// x / T.  For T = 2^k the exponent of x is lowered by k on the integer pipe
+// whenever the result is a normal number (bitwise what the multiply by 1/T
+// gives); zeros pass through; subnormal results, infinities and NaNs take the
+// multiply.  This keeps one FP64 operation per element off the FP64 pipe.
+__device__ __forceinline__ double div_T(const CumArgs& a, double x)
+{
+    const int k = a.tpow2 - 1;  // -1: T is not a power of two
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned ex = (unsigned)(u >> 52) & 0x7ffu;
+    if (k >= 0 && ex > (unsigned)k && ex != 0x7ffu)
+        return __longlong_as_double((long long)(u - ((unsigned long long)k << 52)));
+    if (k >= 0 && (u << 1) == 0) return x;
+    return x * a.invT;
+}
+
 __device__ __forceinline__ double c2_from_sums(const CumArgs& a2, int64_t x)
 {
     const int b = a2.b, bb = b * b;
@@ -265,7 +280,7 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2
             const float2 sR = a.S2[lr][(unsigned)q.y * (unsigned)ipow_c(b, lr) + (unsigned)orr];
             tw_acc_prod(hi, lo, cA, sR);
         }
-        cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
+        cv = div_T(a, sv - (f32_to_f64(hi) + f32_to_f64(lo)));
     } else {
         double acc = sv;
 #pragma unroll(S <= 4 ? NS : 4)
@@ -282,7 +297,7 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2
             const double sR = a.S[lr][(unsigned)q.y * (unsigned)ipow_c(b, lr) + (unsigned)orr];
             acc = fma(-cA, sR, acc);
         }
-        cv = acc * a.invT;
+        cv = div_T(a, acc);
     }
     a.Cout[e] = cv;
     if (S >= kTwoWordMinOrder && a.split) {  // the two-word copies the next orders read
@@ -367,7 +382,7 @@ __device__ __forceinline__ void recover_groups_smem(const CumArgs& a, const Elem
                 const float2 sR = reinterpret_cast<const float2*>(pr.y)[packed & 0xffff];
                 tw_acc_prod(hi, lo, cA, sR);
             }
-            cv = (sv - (f32_to_f64(hi) + f32_to_f64(lo))) * a.invT;
+            cv = div_T(a, sv - (f32_to_f64(hi) + f32_to_f64(lo)));
         } else {
             double acc = sv;
 #pragma unroll 4
@@ -377,7 +392,7 @@ __device__ __forceinline__ void recover_groups_smem(const CumArgs& a, const Elem
                 acc = fma(-reinterpret_cast<const double*>(pr.x)[packed >> 16],
                           reinterpret_cast<const double*>(pr.y)[packed & 0xffff], acc);
             }
-            cv = acc * a.invT;
+            cv = div_T(a, acc);
         }
         a.Cout[e] = cv;
         if (a.split) {

@@ -42,6 +42,7 @@ def test_version_and_errors():
     assert lib.cumwin_version() >= 100
     for code in range(0, -8, -1):
         assert lib.cumwin_strerror(code)
+    assert lib.cumwin_batch_launches(None) == -1  # EINVAL, no device call
     with pytest.raises(ValueError):
         cw.layout_size(4, 2, 9)
     with pytest.raises(ValueError):

@@ -41,10 +41,13 @@ def test_batch_matches_oracle_and_standalone_handles(p):
     ns, ds, Ts = zip(*SPECS)
     with CumWinBatch(ns, ds, Ts, b, p, "bf16") as B:
         assert B.fifo == all(T % p == 0 for T in Ts)
+        assert B.launches() == 0
         B.fill([torch.from_numpy(X[:T]).cuda() for X, (n, d, T) in zip(data, SPECS)])
         for k in range(steps):
             B.push(B.pack([torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda()
                            for X, (n, d, T) in zip(data, SPECS)]))
+            # staging, operand build, GEMM, at least one recovery launch
+            assert B.launches() >= 4
         fro, nu = B.norms()
         for i, (X, (n, d, T)) in enumerate(zip(data, SPECS)):
             Xw = X[steps * p: steps * p + T]
