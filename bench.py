@@ -68,7 +68,7 @@ def algorithmic_flops(W, fifo: bool = False) -> dict:
 
 # DRAM bytes (read + write) per launch of the recovery from one ncu capture of the current
 # kernel (see profiles/), by workload; None where no capture of the current kernel exists.
-RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 16044800}
+RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 13002496}
 # the same for the GEMM (k_kr_gemm)
 GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15818240}
 
