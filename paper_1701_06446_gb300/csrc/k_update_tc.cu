@@ -216,8 +216,11 @@ __device__ __forceinline__ UnitRange unit_range(const TcGemmArgs& args, int spli
 }
 
 // The bound of 4 CTAs per SM only caps the registers at 80 (shared memory allows
-// one CTA per SM): the GEMM of the next shift then fits on an SM beside the three
-// CTAs of the previous shift's recovery.
+// one CTA per SM); uncapped (124 registers) pipelined shifts were about 1 us
+// slower.  The GEMM of the next shift still starts only as the previous shift's
+// recovery leaves an SM: to start beside the recovery's three CTAs it needs 64
+// registers and the largest shared-memory split on both sides, which slowed the
+// host-driven streaming loop.
 template <bool BF16>
 __global__ void __launch_bounds__(GEMM_THREADS, 4)
 k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB32,
