@@ -352,19 +352,25 @@ int cumwin_status(cumwin_t h);
  * must not risk the implicit synchronisation an allocation can bring.
  *
  * out_dev[0] = sum over stored blocks j of (order!/prod r_l!) * sum_{e in block j} e^2,
- * i.e. ||A||_F^2 of the full n^order tensor (Algorithm 5 with k = 2, before the
- * root), for A_dev in the block layout (cumwin_layout_size(n, b, order)
- * doubles, device).  Asynchronous on cuda_stream; the caller passes the input
- * and the output and the call allocates nothing: its scratch, one double per
- * stored block, is a fixed array of CUMWIN_NOALLOC_MAX_BLOCKS doubles in the
- * library's device memory, which every GPU that loads the library holds until
- * the process exits.  Tensors with more stored blocks than that are rejected
- * with CUMWIN_EINVAL and a message in cumwin_last_error().
- * The first call on a device looks up the scratch's device address (with that
- * device current) and caches it; make that first call before any stream
- * capture.  All calls share the one scratch array and each call overwrites
- * the slots it reads, so calls that overlap on the GPU (different streams
- * without ordering) race and may return wrong sums.
+ * where r_l are the run lengths of equal entries of the sorted block index j,
+ * i.e. ||A||_F^2 of the full n^order tensor, for A_dev in the block layout
+ * (cumwin_layout_size(n, b, order) doubles, device).  Asynchronous on
+ * cuda_stream; the caller passes the input and the output and the call
+ * allocates nothing: its scratch, one double per stored block, is a fixed
+ * array of CUMWIN_NOALLOC_MAX_BLOCKS doubles in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ * Errors (returned before anything is launched): EINVAL for a bad argument,
+ * for ceil(n/b)*b > CUMWIN_MAX_N or b^order >= 2^31, and for tensors with more
+ * stored blocks than the scratch holds (with a message in cumwin_last_error());
+ * ECUDA for a failed CUDA call.
+ * The scratch's device address is looked up (with the current device) on
+ * every call made outside stream capture, so a device reset does not leave a
+ * stale address; a call made while cuda_stream is being captured reuses the
+ * address of the last uncaptured call on that device, so the first call on a
+ * device must come before any stream capture (ESTATE otherwise).  All calls
+ * share the one scratch array and each call overwrites the slots it reads, so
+ * calls that overlap on the GPU (different streams without ordering) race and
+ * may return wrong sums.
  */
 #define CUMWIN_NOALLOC_MAX_BLOCKS 16384
 int cumwin_block_norm2_noalloc(int n, int b, int order, const double* A_dev, double* out_dev,

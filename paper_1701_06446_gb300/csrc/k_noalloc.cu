@@ -10,8 +10,12 @@
 // fixed size that every GPU loading the library keeps until exit.
 //
 // The host code below never hands the array's host-side name to a kernel:
-// the device address is looked up with cudaGetSymbolAddress once per device,
-// with that device current, and cached.
+// the device address is looked up with cudaGetSymbolAddress with the device
+// current.  Outside stream capture it is looked up on every call (the lookup
+// allocates nothing), so a device reset that tears the context down cannot
+// leave a stale address behind; under capture the address cached by the last
+// uncaptured call on that device is used.
+#include <climits>
 #include <mutex>
 #include <string>
 
@@ -37,9 +41,10 @@ __device__ __forceinline__ int64_t d_binom(int64_t a, int k)
 }
 
 // Pass 1: one warp per block; lane 0 recovers the sorted block tuple from its
-// lexicographic rank to get the multiplicity s!/prod r_l! (Algorithm 5).
+// lexicographic rank to get the multiplicity s!/prod r_l! (r_l the run
+// lengths of equal block indices).
 __global__ void __launch_bounds__(256)
-k_block_sumsq(const double* __restrict__ A, int64_t nblocks, int bs, int s, int nbar,
+k_block_sumsq(const double* __restrict__ A, int64_t nblocks, int64_t bs, int s, int nbar,
               double* __restrict__ part)
 {
     const int lane = threadIdx.x & 31;
@@ -47,7 +52,7 @@ k_block_sumsq(const double* __restrict__ A, int64_t nblocks, int bs, int s, int 
     for (int64_t blk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); blk < nblocks;
          blk += warps) {
         double acc = 0.0;
-        for (int e = lane; e < bs; e += 32) {
+        for (int64_t e = lane; e < bs; e += 32) {
             const double v = A[blk * bs + e];
             acc = fma(v, v, acc);
         }
@@ -112,6 +117,20 @@ extern "C" int cumwin_block_norm2_noalloc(int n, int b, int order, const double*
         return CUMWIN_EINVAL;
     }
     const int nbar = (n + b - 1) / b;
+    // the padded variable count is bounded as for cumwin_create (so b <= 256),
+    // and a block must hold fewer than 2^31 elements; b^order is formed with a
+    // check after every factor, so it cannot overflow
+    int64_t bs = 1;
+    bool big = (int64_t)nbar * b > kMaxN;
+    for (int k = 0; k < order && !big; ++k) {
+        bs *= b;
+        big = bs > INT_MAX;
+    }
+    if (big) {
+        set_last_error("block size too large: nbar * b must be at most " + std::to_string(kMaxN) +
+                       " and b^order below 2^31");
+        return CUMWIN_EINVAL;
+    }
     const int64_t nblocks = n_sorted(nbar, order);
     if (nblocks > CUMWIN_NOALLOC_MAX_BLOCKS) {
         set_last_error("tensor has " + std::to_string(nblocks) +
@@ -124,10 +143,16 @@ extern "C" int cumwin_block_norm2_noalloc(int n, int b, int order, const double*
         set_last_error("no usable current device");
         return CUMWIN_ECUDA;
     }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // Look the scratch address up on every call made outside stream capture
+    // (cheap, no allocation; survives a device reset), and fall back to the
+    // address of the last uncaptured call on this device while capturing.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool capture = cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (g_scratch_addr[dev] == nullptr) {
+        if (!capture) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_block_norm_scratch);
             if (e != cudaSuccess || p == nullptr) {
@@ -138,8 +163,10 @@ extern "C" int cumwin_block_norm2_noalloc(int n, int b, int order, const double*
         }
         scratch = g_scratch_addr[dev];
     }
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const int bs = (int)ipow(b, order);
+    if (scratch == nullptr) {
+        set_last_error("the first call on a device must come before any stream capture");
+        return CUMWIN_ESTATE;
+    }
     int64_t grid = (nblocks + 7) / 8;
     if (grid > 1024) grid = 1024;
     k_block_sumsq<<<(int)grid, 256, 0, st>>>(A_dev, nblocks, bs, order, nbar, scratch);

@@ -90,3 +90,20 @@ def test_bad_arguments_rejected_without_gpu():
     assert lib.cumwin_create(4, 4, 2, 100, 10, 7, None, ctypes.byref(h)) == _lib.CODES["EINVAL"]
     assert lib.cumwin_push(None, None, None, 1, 4) == _lib.CODES["EINVAL"]
     assert lib.cumwin_norms(None, None, None) == _lib.CODES["EINVAL"]
+
+
+def test_noalloc_norm_rejects_oversized_blocks_without_gpu():
+    """The allocation-free norm bounds the block size as cumwin_create does (the
+    padded variable count at most 256, b^order below 2^31) and returns EINVAL
+    before any CUDA call; a non-null dummy pointer is never dereferenced."""
+    lib = _lib.load()
+    dummy = ctypes.c_void_p(16)
+    # n=10, b=16, order 8: one block of 16^8 = 2^32 elements (would wrap to 0 in 32 bits)
+    # n=200, b=150: 300 padded variables; n=256, b=256, order 4: 2^32 elements in one block
+    for n, b, s in [(10, 16, 8), (200, 150, 2), (256, 256, 4), (9, 40, 6)]:
+        rc = lib.cumwin_block_norm2_noalloc(n, b, s, dummy, dummy, None)
+        assert rc == _lib.CODES["EINVAL"], (n, b, s, rc)
+        assert "block size" in lib.cumwin_last_error().decode()
+    for args in [(0, 2, 2), (4, 0, 2), (4, 2, 0), (4, 2, 9)]:
+        assert lib.cumwin_block_norm2_noalloc(*args, dummy, dummy, None) == _lib.CODES["EINVAL"]
+    assert lib.cumwin_block_norm2_noalloc(4, 2, 2, None, dummy, None) == _lib.CODES["EINVAL"]

@@ -43,6 +43,32 @@ def test_noalloc_norm_matches_handle_norms_on_consecutive_calls():
                 assert abs(got - ref[s - 1]) <= TOL * ref[s - 1], (s, got, ref[s - 1])
 
 
+@pytest.mark.parametrize("n,d,b", [(10, 8, 3), (13, 6, 4), (7, 5, 2)])
+def test_noalloc_norm_ragged_blocks_every_order(n, d, b):
+    """b does not divide n (padded variables), and every order up to d: the
+    multiplicity rebuilt from the block rank sees its longest runs of equal
+    block indices at the high orders.  Two calls in a row per order."""
+    lib = _lib.load()
+    T, p = 512, 64
+    rng = np.random.default_rng(100 * n + d)
+    X = (rng.standard_t(6, size=(T, n)) @ rng.standard_normal((n, n)) / np.sqrt(n) + 0.3).astype(np.float32)
+    with CumWin(n, d, b, T, p, "fp64") as h:
+        h.fill(torch.from_numpy(X).cuda())
+        ref = h.norms_device().cpu().numpy()
+        out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        for s in range(1, d + 1):
+            C = h.cumulants(s)
+            for _ in range(2):
+                rc = lib.cumwin_block_norm2_noalloc(n, b, s, ctypes.c_void_p(C.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()), stream)
+                assert rc == 0, lib.cumwin_last_error().decode()
+                torch.cuda.synchronize()
+                got = float(out.item())
+                assert abs(got - ref[s - 1]) <= TOL * abs(ref[s - 1]), (s, got, ref[s - 1])
+                out.fill_(-1.0)
+
+
 def test_noalloc_norm_rejects_tensors_beyond_its_scratch():
     lib = _lib.load()
     buf = torch.zeros(1, dtype=torch.float64, device="cuda")
