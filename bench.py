@@ -4,12 +4,15 @@ One step = one window shift of the whole hot path: ring append / X_(-)
 extraction, moment-sum update of orders 1..d, moment-to-cumulant recovery of
 orders 1..d, and the norm reduction (Algorithm 1, one loop iteration).
 
-Default workload: n=60 variables, orders 1..4, block size 3, window T=2^15,
-shift p=2^10, FP32 samples (Gaussian, then a Gaussian copula with
-exponential(1) marginals), seeded and synthetic.
+Default workload: n=48 variables, orders 1..6, block size 4, window T=2^16,
+shift p=2^12, FP32 samples from a multivariate t(5) with a random correlation
+matrix, seeded and synthetic: the largest single-window configuration, whose
+order-6 moment tensor (50.7 M stored elements, 405 MB in FP64) is larger than
+L2.  The plain FP64 form is measured on the same stream beside the mixed one.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|bf16|fp16]
     python bench.py --impl reference      # the CPU oracle on the same workload
+    python bench.py --workload n32_d4_b4_T4096_ica --grad   # forward + backward
 
 Prints one JSON line (rank 0).  Under torchrun each rank advances its own
 independent stream (weak scaling, no collective on the data path).
@@ -36,9 +39,11 @@ from paper_1701_06446_gb300.streams import WORKLOADS  # noqa: E402
 
 METRIC = "window updates/s and TFLOP/s vs tensor-core peak at stated error vs FP64 oracle"
 UNIT = "window updates/s"
-DEFAULT_WORKLOAD = "n60_d4_b3_T32768_p1024"
+DEFAULT_WORKLOAD = "n48_d6_b4_T65536_p4096"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (CUDA cores), nominal
+FP32_LANES_PER_SM = 128     # FP32 FMA-pipe lanes per SM (Blackwell)
+TWO_WORD_MIN_ORDER = 5      # orders whose subset products run in two-word FP32 arithmetic
+TWO_WORD_OPS_PER_TERM = 12  # FP32 operations of one two-word multiply-accumulate
 
 
 def _peaks():
@@ -50,27 +55,62 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def algorithmic_flops(W, fifo: bool = False) -> dict:
-    """Flops of one shift: update 2 * K * E_s per order (one product per
-    multiply-add) with K = 2p samples (entering and leaving), or K = p when
-    the leaving batch's sums come from the batch-sum FIFO; recovery
-    2 * (2^{s-1} - 1) * E_s (one multiply-add per subset term)."""
+def algorithmic_work(W, fifo: bool = False) -> dict:
+    """Algorithmic work of one shift.
+
+    * update: 2 * K * E_s flops per order (one product per multiply-add), K = 2p
+      samples (entering and leaving), or K = p when the leaving batch's sums come
+      from the batch-sum FIFO; the tensor pipe issues three MMAs per product in
+      the split forms (hi*hi + hi*lo + lo*hi).
+    * recovery, per stored element of order s: 2^{s-1} - 1 subset terms.  Orders
+      below TWO_WORD_MIN_ORDER run them as FP64 multiply-adds, plus the 1/T
+      scaling, the multiplicity-weighted square (2) and the fold of the shift's
+      batch sums (2): `recovery_fp64` flops.  Orders from TWO_WORD_MIN_ORDER up (mixed
+      forms) run each term as a two-word FP32 multiply-accumulate
+      (TWO_WORD_OPS_PER_TERM FP32 operations on the FMA pipe): `recovery_fp32_ops`.
+    * recovery bytes, per stored element: the FP64 sum read and written (16), the
+      cumulant written (8), the shift's FP32 tile sum read (4) and the FIFO slot
+      read and written (8, FIFO) or the leaving tile sum read (4); orders below d
+      also write their two-word copies (16) in the forms that have them.
+    """
     from paper_1701_06446_gb300 import layout_size
+    E = {s: layout_size(W.n, W.b, s) for s in range(1, W.d + 1)}
     K = W.p if fifo else 2 * W.p
-    upd = sum(2.0 * K * layout_size(W.n, W.b, s) for s in range(1, W.d + 1))
-    rec = sum(2.0 * (2 ** (s - 1) - 1) * layout_size(W.n, W.b, s) for s in range(2, W.d + 1))
-    # the recovery launch(es) as a whole, FP64: per stored element of order s the subset
-    # recursion (2 per term), the 1/T scaling (1), multiplicity * C^2 (2) and the fold of the
-    # shift's batch sums into S_s (2)
-    rec_launch = sum((2.0 * (2 ** (s - 1) - 1) + 5.0) * layout_size(W.n, W.b, s) for s in range(1, W.d + 1))
-    return {"update": upd, "recovery": rec, "recovery_launch": rec_launch}
+    upd = sum(2.0 * K * E[s] for s in E)
+    terms = {s: 2 ** (s - 1) - 1 for s in E}
+    two_word = W.d >= TWO_WORD_MIN_ORDER
+    fp64 = sum((2.0 * terms[s] + 5.0) * E[s] for s in E if not (two_word and s >= TWO_WORD_MIN_ORDER))
+    fp32_ops = sum(TWO_WORD_OPS_PER_TERM * terms[s] * E[s] for s in E if two_word and s >= TWO_WORD_MIN_ORDER)
+    per_elem = 16 + 8 + 4 + (8 if fifo else 4)
+    rec_bytes = sum(per_elem * E[s] + (16 * E[s] if two_word and s < W.d else 0) for s in E)
+    return {"update": upd, "recovery_fp64": fp64, "recovery_fp32_ops": fp32_ops,
+            "recovery_bytes": rec_bytes, "elements": E, "two_word": two_word}
 
 
-# DRAM bytes (read + write) per launch of the recovery from one ncu capture of the current
-# kernel (see profiles/), by workload; None where no capture of the current kernel exists.
-RECOVERY_TRAFFIC = {"n60_d4_b3_T32768_p1024": 13002496}
-# the same for the GEMM (k_kr_gemm)
-GEMM_TRAFFIC = {"n60_d4_b3_T32768_p1024": 15818240}
+# DRAM bytes (read + write) per launch from an ncu capture of the current kernels (see
+# profiles/), by workload: the recovery's launches of one shift, and the GEMM.  None where
+# no capture of the current kernels exists.
+RECOVERY_TRAFFIC: dict[str, int] = {}
+GEMM_TRAFFIC: dict[str, int] = {}
+
+
+def fp64_peak_tflops(dev) -> float:
+    """Measured FP64 rate of this GPU: cuBLAS DGEMM 4096^3 through torch, best of 3
+    (CUDA events), as the bf16 peak of MEASURED_PEAKS.json is a cuBLAS GEMM."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del a, b
+    return 2.0 * 4096 ** 3 / best / 1e12
 
 
 def device_uuid(dev):
@@ -132,32 +172,39 @@ class ClockSampler:
 # CPU oracle timing (cpu_baseline leg and the --impl reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_sample_time(X: np.ndarray, W, per_order: int, seed: int) -> tuple[float, str]:
-    """Seconds one full oracle recomputation of C_1..C_d for window X would take,
-    from timing every sorted tuple of orders <= 2 and `per_order` seeded
-    sorted tuples of each higher order (extrapolated linearly by tuple count)."""
+def oracle_sample(X: np.ndarray, W, per_order: int, seed: int, full_upto: int) -> tuple[float, float, str]:
+    """Time the oracle on a bounded sample of one full recomputation of C_1..C_d for
+    window X: every sorted tuple of the orders <= full_upto, `per_order` seeded sorted
+    tuples of each higher order.  Returns (seconds measured, seconds the whole
+    recomputation would take -- the sampled orders extrapolated linearly by tuple
+    count --, a description)."""
+    import itertools
+
     import oracle
     t0 = time.perf_counter()
     cen = oracle.center(X)
-    total = time.perf_counter() - t0
+    measured = time.perf_counter() - t0
+    total = measured
     parts = []
     for s in range(1, W.d + 1):
         n_tuples = math.comb(W.n + s - 1, s)
-        if s <= 2 or n_tuples <= per_order:
-            import itertools
+        if s <= full_upto or n_tuples <= per_order:
             tup = np.array(list(itertools.combinations_with_replacement(range(W.n), s)), np.int32)
             t0 = time.perf_counter()
             oracle.cumulant_tuples(X, tup, centred=cen)
-            total += time.perf_counter() - t0
-            parts.append(f"order {s}: all {n_tuples}")
+            dt = time.perf_counter() - t0
+            measured += dt
+            total += dt
+            parts.append(f"order {s}: all {n_tuples} tuples")
         else:
             tup = oracle.sample_sorted_tuples(W.n, s, per_order, seed + s)
             t0 = time.perf_counter()
             oracle.cumulant_tuples(X, tup, centred=cen)
             dt = time.perf_counter() - t0
+            measured += dt
             total += dt * n_tuples / per_order
-            parts.append(f"order {s}: {per_order} of {n_tuples} tuples, extrapolated")
-    return total, "; ".join(parts)
+            parts.append(f"order {s}: {per_order} of {n_tuples} tuples (extrapolated)")
+    return measured, total, "; ".join(parts)
 
 
 def oracle_threads() -> int:
@@ -165,25 +212,39 @@ def oracle_threads() -> int:
 
 
 def run_reference(args, W, rank: int):
+    """The oracle as the reference arm, on the machine's host cores (rank 0 only).
+    Each step is one timed bounded sample of a full-window recomputation (all
+    tuples of orders <= 2, `--ref-tuples` seeded tuples of each higher order, a
+    different seed per step): `ms_per_step` is that sample's measured time, and
+    `value` (window updates/s) is 1 / the full recomputation time extrapolated
+    from the samples, stated as such."""
     if rank != 0:
         return
     X = W.stream().rows(0, W.T).astype(np.float64)
-    for _ in range(args.warmup):
-        oracle_sample_time(X, W, 100, seed=0)
-    secs = []
+    for k in range(args.warmup):
+        oracle_sample(X, W, max(1, args.ref_tuples // 10), seed=100 + k, full_upto=1)
+    measured, total = [], []
     sample = ""
+    t_start = time.perf_counter()
     for k in range(args.steps):
-        dt, sample = oracle_sample_time(X, W, args.ref_tuples, seed=k)
-        secs.append(dt)
-    per = statistics.mean(secs)
-    value = 1.0 / per
+        m, t, sample = oracle_sample(X, W, args.ref_tuples, seed=k, full_upto=2)
+        measured.append(m)
+        total.append(t)
+    wall = time.perf_counter() - t_start
+    per_window = statistics.mean(total)
+    value = 1.0 / per_window
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(W, "fp64-oracle"),
+        "sample_s_per_step": statistics.mean(measured),
+        "extrapolated_s_per_window": per_window,
+        "value_basis": "1 / full-window recomputation time extrapolated by tuple count from the timed samples",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                         "sample": f"full recomputation of one window from scratch per step; {sample}"},
+                         "sample": f"per step, one bounded sample of a full recomputation: {sample}; "
+                                   f"measured {statistics.mean(measured):.3f} s per step, "
+                                   f"extrapolated {per_window:.4g} s per window"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -213,28 +274,46 @@ def sampled_error(h, X: np.ndarray, per_order: int = 200) -> dict:
 
 
 def measure_fp64_form(W, stream, base: int, steps: int, dev) -> dict:
-    """The plain FP64 GPU form on the same stretch of the stream, for comparison."""
+    """The plain FP64 GPU form on the same stretch of the stream, for comparison
+    (FP64 products and sums, the paper's arithmetic): window updates/s with the
+    L2 flushed before every timed shift, and its update's FP64 rate."""
     import torch
     from paper_1701_06446_gb300 import CumWin
     X = torch.from_numpy(stream.rows(base, base + W.T + (steps + 3) * W.p)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = CumWin(W.n, W.d, W.b, W.T, W.p, "fp64", device=dev)
     h.fill(X[: W.T])
     for k in range(3):
         h.push(X[W.T + k * W.p: W.T + (k + 1) * W.p])
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h.set_timing(True)
-    e0.record()
+    st = torch.cuda.current_stream(dev)
+    total = 0.0
     for k in range(3, 3 + steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
         h.push(X[W.T + k * W.p: W.T + (k + 1) * W.p])
-    e1.record()
-    torch.cuda.synchronize()
+        e1.record(st)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
     t = h.get_timing()
     h.close()
-    ms = e0.elapsed_time(e1) / steps
+    ms = total / steps
     upd = t["update_ms"] / max(t["shifts"], 1)
     return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "update_ms": upd,
-            "update_tflops": algorithmic_flops(W)["update"] / (upd * 1e-3) / 1e12, "steps": steps}
+            "update_tflops": algorithmic_work(W)["update"] / (upd * 1e-3) / 1e12, "steps": steps,
+            "l2": "flushed before every timed shift"}
+
+
+# per-order relative Frobenius bounds of the final window against the oracle, about 3x the
+# error measured on GB300, per workload and form
+ERROR_BOUND = {
+    "n48_d6_b4_T65536_p4096": {"bf16": {1: 3e-5, 2: 6e-5, 3: 5e-5, 4: 4e-5, 5: 3e-5, 6: 3e-5},
+                               "fp16": {1: 3e-5, 2: 7e-5, 3: 4e-5, 4: 3e-5, 5: 2e-5, 6: 2e-5}},
+    "n60_d4_b3_T32768_p1024": {"bf16": {1: 2e-5, 2: 2e-5, 3: 2e-5, 4: 2e-4},
+                               "fp16": {1: 2e-5, 2: 2e-5, 3: 2e-5, 4: 2e-4}},
+}
 
 
 def run_ours(args, W, rank: int, world: int):
@@ -294,16 +373,18 @@ def run_ours(args, W, rank: int, world: int):
     step_ms = ranks.max_over_ranks([sum(s.elapsed_time(e) for s, e in zip(starts, ends))], dev, world)[0]
     ms_per_step = step_ms / args.steps
     value = ranks.job_rate(world, args.steps, step_ms * 1e-3)
+    del batches, Xd
 
     # end-to-end through the C ABI with host buffers: H2D of X_(+) from pinned memory and D2H of
-    # every step's squared norms and status inside the timed region.  Streaming form: each push's
-    # norms are enqueued behind its recovery (which overlaps the next push) and nu is formed on the
-    # host once the loop has been synchronised.  Synchronous form: norms() blocks after every push.
+    # every step's ||C_s||, nu_s and status inside the timed region.  Streaming form: each push's
+    # estimators are formed on the device and enqueued behind its recovery (which overlaps the
+    # next push); one synchronisation at the end.  Synchronous form: norms() blocks after every push.
     e2e_steps_total = (e2e_reps + 1) * e2e_steps
     host = torch.from_numpy(stream.rows(base + W.T + nsteps * W.p,
                                         base + W.T + (nsteps + e2e_steps_total) * W.p)).pin_memory()
     hb = [host[k * W.p:(k + 1) * W.p] for k in range(e2e_steps_total)]
-    fro2_host = torch.zeros(e2e_steps, W.d, dtype=torch.float64).pin_memory()
+    fro_host = torch.zeros(e2e_steps, W.d, dtype=torch.float64).pin_memory()
+    nu_host = torch.zeros(e2e_steps, W.d, dtype=torch.float64).pin_memory()
     st_host = torch.full((e2e_steps,), -1, dtype=torch.int32).pin_memory()
     stream_s = []
     for r in range(e2e_reps):
@@ -313,11 +394,9 @@ def run_ours(args, W, rank: int, world: int):
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             h.push_host(hb[r * e2e_steps + k])
-            h.norms_enqueue(fro2_host[k], st_host[k:k + 1])
+            h.estimators_enqueue(fro_host[k], nu_host[k], st_host[k:k + 1])
         h.join()
         torch.cuda.synchronize()
-        fro_all = np.sqrt(fro2_host.numpy())
-        nu_all = fro_all[:, 2:] / fro_all[:, 1:2] ** (0.5 * np.arange(3, W.d + 1)) if W.d >= 3 else None
         t1 = time.perf_counter()
         if int(st_host.abs().max()) != 0:
             raise RuntimeError("device status reported an error during the end-to-end loop")
@@ -339,43 +418,67 @@ def run_ours(args, W, rank: int, world: int):
         h.close()
         return
     fifo = bool(h.fifo)
-    flops = algorithmic_flops(W, fifo)
+    work = algorithmic_work(W, fifo)
     peaks, peak_kind = _peaks()
     rec_ms = timing["cumulant_ms"] / max(timing["shifts"], 1)  # timed region
     upd_ms = timing_split["update_ms"] / max(timing_split["shifts"], 1)  # instrumented pass
     stg_ms = timing_split["stage_ms"] / max(timing_split["shifts"], 1)
+    h.close()
+    fp64_peak = fp64_peak_tflops(dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = sm_count * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12  # T FP32 lane ops/s
+    rec_s = rec_ms * 1e-3
+    rec_names = ("k_recover_fused" if W.d <= 4 else
+                 "recovery: k_recover_fused<4>, k_split, k_cumulants<5..d>, k_fold_linear, k_norm_final")
+    rec_common = {"kernel": rec_names, "avg_launch_ms": rec_ms, "share_of_step": rec_ms / ms_per_step,
+                  "traffic": RECOVERY_TRAFFIC.get(W.name)}
     if precision == "fp64":
-        achieved = flops["update"] / (upd_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_update_f64", "bound": "alu", "achieved": achieved,
-                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "peak_kind": "nominal FP64 (CUDA cores)", "traffic": None,
-                "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x 2p x E_s summed over orders)",
+        achieved = work["update"] / (upd_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_update_f64", "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "peak_kind": "measured FP64 (cuBLAS DGEMM 4096^3 in this run)", "traffic": None,
+                "per_launch": f"{work['update']:.4g} algorithmic flops (2 x 2p x E_s summed over orders)",
                 "avg_launch_ms": upd_ms}
         roof_other = None
+        roof_hbm = None
     else:
-        achieved = flops["update"] / (upd_ms * 1e-3) / 1e12
+        achieved = work["update"] / (upd_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
         roof_gemm = {"kernel": "k_kr_gemm", "bound": "tensor", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_kind": f"{peak_kind} bf16 sustained (of measured)",
+                     "issued_frac": 3.0 * achieved / peak,
+                     "peak_kind": f"{peak_kind} bf16 sustained (of {peak_kind})",
                      "traffic": GEMM_TRAFFIC.get(W.name), "avg_launch_ms": upd_ms,
                      "share_of_step": upd_ms / ms_per_step,
-                     "per_launch": f"{flops['update']:.4g} algorithmic flops (2 x K x E_s summed over "
+                     "per_launch": f"{work['update']:.4g} algorithmic flops (2 x K x E_s summed over "
                                    f"orders, K = {'p: entering samples; leaving sums from the FIFO' if fifo else '2p'}); "
-                                   f"the tensor pipe issues 3x (hi*hi + hi*lo + lo*hi)"}
-        rec_achieved = flops["recovery_launch"] / (rec_ms * 1e-3) / 1e12
-        roof_rec = {"kernel": "k_recover_fused" if W.d <= 4 else
-                    "recovery (k_recover_fused, k_split, k_cumulants<5..d>, k_norm_final)",
-                    "bound": "alu", "achieved": rec_achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                    "frac": rec_achieved / FP64_NOMINAL_TFLOPS,
-                    "peak_kind": "nominal FP64 rate (the recovery's scarcest pipe)",
-                    "traffic": RECOVERY_TRAFFIC.get(W.name), "avg_launch_ms": rec_ms,
-                    "share_of_step": rec_ms / ms_per_step,
-                    "per_launch": f"{flops['recovery_launch']:.4g} algorithmic FP64 flops (per stored element "
-                                  f"of order s: 2(2^(s-1)-1) subset recursion + 1 scaling + 2 norm + 2 fold)"}
-        if W.d >= 5:
-            roof_rec["note"] = ("orders >= 5 form their subset products in two-word FP32 arithmetic on the "
-                                "FMA pipe, so these FP64-class flops can run faster than the FP64 pipe's peak")
+                                   f"the tensor pipe issues 3x that (hi*hi + hi*lo + lo*hi), so frac <= 1/3 "
+                                   f"and issued_frac = 3 x frac"}
+        if work["two_word"]:
+            # the recovery's time goes to the two-word products of the orders >= 5 on the FMA pipe
+            ops = work["recovery_fp32_ops"] / rec_s / 1e12
+            roof_rec = dict(rec_common, bound="alu", achieved=ops, peak=fp32_peak, unit="Tops/s",
+                            frac=ops / fp32_peak,
+                            peak_kind=f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                      f"{clk_mhz:.0f} MHz (median SM clock of the timed region)",
+                            per_launch=f"{work['recovery_fp32_ops']:.4g} FP32 operations: per stored element "
+                                       f"of order s >= {TWO_WORD_MIN_ORDER}, 2^(s-1)-1 subset terms x "
+                                       f"{TWO_WORD_OPS_PER_TERM} (two-word multiply-accumulate); the orders "
+                                       f"below run on the FP64 pipe ({work['recovery_fp64']:.3g} flops)")
+        else:
+            fl = work["recovery_fp64"] / rec_s / 1e12
+            roof_rec = dict(rec_common, bound="alu", achieved=fl, peak=fp64_peak, unit="TFLOP/s",
+                            frac=fl / fp64_peak,
+                            peak_kind="measured FP64 (cuBLAS DGEMM 4096^3 in this run)",
+                            per_launch=f"{work['recovery_fp64']:.4g} algorithmic FP64 flops (per stored element "
+                                       f"of order s: 2(2^(s-1)-1) subset recursion + 1 scaling + 2 norm + 2 fold)")
+        gbs = work["recovery_bytes"] / rec_s / 1e9
+        roof_hbm = dict(rec_common, bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s",
+                        frac=gbs / peaks["hbm_gbs"], peak_kind=f"{peak_kind} HBM copy (of {peak_kind})",
+                        per_launch=f"{work['recovery_bytes']:.4g} algorithmic bytes (per stored element: FP64 "
+                                   f"sum read + write, cumulant write, FP32 tile sum read, FIFO slot read + "
+                                   f"write; two-word copies of the orders below d)")
         # the roofline line is the dominant kernel's; the other is kept beside it
         if rec_ms >= upd_ms:
             roof, roof_other = roof_rec, roof_gemm
@@ -385,11 +488,16 @@ def run_ours(args, W, rank: int, world: int):
     fp64_form = None
     if precision != "fp64" and args.fp64_steps > 0:
         fp64_form = measure_fp64_form(W, stream, base, args.fp64_steps, dev)
+        fp64_form["update_frac_of_fp64_peak"] = fp64_form["update_tflops"] / fp64_peak
     if world == 1 and not args.no_cpu_baseline:
         Xw = final.astype(np.float64)
-        secs, sample = oracle_sample_time(Xw, W, args.ref_tuples, seed=7)
-        cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"full recomputation of one window; {sample}"}
+        m, tot, sample = oracle_sample(Xw, W, args.cpu_tuples, seed=7, full_upto=3)
+        cpu = {"value": 1.0 / tot, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+               "sample": f"one full recomputation of the final window: {sample}; measured {m:.2f} s, "
+                         f"extrapolated {tot:.4g} s per window",
+               "sample_s": m, "extrapolated_s_per_window": tot}
+    bound = {s_: 1e-10 for s_ in range(1, 9)} if precision == "fp64" else \
+        ERROR_BOUND.get(W.name, {}).get(precision, {})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -397,22 +505,82 @@ def run_ours(args, W, rank: int, world: int):
         "dtype": "f64" if precision == "fp64" else f"{precision}x3+f32acc+f64sum",
         "data": "synthetic", "config": dict(config_of(W, precision), ksplit=ksplit, fifo=fifo),
         "samples_per_s": value * W.p,
-        "tflops": flops["update"] / (ms_per_step * 1e-3) / 1e12,
+        "tflops": work["update"] / (ms_per_step * 1e-3) / 1e12,
         "stage_ms": stg_ms, "update_ms": upd_ms, "recovery_ms": rec_ms,
         "fp64_form": fp64_form,
         "error_vs_oracle": {"metric": "relative Frobenius error per order on 200 sampled tuples",
-                            "per_order": err},
-        "roofline": roof, "roofline_other": roof_other, "cpu_baseline": cpu,
+                            "per_order": err,
+                            "bound": {str(s_): bound.get(s_) for s_ in range(1, W.d + 1)},
+                            "within_bound": (all(err[str(s_)] <= bound[s_] for s_ in range(1, W.d + 1))
+                                             if err and len(bound) >= W.d else None)},
+        "roofline": roof, "roofline_other": roof_other, "roofline_recovery_hbm": roof_hbm,
+        "fp64_peak_tflops_measured": fp64_peak, "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W.p * W.n * 4,
-                "d2h_bytes_per_step": W.d * 8 + 4, "steps": e2e_steps, "loops": e2e_reps,
-                "form": "push_host + norms_enqueue per step (recovery pipelined with the next push), "
-                        "one synchronisation at the end of each loop; no L2 flush; median of the loops",
+                "d2h_bytes_per_step": 2 * W.d * 8 + 4, "steps": e2e_steps, "loops": e2e_reps,
+                "form": "push_host + estimators_enqueue per step (||C_s||, nu_s and status formed on the device "
+                        "and copied to pinned host memory behind the pipelined recovery), one synchronisation at "
+                        "the end of each loop; no L2 flush; median of the loops",
                 "synchronous": {"value": e2e_sync_value, "unit": UNIT,
                                 "form": "push_host + blocking norms() per step"}},
         "gpu_launches": timing["launches"], "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_grad(args, W, rank: int, world: int):
+    """Forward + backward of L = sum_s w_s ||C_s||_F^2 (w_3 = w_4 = 1) for the T x n
+    window of the ICA workload: the window is loaded as a fresh window (all moments
+    recomputed), L formed on the device, and dL/dX computed by the adjoint, per step."""
+    import torch
+    from paper_1701_06446_gb300 import CumWin
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(5 + rank)
+    X0 = W.stream().rows(0, W.T)
+    # each step a different window: the source rows permuted (same distribution)
+    Xs = [torch.from_numpy(np.ascontiguousarray(X0[rng.permutation(W.T)])).to(dev)
+          for _ in range(args.warmup + args.steps)]
+    w = [0.0, 0.0, 0.0, 1.0, 1.0][: W.d + 1]
+    h = CumWin(W.n, W.d, W.b, W.T, W.p, "fp64", device=dev)
+    L = torch.empty((), dtype=torch.float64, device=dev)
+    for k in range(args.warmup):
+        h.fill(Xs[k])
+        h.loss(w, L)
+        h.grad(w)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    fwd = bwd = 0.0
+    ranks.barrier(world)
+    sampler = ClockSampler(device_uuid(dev)) if rank == 0 else None
+    for k in range(args.steps):
+        e0.record(st)
+        h.fill(Xs[args.warmup + k])
+        h.loss(w, L)
+        e1.record(st)
+        g = h.grad(w)
+        e2.record(st)
+        torch.cuda.synchronize()
+        fwd += e0.elapsed_time(e1)
+        bwd += e1.elapsed_time(e2)
+    clocks = sampler.stop() if sampler else None
+    ms = ranks.max_over_ranks([(fwd + bwd) / args.steps], dev, world)[0]
+    # error against the oracle's closed-form gradient on the last window
+    import oracle
+    ref = oracle.grad(Xs[-1].cpu().numpy().astype(np.float64), w)
+    gerr = float(np.linalg.norm(g.cpu().numpy() - ref) / np.linalg.norm(ref))
     h.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": ranks.job_rate(world, 1, ms * 1e-3), "unit": "forward+backward passes/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 sums, f32 adjoint",
+            "data": "synthetic", "config": dict(config_of(W, "fp64"), loss="w3 = w4 = 1",
+                                                 l2="window and state smaller than L2, no flush"),
+            "forward_ms": fwd / args.steps, "backward_ms": bwd / args.steps,
+            "grad_rel_error_vs_oracle": gerr, "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 BATCH_WORKLOAD = "batch512_b4_p256"
@@ -569,10 +737,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "bf16", "fp16"], default="bf16")
-    ap.add_argument("--fp64-steps", type=int, default=10,
+    ap.add_argument("--fp64-steps", type=int, default=3,
                     help="shifts of the FP64 GPU form measured for comparison (0: skip)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [BATCH_WORKLOAD])
-    ap.add_argument("--ref-tuples", type=int, default=3000)
+    ap.add_argument("--ref-tuples", type=int, default=1000,
+                    help="seeded tuples of each order >= 3 timed per step of the reference arm")
+    ap.add_argument("--cpu-tuples", type=int, default=5000,
+                    help="seeded tuples of each order >= 4 in the cpu_baseline leg (orders <= 3 in full)")
+    ap.add_argument("--grad", action="store_true", help="time forward + backward (adjoint) instead of shifts")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -602,7 +774,7 @@ def main():
         torch.cuda.set_device(local_rank)
     ranks.init(world, "nccl")
     try:
-        run_ours(args, W, rank, world)
+        (run_grad if args.grad else run_ours)(args, W, rank, world)
     finally:
         ranks.finish(world)
 

@@ -68,6 +68,33 @@ enum {
     CUMWIN_MIXED_FP16 = 2   /* as above with FP16 hi+lo splits                     */
 };
 
+/*
+ * Device memory.  Every byte of device state a handle or a batch holds (ring
+ * buffer, sums, cumulants, tables, workspaces, the scratch of every call) is
+ * taken from an allocator when the handle is created (the adjoint's
+ * workspace: at the first cumwin_grad) and given back when it is destroyed;
+ * no other call allocates.  The paper has no counterpart (it states the
+ * method on a window held in memory); the allocator only decides where that
+ * memory comes from:
+ *   alloc(ctx, bytes, stream, &ptr) returns 0 and a device pointer (aligned
+ *     to at least 256 bytes) usable on every stream once it returns, or a
+ *     nonzero value when it cannot (the library then reports ENOMEM);
+ *   free(ctx, ptr, bytes, stream) gives it back; the library has synchronised
+ *     its streams before it frees.
+ * `stream` is the handle's stream at the time of the call.
+ */
+typedef int (*cumwin_alloc_fn)(void* ctx, size_t bytes, void* cuda_stream, void** out_dev);
+typedef void (*cumwin_free_fn)(void* ctx, void* dev_ptr, size_t bytes, void* cuda_stream);
+
+/* Process-wide allocator for handles and batches created from now on (each
+ * keeps the allocator it was created with until it is destroyed).  Both NULL
+ * restores the default: cudaMallocAsync on the handle's stream, synchronised,
+ * and cudaFree.  Thread-safe.  Errors: EINVAL when only one is NULL. */
+int cumwin_set_allocator(cumwin_alloc_fn alloc, cumwin_free_fn free_fn, void* ctx);
+
+/* Bytes of device memory the handle holds (all taken from its allocator). */
+int64_t cumwin_device_bytes(cumwin_t h);
+
 /* Largest supported order d and variable count n. */
 #define CUMWIN_MAX_ORDER 8
 #define CUMWIN_MAX_N 256
@@ -77,8 +104,8 @@ enum {
  * length T samples, nominal shift size p (the paper's t_up, 1 <= p <= T),
  * arithmetic `precision`, issuing work on `cuda_stream` (a cudaStream_t;
  * NULL = legacy default stream).  Allocates all device state (ring buffer of
- * T samples, FP64 moment sums and cumulants of every order, tables) with
- * cudaMalloc on the current device.  Synchronous.
+ * T samples, FP64 moment sums and cumulants of every order, tables) on the
+ * current device from the allocator of cumwin_set_allocator.  Synchronous.
  * In the mixed forms the FP32 tile sums are formed per batch of p samples and
  * the first window is summed in batches of p aligned with the later shifts,
  * so when every push has p rows and p divides T a batch's FP32 sum leaving
@@ -157,6 +184,26 @@ int cumwin_join(cumwin_t h);
  * been synchronised).  Nothing is allocated; the host does not block.
  */
 int cumwin_norms_enqueue(cumwin_t h, double* fro2_out, int* status_out);
+
+/*
+ * As cumwin_norms_enqueue, with the estimators formed on the device: the
+ * Frobenius norms ||C_s||_F, s = 1..d (Eq. me, d doubles, into fro_out), the
+ * non-Gaussianity estimators nu_s = ||C_s|| / ||C_2||^{s/2} (Eq. mef, d
+ * doubles into nu_out, NaN for s < 3 and when ||C_2|| = 0) and the sticky
+ * status (into status_out).  Any of the three may be NULL, not all; each may
+ * be device or host memory.  Ordering and validity as cumwin_norms_enqueue;
+ * nothing is allocated and the host does not block.
+ */
+int cumwin_estimators_enqueue(cumwin_t h, double* fro_out, double* nu_out, int* status_out);
+
+/*
+ * L = sum_{s=1..d} w[s] ||C_s||_F^2 of the current window (w_host: d+1
+ * doubles, w[0] ignored; full-tensor norms, Eq. me) into L_dev[0] (device,
+ * FP64).  Not in the paper: it is the scalar whose gradient cumwin_grad
+ * evaluates.  Asynchronous on the handle's stream; w_host is read before the
+ * call returns.  Errors: EINVAL, ESTATE.
+ */
+int cumwin_loss(cumwin_t h, const double* w_host, double* L_dev);
 
 /* Turn pipelined shifts (cumwin_push) on (enable != 0, the default) or off.
  * Results are bitwise the same either way. */

@@ -207,6 +207,37 @@ class CumWin:
         check(self.lib.cumwin_norms_enqueue(self._h, ptr(fro2_out, torch.float64, self.d, "fro2_out"), sp),
               "cumwin_norms_enqueue")
 
+    def estimators_enqueue(self, fro_out: torch.Tensor | None = None, nu_out: torch.Tensor | None = None,
+                           status_out: torch.Tensor | None = None):
+        """Enqueue ||C_s||_F and nu_s (d float64 each, formed on the device) and the
+        device status (int32) into the given tensors (CUDA or host memory), behind
+        the last push's recovery; valid after ``join()`` and a synchronisation
+        (see cumwin_estimators_enqueue)."""
+        def ptr(t, dtype, count, what):
+            if t is None:
+                return None
+            if t.dtype != dtype or not t.is_contiguous() or t.numel() < count:
+                raise ValueError(f"{what} must be a contiguous {dtype} tensor of at least {count} elements")
+            return ctypes.c_void_p(t.data_ptr())
+        args = (ptr(fro_out, torch.float64, self.d, "fro_out"), ptr(nu_out, torch.float64, self.d, "nu_out"),
+                ptr(status_out, torch.int32, 1, "status_out"))
+        if all(a is None for a in args):
+            raise ValueError("give at least one output")
+        self._sync_stream()
+        check(self.lib.cumwin_estimators_enqueue(self._h, *args), "cumwin_estimators_enqueue")
+
+    def loss(self, w, out: torch.Tensor | None = None) -> torch.Tensor:
+        """L = sum_s w[s] ||C_s||_F^2 of the current window as a 0-d float64 CUDA tensor
+        (cumwin_loss; w[0] ignored)."""
+        wa = np.zeros(self.d + 1)
+        wv = np.asarray(w, dtype=np.float64)[: self.d + 1]
+        wa[:len(wv)] = wv
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=self.device)
+        self._sync_stream()
+        check(self.lib.cumwin_loss(self._h, wa.ctypes.data, _dev_ptr(out, torch.float64, "out")), "cumwin_loss")
+        return out
+
     def recompute(self):
         self._sync_stream()
         check(self.lib.cumwin_recompute(self._h), "cumwin_recompute")
@@ -389,8 +420,9 @@ class CumWinBatch:
 class CumulantNormLoss(torch.autograd.Function):
     """L(X) = sum_s w[s] ||C_s(X)||_F^2 for a window X (T x n), with a hand-written adjoint.
 
-    Forward loads X as a fresh window into a handle and reads the norms;
-    backward calls ``cumwin_grad`` on the same handle.
+    Forward loads X as a fresh window into a handle and has the library form L
+    on the device (``cumwin_loss``); backward calls ``cumwin_grad`` on the same
+    handle.
     """
 
     @staticmethod
@@ -399,11 +431,9 @@ class CumulantNormLoss(torch.autograd.Function):
         d = len(w) - 1
         cw = CumWin(n, d, b, T, T, "fp64", device=X.device)
         cw.fill(X.detach().contiguous())
-        fro, _ = cw.norms()
-        val = sum(float(w[s]) * fro[s - 1] ** 2 for s in range(1, d + 1))
         ctx.cw = cw
         ctx.w = list(w)
-        return torch.tensor(val, dtype=torch.float64, device=X.device)
+        return cw.loss(w)  # formed by the library on the device (cumwin_loss)
 
     @staticmethod
     def backward(ctx, gout):

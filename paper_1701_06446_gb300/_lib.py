@@ -66,7 +66,51 @@ SIGNATURES = {
     "cumwin_strerror": (ctypes.c_char_p, [c_int]),
     "cumwin_last_error": (ctypes.c_char_p, []),
     "cumwin_version": (c_int, []),
+    "cumwin_set_allocator": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_estimators_enqueue": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "cumwin_loss": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_device_bytes": (c_i64, [c_vp]),
 }
+
+# allocator callbacks of cumwin_set_allocator
+ALLOC_FN = ctypes.CFUNCTYPE(c_int, c_vp, ctypes.c_size_t, c_vp, ctypes.POINTER(c_vp))
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_vp, ctypes.c_size_t, c_vp)
+
+
+def _torch_alloc(ctx, nbytes, stream, out):
+    """Device memory for the library from PyTorch's caching allocator."""
+    try:
+        import torch
+        dev = torch.cuda.current_device()
+        out[0] = torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        return 0
+    except Exception:  # reported by the library as ENOMEM
+        return 1
+
+
+def _torch_free(ctx, ptr, nbytes, stream):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # interpreter shutdown: the process gives the memory back
+        pass
+
+
+_TORCH_ALLOC = ALLOC_FN(_torch_alloc)
+_TORCH_FREE = FREE_FN(_torch_free)
+_installed = []  # callbacks currently installed (kept alive while the library may call them)
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Install ctypes callbacks (ALLOC_FN / FREE_FN) as the library's allocator
+    for handles created from now on; no arguments restores PyTorch's caching
+    allocator, which the binding installs when it loads the library."""
+    lib = load()
+    if alloc is None and free is None:
+        alloc, free = _TORCH_ALLOC, _TORCH_FREE
+    _installed.append((alloc, free))
+    check(lib.cumwin_set_allocator(ctypes.cast(alloc, c_vp), ctypes.cast(free, c_vp), None),
+          "cumwin_set_allocator")
 
 
 def path() -> str:
@@ -84,6 +128,10 @@ def load():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            # handles take their device memory from PyTorch's caching allocator
+            if lib.cumwin_set_allocator(ctypes.cast(_TORCH_ALLOC, c_vp), ctypes.cast(_TORCH_FREE, c_vp),
+                                        None) != 0:
+                raise RuntimeError("cumwin_set_allocator failed")
             _lib = lib
     return _lib
 

@@ -36,16 +36,55 @@ int fail_cuda(cudaError_t e, const char* what)
         if (_e != cudaSuccess) return fail_cuda(_e, #expr); \
     } while (0)
 
-// Device allocations of one object, freed together.
+// The allocator handles take their device memory from (cumwin_set_allocator):
+// the caller's callbacks, or cudaMallocAsync on the handle's stream (then
+// synchronised, since the creating code touches the memory on other streams)
+// and cudaFree.
+struct Allocator {
+    cumwin_alloc_fn alloc = nullptr;
+    cumwin_free_fn free = nullptr;
+    void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc;
+}
+
+// Device allocations of one object, all through its allocator, freed together.
 struct Arena {
-    std::vector<void*> ptrs;
+    struct Block {
+        void* p;
+        size_t bytes;
+    };
+    std::vector<Block> blocks;
+    Allocator al;
+    cudaStream_t stream = nullptr;
+    size_t total = 0;
+    cudaError_t raw(void** q, size_t bytes)
+    {
+        *q = nullptr;
+        if (al.alloc != nullptr) {
+            const int rc = al.alloc(al.ctx, bytes, (void*)stream, q);
+            if (rc != 0 || *q == nullptr) return cudaErrorMemoryAllocation;
+        } else {
+            cudaError_t e = cudaMallocAsync(q, bytes, stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e != cudaSuccess) return e;
+        }
+        blocks.push_back({*q, bytes});
+        total += bytes;
+        return cudaSuccess;
+    }
     template <class T>
     cudaError_t alloc(T** p, size_t count)
     {
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        cudaError_t e = raw(&q, std::max<size_t>(count, 1) * sizeof(T));
         if (e != cudaSuccess) return e;
-        ptrs.push_back(q);
         *p = (T*)q;
         return cudaSuccess;
     }
@@ -66,14 +105,20 @@ struct Arena {
     }
     void release()
     {
-        for (void* q : ptrs) cudaFree(q);
-        ptrs.clear();
+        for (const Block& b : blocks) {
+            if (al.free != nullptr) al.free(al.ctx, b.p, b.bytes, (void*)stream);
+            else cudaFree(b.p);
+        }
+        blocks.clear();
+        total = 0;
     }
 };
 
 }  // namespace
 
 void cw::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+constexpr int kKnormParts = 512;  // partial sums per order of cumwin_norms_k
 
 // Fused recovery of orders 1..dfused (see FusedRecovery); dfused = 0 when the
 // device cannot run the cooperative launch, and one launch per order is used.
@@ -131,6 +176,13 @@ struct cumwin_s {
     NormArgs* norm_dev = nullptr;
     TcAccSeg* segs = nullptr;  // workspace segments of this window's orders (own plan)
     int nsegs = 0;
+    // scratch of cumwin_norms_k (kKnormParts partials per order) and of
+    // cumwin_marginals (the storage indices of the diagonal entries i..i of
+    // orders 2..min(d, 4) and the gathered values), allocated at create
+    double* knorm_parts = nullptr;
+    double* est = nullptr;  // [2d]: ||C_s|| and nu_s staged by cumwin_estimators_enqueue
+    int64_t* diag_idx = nullptr;
+    double* diag_val = nullptr;
 
     // adjoint workspace (allocated by the first cumwin_grad)
     struct Grad {
@@ -285,6 +337,8 @@ std::string plan_signature(const TcPlan& tc, const std::vector<cumwin_s*>& wins,
 // ---------------------------------------------------------------------------
 // one window: tables and device state
 // ---------------------------------------------------------------------------
+int64_t element_index_impl(int n, int b, int order, const int* i);
+
 // Allocates and initialises everything a window needs.  own_tc: build the
 // window's own tensor-core plan (mixed forms); batch members leave that to
 // the batch.
@@ -301,6 +355,8 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     h->p = p;
     h->prec = precision;
     h->stream = stream;
+    h->mem.al = current_allocator();
+    h->mem.stream = stream;
     CW_TRY(cudaGetDevice(&h->device));
     CW_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
     if (precision != CUMWIN_FP64) {
@@ -432,6 +488,20 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     }
     CW_TRY(h->alloc(&h->fro2, d));
     CW_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
+    CW_TRY(h->alloc(&h->knorm_parts, (size_t)kKnormParts * d));
+    CW_TRY(h->alloc(&h->est, (size_t)2 * d));
+    {
+        const int dm = std::min(d, 4);
+        std::vector<int64_t> idx((size_t)std::max(dm - 1, 1) * n, 0);
+        for (int s = 2; s <= dm; ++s)
+            for (int i = 0; i < n; ++i) {
+                int v[kMaxOrder];
+                for (int q = 0; q < s; ++q) v[q] = i;
+                idx[(size_t)(s - 2) * n + i] = element_index_impl(n, b, s, v);
+            }
+        CW_TRY(h->upload(&h->diag_idx, idx));
+        CW_TRY(h->alloc(&h->diag_val, idx.size()));
+    }
 
     if (precision != CUMWIN_FP64 && own_tc) {
         TcPlanStream ps{};
@@ -768,10 +838,6 @@ int check_args(int n, int d, int b, int64_t T, int p, int precision)
     const int nbar = (n + b - 1) / b;
     if ((int64_t)nbar * b > kMaxN) return CUMWIN_EINVAL;
     if (T > ((int64_t)1 << 40)) return CUMWIN_EINVAL;
-    if (precision == CUMWIN_MIXED_FP16) {
-        g_last_error = "the FP16 split form is not implemented (use the BF16 split form)";
-        return CUMWIN_ENOTSUP;
-    }
     return CUMWIN_OK;
 }
 
@@ -814,6 +880,22 @@ const char* cumwin_strerror(int code)
 }
 
 const char* cumwin_last_error(void) { return g_last_error.c_str(); }
+
+int cumwin_set_allocator(cumwin_alloc_fn alloc, cumwin_free_fn free_fn, void* ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return CUMWIN_EINVAL;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.ctx = alloc != nullptr ? ctx : nullptr;
+    return CUMWIN_OK;
+}
+
+int64_t cumwin_device_bytes(cumwin_t h)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    return (int64_t)h->mem.total;
+}
 
 int64_t cumwin_layout_size(int n, int b, int order)
 {
@@ -1025,6 +1107,7 @@ int cumwin_set_stream(cumwin_t h, void* cuda_stream)
         CW_TRY(err);
     }
     h->stream = next;
+    h->mem.stream = next;
     CW_TRY(join(h));
     return CUMWIN_OK;
 }
@@ -1088,6 +1171,44 @@ int cumwin_norms_enqueue(cumwin_t h, double* fro2_out, int* status_out)
     if (status_out != nullptr)
         CW_TRY(cudaMemcpyAsync(status_out, h->status, sizeof(int), cudaMemcpyDefault, st));
     if (behind) CW_TRY(cudaEventRecord(h->ev_rec[h->last], h->rstream));
+    return CUMWIN_OK;
+}
+
+int cumwin_estimators_enqueue(cumwin_t h, double* fro_out, double* nu_out, int* status_out)
+{
+    if (h == nullptr || (fro_out == nullptr && nu_out == nullptr && status_out == nullptr)) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    // as cumwin_norms_enqueue: behind the last pipelined recovery when there is one
+    const bool behind = h->pend[h->last] && !capturing(h->stream);
+    cudaStream_t st = behind ? h->rstream : h->stream;
+    if (!behind) CW_TRY(join(h));
+    if (fro_out != nullptr || nu_out != nullptr) {
+        EstArgs a{};
+        a.fro = h->est;
+        a.nu = h->est + h->d;
+        a.d = h->d;
+        CW_TRY(launch_estimators(h->fro2, a, st));
+        if (fro_out != nullptr)
+            CW_TRY(cudaMemcpyAsync(fro_out, h->est, sizeof(double) * h->d, cudaMemcpyDefault, st));
+        if (nu_out != nullptr)
+            CW_TRY(cudaMemcpyAsync(nu_out, h->est + h->d, sizeof(double) * h->d, cudaMemcpyDefault, st));
+    }
+    if (status_out != nullptr)
+        CW_TRY(cudaMemcpyAsync(status_out, h->status, sizeof(int), cudaMemcpyDefault, st));
+    if (behind) CW_TRY(cudaEventRecord(h->ev_rec[h->last], h->rstream));
+    return CUMWIN_OK;
+}
+
+int cumwin_loss(cumwin_t h, const double* w_host, double* L_dev)
+{
+    if (h == nullptr || w_host == nullptr || L_dev == nullptr) return CUMWIN_EINVAL;
+    if (!h->filled) return CUMWIN_ESTATE;
+    CW_TRY(join(h));
+    EstArgs a{};
+    a.loss = L_dev;
+    a.d = h->d;
+    for (int s = 1; s <= h->d; ++s) a.w[s] = w_host[s];
+    CW_TRY(launch_estimators(h->fro2, a, h->stream));
     return CUMWIN_OK;
 }
 
@@ -1206,26 +1327,18 @@ int cumwin_norms_k(cumwin_t h, double k, double* out_host)
     if (h == nullptr || out_host == nullptr || !(k >= 1.0) || !std::isfinite(k)) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
     CW_TRY(join(h));
-    constexpr int kParts = 512;
-    double* parts = nullptr;
-    CW_TRY(cudaMallocAsync((void**)&parts, sizeof(double) * kParts * h->d, h->stream));
+    double* parts = h->knorm_parts;  // kKnormParts per order, allocated at create
     for (int s = 1; s <= h->d; ++s) {
-        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kParts, (h->E[s] + 255) / 256));
-        const cudaError_t e = launch_knorm(h->cum_dev + s, h->E[s], k, parts + (size_t)(s - 1) * kParts, np,
-                                           h->stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(parts, h->stream);
-            return fail_cuda(e, "cumwin_norms_k");
-        }
+        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kKnormParts, (h->E[s] + 255) / 256));
+        CW_TRY(launch_knorm(h->cum_dev + s, h->E[s], k, parts + (size_t)(s - 1) * kKnormParts, np, h->stream));
     }
-    std::vector<double> host((size_t)kParts * h->d, 0.0);
+    std::vector<double> host((size_t)kKnormParts * h->d, 0.0);
     CW_TRY(cudaMemcpyAsync(host.data(), parts, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
-    CW_TRY(cudaFreeAsync(parts, h->stream));
     CW_TRY(cudaStreamSynchronize(h->stream));
     for (int s = 1; s <= h->d; ++s) {
-        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kParts, (h->E[s] + 255) / 256));
+        const int np = (int)std::max<int64_t>(1, std::min<int64_t>(kKnormParts, (h->E[s] + 255) / 256));
         double z = 0.0;
-        for (int q = 0; q < np; ++q) z += host[(size_t)(s - 1) * kParts + q];
+        for (int q = 0; q < np; ++q) z += host[(size_t)(s - 1) * kKnormParts + q];
         out_host[s - 1] = std::pow(z, 1.0 / k);
     }
     return CUMWIN_OK;
@@ -1238,25 +1351,12 @@ int cumwin_marginals(cumwin_t h, double* skew_host, double* kurt_host)
     CW_TRY(join(h));
     const int n = h->n, dm = std::min(h->d, 4);
     std::vector<double> diag((size_t)(dm + 1) * n, NAN);
-    if (dm >= 2) {
-        std::vector<int64_t> idx((size_t)(dm - 1) * n);
+    if (dm >= 2) {  // the diagonal entries C_s[i..i], s = 2..dm, through the index table of create
         for (int s = 2; s <= dm; ++s)
-            for (int i = 0; i < n; ++i) {
-                int v[kMaxOrder];
-                for (int q = 0; q < s; ++q) v[q] = i;
-                idx[(size_t)(s - 2) * n + i] = element_index_impl(n, h->b, s, v);
-            }
-        int64_t* didx = nullptr;
-        double* dout = nullptr;
-        CW_TRY(cudaMallocAsync((void**)&didx, sizeof(int64_t) * idx.size(), h->stream));
-        CW_TRY(cudaMallocAsync((void**)&dout, sizeof(double) * idx.size(), h->stream));
-        CW_TRY(cudaMemcpyAsync(didx, idx.data(), sizeof(int64_t) * idx.size(), cudaMemcpyHostToDevice, h->stream));
-        for (int s = 2; s <= dm; ++s)
-            CW_TRY(launch_gather_idx(h->C[s], didx + (size_t)(s - 2) * n, n, dout + (size_t)(s - 2) * n, h->stream));
-        CW_TRY(cudaMemcpyAsync(diag.data() + 2 * (size_t)n, dout, sizeof(double) * idx.size(), cudaMemcpyDeviceToHost,
-                               h->stream));
-        CW_TRY(cudaFreeAsync(didx, h->stream));
-        CW_TRY(cudaFreeAsync(dout, h->stream));
+            CW_TRY(launch_gather_idx(h->C[s], h->diag_idx + (size_t)(s - 2) * n, n, h->diag_val + (size_t)(s - 2) * n,
+                                     h->stream));
+        CW_TRY(cudaMemcpyAsync(diag.data() + 2 * (size_t)n, h->diag_val, sizeof(double) * (size_t)(dm - 1) * n,
+                               cudaMemcpyDeviceToHost, h->stream));
         CW_TRY(cudaStreamSynchronize(h->stream));
     }
     for (int i = 0; i < n; ++i) {
@@ -1532,6 +1632,8 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     B->p = p;
     B->prec = precision;
     B->stream = (cudaStream_t)cuda_stream;
+    B->mem.al = current_allocator();
+    B->mem.stream = B->stream;
     auto bail = [&](int code) {
         cumwin_batch_destroy(B);
         return code;

@@ -212,6 +212,16 @@ size_t fused_smem_bytes(const FusedRecovery& f, int dfused);
 // Resident CTAs for the cooperative launch, at most per_sm_max per SM (0: not possible).
 int fused_grid(int dfused, size_t smem, int sm_count, int per_sm_max);
 cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st);
+// ||C_s||, nu_s and L = sum_s w_s ||C_s||^2 from the squared norms (any
+// output may be null).
+struct EstArgs {
+    double* fro;   // [d]
+    double* nu;    // [d]
+    double* loss;  // [1]
+    double w[kMaxOrder + 1];
+    int32_t d;
+};
+cudaError_t launch_estimators(const double* fro2, const EstArgs& a, cudaStream_t st);
 cudaError_t launch_zero(double* p, int64_t count, cudaStream_t st);
 cudaError_t launch_add_shift(const double* C1, const float* shift, int n, int npad, double* out,
                              cudaStream_t st);

@@ -54,6 +54,8 @@ struct TcStreamDesc {
     int64_t* head;      // ring head of the staging (advanced by the operand build of a shift)
     const float* shift;
     float* XT;          // [npad][Kcap]
+    float* vmax;        // [2][npad] largest |staged sample| per variable, entering / leaving half
+                        // (FP16 form: the power-of-two scale of the variable's factors)
     int* status;
     int64_t T;
     int64_t xoff;       // offset of this stream's X_(+) rows in a packed push buffer
@@ -85,6 +87,8 @@ struct TcOrder {
 struct TcGemmArgs {
     const TcOrder* ord;
     const TcItem* items;
+    const int32_t* opexp;  // FP16 form: [2][oprows] power-of-two exponent of each operand row
+    int64_t oprows;
     float* W;            // [ksplit][2][wslice] FP32 tile sums
     int64_t wslice;
     int32_t nitems, ksplit;
@@ -118,6 +122,12 @@ struct TcPlan {
     uint16_t* ops = nullptr;
     int64_t oprows = 0;
     uint64_t* opvars = nullptr;    // per row: packed variables | factors << 32 | stream << 40
+    // FP16 form: the operand rows are scaled by powers of two so that every
+    // factor lies in [-1, 1] (FP16 has 5 exponent bits); vmax holds the largest
+    // |staged sample| per (stream, half, variable), zeroed before each staging,
+    // and opexp the exponent of each row's scale, undone exactly in the epilogue
+    float* vmax = nullptr;         // [nstreams][2][npad_max]
+    int32_t* opexp = nullptr;      // [2][oprows]
     CUtensorMap mapA{}, mapB[3]{};  // A boxes of 128 rows; B boxes of 32, 64, 128 rows
     TcItem* items = nullptr;
     int nitems = 0, ksplit = 1, ksplit_max = 1;

@@ -890,6 +890,27 @@ __global__ void k_norm_final(const NormArgs* __restrict__ args, int64_t advance,
     if (lane == 0) a.fro2[s] = z;
 }
 
+// The estimators of Eqs. me / mef from the squared norms: ||C_s|| = sqrt of
+// the squared norm, nu_s = ||C_s|| / ||C_2||^{s/2} for s >= 3 (NaN below, and
+// NaN when ||C_2|| = 0 by 0/0), and L = sum_s w_s ||C_s||^2.  One warp.
+__global__ void k_estimators(const double* __restrict__ fro2, EstArgs a)
+{
+    const int s = threadIdx.x + 1;
+    const bool on = s <= a.d;
+    const double z = on ? fro2[s - 1] : 0.0;
+    const double f = sqrt(z);
+    if (on && a.fro != nullptr) a.fro[s - 1] = f;
+    if (on && a.nu != nullptr) {
+        const double c2 = a.d >= 2 ? sqrt(fro2[1]) : 0.0;
+        a.nu[s - 1] = (s < 3 || a.d < 2) ? __longlong_as_double(0x7ff8000000000000LL) : f / pow(c2, 0.5 * s);
+    }
+    if (a.loss != nullptr) {  // fixed order: lane s-1 contributes w_s z_s, reduced by a fixed tree
+        double v = on ? a.w[s] * z : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *a.loss = v;
+    }
+}
+
 template <int S>
 cudaError_t launch_order(const CumArgs* args, int nwin, const CumLaunch& L, cudaStream_t st)
 {
@@ -1031,6 +1052,12 @@ cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale,
     const int64_t need = (E + NT - 1) / NT;
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(need, 16384));
     k_gather_sums<<<gx, NT, 0, st>>>(args_dev, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimators(const double* fro2, const EstArgs& a, cudaStream_t st)
+{
+    k_estimators<<<1, 32, 0, st>>>(fro2, a);
     return cudaGetLastError();
 }
 

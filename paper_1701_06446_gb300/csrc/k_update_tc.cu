@@ -47,7 +47,8 @@ constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 // slot also writes X_(+) into it.
 __global__ void __launch_bounds__(256)
 k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict__ xin_base,
-                const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap, int leaving)
+                const float* __restrict__ xout_base, int64_t ld_arg, int p, int P, int64_t Kcap, int leaving,
+                int scaled)
 {
     __shared__ float tin[32][33], tout[32][33];
     grid_dep_launch();  // the operand build may launch now; it waits for this grid
@@ -83,6 +84,17 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
         tout[rr][tx] = xo;
     }
     __syncthreads();
+    if (scaled && ty == 0 && v0 + tx < sd.n) {  // FP16 form: largest |sample| per variable and half
+        float mi = 0.0f, mo = 0.0f;
+        for (int rr = 0; rr < 32; ++rr) {
+            mi = fmaxf(mi, fabsf(tin[rr][tx]));
+            mo = fmaxf(mo, fabsf(tout[rr][tx]));
+        }
+        // non-negative floats order as their bit patterns
+        if (mi > 0.0f) atomicMax(reinterpret_cast<unsigned*>(sd.vmax) + v0 + tx, __float_as_uint(mi));
+        if (leaving && mo > 0.0f)
+            atomicMax(reinterpret_cast<unsigned*>(sd.vmax) + sd.npad + v0 + tx, __float_as_uint(mo));
+    }
     for (int vv = ty; vv < 32; vv += 8) {
         const int v = v0 + vv, r = r0 + tx;
         if (v < sd.npad && r < P) {
@@ -96,12 +108,14 @@ k_tc_stage_push(const TcStreamDesc* __restrict__ sdesc, const float* __restrict_
 // Window rows [q*p, q*p + p) (window order, oldest first) into samples [0, P);
 // blockIdx.y = stream.
 __global__ void __launch_bounds__(256)
-k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, int64_t Kcap)
+k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, int64_t Kcap, int scaled)
 {
     grid_dep_launch();
     const TcStreamDesc sd = sdesc[blockIdx.y];
     const int64_t head = *sd.head;
     const int64_t total = (int64_t)sd.npad * P;
+    // P is a multiple of 64 and the stride a multiple of 32, so the 32 lanes of a
+    // warp always take the same variable in the same iteration (the reduction below)
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int v = (int)(e / P);
@@ -114,7 +128,31 @@ k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, in
             x = sd.ring[slot * sd.npad + v] - sd.shift[v];
         }
         sd.XT[(int64_t)v * Kcap + r] = x;
+        if (scaled) {  // FP16 form: largest |sample| of the variable in this batch
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(x)));
+            if ((threadIdx.x & 31) == 0 && m != 0u && v < sd.n)
+                atomicMax(reinterpret_cast<unsigned*>(sd.vmax) + v, m);
+        }
     }
+}
+
+// Exponent e of the power-of-two scale 2^-e that maps |x| <= m into [0, 1):
+// m = f * 2^e with f in [0.5, 1); 0 for m = 0 (or subnormal), clamped so that
+// 2^-e is a normal float.
+__device__ __forceinline__ int scale_exp(float m)
+{
+    const int ex = (int)((__float_as_uint(m) >> 23) & 0xffu);
+    if (ex == 0) return 0;
+    return min(125, max(-125, ex - 126));
+}
+
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((unsigned)(127 + k) << 23); }
+
+// x * 2^k, exact unless the result leaves the float range (|k| <= 250).
+__device__ __forceinline__ float scale_pow2(float x, int k)
+{
+    const int k1 = k / 2, k2 = k - k1;
+    return __fmul_rn(__fmul_rn(x, pow2f(k1)), pow2f(k2));
 }
 
 // ---------------------------------------------------------------------------
@@ -125,7 +163,8 @@ k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, in
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t* __restrict__ opvars,
-           int64_t rows, int nkb, uint16_t* __restrict__ ops, int nstreams, int64_t advance)
+           int64_t rows, int nkb, uint16_t* __restrict__ ops, int nstreams, int64_t advance, int P,
+           int32_t* __restrict__ opexp)
 {
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
     grid_dep_launch();  // the GEMM may launch now; its TMA warp waits for this grid
@@ -145,16 +184,30 @@ k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t*
         const uint64_t w = opvars[row];
         const uint32_t vars = (uint32_t)w;
         const int nf = (int)((w >> 32) & 0xffu);
-        const float* XT = sdesc[(int)(w >> 40)].XT;
+        const TcStreamDesc* sd = &sdesc[(int)(w >> 40)];
+        const float* XT = sd->XT;
         float p[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) p[t] = 1.0f;
+        const int half = 8 * kb >= P ? 1 : 0;  // entering or leaving samples
+        int esum = 0;
         for (int f = 0; f < nf; ++f) {
-            const float* xr = XT + (int64_t)((vars >> (8 * f)) & 0xffu) * Kcap + 8 * kb;
-            const float4 a = *reinterpret_cast<const float4*>(xr);
-            const float4 c = *reinterpret_cast<const float4*>(xr + 4);
+            const int var = (int)((vars >> (8 * f)) & 0xffu);
+            const float* xr = XT + (int64_t)var * Kcap + 8 * kb;
+            float4 a = *reinterpret_cast<const float4*>(xr);
+            float4 c = *reinterpret_cast<const float4*>(xr + 4);
+            if constexpr (!BF16) {  // every factor scaled into [-1, 1] by a power of two (exact)
+                const int e = scale_exp(sd->vmax[half * sd->npad + var]);
+                const float sc = pow2f(-e);
+                esum += e;
+                a.x *= sc; a.y *= sc; a.z *= sc; a.w *= sc;
+                c.x *= sc; c.y *= sc; c.z *= sc; c.w *= sc;
+            }
             p[0] *= a.x; p[1] *= a.y; p[2] *= a.z; p[3] *= a.w;
             p[4] *= c.x; p[5] *= c.y; p[6] *= c.z; p[7] *= c.w;
+        }
+        if constexpr (!BF16) {
+            if (8 * kb == half * P) opexp[(int64_t)half * rows + row] = esum;  // the row's scale, once per half
         }
         uint32_t h[4], l[4];
 #pragma unroll
@@ -359,6 +412,8 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         // ---------------- epilogue: TMEM -> FP32 workspace ----------------
         const int ew = warp - 2;  // 0..3
         const int quarter = warp & 3;
+        const bool scaled = args.opexp != nullptr;
+        if (scaled) grid_dep_wait();  // the row scales come from the operand build
         uint32_t it = 0;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x, ++it) {
             const TcItem item = args.items[u / args.ksplit];
@@ -391,6 +446,12 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
             float* Win = args.W + (int64_t)(2 * split) * args.wslice + od.woff;
             float* Wout = Win + args.wslice;
             const int NB = (item.nrows + 15) & ~15;
+            // FP16 form: the exponents of this lane's column (A row) scale, per half
+            int ec0 = 0, ec1 = 0;
+            if (scaled && ivalid) {
+                ec0 = args.opexp[item.acol + i];
+                if (args.nminus > 0) ec1 = args.opexp[args.oprows + item.acol + i];
+            }
             // 16 rows per round: one TMEM load per accumulator, one wait, then
             // one coalesced 64-byte store per row (lanes = consecutive slots)
             for (int jb = 0; jb < NB; jb += 16) {
@@ -399,6 +460,16 @@ k_kr_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                 if (R.nplus > 0) tmem_ld16p(ta, d0);
                 if (R.nminus > 0) tmem_ld16p(ta + (uint32_t)NMAX, d1);
                 tmem_ld_wait();
+                if (scaled) {  // undo the operand scales: D * 2^(row exponent + column exponent), exact
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int r = min(jb + t, item.nrows - 1);
+                        d0[t] = __float_as_uint(scale_pow2(__uint_as_float(d0[t]), ec0 + args.opexp[item.brow + r]));
+                        if (args.nminus > 0)
+                            d1[t] = __float_as_uint(
+                                scale_pow2(__uint_as_float(d1[t]), ec1 + args.opexp[args.oprows + item.brow + r]));
+                    }
+                }
                 if (item.fast) {
                     const int64_t w0 = (int64_t)item.wrow0 + (int64_t)jb * item.wwidth + cglob;
 #pragma unroll
@@ -494,6 +565,8 @@ cudaError_t launch_gemm(const TcPlan& plan, float* W, int nplus, int nminus, int
     TcGemmArgs a{};
     a.ord = plan.ord;
     a.items = plan.items;
+    a.opexp = plan.precision == 2 ? plan.opexp : nullptr;
+    a.oprows = plan.oprows;
     a.W = W;
     a.wslice = plan.wslice;
     a.nitems = plan.nitems;
@@ -522,9 +595,11 @@ cudaError_t launch_build(const TcPlan& plan, int nsamples, int64_t advance, cuda
     pdl_config(cfg, attr, dim3(grid_for(work)), dim3(256), 0, st);
     if (plan.precision == 1)
         return cudaLaunchKernelEx(&cfg, k_kr_build<true>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
-                                  (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance);
+                                  (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance,
+                                  plan.P, plan.opexp);
     return cudaLaunchKernelEx(&cfg, k_kr_build<false>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
-                              (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance);
+                              (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance,
+                              plan.P, plan.opexp);
 }
 
 // --------------------------------------------------------------------------
@@ -597,6 +672,11 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     std::vector<TcStreamDesc> sdesc(plan.nstreams);
     plan.nbatch = 0;
     plan.nbatch_stream.assign(plan.nstreams, 0);
+    for (const TcPlanStream& S : streams) plan.npad_max = std::max(plan.npad_max, S.npad);
+    if (precision == 2) {
+        cudaError_t e = alloc(sizeof(float) * 2 * (size_t)plan.npad_max * plan.nstreams, (void**)&plan.vmax);
+        if (e != cudaSuccess) return (int)e;
+    }
     for (int i = 0; i < plan.nstreams; ++i) {
         const TcPlanStream& S = streams[i];
         TcStreamDesc& sd = sdesc[i];
@@ -612,7 +692,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
         sd.xoff = S.xoff;
         sd.n = S.n;
         sd.npad = S.npad;
-        plan.npad_max = std::max(plan.npad_max, S.npad);
+        sd.vmax = plan.vmax != nullptr ? plan.vmax + (size_t)2 * plan.npad_max * i : nullptr;
         plan.nbatch_stream[i] = (int)((S.T + p - 1) / p);
         plan.nbatch = std::max(plan.nbatch, plan.nbatch_stream[i]);
     }
@@ -759,6 +839,12 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     plan.oprows = (int64_t)opvars.size();
     if (plan.oprows * (plan.Kcap / 8) >= ((int64_t)1 << 31) || plan.oprows >= ((int64_t)1 << 31))
         return (int)cudaErrorInvalidValue;
+    if (precision == 2) {
+        e = alloc(sizeof(int32_t) * 2 * (size_t)plan.oprows, (void**)&plan.opexp);
+        if (e != cudaSuccess) return (int)e;
+        e = cudaMemset(plan.opexp, 0, sizeof(int32_t) * 2 * (size_t)plan.oprows);
+        if (e != cudaSuccess) return (int)e;
+    }
     e = alloc(sizeof(uint64_t) * opvars.size(), (void**)&plan.opvars);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.opvars, opvars.data(), sizeof(uint64_t) * opvars.size(), cudaMemcpyHostToDevice);
@@ -820,7 +906,13 @@ cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xou
 {
     if (p > plan.p) return cudaErrorInvalidValue;
     const dim3 grid((plan.P + 31) / 32, (plan.npad_max + 31) / 32, plan.nstreams);
-    k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap, leaving ? 1 : 0);
+    const int scaled = plan.precision == 2;
+    if (scaled) {  // the per-variable maxima of this staging start from zero
+        const cudaError_t e0 = cudaMemsetAsync(plan.vmax, 0, sizeof(float) * 2 * (size_t)plan.npad_max *
+                                                                 plan.nstreams, st);
+        if (e0 != cudaSuccess) return e0;
+    }
+    k_tc_stage_push<<<grid, 256, 0, st>>>(plan.sdesc, xin, xout, ld, p, plan.P, plan.Kcap, leaving ? 1 : 0, scaled);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_build(plan, (leaving ? 2 : 1) * plan.P, p, st);
@@ -835,7 +927,13 @@ cudaError_t tc_gemm_push(const TcPlan& plan, bool leaving, int parity, cudaStrea
 cudaError_t tc_update_window_batch(const TcPlan& plan, int q, cudaStream_t st)
 {
     const int gx = std::max(1, std::min(64, (plan.npad_max * plan.P + 255) / 256));
-    k_tc_stage_batch<<<dim3(gx, plan.nstreams), 256, 0, st>>>(plan.sdesc, q, plan.p, plan.P, plan.Kcap);
+    const int scaled = plan.precision == 2;
+    if (scaled) {
+        const cudaError_t e0 = cudaMemsetAsync(plan.vmax, 0, sizeof(float) * 2 * (size_t)plan.npad_max *
+                                                                 plan.nstreams, st);
+        if (e0 != cudaSuccess) return e0;
+    }
+    k_tc_stage_batch<<<dim3(gx, plan.nstreams), 256, 0, st>>>(plan.sdesc, q, plan.p, plan.P, plan.Kcap, scaled);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_build(plan, plan.P, 0, st);

@@ -63,7 +63,7 @@ def test_grad_vs_central_finite_differences():
     w = [0, 0, 0, 1, 1]
     hstep = 1e-3
     rng = np.random.default_rng(17)
-    picks = [(int(rng.integers(T)), int(rng.integers(n))) for _ in range(48)]
+    picks = [(int(rng.integers(T)), int(rng.integers(n))) for _ in range(256)]
     with CumWin(n, d, b, T, T, "fp64") as h:
         h.fill(dev(X))
         g = h.grad(w).cpu().numpy()
@@ -120,6 +120,19 @@ def test_autograd_function_backward():
     assert rel_fro(X.grad.cpu().numpy(), ref) <= 1e-5
     fro, _ = oracle.norms(X.detach().cpu().numpy(), 4)
     assert abs(L.item() - (fro[2] ** 2 + fro[3] ** 2)) <= 1e-9 * L.item()
+
+
+@pytest.mark.parametrize("w", [[0, 0, 0, 1, 1], [0, 0.5, 0.3, 1.0, 2.0]])
+def test_library_loss_matches_oracle(w):
+    """cumwin_loss forms L = sum_s w_s ||C_s||^2 on the device; the oracle's loss is
+    the full-tensor sum over its own cumulants."""
+    W = WORKLOADS["n32_d4_b4_T4096_ica"]
+    X = W.stream().rows(0, W.T)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as h:
+        h.fill(dev(X))
+        L = float(h.loss(w).item())
+    ref = oracle.loss(X.astype(np.float64), w)
+    assert abs(L - ref) <= 1e-10 * abs(ref), (L, ref)
 
 
 def test_mixed_form_grad_close_to_fp64_form():

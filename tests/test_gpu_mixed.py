@@ -1,11 +1,17 @@
-"""GPU parity of the tensor-core (BF16 hi+lo split, FP32 accumulate, FP64 sums)
-form of the moment-sum update, through the C ABI.
+"""GPU parity of the tensor-core forms (BF16 or FP16 hi+lo split, FP32
+accumulate, FP64 sums) of the moment-sum update, through the C ABI.
 
-Per-order bound: the split represents each FP32 product to about 2^-16 relative
-(hi and lo carry 8 significant bits each, and lo*lo is dropped), so moments
-carry ~1e-5 relative error and cumulants of order s amplify it by the
-cancellation in the moment-to-cumulant relation.  The bounds below are stated
-per order as relative Frobenius errors against the FP64 oracle.
+Per-order bounds: the BF16 split represents each FP32 product to about 2^-16
+relative (hi and lo carry 8 significant bits each, and lo*lo is dropped), the
+FP16 split to about 2^-22 (11 + 11 bits, every factor scaled into [-1, 1] by a
+power of two); the FP32 sum of a batch of p products adds its own rounding,
+which dominates both forms once p reaches ~10^3.  Moments carry that relative
+error and cumulants of order s amplify it by the cancellation in the
+moment-to-cumulant relation.  The split forms have no closed-form error, so
+the bounds are stated per configuration, per order and per form as about
+three times the relative Frobenius error against the FP64 oracle measured on
+GB300 (rounded up to one significant digit): a regression of a few times
+fails.
 
 Exactness of the sliding update: a batch is reduced by the same instruction
 sequence when it enters (D_in) and when it leaves (D_out), so its FP32 sum
@@ -17,13 +23,39 @@ import pytest
 import torch
 
 import oracle
-from paper_1701_06446_gb300 import CumWin, CumwinError
+from paper_1701_06446_gb300 import CumWin
 from paper_1701_06446_gb300.streams import WORKLOADS
 
 pytestmark = pytest.mark.gpu
 
-# relative Frobenius error bound per order (index = order)
+# relative Frobenius error bounds per order, about 3x the measured error of each
+# configuration (index = order)
+BOUND = {
+    "small_stream": {"bf16": {1: 6e-5, 2: 2e-5, 3: 5e-5, 4: 5e-4}, "fp16": {1: 4e-6, 2: 3e-6, 3: 5e-6, 4: 7e-5}},
+    "fifo13": {"bf16": {1: 3e-7, 2: 2e-5, 3: 2e-5, 4: 2e-5}, "fp16": {1: 3e-8, 2: 3e-6, 3: 2e-6, 4: 4e-6}},
+    "n60": {"bf16": {1: 4e-6, 2: 2e-5, 3: 2e-5, 4: 5e-5}, "fp16": {1: 5e-6, 2: 2e-5, 3: 3e-5, 4: 5e-5}},
+    "n48": {"bf16": {1: 2e-5, 2: 6e-5, 3: 4e-5, 4: 3e-5, 5: 2e-5, 6: 3e-5},
+            "fp16": {1: 2e-5, 2: 8e-5, 3: 4e-5, 4: 2e-5, 5: 9e-6, 6: 4e-6}},
+    "drift_after": {"bf16": {1: 5e-8, 2: 2e-5, 3: 1e-5, 4: 9e-6}, "fp16": {1: 1e-8, 2: 3e-6, 3: 2e-6, 4: 2e-6}},
+    # the gamma-distributed ragged shapes of test_mixed_ragged_shapes
+    (7, 4, 3, 256, 40): {"bf16": {1: 2e-7, 2: 9e-6, 3: 7e-6, 4: 3e-5}, "fp16": {1: 1e-8, 2: 9e-7, 3: 7e-7, 4: 2e-6}},
+    (5, 5, 2, 200, 33): {"bf16": {1: 4e-7, 2: 2e-5, 3: 9e-6, 4: 5e-5, 5: 8e-5},
+                         "fp16": {1: 3e-8, 2: 9e-7, 3: 8e-7, 4: 2e-6, 5: 4e-6}},
+    (9, 3, 4, 97, 97): {"bf16": {1: 6e-7, 2: 8e-6, 3: 2e-5}, "fp16": {1: 4e-8, 2: 2e-6, 3: 2e-6}},
+    (10, 6, 3, 300, 64): {"bf16": {1: 3e-7, 2: 9e-6, 3: 9e-6, 4: 2e-5, 5: 3e-5, 6: 6e-5},
+                          "fp16": {1: 2e-8, 2: 2e-6, 3: 8e-7, 4: 2e-6, 5: 2e-6, 6: 3e-6}},
+    (33, 3, 4, 600, 100): {"bf16": {1: 3e-7, 2: 9e-6, 3: 2e-5}, "fp16": {1: 4e-8, 2: 2e-6, 3: 2e-6}},
+    (3, 8, 1, 120, 24): {"bf16": {1: 2e-7, 2: 7e-6, 3: 2e-5, 4: 4e-5, 5: 6e-5, 6: 2e-4, 7: 8e-5, 8: 9e-5},
+                         "fp16": {1: 3e-8, 2: 7e-7, 3: 8e-7, 4: 2e-6, 5: 3e-6, 6: 4e-6, 7: 3e-6, 8: 4e-6}},
+    (100, 3, 8, 512, 128): {"bf16": {1: 3e-7, 2: 9e-6, 3: 2e-5}, "fp16": {1: 4e-8, 2: 2e-6, 3: 2e-6}},
+    (64, 4, 4, 400, 50): {"bf16": {1: 3e-7, 2: 8e-6, 3: 2e-5, 4: 3e-5}, "fp16": {1: 2e-8, 2: 2e-6, 3: 2e-6, 4: 3e-6}},
+    (1, 6, 1, 64, 8): {"bf16": {1: 7e-7, 2: 1e-6, 3: 6e-7, 4: 5e-5, 5: 3e-4, 6: 8e-5},
+                       "fp16": {1: 1e-8, 2: 7e-7, 3: 2e-7, 4: 2e-6, 5: 2e-5, 6: 1e-6}},
+}
+# loose per-order bounds for the configurations that were not calibrated one by one
+# (retirement / restoration of the FIFO, graph replay, pipelining, heavy-tailed FP16 data)
 MIXED_BOUND = {1: 2e-5, 2: 5e-5, 3: 5e-4, 4: 2e-3, 5: 5e-3, 6: 2e-2, 7: 5e-2, 8: 1e-1}
+FORMS = ["bf16", "fp16"]
 
 
 def dev(a):
@@ -40,56 +72,61 @@ def errors_vs_oracle(h, X):
     return {s: rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) for s in range(1, h.d + 1)}
 
 
-def check_bounds(errs, scale=1.0):
+def check_bounds(errs, bound=None):
+    bound = bound or MIXED_BOUND
     for s, e in errs.items():
-        assert e <= MIXED_BOUND[s] * scale, (s, e, errs)
+        assert e <= bound[s], (s, e, bound[s], errs)
 
 
-def test_mixed_small_stream_every_tenth_shift():
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_small_stream_every_tenth_shift(form):
     W = WORKLOADS["n4_d4_b2_T1000_p100"]
     X = W.stream().rows(0, W.length)
     Xd = dev(X)
     worst = {}
-    with CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as h:
+    bound = BOUND["small_stream"][form]
+    with CumWin(W.n, W.d, W.b, W.T, W.p, form) as h:
         h.fill(Xd[: W.T])
-        check_bounds(errors_vs_oracle(h, X[: W.T]))
+        check_bounds(errors_vs_oracle(h, X[: W.T]), bound)
         for w in range(W.shifts):
             h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
             if w % 10 == 9:
                 errs = errors_vs_oracle(h, X[(w + 1) * W.p: (w + 1) * W.p + W.T])
                 for s, e in errs.items():
                     worst[s] = max(worst.get(s, 0.0), e)
-                check_bounds(errs)
-    print("worst per-order error", worst)
+                check_bounds(errs, bound)
+    print("worst per-order error", form, worst)
 
 
 @pytest.mark.parametrize("n,d,b,T,p", [(7, 4, 3, 256, 40), (5, 5, 2, 200, 33), (9, 3, 4, 97, 97),
                                        (10, 6, 3, 300, 64), (33, 3, 4, 600, 100), (3, 8, 1, 120, 24),
                                        (100, 3, 8, 512, 128), (64, 4, 4, 400, 50), (1, 6, 1, 64, 8)])
-def test_mixed_ragged_shapes(n, d, b, T, p):
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_ragged_shapes(n, d, b, T, p, form):
     rng = np.random.default_rng(11 * n + d)
     steps = 4
     A = rng.standard_normal((n, n)) / np.sqrt(n)
     X = (rng.gamma(2.0, size=(T + steps * p, n)) @ A + 0.5).astype(np.float32)
     Xd = dev(X)
-    with CumWin(n, d, b, T, p, "bf16") as h:
+    with CumWin(n, d, b, T, p, form) as h:
         h.fill(Xd[:T])
         for w in range(steps):
             h.push(Xd[T + w * p: T + (w + 1) * p])
         errs = errors_vs_oracle(h, X[steps * p: steps * p + T])
-        print((n, d, b, T, p), errs)
-        check_bounds(errs, scale=2.0)
+        print(form, (n, d, b, T, p), errs)
+        check_bounds(errs, BOUND[(n, d, b, T, p)][form])
         assert np.array_equal(h.window().cpu().numpy(), X[steps * p: steps * p + T])
 
 
-def test_mixed_sliding_equals_recompute_exactly():
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_sliding_equals_recompute_exactly(form):
     """Two full window rotations: the sliding sums equal a fresh recomputation
     to FP64 rounding, because in/out batch sums cancel bitwise."""
     n, d, b, T, p = 12, 4, 3, 2048, 256
     rng = np.random.default_rng(5)
     X = (rng.standard_t(5, size=(T + 40 * p, n)) + 3.0).astype(np.float32)
     Xd = dev(X)
-    with CumWin(n, d, b, T, p, "bf16") as h:
+    with CumWin(n, d, b, T, p, form) as h:
         h.fill(Xd[:T])
         for w in range(40):
             h.push(Xd[T + w * p: T + (w + 1) * p])
@@ -100,7 +137,8 @@ def test_mixed_sliding_equals_recompute_exactly():
             assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
 
 
-def test_fifo_matches_recomputing_form_bitwise():
+@pytest.mark.parametrize("form", FORMS)
+def test_fifo_matches_recomputing_form_bitwise(form):
     """The batch-sum FIFO (Section 2.4's alternative scheme) subtracts the stored
     FP32 sum of the leaving batch; recomputing X_(-) (caller-supplied leaving rows)
     gives the same FP32 sum, so both handles hold bitwise equal moments."""
@@ -108,7 +146,7 @@ def test_fifo_matches_recomputing_form_bitwise():
     rng = np.random.default_rng(21)
     X = (rng.standard_t(6, size=(T + 20 * p, n)) + 1.5).astype(np.float32)
     Xd = dev(X)
-    with CumWin(n, d, b, T, p, "bf16") as fifo, CumWin(n, d, b, T, p, "bf16") as rec:
+    with CumWin(n, d, b, T, p, form) as fifo, CumWin(n, d, b, T, p, form) as rec:
         fifo.fill(Xd[:T])
         rec.fill(Xd[:T])
         assert fifo.fifo and rec.fifo
@@ -119,7 +157,7 @@ def test_fifo_matches_recomputing_form_bitwise():
         for s in range(1, d + 1):
             assert torch.equal(fifo.moments(s), rec.moments(s)), s
             assert torch.equal(fifo.cumulants(s), rec.cumulants(s)), s
-        check_bounds(errors_vs_oracle(fifo, X[20 * p: 20 * p + T]))
+        check_bounds(errors_vs_oracle(fifo, X[20 * p: 20 * p + T]), BOUND["fifo13"][form])
 
 
 def test_fifo_retired_by_short_shift_and_restored_by_recompute():
@@ -154,7 +192,8 @@ def test_fifo_retired_by_short_shift_and_restored_by_recompute():
             assert rel_fro(slide[s - 1], h.moments(s).cpu().numpy()) <= 1e-13, s
 
 
-def test_mixed_vs_fp64_form_n60():
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_vs_fp64_form_n60(form):
     """n=60, d=4, b=3, T=2^15, p=2^10: the mixed form against the FP64 GPU form
     (every element) and against the oracle (sampled tuples)."""
     W = WORKLOADS["n60_d4_b3_T32768_p1024"]
@@ -162,7 +201,7 @@ def test_mixed_vs_fp64_form_n60():
     X = W.stream().rows(start, start + W.T + 3 * W.p)
     Xd = dev(X)
     with CumWin(W.n, W.d, W.b, W.T, W.p, "fp64") as f64, \
-            CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as mix:
+            CumWin(W.n, W.d, W.b, W.T, W.p, form) as mix:
         f64.fill(Xd[: W.T])
         mix.fill(Xd[: W.T])
         for w in range(3):
@@ -171,25 +210,26 @@ def test_mixed_vs_fp64_form_n60():
         errs = {}
         for s in range(1, W.d + 1):
             errs[s] = rel_fro(mix.cumulants(s).cpu().numpy(), f64.cumulants(s).cpu().numpy())
-        print("mixed vs FP64 form", errs)
-        check_bounds(errs)
+        print("mixed vs FP64 form", form, errs)
+        check_bounds(errs, BOUND["n60"][form])
         Xw = X[3 * W.p:]
         cen = oracle.center(Xw)
         for s in range(1, W.d + 1):
             tup = oracle.sample_sorted_tuples(W.n, s, 800, seed=600 + s)
             idx = np.array([oracle.storage_index(W.n, W.b, t) for t in tup])
             ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
-            assert rel_fro(mix.cumulants(s).cpu().numpy()[idx], ref) <= MIXED_BOUND[s]
+            assert rel_fro(mix.cumulants(s).cpu().numpy()[idx], ref) <= BOUND["n60"][form][s]
         fm, nm = mix.norms()
         ff, nf = f64.norms()
-        assert np.allclose(fm, ff, rtol=1e-3)
+        assert np.allclose(fm, ff, rtol=3e-5)
 
 
-def test_mixed_n48_order6_sampled():
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_n48_order6_sampled(form):
     W = WORKLOADS["n48_d6_b4_T65536_p4096"]
     X = W.stream().rows(0, W.T + W.p)
     Xd = dev(X)
-    with CumWin(W.n, W.d, W.b, W.T, W.p, "bf16") as h:
+    with CumWin(W.n, W.d, W.b, W.T, W.p, form) as h:
         h.fill(Xd[: W.T])
         h.push(Xd[W.T:])
         Xw = X[W.p:]
@@ -200,16 +240,17 @@ def test_mixed_n48_order6_sampled():
             idx = np.array([oracle.storage_index(W.n, W.b, t) for t in tup])
             ref = oracle.cumulant_tuples(Xw, tup, centred=cen)
             errs[s] = rel_fro(h.cumulants(s).cpu().numpy()[idx], ref)
-        print("n48 order-6 mixed errors", errs)
-        check_bounds(errs)
+        print("n48 order-6 mixed errors", form, errs)
+        check_bounds(errs, BOUND["n48"][form])
 
 
-def test_mixed_graph_replay_matches_eager():
+@pytest.mark.parametrize("form", FORMS)
+def test_mixed_graph_replay_matches_eager(form):
     n, d, b, T, p = 20, 4, 4, 512, 64
     rng = np.random.default_rng(9)
     X = rng.standard_normal((T + 12 * p, n)).astype(np.float32)
     Xd = dev(X)
-    with CumWin(n, d, b, T, p, "bf16") as eager, CumWin(n, d, b, T, p, "bf16") as cap:
+    with CumWin(n, d, b, T, p, form) as eager, CumWin(n, d, b, T, p, form) as cap:
         eager.fill(Xd[:T])
         cap.fill(Xd[:T])
         buf = torch.empty(p, n, device="cuda")
@@ -230,10 +271,23 @@ def test_mixed_graph_replay_matches_eager():
             assert torch.equal(eager.cumulants(k), cap.cumulants(k))
 
 
-def test_fp16_form_reports_not_supported():
-    with pytest.raises(CumwinError) as ei:
-        CumWin(4, 3, 2, 64, 8, "fp16")
-    assert ei.value.code == -7
+@pytest.mark.parametrize("n,d,b,T,p", [(7, 4, 3, 256, 40), (10, 6, 3, 300, 64), (3, 8, 1, 120, 24)])
+def test_fp16_form_matches_oracle(n, d, b, T, p):
+    """The FP16 split (11 + 11 significant bits, every factor scaled into [-1, 1]
+    by a power of two per variable and batch half, undone exactly in the GEMM
+    epilogue) against the oracle, with data whose raw products would leave the
+    FP16 range without the scales (|x| up to ~40, products of up to 4 factors)."""
+    rng = np.random.default_rng(3 * n + d)
+    steps = 4
+    X = (8.0 * rng.standard_t(3, size=(T + steps * p, n)) + 5.0).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, "fp16") as h:
+        h.fill(Xd[:T])
+        for w in range(steps):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        errs = errors_vs_oracle(h, X[steps * p: steps * p + T])
+        print("fp16", (n, d, b, T, p), errs)
+        check_bounds(errs)
 
 
 @pytest.mark.gpu
@@ -324,7 +378,8 @@ def test_norms_enqueue_per_push_matches_serial():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("n,d,b", [(20, 4, 4), (22, 4, 3), (10, 6, 2), (9, 5, 4)])
-def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b):
+@pytest.mark.parametrize("form", FORMS)
+def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b, form):
     """The recovery alone (orders >= 4 form their subset sums in two-word FP32
     arithmetic, the final subtraction in FP64): the cumulants of a mixed-form
     window against Algorithms 3-4 evaluated by the oracle in FP64 on that
@@ -334,7 +389,7 @@ def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b):
     rng = np.random.default_rng(31 + n + d)
     X = rng.standard_normal((T + 4 * p, n)) + 0.3 * rng.exponential(1.0, (T + 4 * p, n))
     Xd = dev(X.astype(np.float32))
-    with CumWin(n, d, b, T, p, "bf16") as h:
+    with CumWin(n, d, b, T, p, form) as h:
         h.fill(Xd[:T])
         for w in range(4):
             h.push(Xd[T + w * p: T + (w + 1) * p])
@@ -380,7 +435,8 @@ def test_phase_timing_levels():
 
 
 @pytest.mark.gpu
-def test_recenter_after_mean_drift():
+@pytest.mark.parametrize("form", FORMS)
+def test_recenter_after_mean_drift(form):
     """A stream whose mean drifts far from the first window's: the sums about
     the old shift carry a large raw-moment cancellation; re-centering at the
     window's own means recomputes them about the new shift, which lowers the
@@ -392,7 +448,7 @@ def test_recenter_after_mean_drift():
     X[T:] += 6.0 + rng.standard_normal(n)  # the stream moves away from the first window's mean
     X = X.astype(np.float32)
     Xd = dev(X)
-    with CumWin(n, d, b, T, p, "bf16") as h:
+    with CumWin(n, d, b, T, p, form) as h:
         h.fill(Xd[:T])
         for w in range(8):
             h.push(Xd[T + w * p: T + (w + 1) * p])
@@ -403,7 +459,7 @@ def test_recenter_after_mean_drift():
         print("error before / after re-centering", before, after)
         for s in range(2, d + 1):
             assert after[s] <= before[s], s
-        check_bounds(after)
+        check_bounds(after, BOUND["drift_after"][form])
         assert h.fifo
         for w in range(8, 16):
             h.push(Xd[T + w * p: T + (w + 1) * p])
@@ -412,7 +468,7 @@ def test_recenter_after_mean_drift():
         fresh = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
         for s in range(1, d + 1):
             assert rel_fro(slide[s - 1], fresh[s - 1]) <= 1e-13, s
-        check_bounds(errors_vs_oracle(h, X[16 * p: 16 * p + T]))
+        check_bounds(errors_vs_oracle(h, X[16 * p: 16 * p + T]), {k: 3 * v for k, v in BOUND["drift_after"][form].items()})
 
 
 @pytest.mark.gpu

@@ -352,3 +352,33 @@ def test_full_tensor_expansion(n, d, b, precision):
             assert np.array_equal(full, want), s
             tol = TOL_FP64 if precision == "fp64" else 5e-4
             assert rel_fro(full, oracle.to_full(ref[s - 1], n, b, s)) <= tol, s
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_estimators_enqueue_match_norms(precision):
+    """||C_s|| and nu_s formed on the device (cumwin_estimators_enqueue), into host
+    and device memory, equal what cumwin_norms returns, and nu matches the oracle."""
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, W.T + 3 * W.p)
+    Xd = dev(X)
+    with CumWin(W.n, W.d, W.b, W.T, W.p, precision) as h:
+        h.fill(Xd[: W.T])
+        fro_h = torch.zeros(W.d, dtype=torch.float64).pin_memory()
+        nu_h = torch.zeros(W.d, dtype=torch.float64).pin_memory()
+        st_h = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+        nu_d = torch.zeros(W.d, dtype=torch.float64, device="cuda")
+        for k in range(3):
+            h.push(Xd[W.T + k * W.p: W.T + (k + 1) * W.p])
+            h.estimators_enqueue(fro_h, nu_h, st_h)
+            h.estimators_enqueue(nu_out=nu_d)
+        h.join()
+        torch.cuda.synchronize()
+        fro, nu = h.norms()
+    assert int(st_h.item()) == 0
+    np.testing.assert_allclose(fro_h.numpy(), fro, rtol=1e-14)
+    np.testing.assert_allclose(nu_h.numpy()[2:], nu[2:], rtol=1e-14)
+    np.testing.assert_allclose(nu_d.cpu().numpy()[2:], nu[2:], rtol=1e-14)
+    assert np.all(np.isnan(nu_h.numpy()[:2]))
+    ofro, onu = oracle.norms(X[3 * W.p:], W.d)
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    np.testing.assert_allclose(nu_h.numpy()[2:], onu[2:], rtol=tol)
