@@ -62,7 +62,10 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
       samples (entering and leaving), or K = p when the leaving batch's sums come
       from the batch-sum FIFO; the tensor pipe issues three MMAs per product in
       the split forms (hi*hi + hi*lo + lo*hi).
-    * recovery, per stored element of order s: 2^{s-1} - 1 subset terms.  Orders
+    * recovery, per element of order s: 2^{s-1} - 1 subset terms.  Orders 5-6 with
+      blocks of >= 256 elements are recovered once per class of entries that
+      super-symmetry makes equal (C(n_pad + s - 1, s) canonical elements instead of
+      E_s stored ones; the copies are memory traffic), the others per stored element.  Orders
       below TWO_WORD_MIN_ORDER run them as FP64 multiply-adds, plus the 1/T
       scaling, the multiplicity-weighted square (2) and the fold of the shift's
       batch sums (2): `recovery_fp64` flops.  Orders from TWO_WORD_MIN_ORDER up (mixed
@@ -80,11 +83,13 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
     terms = {s: 2 ** (s - 1) - 1 for s in E}
     two_word = W.d >= TWO_WORD_MIN_ORDER
     fp64 = sum((2.0 * terms[s] + 5.0) * E[s] for s in E if not (two_word and s >= TWO_WORD_MIN_ORDER))
-    fp32_ops = sum(TWO_WORD_OPS_PER_TERM * terms[s] * E[s] for s in E if two_word and s >= TWO_WORD_MIN_ORDER)
+    npad = -(-W.n // W.b) * W.b
+    Ecomp = {s: math.comb(npad + s - 1, s) if 5 <= s <= 6 and W.b ** s >= 256 else E[s] for s in E}
+    fp32_ops = sum(TWO_WORD_OPS_PER_TERM * terms[s] * Ecomp[s] for s in E if two_word and s >= TWO_WORD_MIN_ORDER)
     per_elem = 16 + 8 + 4 + (8 if fifo else 4)
     rec_bytes = sum(per_elem * E[s] + (16 * E[s] if two_word and s < W.d else 0) for s in E)
     return {"update": upd, "recovery_fp64": fp64, "recovery_fp32_ops": fp32_ops,
-            "recovery_bytes": rec_bytes, "elements": E, "two_word": two_word}
+            "recovery_bytes": rec_bytes, "elements": E, "computed_elements": Ecomp, "two_word": two_word}
 
 
 # DRAM bytes (read + write) per launch from an ncu capture of the current kernels (see
@@ -462,8 +467,9 @@ def run_ours(args, W, rank: int, world: int):
                             frac=ops / fp32_peak,
                             peak_kind=f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                       f"{clk_mhz:.0f} MHz (median SM clock of the timed region)",
-                            per_launch=f"{work['recovery_fp32_ops']:.4g} FP32 operations: per stored element "
-                                       f"of order s >= {TWO_WORD_MIN_ORDER}, 2^(s-1)-1 subset terms x "
+                            per_launch=f"{work['recovery_fp32_ops']:.4g} FP32 operations: per computed element "
+                                       f"(canonical: one per class of equal entries) of order s >= "
+                                       f"{TWO_WORD_MIN_ORDER}, 2^(s-1)-1 subset terms x "
                                        f"{TWO_WORD_OPS_PER_TERM} (two-word multiply-accumulate); the orders "
                                        f"below run on the FP64 pipe ({work['recovery_fp64']:.3g} flops)")
         else:
@@ -746,6 +752,9 @@ def main():
                     help="seeded tuples of each order >= 4 in the cpu_baseline leg (orders <= 3 in full)")
     ap.add_argument("--grad", action="store_true", help="time forward + backward (adjoint) instead of shifts")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the workload's variable count")
+    ap.add_argument("--window", type=int, default=None, help="override the workload's window length T")
+    ap.add_argument("--shift", type=int, default=None, help="override the workload's shift size p")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -765,6 +774,11 @@ def main():
             ranks.finish(world)
         return
     W = WORKLOADS[args.workload]
+    if args.n or args.window or args.shift:  # a smaller variant of the workload (profiling captures)
+        import dataclasses
+        n, T, p = args.n or W.n, args.window or W.T, args.shift or W.p
+        W = dataclasses.replace(W, name=f"n{n}_d{W.d}_b{W.b}_T{T}_p{p}" + ("_ica" if W.kind == "ica_mix" else ""),
+                                n=n, T=T, p=p, length=max(W.length, T + 64 * p))
     if args.impl == "reference":
         # the oracle runs on the host cores of rank 0 only
         run_reference(args, W, rank)

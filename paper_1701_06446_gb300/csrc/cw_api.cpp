@@ -169,6 +169,7 @@ struct cumwin_s {
     CumArgs cum[kMaxOrder + 1]{};
     CumArgs* cum_dev = nullptr;
     CumLaunch cum_launch[kMaxOrder + 1] = {};
+    int canon_units[kMaxOrder + 1] = {};  // units of the canonical recovery of each order (0: not used)
     FusedPlan fused;
     int parts = 0;  // norm partial slots per order
     double* normpart = nullptr;
@@ -485,6 +486,28 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             a.wblk = wb;
         }
         h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
+        // single windows: orders 5-6 with blocks of at least 256 elements compute one
+        // element per class of equal entries (CanonTables)
+        if (own_tc && s >= kCanonMinOrder && s <= kCanonMaxOrder && ipow(b, s) >= kCanonMinBlock &&
+            ipow(b, s - 1) <= 0xffff) {
+            const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup);
+            CW_TRY(h->upload((int32_t**)&a.blkpat, cn.blkpat));
+            CW_TRY(h->upload((int32_t**)&a.can_start, cn.can_start));
+            CW_TRY(h->upload((int32_t**)&a.can_off, cn.can_off));
+            CW_TRY(h->upload((int32_t**)&a.map_off, cn.map_off));
+            CW_TRY(h->upload((int32_t**)&a.can_copies, cn.can_copies));
+            CW_TRY(h->upload((int32_t**)&a.dup_start, cn.dup_start));
+            int32_t* dd = nullptr;
+            CW_TRY(h->upload(&dd, cn.dup));
+            a.dup = reinterpret_cast<const int2*>(dd);
+            CW_TRY(h->upload((int32_t**)&a.pblocks, cn.pblocks));
+            int32_t* du = nullptr;
+            CW_TRY(h->upload(&du, cn.units));
+            a.units = reinterpret_cast<const int4*>(du);
+            a.nunits = (int32_t)(cn.units.size() / 4);
+            a.canon = 1;
+            h->canon_units[s] = a.nunits;
+        }
     }
     CW_TRY(h->alloc(&h->fro2, d));
     CW_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
@@ -656,7 +679,8 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
 // folded into the sums first (CumArgs::accum; 0 = it is not).  Returns the
 // number of launches through *launches.
 int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_launch, const NormArgs* norm_dev,
-            int nwin, int d, int64_t advance, int accum, int sm_count, cudaStream_t st, int64_t* launches)
+            int nwin, int d, int64_t advance, int accum, int sm_count, cudaStream_t st, int64_t* launches,
+            const int* canon_units = nullptr)
 {
     const CumArgs* args = cum_dev + (size_t)accum * (kMaxOrder + 1) * nwin;
     int s0 = 1;
@@ -678,12 +702,23 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
             CW_TRY(launch_split(args, nwin, s_hi, maxE, sm_count, st));
             *launches += 1;
         }
-        if (accum != 0) {  // windows whose top order is s fold it in one linear pass first
+        const bool canon = canon_units != nullptr && canon_units[s] > 0;
+        // the top order (workspace order) and canonical orders are folded first, except a
+        // canonical top order, which k_canon folds at its canonical elements
+        if (accum != 0 && !(canon && s == d)) {
             CW_TRY(launch_fold_linear(args + (size_t)s * nwin, nwin, fp.emax[s], sm_count, st));
             *launches += 1;
         }
-        CW_TRY(launch_cumulants(s, args + (size_t)s * nwin, nwin, cum_launch[s], st));
-        *launches += 1;
+        if (canon) {  // one window, canonical elements
+            // grids within the order's norm partial slots (gx * gy of its launch shape)
+            const int slots = cum_launch[s].gx * cum_launch[s].gy;
+            CW_TRY(launch_canon(s, args + s, std::min(canon_units[s], slots), st));
+            CW_TRY(launch_canon_expand(args + s, slots, st));
+            *launches += 2;
+        } else {
+            CW_TRY(launch_cumulants(s, args + (size_t)s * nwin, nwin, cum_launch[s], st));
+            *launches += 1;
+        }
     }
     if (s0 <= d) {
         CW_TRY(launch_norm_final(norm_dev, nwin, advance, s0, st));
@@ -696,7 +731,7 @@ int run_cumulants(cumwin_t h, int64_t advance, int accum = 0, int parity = 0, cu
 {
     cudaStream_t st = on != nullptr ? on : h->stream;
     const int rc = recover(h->fused, h->cum_dev + (size_t)parity * kAccModes * (kMaxOrder + 1), h->cum_launch,
-                           h->norm_dev, 1, h->d, advance, accum, h->sm_count, st, &h->launches);
+                           h->norm_dev, 1, h->d, advance, accum, h->sm_count, st, &h->launches, h->canon_units);
     if (rc) return rc;
     if (h->mark(3, st) != nullptr) h->timed++;
     return CUMWIN_OK;
@@ -956,7 +991,52 @@ int cumwin_selftest_tables(int n, int b, int s)
     }
     for (int64_t e = 0; e < E; ++e)
         if (hits[e] != 1 || whits[e] != 1) return 3;
-    // 2. cumulant tables: sub-block lookups of a synthetic symmetric tensor
+    // 2. canonical tables: the canonical offset of every stored element holds the
+    //    same multiset of variables, is its own canonical offset, appears once in
+    //    its pattern's list, and the units cover every (block, canonical element)
+    //    of every pattern exactly once
+    if (s >= 2 && E <= (int64_t)1 << 22) {
+        const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup);
+        const std::vector<int> blocks = enumerate_sorted(nbar, s);
+        const int64_t nb = (int64_t)blocks.size() / s;
+        int64_t canon = 0;
+        std::vector<int> seen(E, 0);
+        for (size_t u = 0; u < cn.units.size(); u += 4) {
+            const int q = cn.units[u], sl = cn.units[u + 1], g = cn.units[u + 2], cnt = cn.units[u + 3];
+            const int c0 = cn.can_start[q] + sl * kCanonSlice;
+            const int c1 = std::min(cn.can_start[q + 1], c0 + kCanonSlice);
+            for (int k = 0; k < cnt; ++k) {
+                const int blk = cn.pblocks[g + k];
+                if (cn.blkpat[blk] != q) return 7;
+                for (int c = c0; c < c1; ++c) seen[(int64_t)blk * bs + cn.can_off[c]]++;
+            }
+        }
+        for (int64_t q = 0; q < nb; ++q) {
+            const int* j = &blocks[q * s];
+            const int pat = cn.blkpat[q];
+            for (int64_t o = 0; o < bs; ++o) {
+                const int64_t co = cn.map_off[(size_t)pat * bs + o];
+                if (co < 0 || co >= bs || cn.map_off[(size_t)pat * bs + co] != co) return 8;
+                int va[kMaxOrder], vb[kMaxOrder];
+                int64_t ra = o, rb = co;
+                for (int k = s - 1; k >= 0; --k) {
+                    va[k] = j[k] * b + (int)(ra % b);
+                    vb[k] = j[k] * b + (int)(rb % b);
+                    ra /= b;
+                    rb /= b;
+                }
+                std::sort(va, va + s);
+                std::sort(vb, vb + s);
+                for (int k = 0; k < s; ++k)
+                    if (va[k] != vb[k]) return 9;
+                const int64_t e = q * bs + o;
+                if ((co == o) != (seen[e] == 1) || seen[e] > 1) return 10;
+                canon += co == o;
+            }
+        }
+        if (canon != cn.canonical) return 11;
+    }
+    // 3. cumulant tables: sub-block lookups of a synthetic symmetric tensor
     //    f(i) = prod_k (i_k + 1.5) return f of the sub-multi-index.
     if (s >= 2) {
         CumTables ct = build_cum_tables(n, b, s);

@@ -110,8 +110,28 @@ struct CumArgs {
     float2* C2[kMaxOrder + 1];
     float2* S2[kMaxOrder + 1];
     int32_t split, twoword;
+    // Canonical recovery (CanonTables, cw_layout.h): C_s is computed once per
+    // class of entries that super-symmetry makes equal, at the canonical
+    // in-block offset, then copied to the other offsets of its block; canon = 0
+    // when the order uses the per-element path.
+    const int32_t* blkpat;
+    const int32_t* can_start;
+    const int32_t* can_off;
+    const int32_t* map_off;
+    const int32_t* can_copies;
+    const int32_t* dup_start;
+    const int2* dup;
+    const int32_t* pblocks;
+    const int4* units;
+    int32_t nunits, canon;
 };
 constexpr int kTwoWordMinOrder = 5;
+// Orders with the canonical recovery (when b^s >= kCanonMinBlock, single windows).
+constexpr int kCanonMinOrder = 5;
+constexpr int kCanonMaxOrder = 6;
+constexpr int kCanonMinBlock = 256;
+constexpr int kCanonSlice = 256;  // threads of a unit (one canonical element each)
+constexpr int kCanonGroup = 8;    // blocks of a unit
 
 // Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
 // trailing indices, seeding, compaction over sorted tuples, and dL/dX.
@@ -158,8 +178,17 @@ CumLaunch plan_cumulants(int s, int bs, int64_t nblocks, int sm_count);
 // Recovery of order s for nwin windows at once (args_dev[w] for window w;
 // windows without order s have E = 0).
 cudaError_t launch_cumulants(int s, const CumArgs* args_dev, int nwin, const CumLaunch& L, cudaStream_t st);
-// Fold of the workspace into sums kept in workspace order (args with sgemm),
-// one linear pass per window; others are skipped.
+// Canonical recovery of order s (kCanonMinOrder..kCanonMaxOrder): the
+// canonical elements with their norm partials (grid CTAs over the order's
+// units, one partial each; grid <= the order's norm partial slots) and, for
+// the top order, the fold of the shift's batch sums at those elements; then
+// the copies to the other offsets of every block (and their two-word copies
+// for orders below d).
+cudaError_t launch_canon(int s, const CumArgs* args_dev, int grid, cudaStream_t st);
+cudaError_t launch_canon_expand(const CumArgs* args_dev, int grid, cudaStream_t st);
+// Fold of the workspace into the sums of orders that are folded before their
+// recovery runs (sums kept in workspace order, and canonical orders), one
+// linear pass per window; others are skipped.
 cudaError_t launch_fold_linear(const CumArgs* args_dev, int nwin, int64_t maxE, int sm_count, cudaStream_t st);
 // Per-CTA partials of sum multiplicity * |C_s|^k (nparts CTAs).
 cudaError_t launch_knorm(const CumArgs* args_dev, int64_t E, double k, double* partials, int nparts, cudaStream_t st);

@@ -232,4 +232,90 @@ CumTables build_cum_tables(int n, int b, int s)
     return t;
 }
 
+CanonTables build_canon_tables(int n, int b, int s, int slice, int group)
+{
+    CanonTables t;
+    const int nbar = (n + b - 1) / b;
+    const int64_t bs = ipow(b, s);
+    t.s = s;
+    t.bs = (int)bs;
+    const std::vector<int> blocks = enumerate_sorted(nbar, s);
+    const int64_t nb = (int64_t)blocks.size() / s;
+    // patterns: run-length compositions of s, as bit masks of "same block as the
+    // previous position" (bit k set: j[k] == j[k-1])
+    std::vector<int> pat_of_mask(1 << kMaxOrder, -1), masks;
+    t.blkpat.resize(nb);
+    for (int64_t q = 0; q < nb; ++q) {
+        const int* j = &blocks[q * s];
+        int m = 0;
+        for (int k = 1; k < s; ++k)
+            if (j[k] == j[k - 1]) m |= 1 << k;
+        if (pat_of_mask[m] < 0) {
+            pat_of_mask[m] = (int)masks.size();
+            masks.push_back(m);
+        }
+        t.blkpat[q] = pat_of_mask[m];
+    }
+    t.npat = (int)masks.size();
+    t.can_start.assign(t.npat + 1, 0);
+    t.map_off.assign((size_t)t.npat * bs, 0);
+    std::vector<int64_t> count(t.npat, 0);
+    for (int64_t q = 0; q < nb; ++q) count[t.blkpat[q]]++;
+    for (int q = 0; q < t.npat; ++q) {
+        const int m = masks[q];
+        t.can_start[q] = (int32_t)t.can_off.size();
+        int dig[kMaxOrder];
+        for (int64_t o = 0; o < bs; ++o) {
+            int64_t rem = o;
+            for (int k = s - 1; k >= 0; --k) {
+                dig[k] = (int)(rem % b);
+                rem /= b;
+            }
+            // sort the digits inside each run (positions k-1, k with bit k set)
+            for (int k0 = 0; k0 < s;) {
+                int k1 = k0 + 1;
+                while (k1 < s && ((m >> k1) & 1)) ++k1;
+                std::sort(dig + k0, dig + k1);
+                k0 = k1;
+            }
+            int64_t co = 0;
+            for (int k = 0; k < s; ++k) co = co * b + dig[k];
+            t.map_off[(size_t)q * bs + o] = (int32_t)co;
+            if (co == o) t.can_off.push_back((int32_t)o);
+        }
+        t.can_start[q + 1] = (int32_t)t.can_off.size();
+        // copies per canonical offset, and the non-canonical offsets with their source
+        t.dup_start.push_back((int32_t)(t.dup.size() / 2));
+        std::vector<int32_t> copies(bs, 0);
+        for (int64_t o = 0; o < bs; ++o) {
+            const int32_t co = t.map_off[(size_t)q * bs + o];
+            copies[co]++;
+            if (co != o) {
+                t.dup.push_back((int32_t)o);
+                t.dup.push_back(co);
+            }
+        }
+        for (int c = t.can_start[q]; c < t.can_start[q + 1]; ++c) t.can_copies.push_back(copies[t.can_off[c]]);
+        t.canonical += count[q] * (t.can_start[q + 1] - t.can_start[q]);
+    }
+    t.dup_start.push_back((int32_t)(t.dup.size() / 2));
+    // blocks grouped by pattern, and the work units
+    std::vector<int64_t> pstart(t.npat + 1, 0);
+    for (int q = 0; q < t.npat; ++q) pstart[q + 1] = pstart[q] + count[q];
+    t.pblocks.resize(nb);
+    std::vector<int64_t> fill(pstart.begin(), pstart.end() - 1);
+    for (int64_t q = 0; q < nb; ++q) t.pblocks[fill[t.blkpat[q]]++] = (int32_t)q;
+    for (int q = 0; q < t.npat; ++q) {
+        const int nc = t.can_start[q + 1] - t.can_start[q];
+        for (int sl = 0; sl * slice < nc; ++sl)
+            for (int64_t g = pstart[q]; g < pstart[q + 1]; g += group) {
+                t.units.push_back(q);
+                t.units.push_back(sl);
+                t.units.push_back((int32_t)g);
+                t.units.push_back((int32_t)std::min<int64_t>(group, pstart[q + 1] - g));
+            }
+    }
+    return t;
+}
+
 }  // namespace cw

@@ -50,6 +50,28 @@ struct CumTables {
 };
 CumTables build_cum_tables(int n, int b, int s);
 
+// Canonical elements of order s (the recovery computes one element per class
+// of entries that super-symmetry makes equal).  A block j whose sorted block
+// indices form runs of equal values (lengths r_1..r_k, its "pattern") stores,
+// for in-block digits that differ only by a permutation inside a run, the same
+// tensor entry several times (Section 2.3 keeps diagonal blocks whole).  The
+// canonical offset of a class has its digits non-decreasing inside every run.
+struct CanonTables {
+    int s = 0, bs = 0, npat = 0;
+    std::vector<int32_t> blkpat;     // [nblocks] pattern of each block
+    std::vector<int32_t> can_start;  // [npat + 1] canonical offsets of pattern q at can_off[can_start[q]..]
+    std::vector<int32_t> can_off;    // canonical in-block offsets, increasing, per pattern
+    std::vector<int32_t> map_off;    // [npat][bs] canonical offset of each in-block offset
+    std::vector<int32_t> can_copies; // per canonical offset: the offsets of its block holding the same entry
+    std::vector<int32_t> dup_start;  // [npat + 1] non-canonical offsets of pattern q at dup[dup_start[q]..]
+    std::vector<int32_t> dup;        // pairs {offset, its canonical offset}, per pattern
+    std::vector<int32_t> pblocks;    // block ranks grouped by pattern (pattern order, then rank)
+    std::vector<int32_t> units;      // [nunits][4] {pattern, slice, first index into pblocks, blocks}
+    int64_t canonical = 0;           // canonical elements of the order (all blocks)
+};
+// Units of `slice` threads x up to `group` blocks of one pattern.
+CanonTables build_canon_tables(int n, int b, int s, int slice, int group);
+
 // Split of order s into row factors (h) and column factors (s - h).
 inline int split_rows(int s) { return (s + 1) / 2; }
 

@@ -806,15 +806,178 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
         }
 }
 
-// Fold of orders whose sums are in workspace order (the top order of windows
-// whose recovery is not fused): one linear coalesced pass per window.
+// Fold of the orders that take the shift's workspace before their recovery
+// runs: sums in workspace order (the top order of windows whose recovery is
+// not fused) in one linear coalesced pass, and canonical orders whose sums are
+// in the block layout element by element through the slot table.
 __global__ void __launch_bounds__(NT) k_fold_linear(const CumArgs* __restrict__ args)
 {
     const CumArgs& a = args[blockIdx.y];
-    if (a.E == 0 || !a.accum || !a.sgemm) return;
+    // (a canonical top order takes its batch sums inside k_canon, at its canonical elements)
+    if (a.E == 0 || !a.accum || !(a.sgemm || a.canon) || (a.sgemm && a.canon)) return;
     const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
-    for (int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x; w < a.E; w += (int64_t)gridDim.x * NT)
-        fold_store(fold_load_at(a, w, w, fslot));
+    for (int64_t w = (int64_t)blockIdx.x * NT + threadIdx.x; w < a.E; w += (int64_t)gridDim.x * NT) {
+        if (a.sgemm) {
+            fold_store(fold_load_at(a, w, w, fslot));
+        } else {
+            const int64_t blk = w / a.bs;
+            fold_elem(a, blk, (int)(w - blk * a.bs), w, fslot);
+        }
+    }
+}
+
+// Canonical recovery, pass 1.  A unit is (pattern, slice, up to kCanonGroup
+// blocks of that pattern): thread k of the unit owns canonical element
+// slice * NT + k of the pattern, i.e. one in-block offset whose digits are
+// non-decreasing inside every run of equal block indices; its per-subset
+// operand offsets (packed 16 + 16 bits) are formed when the (pattern, slice)
+// changes, the blocks' operand addresses are staged per unit, and each owned
+// element of each block is recovered (the subset recursion, two-word products
+// in the mixed forms) and written at its own, canonical, position.  The top
+// order (sums in workspace order) first takes the shift's batch sums there:
+// its sums and FIFO are only ever read at canonical elements.  The norm
+// partial weights each element by its block's multiplicity and by the number
+// of offsets of its block that hold the same entry, so it is the sum over all
+// stored elements.  Each CTA takes a contiguous run of units, so the
+// (pattern, slice) changes rarely.
+template <int S>
+__global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ args)
+{
+    constexpr int NS = Subsets<S>::N;
+    constexpr int GB = kCanonGroup;
+    __shared__ double red[NT / 32];
+    const CumArgs& a = *args;
+    extern __shared__ ulonglong2 dyn[];  // [GB][NS] operand address pairs, then [NS][NT] offsets
+    ulonglong2* ptrs = dyn;
+    int* offs = reinterpret_cast<int*>(dyn + GB * NS);
+    const int b = a.b;
+    const bool tw = a.twoword != 0;
+    const bool fold = a.accum != 0 && a.sgemm;
+    const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
+    const int per = (a.nunits + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int u0 = min(a.nunits, (int)blockIdx.x * per), u1 = min(a.nunits, u0 + per);
+    int cur_q = -1, cur_sl = -1, off = 0;
+    double copies = 0.0;
+    bool valid = false;
+    double local = 0.0;
+    for (int u = u0; u < u1; ++u) {
+        const int4 U = a.units[u];  // {pattern, slice, first index into pblocks, blocks}
+        __syncthreads();            // the previous unit's readers of ptrs / offs are done
+        if (U.x != cur_q || U.y != cur_sl) {
+            cur_q = U.x;
+            cur_sl = U.y;
+            const int c = cur_sl * NT + (int)threadIdx.x;
+            const int c0 = a.can_start[cur_q], c1 = a.can_start[cur_q + 1];
+            valid = c0 + c < c1;
+            off = valid ? a.can_off[c0 + c] : 0;
+            copies = valid ? (double)a.can_copies[c0 + c] : 0.0;
+            int dig[S];
+            int rem = off;
+#pragma unroll
+            for (int k = S - 1; k >= 0; --k) {
+                const int q = rem / b;
+                dig[k] = rem - q * b;
+                rem = q;
+            }
+            for (int t = 0; t < NS; ++t) {
+                const unsigned mask = 2u * t + 1u;
+                int oa = 0, orr = 0;
+#pragma unroll
+                for (int k = 0; k < S; ++k) {
+                    if ((mask >> k) & 1u) oa = oa * b + dig[k];
+                    else orr = orr * b + dig[k];
+                }
+                offs[t * NT + threadIdx.x] = (oa << 16) | orr;  // both < b^{S-1} <= 2^16
+            }
+        }
+        for (int i = threadIdx.x; i < U.w * NS; i += NT) {
+            const int jg = i / NS, t = i - jg * NS;
+            const int64_t blk = a.pblocks[U.z + jg];
+            const int2 q = *reinterpret_cast<const int2*>(a.subrank + ((size_t)blk * NS + t) * 2);
+            const int la = __popc(2u * t + 1u), lr = S - la;
+            const char* ca = tw ? (const char*)a.C2[la] : (const char*)a.C[la];
+            const char* sr = tw ? (const char*)a.S2[lr] : (const char*)a.S[lr];
+            ptrs[i] = make_ulonglong2((unsigned long long)(ca + (size_t)q.x * ipow_c(b, la) * 8),
+                                      (unsigned long long)(sr + (size_t)q.y * ipow_c(b, lr) * 8));
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int jg = 0; jg < U.w; ++jg) {
+            const int64_t blk = a.pblocks[U.z + jg];
+            const int64_t e = blk * a.bs + off;
+            double sv;
+            if (a.sgemm) {
+                const int64_t w = wslot(a, blk, off);
+                if (fold) {
+                    FoldVal fv = fold_load_at(a, w, w, fslot);
+                    fold_store(fv);
+                    sv = fv.s + (f32_to_f64(fv.din) - f32_to_f64(fv.dout));
+                } else {
+                    sv = a.S[S][w];
+                }
+            } else {
+                sv = a.S[S][e];  // folded before (k_fold_linear), every element
+            }
+            const ulonglong2* pp = ptrs + jg * NS;
+            double cv;
+            if (tw) {
+                float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
+                for (int t = 0; t < NS; ++t) {
+                    const ulonglong2 pr = pp[t];
+                    const int packed = offs[t * NT + threadIdx.x];
+                    const float2 cA = reinterpret_cast<const float2*>(pr.x)[packed >> 16];
+                    const float2 sR = reinterpret_cast<const float2*>(pr.y)[packed & 0xffff];
+                    tw_acc_prod(hi, lo, cA, sR);
+                }
+                cv = div_T(a, sv - (f32_to_f64(hi) + f32_to_f64(lo)));
+            } else {
+                double acc = sv;
+#pragma unroll 4
+                for (int t = 0; t < NS; ++t) {
+                    const ulonglong2 pr = pp[t];
+                    const int packed = offs[t * NT + threadIdx.x];
+                    acc = fma(-reinterpret_cast<const double*>(pr.x)[packed >> 16],
+                              reinterpret_cast<const double*>(pr.y)[packed & 0xffff], acc);
+                }
+                cv = div_T(a, acc);
+            }
+            a.Cout[e] = cv;
+            if (a.split) {
+                a.C2[S][e] = tw_split(cv);
+                a.S2[S][e] = tw_split(sv);
+            }
+            local = fma(a.mult[blk] * copies * cv, cv, local);
+        }
+    }
+    const double z = cta_sum(local, red);
+    if (threadIdx.x == 0) a.normpart[blockIdx.x] = z;
+}
+
+// Canonical recovery, pass 2: in every block whose pattern has repeated
+// block indices, each non-canonical offset takes the value of its canonical
+// offset (the same tensor entry), and orders below d write their two-word
+// copies there too.  One block per CTA at a time, threads over the pattern's
+// list of non-canonical offsets.
+__global__ void __launch_bounds__(NT) k_canon_expand(const CumArgs* __restrict__ args)
+{
+    const CumArgs& a = *args;
+    const int64_t nblocks = a.E / a.bs;
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int q = a.blkpat[blk];
+        const int d0 = a.dup_start[q], d1 = a.dup_start[q + 1];
+        double* C = a.Cout + blk * a.bs;
+        for (int i = d0 + (int)threadIdx.x; i < d1; i += NT) {
+            const int2 oc = a.dup[i];  // {offset, canonical offset}
+            const double v = C[oc.y];
+            C[oc.x] = v;
+            if (a.split) {
+                const int64_t e = blk * a.bs + oc.x;
+                a.C2[a.s][e] = tw_split(v);
+                a.S2[a.s][e] = tw_split(a.S[a.s][e]);
+            }
+        }
+    }
 }
 
 // Two-word copies of C_k and S_k for the orders k <= s_hi recovered below
@@ -837,7 +1000,9 @@ __global__ void __launch_bounds__(NT) k_gather_sums(const CumArgs* __restrict__ 
     const CumArgs& a = *args;
     for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < a.E; e += (int64_t)gridDim.x * NT) {
         const int64_t blk = e / a.bs;
-        out[e] = a.S[a.s][wslot(a, blk, (int)(e - blk * a.bs))] * scale;
+        int off = (int)(e - blk * a.bs);
+        if (a.canon) off = a.map_off[(int64_t)a.blkpat[blk] * a.bs + off];  // sums kept at canonical elements
+        out[e] = a.S[a.s][wslot(a, blk, off)] * scale;
     }
 }
 
@@ -1052,6 +1217,35 @@ cudaError_t launch_gather_sums(const CumArgs* args_dev, int64_t E, double scale,
     const int64_t need = (E + NT - 1) / NT;
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(need, 16384));
     k_gather_sums<<<gx, NT, 0, st>>>(args_dev, scale, out);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_canon_s(const CumArgs* args_dev, int grid, cudaStream_t st)
+{
+    constexpr int NS = Subsets<S>::N;
+    const size_t smem = sizeof(ulonglong2) * kCanonGroup * NS + sizeof(int) * (size_t)NS * NT;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = smem_opt_in((const void*)k_canon<S>, smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_canon<S><<<grid, NT, smem, st>>>(args_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_canon(int s, const CumArgs* args_dev, int grid, cudaStream_t st)
+{
+    static_assert(kCanonSlice == NT, "a unit is one CTA");
+    switch (s) {
+    case 5: return launch_canon_s<5>(args_dev, grid, st);
+    case 6: return launch_canon_s<6>(args_dev, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_canon_expand(const CumArgs* args_dev, int grid, cudaStream_t st)
+{
+    k_canon_expand<<<grid, NT, 0, st>>>(args_dev);
     return cudaGetLastError();
 }
 

@@ -382,3 +382,31 @@ def test_estimators_enqueue_match_norms(precision):
     ofro, onu = oracle.norms(X[3 * W.p:], W.d)
     tol = 1e-10 if precision == "fp64" else 1e-3
     np.testing.assert_allclose(nu_h.numpy()[2:], onu[2:], rtol=tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+@pytest.mark.parametrize("n,d,b", [(10, 6, 4), (9, 5, 4), (7, 6, 3)])
+def test_canonical_orders_are_exactly_symmetric(n, d, b, precision):
+    """Orders 5-6 with blocks of >= 256 elements are recovered once per class of
+    entries that super-symmetry makes equal and copied to the permuted offsets of
+    diagonal blocks: the full tensor is then bitwise invariant under every
+    permutation of its indices, and matches the oracle."""
+    import itertools
+    T, p = 400, 50
+    rng = np.random.default_rng(7 * n + d + b)
+    X = (rng.standard_t(6, size=(T + 3 * p, n)) @ rng.standard_normal((n, n)) / np.sqrt(n) + 0.2)
+    X = X.astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p, precision) as h:
+        h.fill(Xd[:T])
+        for w in range(3):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        ref = oracle.cumulants(X[3 * p:], d, b)
+        tol = TOL_FP64 if precision == "fp64" else 1e-3
+        for s in (5, 6):
+            if s > d:
+                continue
+            full = h.full(s).cpu().numpy()
+            for perm in itertools.permutations(range(s)):
+                assert np.array_equal(full, full.transpose(perm)), (s, perm)
+            assert rel_fro(h.cumulants(s).cpu().numpy(), ref[s - 1]) <= tol, s
