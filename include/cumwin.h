@@ -290,6 +290,27 @@ int cumwin_recompute(cumwin_t h);
  * cumwin_recompute.  Asynchronous; errors: EINVAL, ESTATE. */
 int cumwin_recenter(cumwin_t h);
 
+/*
+ * Automatic re-centring (mixed forms; not in the paper).  The moments are
+ * accumulated about the shift vector fixed at cumwin_fill; when the stream's
+ * mean moves away from it, the raw-moment cancellation in the recovery grows
+ * (cumwin_recenter).  With limit > 0, every recovery of orders 1-2 measures
+ * the drift r = max_i |mean_i - shift_i| / sqrt(C_2[i,i]) on the device and,
+ * when r > limit, raises a flag in mapped host memory.  Each eager cumwin_push
+ * (not one under stream capture) first waits for the recovery of the push two
+ * before it, so that the flag lags the stream by at most two shifts and the
+ * host runs at most two shifts ahead of the device; when the flag is up it
+ * waits for the pending recoveries and re-centres before its shift.  limit = 0
+ * turns it off (the default).  Synchronises.
+ * Errors: EINVAL (limit < 0 or not finite, d < 2), ENOTSUP (FP64 form).
+ */
+int cumwin_set_auto_recenter(cumwin_t h, double limit);
+
+/* The drift ratio r of the last recovery that measured it (NaN before any;
+ * measured only while automatic re-centring is on) and the number of
+ * automatic re-centrings so far.  Either pointer may be NULL.  Synchronises. */
+int cumwin_drift(cumwin_t h, double* ratio_host, int64_t* recenters);
+
 /* Copy the current window, oldest sample first, T x n FP32 row-major (ld = n). */
 int cumwin_window(cumwin_t h, float* out_dev);
 

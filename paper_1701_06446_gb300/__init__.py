@@ -247,6 +247,19 @@ class CumWin:
         self._sync_stream()
         check(self.lib.cumwin_recenter(self._h), "cumwin_recenter")
 
+    def set_auto_recenter(self, limit: float):
+        """Re-centre automatically when the mean drifts more than `limit` standard
+        deviations from the shift (cumwin_set_auto_recenter; 0 turns it off)."""
+        self._sync_stream()
+        check(self.lib.cumwin_set_auto_recenter(self._h, ctypes.c_double(limit)), "cumwin_set_auto_recenter")
+
+    def drift(self) -> tuple[float, int]:
+        """(last measured drift ratio, automatic re-centrings so far) (cumwin_drift)."""
+        r, k = ctypes.c_double(), ctypes.c_int64()
+        self._sync_stream()
+        check(self.lib.cumwin_drift(self._h, ctypes.byref(r), ctypes.byref(k)), "cumwin_drift")
+        return r.value, k.value
+
     def window(self) -> torch.Tensor:
         out = torch.empty(self.T, self.n, dtype=torch.float32, device=self.device)
         self._sync_stream()

@@ -69,6 +69,8 @@ SIGNATURES = {
     "cumwin_set_allocator": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_estimators_enqueue": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "cumwin_loss": (c_int, [c_vp, c_vp, c_vp]),
+    "cumwin_set_auto_recenter": (c_int, [c_vp, c_double]),
+    "cumwin_drift": (c_int, [c_vp, c_vp, c_vp]),
     "cumwin_device_bytes": (c_i64, [c_vp]),
 }
 

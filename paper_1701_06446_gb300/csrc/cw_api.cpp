@@ -181,6 +181,15 @@ struct cumwin_s {
     // cumwin_marginals (the storage indices of the diagonal entries i..i of
     // orders 2..min(d, 4) and the gathered values), allocated at create
     double* knorm_parts = nullptr;
+    // drift of the mean from the shift (cumwin_set_auto_recenter): the last
+    // measured ratio (device) and a flag the recovery raises in mapped host memory
+    double* drift = nullptr;
+    int* drift_host = nullptr;   // pinned, mapped
+    int* drift_flag_dev = nullptr;
+    double drift_limit = 0.0;    // 0: not measured
+    int64_t recenters = 0;
+    cudaEvent_t ev_drift[2] = {nullptr, nullptr};  // after the recoveries of the last two pushes
+    int64_t pushes = 0;
     double* est = nullptr;  // [2d]: ||C_s|| and nu_s staged by cumwin_estimators_enqueue
     int64_t* diag_idx = nullptr;
     double* diag_val = nullptr;
@@ -244,9 +253,14 @@ struct cumwin_s {
                 *q = nullptr;
             }
         mem.release();
+        if (drift_host != nullptr) {
+            cudaFreeHost(drift_host);
+            drift_host = nullptr;
+        }
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         ev.clear();
-        for (cudaEvent_t* e : {&ev_gemm, &ev_rec[0], &ev_rec[1], &ev_h2d[0], &ev_h2d[1], &ev_staged[0], &ev_staged[1]})
+        for (cudaEvent_t* e : {&ev_gemm, &ev_rec[0], &ev_rec[1], &ev_h2d[0], &ev_h2d[1], &ev_staged[0], &ev_staged[1],
+                               &ev_drift[0], &ev_drift[1]})
             if (*e != nullptr) {
                 cudaEventDestroy(*e);
                 *e = nullptr;
@@ -513,6 +527,8 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     CW_TRY(cudaMemset(h->fro2, 0, sizeof(double) * d));
     CW_TRY(h->alloc(&h->knorm_parts, (size_t)kKnormParts * d));
     CW_TRY(h->alloc(&h->est, (size_t)2 * d));
+    CW_TRY(h->alloc(&h->drift, 1));
+    CW_TRY(cudaMemset(h->drift, 0xff, sizeof(double)));  // NaN until measured
     {
         const int dm = std::min(d, 4);
         std::vector<int64_t> idx((size_t)std::max(dm - 1, 1) * n, 0);
@@ -590,6 +606,13 @@ int window_finish(cumwin_s* h, int parts, const TcPlan* tc, int index)
     na.T = h->T;
     na.parts = parts;
     na.d = h->d;
+    na.C1 = h->C[1];
+    na.C2 = h->d >= 2 ? h->C[2] : nullptr;
+    na.drift = h->drift;
+    na.drift_flag = nullptr;  // measured once cumwin_set_auto_recenter enables it
+    na.n = h->n;
+    na.b = h->b;
+    na.nbar = h->nbar;
     CW_TRY(h->mem.upload(&h->norm_dev, &na, 1));
     return CUMWIN_OK;
 }
@@ -1214,6 +1237,23 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
         g_last_error = "the mixed forms accept shifts of at most the nominal p given at create";
         return CUMWIN_EINVAL;
     }
+    const bool drift_on = h->drift_host != nullptr && h->drift_limit > 0.0 && !capturing(h->stream);
+    if (drift_on) {
+        // the flag of the recovery two pushes back is in place once its event completes: the
+        // host runs at most two shifts ahead of the device while the policy is on
+        if (h->pushes >= 2) CW_TRY(cudaEventSynchronize(h->ev_drift[h->pushes & 1]));
+        if (*(volatile int*)h->drift_host != 0) {
+            // a recovery found the mean drifted from the shift: re-centre before this shift
+            // (after the pending recoveries, so that none of them raises the flag again)
+            CW_TRY(join(h));
+            if (h->rstream != nullptr) CW_TRY(cudaStreamSynchronize(h->rstream));
+            CW_TRY(cudaStreamSynchronize(h->stream));
+            *(volatile int*)h->drift_host = 0;
+            const int rr = cumwin_recenter(h);
+            if (rr) return rr;
+            h->recenters++;
+        }
+    }
     int accum = 0;
     const bool pipe = pipelined(h);
     const int q = pipe ? h->par : 0;
@@ -1222,7 +1262,12 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
     if (rc) return rc;
     if (!pipe) {
         CW_TRY(join(h));
-        return run_cumulants(h, p, accum);
+        rc = run_cumulants(h, p, accum);
+        if (rc == CUMWIN_OK && drift_on) {
+            CW_TRY(cudaEventRecord(h->ev_drift[h->pushes & 1], h->stream));
+            h->pushes++;
+        }
+        return rc;
     }
     // the recovery of this shift on the recovery stream, after its GEMM
     CW_TRY(cudaEventRecord(h->ev_gemm, h->stream));
@@ -1230,6 +1275,10 @@ int cumwin_push(cumwin_t h, const float* x_in_dev, const float* x_out_dev, int p
     rc = run_cumulants(h, p, accum, q, h->rstream);
     if (rc) return rc;
     CW_TRY(cudaEventRecord(h->ev_rec[q], h->rstream));
+    if (drift_on) {
+        CW_TRY(cudaEventRecord(h->ev_drift[h->pushes & 1], h->rstream));
+        h->pushes++;
+    }
     h->pend[q] = true;
     h->last = q;
     h->par ^= 1;
@@ -1289,6 +1338,44 @@ int cumwin_loss(cumwin_t h, const double* w_host, double* L_dev)
     a.d = h->d;
     for (int s = 1; s <= h->d; ++s) a.w[s] = w_host[s];
     CW_TRY(launch_estimators(h->fro2, a, h->stream));
+    return CUMWIN_OK;
+}
+
+int cumwin_set_auto_recenter(cumwin_t h, double limit)
+{
+    if (h == nullptr || !(limit >= 0.0) || !std::isfinite(limit)) return CUMWIN_EINVAL;
+    if (h->prec == CUMWIN_FP64) {
+        g_last_error = "the FP64 form accumulates raw moments without a shift";
+        return CUMWIN_ENOTSUP;
+    }
+    if (h->d < 2) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
+    CW_TRY(cudaStreamSynchronize(h->stream));
+    if (limit > 0.0 && h->drift_host == nullptr) {
+        CW_TRY(cudaHostAlloc((void**)&h->drift_host, sizeof(int), cudaHostAllocMapped));
+        CW_TRY(cudaHostGetDevicePointer((void**)&h->drift_flag_dev, h->drift_host, 0));
+        for (cudaEvent_t& e : h->ev_drift) CW_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    h->pushes = 0;
+    if (h->drift_host != nullptr) *(volatile int*)h->drift_host = 0;
+    h->drift_limit = limit;
+    NormArgs na{};
+    CW_TRY(cudaMemcpy(&na, h->norm_dev, sizeof(NormArgs), cudaMemcpyDeviceToHost));
+    na.drift_flag = limit > 0.0 ? h->drift_flag_dev : nullptr;
+    na.drift_limit = limit;
+    CW_TRY(cudaMemcpy(h->norm_dev, &na, sizeof(NormArgs), cudaMemcpyHostToDevice));
+    return CUMWIN_OK;
+}
+
+int cumwin_drift(cumwin_t h, double* ratio_host, int64_t* recenters)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    CW_TRY(join(h));
+    if (ratio_host != nullptr) {
+        CW_TRY(cudaMemcpyAsync(ratio_host, h->drift, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CW_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (recenters != nullptr) *recenters = h->recenters;
     return CUMWIN_OK;
 }
 

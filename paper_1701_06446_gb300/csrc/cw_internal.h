@@ -209,6 +209,16 @@ struct NormArgs {
     int64_t* head_stage;  // ring head of the staging, advanced too when not null (FP64 form)
     int64_t T;
     int32_t parts, d;
+    // Drift of the stream's mean from the shift vector (mixed forms; the fused
+    // recovery measures it when drift_flag is not null): max_i |C_1[i]| /
+    // sqrt(C_2[i,i]) with C_1 about the shift, into *drift; when it exceeds
+    // drift_limit, *drift_flag (mapped host memory) is set to 1.
+    const double* C1;
+    const double* C2;
+    double* drift;
+    volatile int* drift_flag;
+    double drift_limit;
+    int32_t n, b, nbar;
 };
 // Orders s >= s_from only.  Also advances each ring head by `advance` rows
 // (mod T): the head lives in device memory so that a captured shift can be

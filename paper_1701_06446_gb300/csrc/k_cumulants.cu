@@ -797,6 +797,29 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
         z = cta_sum(z, red);
         if (threadIdx.x == 0 && s <= na.d) na.fro2[s - 1] = z;
     }
+    // the drift of the mean from the shift (single windows with a drift flag):
+    // C_1 and C_2 are complete after the barriers above; the last CTA measures it
+    if (f.nwin == 1 && DF >= 2 && blockIdx.x == gridDim.x - 1 && f.norm[0].drift_flag != nullptr) {
+        const NormArgs& na = f.norm[0];
+        double r = 0.0;
+        __syncthreads();  // red may still be read by a norm reduction of this CTA
+        for (int i = threadIdx.x; i < na.n; i += NT) {
+            const int j = i / na.b, a = i - j * na.b;
+            // diagonal block (j, j): rank j * nbar - j (j - 1) / 2, in-block offset a * b + a
+            const int64_t rk = (int64_t)j * na.nbar - (int64_t)j * (j - 1) / 2;
+            const double v = na.C2[rk * na.b * na.b + a * (na.b + 1)];
+            const double m = fabs(na.C1[i]);
+            if (v > 0.0) r = fmax(r, m / sqrt(v));
+        }
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < NT / 32; ++w) r = fmax(r, red[w]);
+            *na.drift = r;
+            if (r > na.drift_limit) *na.drift_flag = 1;
+        }
+    }
     // every CTA read the ring heads (FIFO slots) before the last barrier
     if (f.advance_heads)
         for (int w = blockIdx.x * NT + threadIdx.x; w < f.nwin; w += gridDim.x * NT) {

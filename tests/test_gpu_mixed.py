@@ -561,3 +561,47 @@ def test_push_host_matches_device_pushes(precision):
         for s in range(1, d + 1):
             assert torch.equal(hh.cumulants(s), hd.cumulants(s)), s
         assert torch.equal(hh.window(), hd.window())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", FORMS)
+def test_auto_recenter_across_the_n60_mean_switch(form):
+    """The n=60 stream switches at sample 2^19 from N(0, S) to a copula with
+    exponential(1) marginals (mean 1).  A window filled just before the switch
+    and pushed until it holds only copula samples drifts one standard deviation
+    from the shift fixed at fill; with automatic re-centring (limit 0.25) the
+    library re-centres on its own and the final window stays within the
+    workload's calibrated bounds, while the same pushes without it do not."""
+    W = WORKLOADS["n60_d4_b3_T32768_p1024"]
+    start = (1 << 19) - W.T
+    shifts = W.T // W.p + 8
+    X = W.stream().rows(start, start + W.T + shifts * W.p)
+    Xd = dev(X)
+    Xw = X[shifts * W.p:]
+    cen = oracle.center(Xw)
+    refs = {}
+    for s in range(1, W.d + 1):
+        tup = oracle.sample_sorted_tuples(W.n, s, 400, seed=900 + s)
+        refs[s] = (np.array([oracle.storage_index(W.n, W.b, t) for t in tup]),
+                   oracle.cumulant_tuples(Xw, tup, centred=cen))
+    errs = {}
+    for auto in (True, False):
+        with CumWin(W.n, W.d, W.b, W.T, W.p, form) as h:
+            if auto:
+                h.set_auto_recenter(0.25)
+            h.fill(Xd[: W.T])
+            for w in range(shifts):
+                h.push(Xd[W.T + w * W.p: W.T + (w + 1) * W.p])
+            ratio, recenters = h.drift()
+            errs[auto] = {s: rel_fro(h.cumulants(s).cpu().numpy()[refs[s][0]], refs[s][1])
+                          for s in range(1, W.d + 1)}
+            if auto:
+                assert recenters >= 1 and ratio <= 0.3, (ratio, recenters)
+                # later shifts stay exact against a fresh recomputation about the new shift
+                slide = [h.moments(s).cpu().numpy() for s in range(1, W.d + 1)]
+                h.recompute()
+                for s in range(1, W.d + 1):
+                    assert rel_fro(slide[s - 1], h.moments(s).cpu().numpy()) <= 1e-13, s
+    print("auto re-centring", form, errs)
+    check_bounds(errs[True], BOUND["n60"][form])
+    assert errs[True][4] < errs[False][4]
