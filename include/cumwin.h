@@ -118,6 +118,28 @@ int64_t cumwin_device_bytes(cumwin_t h);
 int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream,
                   cumwin_t* out);
 
+/*
+ * Block shards of one stream over several GPUs (one handle per GPU, all fed the
+ * same samples).  The stored blocks of the top order d, in lexicographic order
+ * (Section 2.3), are split into nshards contiguous ranges of nearly equal block
+ * count (cumwin_shard_blocks); shard `shard` updates (Eqs. 6-7) and recovers
+ * (Algorithms 3-4) only the blocks of its range, and its squared norm of order
+ * d is the sum over its blocks, so the norm of the whole tensor is the sum of
+ * the shards' values (an all-reduce).  Orders below d are small and are kept
+ * whole on every shard.  C_d and M_d read from a shard are valid inside its
+ * block range only.  Not in the paper (it parallelises over sub-series of the
+ * samples instead).  Needs a mixed form and d = 5 or 6 with b^d >= 256 for
+ * nshards > 1 (ENOTSUP otherwise); cumwin_grad is not available on a shard.
+ * cumwin_create is cumwin_create_shard with shard 0 of 1.
+ */
+int cumwin_create_shard(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream, int shard,
+                        int nshards, cumwin_t* out);
+/* Host only: the block range [*begin, *end) of order d owned by shard `shard` of `nshards`. */
+int cumwin_shard_blocks(int n, int b, int d, int shard, int nshards, int64_t* begin, int64_t* end);
+/* Host only: ||C_s|| = sqrt(fro2[s-1]) and nu_s (Eq. mef, NaN for s < 3) from the squared
+ * norms of orders 1..d, e.g. after summing the shards' values; either output may be NULL. */
+int cumwin_estimators_from_fro2(int d, const double* fro2_host, double* fro_host, double* nu_host);
+
 /* Free all device state.  Synchronises the handle's stream first.  NULL is a no-op. */
 int cumwin_destroy(cumwin_t h);
 

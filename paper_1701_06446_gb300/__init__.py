@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import CumwinError, check
 
 __all__ = ["CumWin", "CumWinBatch", "CumwinError", "CumulantNormLoss", "layout_size", "block_rank",
-           "element_index", "selftest_tables", "library_path"]
+           "element_index", "selftest_tables", "library_path", "shard_blocks", "estimators_from_fro2"]
 
 
 def library_path() -> str:
@@ -49,6 +49,23 @@ def selftest_tables(n: int, b: int, order: int) -> int:
     return int(_lib.load().cumwin_selftest_tables(n, b, order))
 
 
+def shard_blocks(n: int, b: int, d: int, shard: int, nshards: int) -> tuple[int, int]:
+    """Block range [begin, end) of order d owned by shard `shard` of `nshards` (cumwin_shard_blocks)."""
+    lo, hi = ctypes.c_int64(), ctypes.c_int64()
+    check(_lib.load().cumwin_shard_blocks(n, b, d, shard, nshards, ctypes.byref(lo), ctypes.byref(hi)),
+          "cumwin_shard_blocks")
+    return lo.value, hi.value
+
+
+def estimators_from_fro2(fro2) -> tuple[np.ndarray, np.ndarray]:
+    """(||C_s||, nu_s) from squared norms of orders 1..d (cumwin_estimators_from_fro2)."""
+    z = np.ascontiguousarray(np.asarray(fro2, dtype=np.float64))
+    fro, nu = np.zeros(len(z)), np.zeros(len(z))
+    check(_lib.load().cumwin_estimators_from_fro2(len(z), z.ctypes.data, fro.ctypes.data, nu.ctypes.data),
+          "cumwin_estimators_from_fro2")
+    return fro, nu
+
+
 def _dev_ptr(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
@@ -61,7 +78,7 @@ class CumWin:
     """One sliding window of an n-variate stream with cumulants of orders 1..d."""
 
     def __init__(self, n: int, d: int, b: int, T: int, p: int, precision: str = "fp64",
-                 device=None):
+                 device=None, shard: int = 0, nshards: int = 1):
         self.lib = _lib.load()
         if precision not in _lib.PRECISION:
             raise ValueError(f"precision must be one of {list(_lib.PRECISION)}")
@@ -69,12 +86,14 @@ class CumWin:
                                    else torch.device(device).index or 0)
         self.n, self.d, self.b, self.T, self.p = n, d, b, T, p
         self.precision = precision
+        self.shard, self.nshards = shard, nshards
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             self._stream = torch.cuda.current_stream(self.device).cuda_stream
-            check(self.lib.cumwin_create(n, d, b, T, p, _lib.PRECISION[precision],
-                                         ctypes.c_void_p(self._stream), ctypes.byref(self._h)),
-                  "cumwin_create")
+            check(self.lib.cumwin_create_shard(n, d, b, T, p, _lib.PRECISION[precision],
+                                               ctypes.c_void_p(self._stream), shard, nshards,
+                                               ctypes.byref(self._h)),
+                  "cumwin_create_shard")
         self.sizes = [layout_size(n, b, s) for s in range(1, d + 1)]
 
     # -- stream management ---------------------------------------------------

@@ -131,6 +131,8 @@ struct FusedPlan {
 
 struct cumwin_s {
     int n = 0, d = 0, b = 0, nbar = 0, npad = 0, prec = 0;
+    int shard = 0, nshards = 1;    // block shard of the top order (cumwin_create_shard)
+    int64_t top0 = 0, top1 = -1;   // its lexicographic block range (top1 < 0: all)
     int64_t T = 0;
     int p = 1;  // nominal shift size (batch of the mixed-form FP32 sums)
     cudaStream_t stream = nullptr;
@@ -504,7 +506,9 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         // element per class of equal entries (CanonTables)
         if (own_tc && s >= kCanonMinOrder && s <= kCanonMaxOrder && ipow(b, s) >= kCanonMinBlock &&
             ipow(b, s - 1) <= 0xffff) {
-            const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup);
+            const bool sh = s == d && h->top1 >= 0;  // a shard recovers its block range of the top order
+            const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup, sh ? h->top0 : 0,
+                                                      sh ? h->top1 : -1);
             CW_TRY(h->upload((int32_t**)&a.blkpat, cn.blkpat));
             CW_TRY(h->upload((int32_t**)&a.can_start, cn.can_start));
             CW_TRY(h->upload((int32_t**)&a.can_off, cn.can_off));
@@ -519,6 +523,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             CW_TRY(h->upload(&du, cn.units));
             a.units = reinterpret_cast<const int4*>(du);
             a.nunits = (int32_t)(cn.units.size() / 4);
+            a.npblocks = (int32_t)cn.pblocks.size();
             a.canon = 1;
             h->canon_units[s] = a.nunits;
         }
@@ -556,6 +561,8 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         ps.shift = h->shift;
         ps.status = h->status;
         ps.xoff = 0;
+        ps.top0 = h->top0;
+        ps.top1 = h->top1;
         int rc = tc_plan_create(h->tc_own, {ps}, b, p, h->sm_count, precision, h->status, true, true,
                                 [&](size_t bytes, void** q) { return h->alloc((char**)q, bytes); });
         if (rc != 0) {
@@ -939,6 +946,19 @@ const char* cumwin_strerror(int code)
 
 const char* cumwin_last_error(void) { return g_last_error.c_str(); }
 
+static void nu_from_fro(const double* fro, int d, double* nu);
+
+int cumwin_estimators_from_fro2(int d, const double* fro2_host, double* fro_host, double* nu_host)
+{
+    if (d < 1 || d > kMaxOrder || fro2_host == nullptr) return CUMWIN_EINVAL;
+    double fro[kMaxOrder];
+    for (int s = 0; s < d; ++s) fro[s] = std::sqrt(fro2_host[s]);
+    if (fro_host)
+        for (int s = 0; s < d; ++s) fro_host[s] = fro[s];
+    if (nu_host) nu_from_fro(fro, d, nu_host);
+    return CUMWIN_OK;
+}
+
 int cumwin_set_allocator(cumwin_alloc_fn alloc, cumwin_free_fn free_fn, void* ctx)
 {
     if ((alloc == nullptr) != (free_fn == nullptr)) return CUMWIN_EINVAL;
@@ -1136,11 +1156,35 @@ int cumwin_selftest_tables(int n, int b, int s)
 int cumwin_create(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream,
                   cumwin_t* out)
 {
+    return cumwin_create_shard(n, d, b, T, p, precision, cuda_stream, 0, 1, out);
+}
+
+int cumwin_shard_blocks(int n, int b, int d, int shard, int nshards, int64_t* begin, int64_t* end)
+{
+    if (n < 1 || b < 1 || d < 1 || d > kMaxOrder || nshards < 1 || shard < 0 || shard >= nshards ||
+        begin == nullptr || end == nullptr)
+        return CUMWIN_EINVAL;
+    shard_blocks((n + b - 1) / b, d, shard, nshards, begin, end);
+    return CUMWIN_OK;
+}
+
+int cumwin_create_shard(int n, int d, int b, int64_t T, int p, int precision, void* cuda_stream, int shard,
+                        int nshards, cumwin_t* out)
+{
     if (out == nullptr) return CUMWIN_EINVAL;
     *out = nullptr;
     int rc = check_args(n, d, b, T, p, precision);
     if (rc) return rc;
+    if (nshards < 1 || shard < 0 || shard >= nshards) return CUMWIN_EINVAL;
+    if (nshards > 1 && (precision == CUMWIN_FP64 || d < kCanonMinOrder || d > kCanonMaxOrder ||
+                        ipow(b, d) < kCanonMinBlock)) {
+        g_last_error = "block shards need a mixed form and a top order of 5 or 6 with b^d >= 256";
+        return CUMWIN_ENOTSUP;
+    }
     cumwin_s* h = new cumwin_s();
+    h->shard = shard;
+    h->nshards = nshards;
+    if (nshards > 1) shard_blocks((n + b - 1) / b, d, shard, nshards, &h->top0, &h->top1);
     rc = window_init(h, n, d, b, T, p, precision, (cudaStream_t)cuda_stream, true);
     int parts = 1;
     for (int s = 1; s <= d; ++s) parts = std::max(parts, h->cum_launch[s].gx * h->cum_launch[s].gy);
@@ -1600,6 +1644,10 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
 {
     if (h == nullptr || w_host == nullptr || dX_dev == nullptr) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
+    if (h->nshards > 1) {
+        g_last_error = "the adjoint needs the whole top-order tensor, not a block shard";
+        return CUMWIN_ENOTSUP;
+    }
     CW_TRY(join(h));
     const int n = h->n, d = h->d;
     auto& g = h->grad;

@@ -121,9 +121,9 @@ struct CumArgs {
     const int32_t* can_copies;
     const int32_t* dup_start;
     const int2* dup;
-    const int32_t* pblocks;
+    const int32_t* pblocks;    // the blocks recovered (all, or a shard's range), grouped by pattern
     const int4* units;
-    int32_t nunits, canon;
+    int32_t nunits, canon, npblocks;
 };
 constexpr int kTwoWordMinOrder = 5;
 // Orders with the canonical recovery (when b^s >= kCanonMinBlock, single windows).

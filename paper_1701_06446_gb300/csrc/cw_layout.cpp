@@ -232,7 +232,14 @@ CumTables build_cum_tables(int n, int b, int s)
     return t;
 }
 
-CanonTables build_canon_tables(int n, int b, int s, int slice, int group)
+void shard_blocks(int nbar, int s, int shard, int nshards, int64_t* begin, int64_t* end)
+{
+    const int64_t nb = n_sorted(nbar, s);
+    *begin = nb * shard / nshards;
+    *end = nb * (shard + 1) / nshards;
+}
+
+CanonTables build_canon_tables(int n, int b, int s, int slice, int group, int64_t blk0, int64_t blk1)
 {
     CanonTables t;
     const int nbar = (n + b - 1) / b;
@@ -259,8 +266,12 @@ CanonTables build_canon_tables(int n, int b, int s, int slice, int group)
     t.npat = (int)masks.size();
     t.can_start.assign(t.npat + 1, 0);
     t.map_off.assign((size_t)t.npat * bs, 0);
+    if (blk1 < 0 || blk1 > nb) blk1 = nb;
+    blk0 = std::max<int64_t>(0, std::min(blk0, blk1));
+    auto owned = [&](int64_t q) { return q >= blk0 && q < blk1; };
     std::vector<int64_t> count(t.npat, 0);
-    for (int64_t q = 0; q < nb; ++q) count[t.blkpat[q]]++;
+    for (int64_t q = 0; q < nb; ++q)
+        if (owned(q)) count[t.blkpat[q]]++;
     for (int q = 0; q < t.npat; ++q) {
         const int m = masks[q];
         t.can_start[q] = (int32_t)t.can_off.size();
@@ -302,9 +313,10 @@ CanonTables build_canon_tables(int n, int b, int s, int slice, int group)
     // blocks grouped by pattern, and the work units
     std::vector<int64_t> pstart(t.npat + 1, 0);
     for (int q = 0; q < t.npat; ++q) pstart[q + 1] = pstart[q] + count[q];
-    t.pblocks.resize(nb);
+    t.pblocks.resize(pstart[t.npat]);
     std::vector<int64_t> fill(pstart.begin(), pstart.end() - 1);
-    for (int64_t q = 0; q < nb; ++q) t.pblocks[fill[t.blkpat[q]]++] = (int32_t)q;
+    for (int64_t q = 0; q < nb; ++q)
+        if (owned(q)) t.pblocks[fill[t.blkpat[q]]++] = (int32_t)q;
     for (int q = 0; q < t.npat; ++q) {
         const int nc = t.can_start[q + 1] - t.can_start[q];
         for (int sl = 0; sl * slice < nc; ++sl)

@@ -69,8 +69,13 @@ struct CanonTables {
     std::vector<int32_t> units;      // [nunits][4] {pattern, slice, first index into pblocks, blocks}
     int64_t canonical = 0;           // canonical elements of the order (all blocks)
 };
-// Units of `slice` threads x up to `group` blocks of one pattern.
-CanonTables build_canon_tables(int n, int b, int s, int slice, int group);
+// Units of `slice` threads x up to `group` blocks of one pattern, over the
+// blocks of lexicographic rank in [blk0, blk1) (blk1 < 0: all blocks).
+CanonTables build_canon_tables(int n, int b, int s, int slice, int group, int64_t blk0 = 0, int64_t blk1 = -1);
+
+// Block range [begin, end) of shard `shard` of `nshards` over the sorted blocks
+// of order s (contiguous in lexicographic order, balanced by block count).
+void shard_blocks(int nbar, int s, int shard, int nshards, int64_t* begin, int64_t* end);
 
 // Split of order s into row factors (h) and column factors (s - h).
 inline int split_rows(int s) { return (s + 1) / 2; }

@@ -109,6 +109,9 @@ struct TcPlanStream {
     const float* shift;
     int* status;
     int64_t xoff;
+    // block shard of the top order d (lexicographic block ranks [top0, top1)):
+    // only the rows whose blocks meet it are updated; top1 < 0 = all blocks
+    int64_t top0 = 0, top1 = -1;
 };
 
 struct TcPlan {

@@ -977,16 +977,16 @@ __global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ arg
     if (threadIdx.x == 0) a.normpart[blockIdx.x] = z;
 }
 
-// Canonical recovery, pass 2: in every block whose pattern has repeated
-// block indices, each non-canonical offset takes the value of its canonical
-// offset (the same tensor entry), and orders below d write their two-word
-// copies there too.  One block per CTA at a time, threads over the pattern's
-// list of non-canonical offsets.
+// Canonical recovery, pass 2: in every recovered block whose pattern has
+// repeated block indices, each non-canonical offset takes the value of its
+// canonical offset (the same tensor entry), and orders below d write their
+// two-word copies there too.  One block per CTA at a time, threads over the
+// pattern's list of non-canonical offsets.
 __global__ void __launch_bounds__(NT) k_canon_expand(const CumArgs* __restrict__ args)
 {
     const CumArgs& a = *args;
-    const int64_t nblocks = a.E / a.bs;
-    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    for (int i = blockIdx.x; i < a.npblocks; i += gridDim.x) {
+        const int64_t blk = a.pblocks[i];
         const int q = a.blkpat[blk];
         const int d0 = a.dup_start[q], d1 = a.dup_start[q + 1];
         double* C = a.Cout + blk * a.bs;

@@ -756,8 +756,34 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
             // modelled cost
             struct Range { int r0, r1, c0; };
             std::vector<Range> ranges;
+            // a block shard of the top order keeps, per group, the rows of the left tuples
+            // whose blocks (jL ++ any sorted jR) meet [top0, top1): a contiguous run of the
+            // group's rows, as the blocks of consecutive left tuples follow each other
+            std::vector<int> keep0(t.rowstart.begin(), t.rowstart.end() - 1), keep1(t.rowstart.begin() + 1,
+                                                                                        t.rowstart.end());
+            if (s == S.d && S.top1 >= 0 && t.sh > 0) {
+                for (int m = 0; m < nbar; ++m) {
+                    keep0[m] = INT_MAX;
+                    keep1[m] = INT_MIN;
+                }
+                const std::vector<int> left = enumerate_sorted(nbar, t.h);
+                const int64_t bh = ipow(b, t.h);
+                std::vector<int> full(s);
+                for (size_t q = 0; q < left.size() / t.h; ++q) {
+                    const int* jl = &left[q * t.h];
+                    const int m = jl[t.h - 1];
+                    for (int k = 0; k < t.h; ++k) full[k] = jl[k];
+                    for (int k = t.h; k < s; ++k) full[k] = m;
+                    const int64_t lo = rank_sorted(full.data(), s, nbar);
+                    for (int k = t.h; k < s; ++k) full[k] = nbar - 1;
+                    const int64_t hi = rank_sorted(full.data(), s, nbar);
+                    if (hi < S.top0 || lo >= S.top1) continue;
+                    keep0[m] = std::min(keep0[m], t.leftrow[q]);
+                    keep1[m] = std::max(keep1[m], (int)(t.leftrow[q] + bh));
+                }
+            }
             for (int m = 0; m < nbar; ++m) {
-                const int r0 = t.rowstart[m], r1 = t.rowstart[m + 1];
+                const int r0 = keep0[m], r1 = keep1[m];
                 if (r1 <= r0 || t.colstart[m] >= ncols) continue;
                 for (int r = r0; r < r1; r += NMAX) ranges.push_back({r, std::min(r1, r + NMAX), t.colstart[m]});
             }

@@ -107,3 +107,26 @@ def test_noalloc_norm_rejects_oversized_blocks_without_gpu():
     for args in [(0, 2, 2), (4, 0, 2), (4, 2, 0), (4, 2, 9)]:
         assert lib.cumwin_block_norm2_noalloc(*args, dummy, dummy, None) == _lib.CODES["EINVAL"]
     assert lib.cumwin_block_norm2_noalloc(4, 2, 2, None, dummy, None) == _lib.CODES["EINVAL"]
+
+
+@pytest.mark.parametrize("n,b,d,k", [(48, 4, 6, 2), (48, 4, 6, 8), (7, 3, 5, 3), (4, 2, 4, 2), (60, 3, 4, 5)])
+def test_shard_blocks_partition_the_top_order(n, b, d, k):
+    """The shards' block ranges are contiguous, cover every sorted block of order d
+    once, and hold nearly equal block counts."""
+    nb = len(oracle.sorted_block_tuples(n, b, d))
+    ranges = [cw.shard_blocks(n, b, d, r, k) for r in range(k)]
+    assert ranges[0][0] == 0 and ranges[-1][1] == nb
+    for (a0, a1), (b0, b1) in zip(ranges, ranges[1:]):
+        assert a1 == b0
+    sizes = [e - s for s, e in ranges]
+    assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(cw.CumwinError):
+        cw.shard_blocks(n, b, d, k, k)
+
+
+def test_estimators_from_squared_norms():
+    fro2 = np.array([4.0, 9.0, 8.0, 3.0])
+    fro, nu = cw.estimators_from_fro2(fro2)
+    assert np.allclose(fro, np.sqrt(fro2))
+    assert np.isnan(nu[:2]).all()
+    assert np.allclose(nu[2:], [np.sqrt(8.0) / 3.0 ** 1.5, np.sqrt(3.0) / 3.0 ** 2])
