@@ -368,15 +368,28 @@ int cumwin_get_timing(cumwin_t h, double* stage_ms, double* update_ms, double* c
                       int64_t* shifts, int64_t* launches);
 
 /*
- * Autotune the tensor-core update of this handle (mixed forms): time `reps`
- * launches of the update GEMM for each candidate split of the samples over
- * CTAs (1, 2, 4, ... up to a workspace limit) on the data of the last shift,
- * keep the fastest, and report it in *ksplit_out (0 in the FP64 form).  When
- * the environment variable CUMWIN_TUNE_CACHE names a file, the choice is
- * appended to it and later handles of the same problem on the same device
- * start from it.  Requires a prior fill; synchronises.
+ * Autotune the tensor-core update of this handle (mixed forms; not in the
+ * paper).  On the data of the last shift it times `reps` launches of the
+ * update GEMM for each tile shape -- at most 128 or 64 rows of the left factor
+ * per work item, and items issued in super-blocks of 1, 4, 8 or 16 row tiles
+ * by all their column tiles, so that the CTAs running together share operand
+ * tiles in L2 -- keeps the fastest, then times each split of the samples over
+ * CTAs (1, 2, 4, ... up to a workspace limit) and keeps the fewest splits
+ * within 10% of the fastest; *ksplit_out receives the split (0 in the FP64
+ * form).  When the environment variable CUMWIN_TUNE_CACHE names a file, the
+ * choice is appended to it and later handles of the same problem on the same
+ * device start from it.  Requires a prior fill; synchronises.
  */
 int cumwin_tune(cumwin_t h, int reps, int* ksplit_out);
+
+/* The update's current tile choice: K-split, rows per item, super-block height
+ * (all 0 in the FP64 form).  Any pointer may be NULL. */
+int cumwin_get_tiles(cumwin_t h, int* ksplit, int* nmax, int* group);
+/* Pin a tile choice instead of tuning: ksplit in [1, the plan's limit], nmax a
+ * multiple of 16 in [16, 128], group >= 1 (EINVAL otherwise; a no-op in the
+ * FP64 form).  At a fixed K-split the results do not depend on the tile shape.
+ * Synchronises the device. */
+int cumwin_set_tiles(cumwin_t h, int ksplit, int nmax, int group);
 
 /*
  * Batches: many independent windows (streams) of uneven n and d, with a
@@ -415,8 +428,9 @@ int cumwin_batch_cumulants(cumwin_batch_t B, int window, int order, double* out_
  * Synchronises; returns ENONFINITE / ETIMEOUT if any window saw one. */
 int cumwin_batch_norms(cumwin_batch_t B, double* fro_host, double* nu_host);
 
-/* Autotune the batch's update GEMM (as cumwin_tune). */
+/* Autotune the batch's update GEMM (as cumwin_tune), and its tile choice. */
 int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out);
+int cumwin_batch_get_tiles(cumwin_batch_t B, int* ksplit, int* nmax, int* group);
 
 /* 1 when the batch's shifts use the batch-sum FIFO (every T[i] a multiple of
  * p and room for it, see cumwin_push), 0 otherwise, EINVAL. */

@@ -316,6 +316,18 @@ class CumWin:
         check(self.lib.cumwin_tune(self._h, reps, ctypes.byref(ks)), "cumwin_tune")
         return ks.value
 
+    def tiles(self) -> dict:
+        """The update's tile choice (cumwin_get_tiles): K-split, rows per item, super-block height."""
+        a, b_, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.lib.cumwin_get_tiles(self._h, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)),
+              "cumwin_get_tiles")
+        return {"ksplit": a.value, "rows_per_item": b_.value, "group": c.value}
+
+    def set_tiles(self, ksplit: int, rows_per_item: int, group: int):
+        """Pin the update's tile choice (cumwin_set_tiles)."""
+        self._sync_stream()
+        check(self.lib.cumwin_set_tiles(self._h, ksplit, rows_per_item, group), "cumwin_set_tiles")
+
     def norms_k(self, k: float) -> np.ndarray:
         """Entry-wise k-norms ||C_s||_k, s = 1..d (Algorithm 5 with a general k >= 1)."""
         out = np.zeros(self.d)
@@ -431,6 +443,13 @@ class CumWinBatch:
         ks = ctypes.c_int()
         check(self.lib.cumwin_batch_tune(self._h, reps, ctypes.byref(ks)), "cumwin_batch_tune")
         return ks.value
+
+    def tiles(self) -> dict:
+        """The update's tile choice (cumwin_batch_get_tiles)."""
+        a, b_, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(self.lib.cumwin_batch_get_tiles(self._h, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)),
+              "cumwin_batch_get_tiles")
+        return {"ksplit": a.value, "rows_per_item": b_.value, "group": c.value}
 
     @property
     def fifo(self) -> bool:

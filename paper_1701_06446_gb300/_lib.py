@@ -74,6 +74,9 @@ SIGNATURES = {
     "cumwin_create_shard": (c_int, [c_int, c_int, c_int, c_i64, c_int, c_int, c_vp, c_int, c_int, _handle_p]),
     "cumwin_shard_blocks": (c_int, [c_int, c_int, c_int, c_int, c_int, c_vp, c_vp]),
     "cumwin_estimators_from_fro2": (c_int, [c_int, c_vp, c_vp, c_vp]),
+    "cumwin_get_tiles": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "cumwin_set_tiles": (c_int, [c_vp, c_int, c_int, c_int]),
+    "cumwin_batch_get_tiles": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "cumwin_device_bytes": (c_i64, [c_vp]),
 }
 

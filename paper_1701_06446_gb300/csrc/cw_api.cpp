@@ -312,28 +312,43 @@ std::string tune_cache_path()
     return p ? std::string(p) : std::string();
 }
 
-int tune_cache_get(const std::string& sig)
+// one line per problem signature: "signature ksplit nmax group" (the last line wins)
+struct TileChoice {
+    int ksplit = 0, nmax = 0, group = 0;
+};
+
+TileChoice tune_cache_get(const std::string& sig)
 {
+    TileChoice c;
     const std::string path = tune_cache_path();
-    if (path.empty()) return 0;
+    if (path.empty()) return c;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     std::ifstream f(path);
     std::string line;
-    int found = 0;
     while (std::getline(f, line)) {
-        const size_t sp = line.rfind(' ');
-        if (sp != std::string::npos && line.substr(0, sp) == sig) found = std::atoi(line.c_str() + sp + 1);
+        std::istringstream in(line);
+        std::string key;
+        TileChoice t;
+        if (in >> key >> t.ksplit >> t.nmax >> t.group && key == sig) c = t;
     }
-    return found;
+    return c;
 }
 
-void tune_cache_put(const std::string& sig, int ks)
+void tune_cache_put(const std::string& sig, const TcPlan& tc)
 {
     const std::string path = tune_cache_path();
     if (path.empty()) return;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     std::ofstream f(path, std::ios::app);
-    f << sig << ' ' << ks << '\n';
+    f << sig << ' ' << tc.ksplit << ' ' << tc.nmax << ' ' << tc.group << '\n';
+}
+
+// A cached choice, applied to a plan when it is valid for it.
+void tune_cache_apply(TcPlan& tc, const TileChoice& c)
+{
+    if (c.nmax >= 16 && c.nmax <= kTcNmax && c.nmax % 16 == 0 && c.group >= 1 &&
+        tc_plan_items(tc, c.nmax, c.group) == 0 && c.ksplit >= 1 && c.ksplit <= tc.ksplit_max)
+        tc.ksplit = c.ksplit;
 }
 
 std::string plan_signature(const TcPlan& tc, const std::vector<cumwin_s*>& wins, int device)
@@ -341,7 +356,7 @@ std::string plan_signature(const TcPlan& tc, const std::vector<cumwin_s*>& wins,
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, device);
     std::ostringstream o;
-    o << "cumwin1|" << prop.name << "|prec" << tc.precision << "|p" << tc.p << "|items" << tc.nitems << "|w";
+    o << "cumwin2|" << prop.name << "|prec" << tc.precision << "|p" << tc.p << "|sets" << tc.rsets.size() << "|w";
     uint64_t hsh = 1469598103934665603ull;
     for (const cumwin_s* h : wins) {
         const uint64_t v = ((uint64_t)h->n << 40) ^ ((uint64_t)h->d << 32) ^ ((uint64_t)h->b << 24) ^ (uint64_t)h->T;
@@ -1189,8 +1204,7 @@ int cumwin_create_shard(int n, int d, int b, int64_t T, int p, int precision, vo
     int parts = 1;
     for (int s = 1; s <= d; ++s) parts = std::max(parts, h->cum_launch[s].gx * h->cum_launch[s].gy);
     if (rc == CUMWIN_OK && h->tc != nullptr) {
-        const int ks = tune_cache_get(plan_signature(*h->tc, {h}, h->device));
-        if (ks >= 1 && ks <= h->tc->ksplit_max) h->tc->ksplit = ks;
+        tune_cache_apply(*h->tc, tune_cache_get(plan_signature(*h->tc, {h}, h->device)));
     }
     if (rc == CUMWIN_OK) rc = window_finish(h, parts, h->tc, 0);
     if (rc == CUMWIN_OK) rc = fused_setup(h->fused, {h}, b, h->sm_count, h->norm_dev, h->status, h->mem, 3);
@@ -1729,6 +1743,37 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
     return CUMWIN_OK;
 }
 
+// The recovery's copies of the K-split of the handle's plan.
+static int sync_ksplit(cumwin_t h)
+{
+    const int ks = h->tc->ksplit;
+    for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
+    CumArgs arr[2][kAccModes][kMaxOrder + 1] = {};
+    for (int s = 1; s <= h->d; ++s)
+        for (int q = 0; q < 2; ++q)
+            for (int m = 0; m < kAccModes; ++m) {
+                arr[q][m][s] = h->cum[s];
+                arr[q][m][s].accum = m;
+                if (q == 1 && h->tc->W2 != nullptr) arr[q][m][s].W = h->tc->W2;
+            }
+    CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0][0], sizeof(arr), cudaMemcpyHostToDevice));
+    return CUMWIN_OK;
+}
+
+int cumwin_set_tiles(cumwin_t h, int ksplit, int nmax, int group)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    if (h->tc == nullptr) return CUMWIN_OK;  // the FP64 form has no tensor-core update
+    if (ksplit < 1 || ksplit > h->tc->ksplit_max || nmax < 16 || nmax > kTcNmax || nmax % 16 != 0 || group < 1)
+        return CUMWIN_EINVAL;
+    CW_TRY(join(h));
+    CW_TRY(cudaDeviceSynchronize());  // no GEMM of this handle reads the items while they change
+    const int rc = tc_plan_items(*h->tc, nmax, group);
+    if (rc) return fail_cuda((cudaError_t)rc, "tc_plan_items");
+    h->tc->ksplit = ksplit;
+    return sync_ksplit(h);
+}
+
 int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
 {
     if (h == nullptr || reps < 1) return CUMWIN_EINVAL;
@@ -1741,18 +1786,20 @@ int cumwin_tune(cumwin_t h, int reps, int* ksplit_out)
     const bool leaving = !(h->tc->fifo != nullptr && h->fifo_valid);
     const int ks = tc_autotune(*h->tc, reps, leaving, h->stream, nullptr);
     if (ks < 0) return fail_cuda((cudaError_t)(-ks), "tc_autotune");
-    for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
-    CumArgs arr[2][kAccModes][kMaxOrder + 1] = {};
-    for (int s = 1; s <= h->d; ++s)
-        for (int q = 0; q < 2; ++q)
-            for (int m = 0; m < kAccModes; ++m) {
-                arr[q][m][s] = h->cum[s];
-                arr[q][m][s].accum = m;
-                if (q == 1 && h->tc->W2 != nullptr) arr[q][m][s].W = h->tc->W2;
-            }
-    CW_TRY(cudaMemcpy(h->cum_dev, &arr[0][0][0], sizeof(arr), cudaMemcpyHostToDevice));
-    tune_cache_put(plan_signature(*h->tc, {h}, h->device), ks);
+    const int rc = sync_ksplit(h);
+    if (rc) return rc;
+    tune_cache_put(plan_signature(*h->tc, {h}, h->device), *h->tc);
     if (ksplit_out) *ksplit_out = ks;
+    return CUMWIN_OK;
+}
+
+int cumwin_get_tiles(cumwin_t h, int* ksplit, int* nmax, int* group)
+{
+    if (h == nullptr) return CUMWIN_EINVAL;
+    const TcPlan* tc = h->tc;
+    if (ksplit) *ksplit = tc ? tc->ksplit : 0;
+    if (nmax) *nmax = tc ? tc->nmax : 0;
+    if (group) *group = tc ? tc->group : 0;
     return CUMWIN_OK;
 }
 
@@ -1886,8 +1933,7 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
         g_last_error = "tensor-core plan: " + std::string(cudaGetErrorString((cudaError_t)rc));
         return bail(rc == (int)cudaErrorMemoryAllocation ? CUMWIN_ENOMEM : CUMWIN_ECUDA);
     }
-    const int ks = tune_cache_get(plan_signature(B->tc, B->wins, B->wins[0]->device));
-    if (ks >= 1 && ks <= B->tc.ksplit_max) B->tc.ksplit = ks;
+    tune_cache_apply(B->tc, tune_cache_get(plan_signature(B->tc, B->wins, B->wins[0]->device)));
     // recovery launch shapes over all windows (b is shared, so b^s is too)
     int parts = 1;
     for (int s = 1; s <= B->dmax; ++s) {
@@ -2041,8 +2087,17 @@ int cumwin_batch_tune(cumwin_batch_t B, int reps, int* ksplit_out)
     CW_TRY(cudaMemcpy(B->cum_dev, arr.data(), sizeof(CumArgs) * arr.size(), cudaMemcpyHostToDevice));
     for (cumwin_s* h : B->wins)
         for (int s = 1; s <= h->d; ++s) h->cum[s].ksplit = ks;
-    tune_cache_put(plan_signature(B->tc, B->wins, B->wins[0]->device), ks);
+    tune_cache_put(plan_signature(B->tc, B->wins, B->wins[0]->device), B->tc);
     if (ksplit_out) *ksplit_out = ks;
+    return CUMWIN_OK;
+}
+
+int cumwin_batch_get_tiles(cumwin_batch_t B, int* ksplit, int* nmax, int* group)
+{
+    if (B == nullptr) return CUMWIN_EINVAL;
+    if (ksplit) *ksplit = B->tc.ksplit;
+    if (nmax) *nmax = B->tc.nmax;
+    if (group) *group = B->tc.group;
     return CUMWIN_OK;
 }
 

@@ -114,6 +114,19 @@ struct TcPlanStream {
     int64_t top0 = 0, top1 = -1;
 };
 
+// The GEMM of one (stream, order) before it is cut into items: its row ranges
+// (groups split or merged, each pairing with the columns from c0 on), and
+// what an item needs to address its operands and workspace slots.
+struct TcRangeSet {
+    int s = 0, stream = 0, ncols = 0;
+    int64_t loff = 0, roff = 0;           // first row of the left / right operand set in the operand array
+    std::vector<int32_t> rowstart, colstart;
+    std::vector<int64_t> roww;            // workspace slot of (row, column 0)
+    std::vector<int32_t> colmin;          // first valid column of each row
+    struct Range { int r0, r1, c0; };
+    std::vector<Range> ranges;
+};
+
 struct TcPlan {
     int ready = 0;
     int precision = 0;
@@ -134,6 +147,12 @@ struct TcPlan {
     CUtensorMap mapA{}, mapB[3]{};  // A boxes of 128 rows; B boxes of 32, 64, 128 rows
     TcItem* items = nullptr;
     int nitems = 0, ksplit = 1, ksplit_max = 1;
+    // tile shape (tc_plan_items): rows per item at most `nmax` (64 or 128), and
+    // items issued in super-blocks of `group` row tiles x all their column tiles,
+    // column-major inside a block, so that the CTAs running at the same time
+    // share a few left-factor tiles and a run of right-factor tiles in L2
+    int nmax = kTcNmax, group = 8, items_cap = 0;
+    std::vector<TcRangeSet> rsets;
     TcOrder* ord = nullptr;        // device [nstreams][kMaxOrder + 1]
     float* W = nullptr;
     float* W2 = nullptr;           // second workspace (shifts alternate) or null
@@ -193,8 +212,14 @@ struct TcAccSeg {
 cudaError_t launch_tc_accumulate(const TcPlan& plan, const TcAccSeg* segs_dev, int nsegs, int q,
                                  cudaStream_t st);
 
-// Time the GEMM for each candidate K-split on the data currently staged and
-// keep the fastest; returns the chosen K-split (or a negative cudaError_t).
+// Cut the GEMMs into items of at most nmax rows (a multiple of 16, <= kTcNmax)
+// issued in super-blocks of `group` row tiles, and upload them (0 or a
+// cudaError_t code).
+int tc_plan_items(TcPlan& plan, int nmax, int group);
+
+// Time the GEMM for candidate tile shapes (rows per item 128 or 64, super-block
+// heights 1, 4, 8, 16) and then K-splits on the data currently staged, and keep
+// the fastest; returns the chosen K-split (or a negative cudaError_t).
 // `leaving`: time the shape with the X_(-) half.
 int tc_autotune(TcPlan& plan, int reps, bool leaving, cudaStream_t st, double* best_ms);
 

@@ -704,7 +704,6 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     // operand sets per stream: key (factors, grouped?) -> first row; singles
     // and the empty product have one ordering
     std::vector<uint64_t> opvars;
-    std::vector<TcItem> items;
     std::vector<TcOrder> ord((size_t)plan.nstreams * (kMaxOrder + 1));
     plan.wbase.assign(plan.nstreams, 0);
     int64_t wtot = 0;
@@ -805,39 +804,39 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
                 }
                 merged.push_back(R);
             }
-            for (const Range& R : merged) {
-                for (int c = R.c0; c < ncols; c += TM) {
-                    TcItem it{};
-                    it.s = s;
-                    it.row0 = R.r0;
-                    it.nrows = R.r1 - R.r0;
-                    it.col0 = c;
-                    it.ncols = std::min(TM, ncols - c);
-                    it.brow = (int32_t)(loff + R.r0);
-                    it.acol = (int32_t)(roff + c);
-                    it.bbox = b_box_rows(it.nrows);
-                    it.stream = i;
-                    // rows of one group: the slots of a row follow from the first row's
-                    const int m0 = (int)(std::upper_bound(t.rowstart.begin(), t.rowstart.end(), R.r0) -
-                                         t.rowstart.begin()) - 1;
-                    it.fast = R.r1 <= t.rowstart[m0 + 1] ? 1 : 0;
-                    it.wwidth = (int32_t)(ncols - t.colstart[m0]);
-                    it.wrow0 = (int32_t)roww[R.r0];
-                    items.push_back(it);
-                    issued += 3.0 * TM * ((it.nrows + 15) & ~15);
-                }
-                for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, ncols - colmin[r]);
-            }
+            TcRangeSet rs;
+            rs.s = s;
+            rs.stream = i;
+            rs.ncols = ncols;
+            rs.loff = loff;
+            rs.roff = roff;
+            rs.rowstart = t.rowstart;
+            rs.colstart = t.colstart;
+            rs.roww = roww;
+            rs.colmin = colmin;
+            for (const Range& R : merged) rs.ranges.push_back({R.r0, R.r1, R.c0});
+            if (!rs.ranges.empty()) plan.rsets.push_back(std::move(rs));
         }
         wtot += S.Eoff[S.d + 1];
     }
     plan.wslice = wtot;
-    // larger items first, then round-robin over the persistent CTAs
-    std::stable_sort(items.begin(), items.end(),
-                     [](const TcItem& x, const TcItem& y) { return x.nrows > y.nrows; });
-    plan.useful_macs_per_sample = useful;
-    plan.issued_macs_per_sample = issued;
-    plan.nitems = (int)items.size();
+    // the higher orders (the largest GEMMs) first; the small ones fill the tail
+    std::stable_sort(plan.rsets.begin(), plan.rsets.end(),
+                     [](const TcRangeSet& x, const TcRangeSet& y) { return x.s > y.s; });
+    (void)useful;
+    (void)issued;
+    // room for the items of the finest tile shape the autotuner tries
+    int64_t cap = 0;
+    for (const TcRangeSet& rs : plan.rsets)
+        for (const TcRangeSet::Range& R : rs.ranges)
+            cap += (int64_t)((R.r1 - R.r0 + 63) / 64 + 1) * ((rs.ncols - R.c0 + TM - 1) / TM);
+    plan.items_cap = (int)std::max<int64_t>(1, cap);
+    e = alloc(sizeof(TcItem) * (size_t)plan.items_cap, (void**)&plan.items);
+    if (e != cudaSuccess) return (int)e;
+    {
+        const int rc = tc_plan_items(plan, NMAX, 8);
+        if (rc) return rc;
+    }
 
     // K-splits: a few units per persistent CTA, at least 2 chunks per split,
     // the workspace (2 x ksplit x wslice floats) within 256 MB
@@ -852,10 +851,6 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     while (2 * ks <= plan.ksplit_max && (int64_t)plan.nitems * 2 * ks <= (int64_t)sm_count) ks *= 2;
     plan.ksplit = ks;
 
-    e = alloc(sizeof(TcItem) * std::max<size_t>(items.size(), 1), (void**)&plan.items);
-    if (e != cudaSuccess) return (int)e;
-    e = cudaMemcpy(plan.items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return (int)e;
     e = alloc(sizeof(TcOrder) * ord.size(), (void**)&plan.ord);
     if (e != cudaSuccess) return (int)e;
     e = cudaMemcpy(plan.ord, ord.data(), sizeof(TcOrder) * ord.size(), cudaMemcpyHostToDevice);
@@ -927,6 +922,60 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     return 0;
 }
 
+int tc_plan_items(TcPlan& plan, int nmax, int group)
+{
+    if (nmax < 16 || nmax > NMAX || nmax % 16 != 0 || group < 1) return (int)cudaErrorInvalidValue;
+    std::vector<TcItem> items;
+    double issued = 0.0, useful = 0.0;
+    for (const TcRangeSet& rs : plan.rsets) {
+        // row tiles: every range cut into pieces of at most nmax rows
+        std::vector<TcRangeSet::Range> tiles;
+        for (const TcRangeSet::Range& R : rs.ranges) {
+            for (int r = R.r0; r < R.r1; r += nmax) tiles.push_back({r, std::min(R.r1, r + nmax), R.c0});
+            for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, rs.ncols - rs.colmin[r]);
+        }
+        // super-blocks of `group` row tiles; inside one, by column position, then row tile
+        for (size_t g0 = 0; g0 < tiles.size(); g0 += (size_t)group) {
+            const size_t g1 = std::min(tiles.size(), g0 + (size_t)group);
+            std::vector<std::pair<int, int>> order;  // (column, tile)
+            for (size_t k = g0; k < g1; ++k)
+                for (int c = tiles[k].c0; c < rs.ncols; c += TM) order.push_back({c, (int)k});
+            std::stable_sort(order.begin(), order.end());
+            for (const auto& ck : order) {
+                const TcRangeSet::Range& R = tiles[ck.second];
+                const int c = ck.first;
+                TcItem it{};
+                it.s = rs.s;
+                it.row0 = R.r0;
+                it.nrows = R.r1 - R.r0;
+                it.col0 = c;
+                it.ncols = std::min(TM, rs.ncols - c);
+                it.brow = (int32_t)(rs.loff + R.r0);
+                it.acol = (int32_t)(rs.roff + c);
+                it.bbox = b_box_rows(it.nrows);
+                it.stream = rs.stream;
+                // rows of one group: the slots of a row follow from the first row's
+                const int m0 = (int)(std::upper_bound(rs.rowstart.begin(), rs.rowstart.end(), R.r0) -
+                                     rs.rowstart.begin()) - 1;
+                it.fast = R.r1 <= rs.rowstart[m0 + 1] ? 1 : 0;
+                it.wwidth = (int32_t)(rs.ncols - rs.colstart[m0]);
+                it.wrow0 = (int32_t)rs.roww[R.r0];
+                items.push_back(it);
+                issued += 3.0 * TM * ((it.nrows + 15) & ~15);
+            }
+        }
+    }
+    if ((int)items.size() > plan.items_cap) return (int)cudaErrorInvalidValue;
+    const cudaError_t e = cudaMemcpy(plan.items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return (int)e;
+    plan.nitems = (int)items.size();
+    plan.nmax = nmax;
+    plan.group = group;
+    plan.useful_macs_per_sample = useful;
+    plan.issued_macs_per_sample = issued;
+    return 0;
+}
+
 cudaError_t tc_stage_push(const TcPlan& plan, const float* xin, const float* xout, int64_t ld, int p,
                           bool leaving, cudaStream_t st)
 {
@@ -978,42 +1027,77 @@ int tc_autotune(TcPlan& plan, int reps, bool leaving, cudaStream_t st, double* b
 {
     const int chunks = plan.P / KC;
     const int mchunks = leaving ? chunks : 0;
-    int best = plan.ksplit;
-    double best_t = 1e30;
+    // the item list is rewritten below: no GEMM queued before may still read it
+    {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return -(int)e;
+    }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return -(int)cudaErrorUnknown;
-    std::vector<double> times;
-    for (int ks = 1; ks <= plan.ksplit_max && ks <= chunks; ks *= 2) {
-        plan.ksplit = ks;
-        cudaError_t e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);  // warm-up
+    // average time of `reps` GEMM launches of the current shape (after one warm-up)
+    auto time_gemm = [&](double* ms_out) -> cudaError_t {
+        cudaError_t e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm(plan, plan.W, chunks, mchunks, plan.P, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return -(int)e;
+        *ms_out = ms;
+        return e;
+    };
+    auto fail = [&](cudaError_t e) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return -(int)e;
+    };
+    // 1. the tile shape at one K-split: rows per item and super-block height
+    plan.ksplit = 1;
+    int best_nmax = plan.nmax, best_group = plan.group;
+    double best_t = 1e30;
+    for (int nmax : {NMAX, NMAX / 2})
+        for (int group : {1, 4, 8, 16}) {
+            int rc = tc_plan_items(plan, nmax, group);
+            if (rc) return fail((cudaError_t)rc);
+            double ms = 0.0;
+            const cudaError_t e = time_gemm(&ms);
+            if (e != cudaSuccess) return fail(e);
+            if (ms < best_t) {
+                best_t = ms;
+                best_nmax = nmax;
+                best_group = group;
+            }
         }
+    {
+        const int rc = tc_plan_items(plan, best_nmax, best_group);
+        if (rc) return fail((cudaError_t)rc);
+    }
+    // 2. the K-split for that shape: the fewest splits within 10% of the fastest
+    // (every split costs the recovery one more read of the workspace, which this
+    // timing does not see)
+    std::vector<double> times;
+    double fastest = 1e30;
+    for (int ks = 1; ks <= plan.ksplit_max && ks <= chunks; ks *= 2) {
+        plan.ksplit = ks;
+        double ms = 0.0;
+        const cudaError_t e = time_gemm(&ms);
+        if (e != cudaSuccess) return fail(e);
         times.push_back(ms);
-        if (ms < best_t) best_t = ms;
+        fastest = std::min(fastest, ms);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // the fewest splits within 10% of the fastest GEMM: every split costs the
-    // recovery one more read of the workspace, which this timing does not see
+    int best = 1;
+    double chosen = fastest;
     for (size_t i = 0, ks = 1; i < times.size(); ++i, ks *= 2)
-        if (times[i] <= 1.10 * best_t) {
+        if (times[i] <= 1.10 * fastest) {
             best = (int)ks;
-            best_t = times[i];
+            chosen = times[i];
             break;
         }
     plan.ksplit = best;
-    if (best_ms) *best_ms = best_t / std::max(1, reps);
+    if (best_ms) *best_ms = chosen / std::max(1, reps);
     return best;
 }
 

@@ -157,3 +157,33 @@ def test_batch_argument_errors():
     with CumWinBatch([4, 5], [3, 2], [64, 80], 2, 8, "bf16") as B:
         with pytest.raises(CumwinError):
             B.push(torch.zeros(B.offsets[-1], device="cuda"))  # push before fill
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+def test_tile_shape_does_not_change_results(form):
+    """Items of 128 or 64 rows issued in super-blocks of any height compute every
+    output with the same MMA sequence over the samples, so at a fixed K-split the
+    cumulants are bitwise the same; the autotuner's choice is reported."""
+    n, d, b, T, p = 30, 5, 4, 2048, 256
+    rng = np.random.default_rng(8)
+    X = torch.from_numpy(rng.standard_t(6, size=(T + 5 * p, n)).astype(np.float32)).cuda()
+    outs = []
+    for shape in [(1, 128, 1), (1, 64, 16), (1, 128, 4), (1, 64, 1)]:
+        with CumWin(n, d, b, T, p, form) as h:
+            h.set_tiles(*shape)
+            assert h.tiles() == {"ksplit": shape[0], "rows_per_item": shape[1], "group": shape[2]}
+            h.fill(X[:T])
+            for k in range(5):
+                h.push(X[T + k * p: T + (k + 1) * p])
+            outs.append([h.cumulants(s) for s in range(1, d + 1)])
+    for o in outs[1:]:
+        for s in range(d):
+            assert torch.equal(o[s], outs[0][s]), s
+    with CumWin(n, d, b, T, p, form) as h:
+        h.fill(X[:T])
+        h.push(X[T:T + p])
+        h.tune(reps=2)
+        t = h.tiles()
+        assert t["rows_per_item"] in (64, 128) and t["group"] in (1, 4, 8, 16) and t["ksplit"] >= 1
+        with pytest.raises(CumwinError):
+            h.set_tiles(1, 100, 4)
