@@ -931,7 +931,11 @@ int tc_plan_items(TcPlan& plan, int nmax, int group)
         // row tiles: every range cut into pieces of at most nmax rows
         std::vector<TcRangeSet::Range> tiles;
         for (const TcRangeSet::Range& R : rs.ranges) {
-            for (int r = R.r0; r < R.r1; r += nmax) tiles.push_back({r, std::min(R.r1, r + nmax), R.c0});
+            // a tile's columns start at the first valid column of its first row (the
+            // smallest of its rows': groups, in row order, start at increasing columns),
+            // so that a tile inside one group has no masked column
+            for (int r = R.r0; r < R.r1; r += nmax)
+                tiles.push_back({r, std::min(R.r1, r + nmax), std::max(R.c0, (int)rs.colmin[r])});
             for (int r = R.r0; r < R.r1; ++r) useful += 3.0 * std::max(0, rs.ncols - rs.colmin[r]);
         }
         // super-blocks of `group` row tiles; inside one, by column position, then row tile
