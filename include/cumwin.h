@@ -395,9 +395,10 @@ int cumwin_set_tiles(cumwin_t h, int ksplit, int nmax, int group);
  * Batches: many independent windows (streams) of uneven n and d, with a
  * common block size b, shift size p and precision (mixed forms only), advanced
  * together: every phase of a shift (staging, operand build, the tensor-core
- * update, the recovery of each order, the norms) is one launch for all
- * windows, so a shift costs the same number of launches for 1 or 1000
- * windows and can be captured into one CUDA graph.
+ * update, the recovery of each order, the norms) covers all windows, so a
+ * shift costs the same number of launches for 1 or 1000 windows -- one when
+ * every d <= 4 (cumwin_batch_set_single_launch) -- and can be captured into
+ * one CUDA graph.
  */
 typedef struct cumwin_batch_s* cumwin_batch_t;
 
@@ -436,9 +437,23 @@ int cumwin_batch_get_tiles(cumwin_batch_t B, int* ksplit, int* nmax, int* group)
  * p and room for it, see cumwin_push), 0 otherwise, EINVAL. */
 int cumwin_batch_fifo(cumwin_batch_t B);
 
+/*
+ * Single-launch shifts (not in the paper).  When every window's orders are
+ * recovered by the fused recovery (d <= 4) and the device can keep one
+ * 1024-thread CTA with the GEMM's shared memory on every SM, cumwin_batch_push
+ * runs a whole shift -- staging, operand build, the tensor-core update and the
+ * recovery of every order with the norms -- as one cooperative launch whose
+ * phases are separated by bounded grid barriers (on by default).  enable = 0
+ * runs the phases as separate launches instead; the results are the same.
+ * Returns 1 when single-launch shifts are available for this batch, 0 when not,
+ * EINVAL for a null handle.
+ */
+int cumwin_batch_set_single_launch(cumwin_batch_t B, int enable);
+
 /* Kernels launched by the last cumwin_batch_push (staging, operand build,
- * GEMM and the recovery's launches); 0 before the first push, EINVAL for a
- * null handle.  Host bookkeeping only: it does not synchronise. */
+ * GEMM and the recovery's launches; 1 for a single-launch shift); 0 before the
+ * first push, EINVAL for a null handle.  Host bookkeeping only: it does not
+ * synchronise. */
 int64_t cumwin_batch_launches(cumwin_batch_t B);
 
 /* Sticky device status over all windows (synchronises). */

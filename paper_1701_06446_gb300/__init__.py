@@ -461,6 +461,13 @@ class CumWinBatch:
     def status(self) -> int:
         return int(self.lib.cumwin_batch_status(self._h))
 
+    def set_single_launch(self, enable: bool) -> bool:
+        """Run each shift as one cooperative launch (the default where available) or
+        phase by phase; returns whether single-launch shifts are available."""
+        r = int(self.lib.cumwin_batch_set_single_launch(self._h, int(bool(enable))))
+        check(min(r, 0), "cumwin_batch_set_single_launch")
+        return r == 1
+
     def launches(self) -> int:
         """Kernels launched by the last push."""
         r = int(self.lib.cumwin_batch_launches(self._h))

@@ -77,6 +77,7 @@ SIGNATURES = {
     "cumwin_get_tiles": (c_int, [c_vp, c_vp, c_vp, c_vp]),
     "cumwin_set_tiles": (c_int, [c_vp, c_int, c_int, c_int]),
     "cumwin_batch_get_tiles": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "cumwin_batch_set_single_launch": (c_int, [c_vp, c_int]),
     "cumwin_device_bytes": (c_i64, [c_vp]),
 }
 

@@ -297,6 +297,9 @@ struct cumwin_batch_s {
     TcAccSeg* segs = nullptr;
     int nsegs = 0;
     int64_t push_launches = 0;  // kernels the last cumwin_batch_push launched
+    int shift_grid = 0;          // CTAs of the single-launch shift (0: the phases launch one by one)
+    unsigned* shift_bar = nullptr;  // its grid barrier (a counter used by that grid size only)
+    bool single = true;          // cumwin_batch_set_single_launch
 };
 
 namespace {
@@ -1977,6 +1980,14 @@ int cumwin_batch_create(int nwin, const int* n, const int* d, const int64_t* T, 
     if (e == cudaSuccess) {
         rc = fused_setup(B->fused, B->wins, b, B->sm_count, B->norm_dev, B->status, B->mem, 4);
         if (rc) return bail(rc);
+        // a shift as one cooperative launch when every order is in the fused recovery
+        // and one 1024-thread CTA fits on every SM
+        if (B->fused.dfused > 0 && B->dmax <= B->fused.dfused &&
+            batch_shift_blocks_per_sm(precision, B->fused.dfused) >= 1) {
+            e = B->mem.alloc(&B->shift_bar, kBarrierWords);
+            if (e == cudaSuccess) e = cudaMemset(B->shift_bar, 0, kBarrierWords * sizeof(unsigned));
+            if (e == cudaSuccess) B->shift_grid = B->sm_count;
+        }
     }
     std::vector<TcAccSeg> segs = acc_segments(B->wins, B->tc);
     B->nsegs = (int)segs.size();
@@ -2028,6 +2039,39 @@ int cumwin_batch_push(cumwin_batch_t B, const float* x_dev)
 {
     if (B == nullptr || x_dev == nullptr) return CUMWIN_EINVAL;
     if (!B->filled) return CUMWIN_ESTATE;
+    if (B->single && B->shift_grid > 0) {
+        // staging, operand build, GEMM and recovery as the phases of one launch
+        const TcPlan& tc = B->tc;
+        BatchShiftArgs a{};
+        a.sdesc = tc.sdesc;
+        a.xin = x_dev;
+        a.p = B->p;
+        a.P = tc.P;
+        a.nstreams = tc.nstreams;
+        a.tiles_x = (tc.P + 31) / 32;
+        a.tiles_y = (tc.npad_max + 31) / 32;
+        a.leaving = B->fifo ? 0 : 1;
+        a.scaled = tc.precision == 2;
+        a.Kcap = tc.Kcap;
+        a.vmax = tc.vmax;
+        a.nvmax = tc.vmax != nullptr ? 2 * (int64_t)tc.npad_max * tc.nstreams : 0;
+        a.opvars = tc.opvars;
+        a.oprows = tc.oprows;
+        a.ops = tc.ops;
+        a.opexp = tc.opexp;
+        a.nkb = (a.leaving ? 2 : 1) * tc.P / 8;
+        a.gemm = tc_gemm_args(tc, a.leaving != 0, 0);
+        FusedRecovery f = B->fused.f;
+        const int accum = B->fifo ? 2 : 1;
+        f.args = B->cum_dev + (size_t)accum * (kMaxOrder + 1) * B->nwin;
+        f.advance = B->p;
+        f.advance_heads = 1;
+        f.fold = 1;
+        f.bar = B->shift_bar;  // the recovery's own launches use another grid size
+        CW_TRY(launch_batch_shift(tc, a, f, B->fused.dfused, B->shift_grid, B->stream));
+        B->push_launches = 1;
+        return CUMWIN_OK;
+    }
     CW_TRY(tc_stage_push(B->tc, x_dev, nullptr, -1, B->p, !B->fifo, B->stream));  // staging + operand build
     CW_TRY(tc_gemm_push(B->tc, !B->fifo, 0, B->stream));
     int64_t L = 0;
@@ -2099,6 +2143,13 @@ int cumwin_batch_get_tiles(cumwin_batch_t B, int* ksplit, int* nmax, int* group)
     if (nmax) *nmax = B->tc.nmax;
     if (group) *group = B->tc.group;
     return CUMWIN_OK;
+}
+
+int cumwin_batch_set_single_launch(cumwin_batch_t B, int enable)
+{
+    if (B == nullptr) return CUMWIN_EINVAL;
+    B->single = enable != 0;
+    return B->shift_grid > 0 ? 1 : 0;
 }
 
 int cumwin_batch_fifo(cumwin_batch_t B)

@@ -68,4 +68,24 @@ __device__ __forceinline__ float sum_in_partials(const float* __restrict__ w, in
     return din;
 }
 
+// Virtual CTAs of 256 threads.  A kernel of 256-thread CTAs uses its CTAs
+// as they are (V = false); a kernel of 1024-thread CTAs (the single-launch
+// batch shift) runs each quarter of a CTA as a virtual CTA (V = true) with its
+// own named barrier (ids 1-4; id 0 is __syncthreads).
+template <bool V>
+__device__ __forceinline__ int vtid()
+{
+    return V ? (int)(threadIdx.x & 255u) : (int)threadIdx.x;
+}
+
+template <bool V>
+__device__ __forceinline__ void vsync()
+{
+    if constexpr (V) {
+        asm volatile("bar.sync %0, 256;" ::"r"(1 + (int)(threadIdx.x >> 8)) : "memory");
+    } else {
+        __syncthreads();
+    }
+}
+
 }  // namespace cw

@@ -97,6 +97,24 @@ struct TcGemmArgs {
     int* status;
 };
 
+// One shift of a batch as a single cooperative launch (k_batch_shift): the
+// staging, the operand build, the GEMM and the fused recovery of orders 1..4
+// as phases separated by grid barriers.
+struct BatchShiftArgs {
+    const TcStreamDesc* sdesc;
+    const float* xin;         // packed X_(+) of all streams
+    int32_t p, P, nstreams, tiles_x, tiles_y, leaving, scaled;
+    int64_t Kcap;
+    float* vmax;              // FP16 form: per-variable maxima, zeroed first
+    int64_t nvmax;
+    const uint64_t* opvars;   // operand build
+    int64_t oprows;
+    uint16_t* ops;
+    int32_t* opexp;
+    int32_t nkb;
+    TcGemmArgs gemm;
+};
+
 // Host description of one stream for the planner.
 struct TcPlanStream {
     const std::vector<UpdateTables>* tables;  // [order]
@@ -167,6 +185,15 @@ struct TcPlan {
     int* status = nullptr;
     double useful_macs_per_sample = 0, issued_macs_per_sample = 0;
 };
+
+// The single-launch batch shift (k_cumulants.cu): resident CTAs per SM of its
+// 1024-thread CTA (0: it cannot run), and its launch with `grid` CTAs.
+int batch_shift_blocks_per_sm(int precision, int dfused);
+cudaError_t launch_batch_shift(const TcPlan& plan, const BatchShiftArgs& a, const FusedRecovery& f, int dfused,
+                               int grid, cudaStream_t st);
+// The GEMM arguments of one shift (nplus / nminus K-chunks of the entering and
+// leaving samples; parity 1 = the second workspace when there is one).
+TcGemmArgs tc_gemm_args(const TcPlan& plan, bool leaving, int parity);
 
 using DevAlloc = std::function<cudaError_t(size_t, void**)>;
 

@@ -31,6 +31,8 @@
 
 #include "cw_device.cuh"
 #include "cw_internal.h"
+#include "cw_tc.h"
+#include "cw_tc_device.cuh"
 
 namespace cw {
 
@@ -91,16 +93,17 @@ __device__ __forceinline__ void subset_offsets(const Elem<S>& c, int b, int t, i
 
 // Thread -> (slot, in-block offset): `slots` blocks per CTA when b^S < NT,
 // else slice y of NT offsets of one block.
-template <int S>
+template <int S, bool V = false>
 __device__ __forceinline__ Elem<S> make_elem(int b, int bs, int bR, int slots, int y)
 {
     Elem<S> c;
+    const int tid = vtid<V>();
     if (slots == 1) {
         c.slot = 0;
-        c.off = y * NT + (int)threadIdx.x;
+        c.off = y * NT + tid;
     } else {
-        c.slot = (int)threadIdx.x / bs;
-        c.off = (int)threadIdx.x - c.slot * bs;
+        c.slot = tid / bs;
+        c.off = tid - c.slot * bs;
     }
     c.valid = c.slot < slots && c.off < bs;
     int rem = c.off;
@@ -312,15 +315,18 @@ __device__ __forceinline__ void recover_elem(const CumArgs& a, const CumArgs* a2
     }
 }
 
-// Deterministic CTA sum (fixed shuffle tree per warp, warps in order).
+// Deterministic CTA sum (fixed shuffle tree per warp, warps in order) over a
+// (virtual) CTA of NT threads; `red` holds NT / 32 doubles of that CTA.
+template <bool V = false>
 __device__ __forceinline__ double cta_sum(double v, double* red)
 {
+    const int tid = vtid<V>();
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
+    vsync<V>();
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    vsync<V>();
     double z = 0.0;
-    if (threadIdx.x == 0)
+    if (tid == 0)
         for (int w = 0; w < NT / 32; ++w) z += red[w];
     return z;  // valid in thread 0
 }
@@ -516,10 +522,11 @@ __device__ __forceinline__ int unit_window(const int64_t* ustart, int nwin, int6
 // the slot of its first unit and the other units of the run hold zero, so
 // that every unit slot is written and the window's norm is the sum of its
 // unit slots.
-template <int S, int OTF>
+template <int S, int OTF, bool V = false>
 __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArgs* sargs, double* red, int64_t rot,
                                             int cta, int ncta)
 {
+    const int tid = vtid<V>();
     const int slots = f.slots[S], gy = f.gy[S];
     const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
     const int64_t total = us[f.nwin];
@@ -532,34 +539,34 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArg
     const CumArgs* ap = sargs != nullptr ? &sargs[S] : &f.args[(int64_t)S * f.nwin + w];
     const CumArgs* a2 = OTF < 2 ? nullptr : sargs != nullptr ? &sargs[2] : &f.args[(int64_t)2 * f.nwin + w];
     int64_t nblocks = ap->E / ap->bs;
-    Elem<S> c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, 0);
+    Elem<S> c = make_elem<S, V>(ap->b, ap->bs, ap->bR, slots, 0);
     int64_t first = u0;
     double local = 0.0;
     for (int64_t u = u0; u < u1; ++u) {
         if (u >= us[w + 1]) {  // the next window with units: close the run
-            const double z = cta_sum(local, red);
-            if (threadIdx.x == 0) part[first] = z;
+            const double z = cta_sum<V>(local, red);
+            if (tid == 0) part[first] = z;
             first = u;
             local = 0.0;
             while (u >= us[w + 1]) ++w;
             ap = &f.args[(int64_t)S * f.nwin + w];  // several windows: no shared copy
             if (OTF >= 2) a2 = &f.args[(int64_t)2 * f.nwin + w];
             nblocks = ap->E / ap->bs;
-            if (gy == 1) c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, 0);
-        } else if (u != first && threadIdx.x == 0) {
+            if (gy == 1) c = make_elem<S, V>(ap->b, ap->bs, ap->bR, slots, 0);
+        } else if (u != first && tid == 0) {
             part[u] = 0.0;
         }
         const int64_t ul = u - us[w];
         int64_t grp = ul;
         if (gy > 1) {
             grp = ul / gy;
-            c = make_elem<S>(ap->b, ap->bs, ap->bR, slots, (int)(ul - grp * gy));
+            c = make_elem<S, V>(ap->b, ap->bs, ap->bR, slots, (int)(ul - grp * gy));
         }
         const int64_t blk = grp * slots + c.slot;
         if (c.valid && blk < nblocks) recover_elem<S, false, OTF>(*ap, a2, c, blk, 0, local);
     }
-    const double z = cta_sum(local, red);
-    if (threadIdx.x == 0) part[first] = z;
+    const double z = cta_sum<V>(local, red);
+    if (tid == 0) part[first] = z;
 }
 
 // What the fold of one (window, order) segment needs, resolved once per
@@ -636,13 +643,14 @@ __device__ __forceinline__ void fold_commit(const FoldPend& v)
 // access coalesced; the others go through the per-block slot table.  With few
 // segments their descriptors come from shared memory (`sg`, resolved at the
 // start of the launch), otherwise from the argument array.
+template <bool V = false>
 __device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1, int cta,
                                            int ncta)
 {
     const int64_t g0 = f.abeg[seg0], g1 = f.abeg[seg1];
     const int64_t per = ((g1 - g0 + ncta - 1) / ncta + NT - 1) / NT * NT;  // contiguous chunk per CTA
     const int64_t c0 = min(g1, g0 + cta * per), c1 = min(g1, c0 + per);
-    int64_t g = c0 + threadIdx.x;
+    int64_t g = c0 + vtid<V>();
     if (g >= c1) return;
     int seg = seg0, hi = seg1 - 1;  // last segment with abeg <= g
     while (seg < hi) {
@@ -666,13 +674,14 @@ __device__ __forceinline__ void fused_fold(const FusedRecovery& f, const FoldSeg
 // orders, FIFO slots and sums start on 16-byte boundaries; the segments are
 // padded to multiples of four in this index space).  The FP32 partials of a
 // slot are added in slice order, as in sum_partials / sum_in_partials.
+template <bool V = false>
 __device__ __forceinline__ void fused_fold_quads(const FusedRecovery& f, const FoldSeg* sg, int seg0, int seg1,
                                                  int cta, int ncta)
 {
     const int64_t q0 = f.abeg[seg0] >> 2, q1 = f.abeg[seg1] >> 2;
     const int64_t per = ((q1 - q0 + ncta - 1) / ncta + NT - 1) / NT * NT;  // contiguous chunk per CTA
     const int64_t c0 = min(q1, q0 + cta * per), c1 = min(q1, c0 + per);
-    int64_t q = c0 + threadIdx.x;
+    int64_t q = c0 + vtid<V>();
     if (q >= c1) return;
     int lo = seg0, hi = seg1 - 1;  // last segment with abeg <= 4q
     while (lo < hi) {
@@ -720,30 +729,32 @@ __device__ __forceinline__ void fused_fold_quads(const FusedRecovery& f, const F
     }
 }
 
-// Orders 1..DF of every window, cooperative launch (all CTAs resident).
-template <int DF>
-__global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__ FusedRecovery f)
+// Orders 1..DF of every window, as a cooperative grid of (virtual) CTAs: this
+// one is `cta` of G, all resident.  The grid barriers synchronise the real CTAs
+// (every virtual CTA of a real one reaches them together).  `red` is this
+// virtual CTA's reduction buffer; s_seg, s_args and s_base are shared by the
+// real CTA.
+template <int DF, bool V>
+__device__ __forceinline__ void recover_fused_body(const FusedRecovery& f, const int cta, const int G, double* red,
+                                                   FoldSeg* s_seg, CumArgs* s_args, unsigned long long* s_base)
 {
-    __shared__ double red[NT / 32];
-    __shared__ unsigned long long s_base;
-    __shared__ FoldSeg s_seg[kFoldSegSmem];
-    __shared__ CumArgs s_args[DF + 1];
+    const int tid = vtid<V>();
     const bool seg_smem = f.fold && f.nseg <= kFoldSegSmem;
     if (seg_smem && (int)threadIdx.x < f.nseg) s_seg[threadIdx.x] = fold_seg(f.args[f.aarg[threadIdx.x]]);
     if (f.nwin == 1) {  // one window: its arguments of orders 1..DF, copied once
         constexpr int words = (int)(sizeof(CumArgs) / sizeof(int));
         static_assert(sizeof(CumArgs) % sizeof(int) == 0, "CumArgs copied as words");
-        for (int i = threadIdx.x; i < DF * words; i += NT) {
+        for (int i = threadIdx.x; i < DF * words; i += blockDim.x) {
             const int o = i / words + 1, k = i - (i / words) * words;
             reinterpret_cast<int*>(&s_args[o])[k] = reinterpret_cast<const int*>(&f.args[o])[k];
         }
     }
-    GridBarrier gb = grid_barrier_init(f.bar, &s_base);  // synchronises the CTA
+    GridBarrier gb = grid_barrier_init(f.bar, s_base);  // synchronises the CTA
     const FoldSeg* sg = seg_smem ? s_seg : nullptr;
     const CumArgs* sargs = f.nwin == 1 ? s_args : nullptr;
     // 1. the sums of orders 1..min(DF, 3) take the shift's workspace
     if (f.fold) {
-        fused_fold(f, sg, 0, f.nseg_lo, blockIdx.x, gridDim.x);
+        fused_fold<V>(f, sg, 0, f.nseg_lo, cta, G);
         grid_barrier(gb, f.status);
     }
     // 2. orders 1..min(DF, 3): C_1, C_2 recomputed from the sums where a higher
@@ -751,32 +762,31 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
     //    order-4 sums still take their workspace (nothing reads them before
     //    step 3), the first n13 CTAs take the small orders and the others that
     //    fold, so the latency-bound small orders overlap the memory-bound fold.
-    const int G = gridDim.x;
     int64_t u13 = 0;
     for (int k = 1; k <= (DF < 3 ? DF : 3); ++k) u13 += f.ustart[(int64_t)k * (f.nwin + 1) + f.nwin];
     const bool split = f.fold && f.nseg > f.nseg_lo && G > 1;
     const int n13 = split ? (int)(u13 < G / 2 ? (u13 > 0 ? u13 : 1) : G / 2) : G;
-    if ((int)blockIdx.x >= n13) {
-        fused_fold_quads(f, sg, f.nseg_lo, f.nseg, blockIdx.x - n13, G - n13);
+    if (cta >= n13) {
+        fused_fold_quads<V>(f, sg, f.nseg_lo, f.nseg, cta - n13, G - n13);
     } else {
         int64_t rot = 0;
-        fused_order<1, 0>(f, sargs, red, rot, blockIdx.x, n13);
+        fused_order<1, 0, V>(f, sargs, red, rot, cta, n13);
         rot += f.ustart[1 * (f.nwin + 1) + f.nwin];
         if (DF >= 2) {
-            fused_order<(DF >= 2 ? 2 : 1), 1>(f, sargs, red, rot, blockIdx.x, n13);
+            fused_order<(DF >= 2 ? 2 : 1), 1, V>(f, sargs, red, rot, cta, n13);
             rot += f.ustart[2 * (f.nwin + 1) + f.nwin];
         }
-        if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2>(f, sargs, red, rot, blockIdx.x, n13);
+        if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2, V>(f, sargs, red, rot, cta, n13);
     }
     // 3. order 4 reads the stored C_1..C_3
     if (DF >= 4) {
         grid_barrier(gb, f.status);
-        fused_order<(DF >= 4 ? 4 : 1), 0>(f, sargs, red, 0, blockIdx.x, G);
+        fused_order<(DF >= 4 ? 4 : 1), 0, V>(f, sargs, red, 0, cta, G);
     }
     grid_barrier(gb, f.status);
     // norms: one CTA per (window, order), the partials of the order's units of
     // the window added thread-strided, then the fixed CTA tree
-    for (int64_t it = blockIdx.x; it < (int64_t)f.nwin * DF; it += G) {
+    for (int64_t it = cta; it < (int64_t)f.nwin * DF; it += G) {
         const int w = (int)(it / DF), s = (int)(it - (it / DF) * DF) + 1;
         const NormArgs& na = f.norm[w];
         double z = 0.0;
@@ -784,7 +794,7 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
             const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
             const double* part = f.upart + f.upoff[s];
             const int64_t q1 = us[w + 1];
-            int64_t q = us[w] + threadIdx.x;
+            int64_t q = us[w] + tid;
             for (; q + 3 * NT < q1; q += 4 * NT) {  // four loads in flight, added in index order
                 const double v0 = part[q], v1 = part[q + NT], v2 = part[q + 2 * NT], v3 = part[q + 3 * NT];
                 z += v0;
@@ -794,16 +804,16 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
             }
             for (; q < q1; q += NT) z += part[q];
         }
-        z = cta_sum(z, red);
-        if (threadIdx.x == 0 && s <= na.d) na.fro2[s - 1] = z;
+        z = cta_sum<V>(z, red);
+        if (tid == 0 && s <= na.d) na.fro2[s - 1] = z;
     }
     // the drift of the mean from the shift (single windows with a drift flag):
     // C_1 and C_2 are complete after the barriers above; the last CTA measures it
-    if (f.nwin == 1 && DF >= 2 && blockIdx.x == gridDim.x - 1 && f.norm[0].drift_flag != nullptr) {
+    if (f.nwin == 1 && DF >= 2 && cta == G - 1 && f.norm[0].drift_flag != nullptr) {
         const NormArgs& na = f.norm[0];
         double r = 0.0;
-        __syncthreads();  // red may still be read by a norm reduction of this CTA
-        for (int i = threadIdx.x; i < na.n; i += NT) {
+        vsync<V>();  // red may still be read by a norm reduction of this CTA
+        for (int i = tid; i < na.n; i += NT) {
             const int j = i / na.b, a = i - j * na.b;
             // diagonal block (j, j): rank j * nbar - j (j - 1) / 2, in-block offset a * b + a
             const int64_t rk = (int64_t)j * na.nbar - (int64_t)j * (j - 1) / 2;
@@ -812,9 +822,9 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
             if (v > 0.0) r = fmax(r, m / sqrt(v));
         }
         for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = r;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if ((tid & 31) == 0) red[tid >> 5] = r;
+        vsync<V>();
+        if (tid == 0) {
             for (int w = 1; w < NT / 32; ++w) r = fmax(r, red[w]);
             *na.drift = r;
             if (r > na.drift_limit) *na.drift_flag = 1;
@@ -822,11 +832,86 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
     }
     // every CTA read the ring heads (FIFO slots) before the last barrier
     if (f.advance_heads)
-        for (int w = blockIdx.x * NT + threadIdx.x; w < f.nwin; w += gridDim.x * NT) {
+        for (int w = cta * NT + tid; w < f.nwin; w += G * NT) {
             const NormArgs& na = f.norm[w];
             *na.head = (*na.head + f.advance) % na.T;
             if (na.head_stage != nullptr) *na.head_stage = (*na.head_stage + f.advance) % na.T;
         }
+}
+
+template <int DF>
+__global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__ FusedRecovery f)
+{
+    __shared__ double red[NT / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ FoldSeg s_seg[kFoldSegSmem];
+    __shared__ CumArgs s_args[DF + 1];
+    recover_fused_body<DF, false>(f, blockIdx.x, gridDim.x, red, s_seg, s_args, &s_base);
+}
+
+// One shift of a batch of windows whose orders are all recovered by the fused
+// recovery (d <= kFusedMax), as a single cooperative launch: one CTA of 1024
+// threads per SM, its phases separated by the grid barrier.
+//   0. FP16 form: the per-variable maxima start from zero;
+//   1. staging of X_(+) (and X_(-)), four virtual CTAs of 256 threads per CTA;
+//   2. the Khatri-Rao operand build (every thread), after which the staging
+//      ring heads advance; the operands are then fenced for the async proxy,
+//      because the GEMM reads them with TMA;
+//   3. the tcgen05 GEMM on warps 0-5 of every CTA (the other warps wait at the
+//      grid barrier);
+//   4. the fused recovery of orders 1..DF and the norms, the four quarters of a
+//      CTA as virtual CTAs.
+// Every wait is bounded as in the kernels these phases come from.
+constexpr int kShiftThreads = 1024;
+constexpr size_t kShiftStageSmem = 4 * 2 * 32 * 33 * sizeof(float);  // staging tiles of four virtual CTAs
+
+template <bool BF16, int DF>
+__global__ void __launch_bounds__(kShiftThreads, 1)
+k_batch_shift(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB32,
+              const __grid_constant__ CUtensorMap mapB64, const __grid_constant__ CUtensorMap mapB128,
+              const __grid_constant__ BatchShiftArgs a, const __grid_constant__ FusedRecovery f)
+{
+    extern __shared__ unsigned char shift_smem[];  // the GEMM's stages; the staging tiles before them
+    __shared__ double red[4][NT / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ FoldSeg s_seg[kFoldSegSmem];
+    __shared__ CumArgs s_args[DF + 1];
+    const int vid = (int)(threadIdx.x >> 8);
+    const int vcta = (int)blockIdx.x * 4 + vid, nv = (int)gridDim.x * 4;
+    const int gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x), gstride = (int)(gridDim.x * blockDim.x);
+    GridBarrier gb = grid_barrier_init(f.bar, &s_base);
+    // 0. the per-variable maxima of the FP16 form
+    if (a.scaled) {
+        for (int64_t i = gtid; i < a.nvmax; i += gstride) a.vmax[i] = 0.0f;
+        grid_barrier(gb, f.status);
+    }
+    // 1. staging
+    {
+        float(*tin)[33] = reinterpret_cast<float(*)[33]>(shift_smem + (size_t)vid * 2 * 32 * 33 * sizeof(float));
+        float(*tout)[33] = tin + 32;
+        const int per_stream = a.tiles_x * a.tiles_y;
+        for (int t = vcta; t < per_stream * a.nstreams; t += nv) {
+            const int z = t / per_stream, r = t - z * per_stream, y = r / a.tiles_x, x = r - y * a.tiles_x;
+            tcdev::stage_push_tile<true>(a.sdesc, a.xin, nullptr, -1, a.p, a.P, a.Kcap, a.leaving, a.scaled, x, y,
+                                         z, tin, tout);
+        }
+    }
+    grid_barrier(gb, f.status);
+    // 2. operand build; the staging heads advance (every staging read is done)
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < a.nstreams; i += blockDim.x) {
+            int64_t* hp = a.sdesc[i].head;
+            *hp = (*hp + a.p) % a.sdesc[i].T;
+        }
+    tcdev::kr_build_range<BF16>(a.sdesc, a.Kcap, a.opvars, a.oprows, a.nkb, a.ops, a.P, a.opexp, gtid, gstride);
+    ptx::fence_proxy_async_global();
+    grid_barrier(gb, f.status);
+    // 3. the GEMM
+    if (threadIdx.x < tcdev::GEMM_THREADS)
+        tcdev::kr_gemm_body<BF16, true>(&mapA, &mapB32, &mapB64, &mapB128, a.gemm, shift_smem);
+    grid_barrier(gb, f.status);
+    // 4. the recovery of orders 1..DF and the norms
+    recover_fused_body<DF, true>(f, vcta, nv, red[vid], s_seg, s_args, &s_base);
 }
 
 // Fold of the orders that take the shift's workspace before their recovery
@@ -1194,6 +1279,63 @@ int fused_grid(int dfused, size_t smem, int sm_count, int per_sm_max)
     }
     if (e != cudaSuccess || per_sm < 1) return 0;
     return std::min(per_sm, per_sm_max) * sm_count;
+}
+
+template <bool BF16, int DF>
+cudaError_t launch_batch_shift_t(const TcPlan& plan, const BatchShiftArgs& a, const FusedRecovery& f, int grid,
+                                 cudaStream_t st)
+{
+    const size_t smem = std::max(tcdev::GEMM_SMEM, kShiftStageSmem);
+    cudaError_t e = smem_opt_in((const void*)k_batch_shift<BF16, DF>, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kShiftThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_shift<BF16, DF>, plan.mapA, plan.mapB[0], plan.mapB[1], plan.mapB[2], a, f);
+}
+
+template <bool BF16, int DF>
+int batch_shift_blocks_t()
+{
+    const size_t smem = std::max(tcdev::GEMM_SMEM, kShiftStageSmem);
+    if (smem_opt_in((const void*)k_batch_shift<BF16, DF>, smem) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_shift<BF16, DF>, kShiftThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+int batch_shift_blocks_per_sm(int precision, int dfused)
+{
+    const bool bf = precision == 1;
+    switch (dfused) {
+    case 1: return bf ? batch_shift_blocks_t<true, 1>() : batch_shift_blocks_t<false, 1>();
+    case 2: return bf ? batch_shift_blocks_t<true, 2>() : batch_shift_blocks_t<false, 2>();
+    case 3: return bf ? batch_shift_blocks_t<true, 3>() : batch_shift_blocks_t<false, 3>();
+    case 4: return bf ? batch_shift_blocks_t<true, 4>() : batch_shift_blocks_t<false, 4>();
+    default: return 0;
+    }
+}
+
+cudaError_t launch_batch_shift(const TcPlan& plan, const BatchShiftArgs& a, const FusedRecovery& f, int dfused,
+                               int grid, cudaStream_t st)
+{
+    const bool bf = plan.precision == 1;
+    switch (dfused) {
+    case 1: return bf ? launch_batch_shift_t<true, 1>(plan, a, f, grid, st) : launch_batch_shift_t<false, 1>(plan, a, f, grid, st);
+    case 2: return bf ? launch_batch_shift_t<true, 2>(plan, a, f, grid, st) : launch_batch_shift_t<false, 2>(plan, a, f, grid, st);
+    case 3: return bf ? launch_batch_shift_t<true, 3>(plan, a, f, grid, st) : launch_batch_shift_t<false, 3>(plan, a, f, grid, st);
+    case 4: return bf ? launch_batch_shift_t<true, 4>(plan, a, f, grid, st) : launch_batch_shift_t<false, 4>(plan, a, f, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_recover_fused(const FusedRecovery& f, int dfused, int grid, size_t smem, cudaStream_t st)

@@ -95,6 +95,13 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map)
 
 // Make generic-proxy writes to shared memory visible to the async proxy
 // (tensor-core operand reads).
+// Generic-proxy writes to global memory made visible to later async-proxy
+// (TMA) reads, e.g. by other CTAs after a grid barrier.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

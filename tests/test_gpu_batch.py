@@ -187,3 +187,46 @@ def test_tile_shape_does_not_change_results(form):
         assert t["rows_per_item"] in (64, 128) and t["group"] in (1, 4, 8, 16) and t["ksplit"] >= 1
         with pytest.raises(CumwinError):
             h.set_tiles(1, 100, 4)
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+@pytest.mark.parametrize("p", [64, 96])
+def test_single_launch_shift_matches_phase_by_phase(form, p):
+    """A batch whose windows all have d <= 4 runs a shift as one cooperative launch
+    (staging, operand build, tensor-core update and fused recovery as phases
+    separated by grid barriers): bitwise the results of the same shift run phase
+    by phase, with (p = 64) and without (p = 96) the batch-sum FIFO, eagerly and
+    replayed from a captured CUDA graph."""
+    b, steps = 4, 4
+    specs = [s for s in SPECS if s[1] <= 4]
+    data = make_batch_data(specs, p, steps, 300)
+    ns, ds, Ts = zip(*specs)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        with CumWinBatch(ns, ds, Ts, b, p, form) as one, CumWinBatch(ns, ds, Ts, b, p, form) as ph:
+            assert one.set_single_launch(True)
+            assert ph.set_single_launch(False)
+            firsts = [torch.from_numpy(X[:T]).cuda() for X, (n, d, T) in zip(data, specs)]
+            one.fill(firsts)
+            ph.fill(firsts)
+            packs = [one.pack([torch.from_numpy(X[T + k * p: T + (k + 1) * p]).cuda()
+                               for X, (n, d, T) in zip(data, specs)]) for k in range(steps)]
+            one.push(packs[0])
+            ph.push(packs[0])
+            assert one.launches() == 1 and ph.launches() >= 4
+            buf = packs[1].clone()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                one.push(buf)
+            for k in range(1, steps):
+                buf.copy_(packs[k])
+                g.replay()
+                ph.push(packs[k])
+            for i, (n, d, T) in enumerate(specs):
+                for s in range(1, d + 1):
+                    assert torch.equal(one.cumulants(i, s), ph.cumulants(i, s)), (i, s)
+            f1, _ = one.norms()
+            f2, _ = ph.norms()
+            assert np.array_equal(f1, f2, equal_nan=True)
+            assert one.status() == 0
+    torch.cuda.synchronize()
