@@ -659,6 +659,26 @@ def run_batch(args, rank: int, world: int):
             l1[k].record(cap_stream)
     torch.cuda.synchronize()
     lat = sorted(a.elapsed_time(z) for a, z in zip(l0, l1))
+    # the same shifts phase by phase (separate launches, one graph per shift), for comparison
+    phased = None
+    if B.set_single_launch(False):
+        g2 = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cap_stream):
+            with torch.cuda.graph(g2, stream=cap_stream):
+                B.push(buf)
+        torch.cuda.synchronize()
+        p0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        p1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        with torch.cuda.stream(cap_stream):
+            for k in range(steps):
+                buf.copy_(packs[k % nsteps])
+                p0[k].record(cap_stream)
+                g2.replay()
+                p1[k].record(cap_stream)
+        torch.cuda.synchronize()
+        phased = {"shift_ms_mean": statistics.mean(a.elapsed_time(z) for a, z in zip(p0, p1)),
+                  "launches_per_shift": B.launches(), "form": "the same shift as separate launches, one graph"}
+        B.set_single_launch(True)
     # accuracy on a sample of windows after the distinct shifts
     err = {}
     if rank == 0:
@@ -723,7 +743,7 @@ def run_batch(args, rank: int, world: int):
                        "b": b, "T": "U{2^12,2^14}", "p": p, "precision": args.precision,
                        "l2": "inputs and state larger than L2 (GB of sums), no flush",
                        "launch": "one CUDA graph per shift", "ksplit": ksplit, "tiles": B.tiles()},
-            "batch": {"shift_ms_mean": mean_ms, "shift_ms_p50": lat[len(lat) // 2],
+            "batch": {"phase_by_phase": phased, "shift_ms_mean": mean_ms, "shift_ms_p50": lat[len(lat) // 2],
                       "shift_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "replays": reps,
                       "windows": 512, "state_elements": int(sum(
                           sum(__import__("paper_1701_06446_gb300").layout_size(n_, b, s_)

@@ -27,6 +27,7 @@ constexpr int A_PART = TM * 128;      // bytes of one 16-bit part of an A tile (
 constexpr int B_PART = NMAX * 128;    // bytes of one 16-bit part of a B tile (up to NMAX rows)
 constexpr int STAGE_BYTES = 2 * A_PART + 2 * B_PART;
 constexpr size_t GEMM_SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+constexpr size_t gemm_smem(int nst) { return (size_t)nst * STAGE_BYTES + 1024; }
 
 // ---------------------------------------------------------------------------
 // staging: shifted samples, transposed to [variable][sample]
@@ -244,9 +245,9 @@ __device__ __forceinline__ void gemm_sync()
     }
 }
 
-// The GEMM on threads 0..GEMM_THREADS-1 of a CTA; dsm_raw: STAGES stages of
-// dynamic shared memory (GEMM_SMEM bytes).
-template <bool BF16, bool MEGA>
+// The GEMM on threads 0..GEMM_THREADS-1 of a CTA; dsm_raw: NST stages of
+// dynamic shared memory (gemm_smem(NST) bytes).
+template <bool BF16, bool MEGA, int NST = STAGES>
 __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CUtensorMap* mapB32_p,
                                              const CUtensorMap* mapB64_p, const CUtensorMap* mapB128_p,
                                              const TcGemmArgs& args, unsigned char* dsm_raw)
@@ -257,7 +258,7 @@ __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CU
     const CUtensorMap& mapB128 = *mapB128_p;
     unsigned char* dsm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+    __shared__ __align__(8) uint64_t bar_full[NST], bar_empty[NST];
     __shared__ __align__(8) uint64_t bar_accfull[2], bar_accempty[2], bar_final;
     __shared__ uint32_t s_tbase;
     __shared__ int s_abort;
@@ -268,7 +269,7 @@ __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CU
     const int nunits = args.nitems * args.ksplit;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&bar_full[s], 1);
             mbar_init(&bar_empty[s], 1);
         }
@@ -308,8 +309,8 @@ __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CU
                 const uint32_t bytes = 2u * A_PART + 2u * (uint32_t)item.bbox * 128u;
                 const int nch = R.nplus + R.nminus;
                 for (int q = 0; q < nch; ++q, ++g) {
-                    const uint32_t st = g % STAGES, use = g / STAGES;
-                    if (g >= STAGES && !mbar_wait(&bar_empty[st], (use - 1) & 1, kWaitLimit)) {
+                    const uint32_t st = g % NST, use = g / NST;
+                    if (g >= NST && !mbar_wait(&bar_empty[st], (use - 1) & 1, kWaitLimit)) {
                         atomicOr(args.status, kStatusTimeout);
                         s_abort = 1;
                         stop = true;
@@ -330,8 +331,8 @@ __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CU
                 }
             }
             // drain: every issued load has landed before the CTA may exit (bounded)
-            for (uint32_t q = g > STAGES ? g - STAGES : 0; q < g; ++q)
-                mbar_wait(&bar_full[q % STAGES], (q / STAGES) & 1, kWaitLimit);
+            for (uint32_t q = g > NST ? g - NST : 0; q < g; ++q)
+                mbar_wait(&bar_full[q % NST], (q / NST) & 1, kWaitLimit);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
@@ -351,7 +352,7 @@ __device__ __forceinline__ void kr_gemm_body(const CUtensorMap* mapA_p, const CU
                 tc_fence_after();
                 const uint32_t idesc = idesc_f16(TM, (item.nrows + 15) & ~15, BF16);
                 for (int q = 0; q < nch; ++q, ++g) {
-                    const uint32_t st = g % STAGES, use = g / STAGES;
+                    const uint32_t st = g % NST, use = g / NST;
                     if (!mbar_wait(&bar_full[st], use & 1, kWaitLimit)) {
                         atomicOr(args.status, kStatusTimeout);
                         s_abort = 1;

@@ -863,6 +863,9 @@ __global__ void __launch_bounds__(NT, 4) k_recover_fused(const __grid_constant__
 //      CTA as virtual CTAs.
 // Every wait is bounded as in the kernels these phases come from.
 constexpr int kShiftThreads = 1024;
+// GEMM stages of the single-launch shift: one fewer than the GEMM kernel's, so
+// that the recovery phase keeps more of the SM's memory as L1 for its gathers
+constexpr int kShiftStages = 2;
 constexpr size_t kShiftStageSmem = 4 * 2 * 32 * 33 * sizeof(float);  // staging tiles of four virtual CTAs
 
 template <bool BF16, int DF>
@@ -908,7 +911,7 @@ k_batch_shift(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     grid_barrier(gb, f.status);
     // 3. the GEMM
     if (threadIdx.x < tcdev::GEMM_THREADS)
-        tcdev::kr_gemm_body<BF16, true>(&mapA, &mapB32, &mapB64, &mapB128, a.gemm, shift_smem);
+        tcdev::kr_gemm_body<BF16, true, kShiftStages>(&mapA, &mapB32, &mapB64, &mapB128, a.gemm, shift_smem);
     grid_barrier(gb, f.status);
     // 4. the recovery of orders 1..DF and the norms
     recover_fused_body<DF, true>(f, vcta, nv, red[vid], s_seg, s_args, &s_base);
@@ -1285,8 +1288,12 @@ template <bool BF16, int DF>
 cudaError_t launch_batch_shift_t(const TcPlan& plan, const BatchShiftArgs& a, const FusedRecovery& f, int grid,
                                  cudaStream_t st)
 {
-    const size_t smem = std::max(tcdev::GEMM_SMEM, kShiftStageSmem);
+    const size_t smem = std::max(tcdev::gemm_smem(kShiftStages), kShiftStageSmem);
     cudaError_t e = smem_opt_in((const void*)k_batch_shift<BF16, DF>, smem);
+    if (e != cudaSuccess) return e;
+    // the smallest shared-memory split that holds it: the rest of the SM's memory is L1
+    e = cudaFuncSetAttribute((const void*)k_batch_shift<BF16, DF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)std::min<size_t>(100, ((smem + 16 * 1024) * 100 + 228 * 1024 - 1) / (228 * 1024)));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
@@ -1304,7 +1311,7 @@ cudaError_t launch_batch_shift_t(const TcPlan& plan, const BatchShiftArgs& a, co
 template <bool BF16, int DF>
 int batch_shift_blocks_t()
 {
-    const size_t smem = std::max(tcdev::GEMM_SMEM, kShiftStageSmem);
+    const size_t smem = std::max(tcdev::gemm_smem(kShiftStages), kShiftStageSmem);
     if (smem_opt_in((const void*)k_batch_shift<BF16, DF>, smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_shift<BF16, DF>, kShiftThreads, smem) !=
