@@ -92,11 +92,12 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
             "recovery_bytes": rec_bytes, "elements": E, "computed_elements": Ecomp, "two_word": two_word}
 
 
-# DRAM bytes (read + write) per launch from an ncu capture of the current kernels (see
-# profiles/), by workload: the recovery's launches of one shift, and the GEMM.  None where
-# no capture of the current kernels exists.
-RECOVERY_TRAFFIC: dict[str, int] = {}
-GEMM_TRAFFIC: dict[str, int] = {}
+# DRAM bytes (read + write) per shift from an ncu capture of the current kernels (profiles/
+# launches_*.md), by workload: the recovery's launches of one shift, and the GEMM.  The n=48
+# workload's were taken with a window of 2^13 samples, whose per-launch work is the same.
+# None where no capture of the current kernels exists.
+RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2048007509, "n60_d4_b3_T32768_p1024": 13007616}
+GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2579758251, "n60_d4_b3_T32768_p1024": 15829120}
 
 
 def fp64_peak_tflops(dev) -> float:
