@@ -1078,14 +1078,24 @@ __global__ void __launch_bounds__(NT) k_canon_expand(const CumArgs* __restrict__
         const int q = a.blkpat[blk];
         const int d0 = a.dup_start[q], d1 = a.dup_start[q + 1];
         double* C = a.Cout + blk * a.bs;
-        for (int i = d0 + (int)threadIdx.x; i < d1; i += NT) {
-            const int2 oc = a.dup[i];  // {offset, canonical offset}
-            const double v = C[oc.y];
-            C[oc.x] = v;
-            if (a.split) {
-                const int64_t e = blk * a.bs + oc.x;
-                a.C2[a.s][e] = tw_split(v);
-                a.S2[a.s][e] = tw_split(a.S[a.s][e]);
+        // four copies per thread and round, their loads issued before their stores
+        constexpr int U = 4;
+        for (int i0 = d0 + (int)threadIdx.x; i0 < d1; i0 += U * NT) {
+            int2 oc[U];  // {offset, canonical offset}
+            double v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) oc[u] = i0 + u * NT < d1 ? a.dup[i0 + u * NT] : make_int2(-1, 0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = oc[u].x >= 0 ? C[oc[u].y] : 0.0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (oc[u].x < 0) continue;
+                C[oc[u].x] = v[u];
+                if (a.split) {
+                    const int64_t e = blk * a.bs + oc[u].x;
+                    a.C2[a.s][e] = tw_split(v[u]);
+                    a.S2[a.s][e] = tw_split(a.S[a.s][e]);
+                }
             }
         }
     }
