@@ -505,7 +505,11 @@ int64_t cumwin_block_rank(int n, int b, int order, const int* j);
  * its entries, each in [0, n)); -1 on a bad argument. */
 int64_t cumwin_element_index(int n, int b, int order, const int* i);
 /* Self-test of the host tables that map update tiles and cumulant sub-blocks
- * to storage indices against a direct enumeration (0 = pass). */
+ * to storage indices against a direct enumeration (0 = pass): the full update
+ * tables, the canonical-element tables, the compressed update tables (every
+ * canonical element produced once, at the workspace slot its rank pair gives)
+ * and the sub-block lookups of the recovery; a positive code names the first
+ * check that failed. */
 int cumwin_selftest_tables(int n, int b, int order);
 
 /* Message for a return code, and the detail of the last CUDA error seen by

@@ -441,8 +441,17 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     h->upd.npad = npad;
     h->ut.assign(d + 1, UpdateTables{});
     std::vector<UpdTile> tiles;
+    // single windows: orders 5-6 with blocks of at least 256 elements compute one
+    // element per class of equal entries (CanonTables); their update GEMMs then
+    // produce only the rows and columns that canonical elements use, and their sums
+    // exist only there (every sub-tuple of a canonical element is canonical in its
+    // own block, so the recovery of the orders above reads no other element)
+    auto canonical = [&](int s) {
+        return own_tc && s >= kCanonMinOrder && s <= kCanonMaxOrder && ipow(b, s) >= kCanonMinBlock &&
+               ipow(b, s - 1) <= 0xffff;
+    };
     for (int s = 1; s <= d; ++s) {
-        h->ut[s] = build_update_tables(n, b, s);
+        h->ut[s] = build_update_tables(n, b, s, canonical(s));
         const UpdateTables& t = h->ut[s];
         OrderTables& ot = h->upd.ord[s];
         CW_TRY(h->upload((uint32_t**)&ot.rowvar, t.rowvar));
@@ -512,18 +521,17 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         a.accum = 0;
         a.bR = (int32_t)ipow(b, s - split_rows(s));
         // the top order's sums follow the workspace order in the mixed forms,
-        // so that folding a shift into them is one coalesced pass
-        a.sgemm = precision != CUMWIN_FP64 && s == d;
+        // so that folding a shift into them is one coalesced pass; so do the
+        // canonical orders', which exist at canonical elements only (compressed
+        // update tables) and are folded by their recovery
+        a.sgemm = precision != CUMWIN_FP64 && (s == d || canonical(s));
         if (precision != CUMWIN_FP64) {
             int32_t* wb = nullptr;
             CW_TRY(h->upload(&wb, build_w_blocks(h->ut[s], n, b)));
             a.wblk = wb;
         }
         h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
-        // single windows: orders 5-6 with blocks of at least 256 elements compute one
-        // element per class of equal entries (CanonTables)
-        if (own_tc && s >= kCanonMinOrder && s <= kCanonMaxOrder && ipow(b, s) >= kCanonMinBlock &&
-            ipow(b, s - 1) <= 0xffff) {
+        if (canonical(s)) {
             const bool sh = s == d && h->top1 >= 0;  // a shard recovers its block range of the top order
             const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup, sh ? h->top0 : 0,
                                                       sh ? h->top1 : -1);
@@ -532,6 +540,10 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             CW_TRY(h->upload((int32_t**)&a.can_off, cn.can_off));
             CW_TRY(h->upload((int32_t**)&a.map_off, cn.map_off));
             CW_TRY(h->upload((int32_t**)&a.can_copies, cn.can_copies));
+            if (a.sgemm) {
+                CW_TRY(h->upload((int32_t**)&a.can_lr, cn.can_lr));
+                CW_TRY(h->upload((int32_t**)&a.map_lr, cn.map_lr));
+            }
             CW_TRY(h->upload((int32_t**)&a.dup_start, cn.dup_start));
             int32_t* dd = nullptr;
             CW_TRY(h->upload(&dd, cn.dup));
@@ -543,6 +555,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             a.nunits = (int32_t)(cn.units.size() / 4);
             a.npblocks = (int32_t)cn.pblocks.size();
             a.canon = 1;
+            for (int k = s + 1; k <= d; ++k) a.split_copies |= canonical(k) ? 0 : 1;
             h->canon_units[s] = a.nunits;
         }
     }
@@ -751,9 +764,9 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
             *launches += 1;
         }
         const bool canon = canon_units != nullptr && canon_units[s] > 0;
-        // the top order (workspace order) and canonical orders are folded first, except a
-        // canonical top order, which k_canon folds at its canonical elements
-        if (accum != 0 && !(canon && s == d)) {
+        // the top order (workspace order) is folded first; canonical orders (workspace
+        // order too) are folded by k_canon at their canonical elements
+        if (accum != 0 && !canon) {
             CW_TRY(launch_fold_linear(args + (size_t)s * nwin, nwin, fp.emax[s], sm_count, st));
             *launches += 1;
         }
@@ -830,7 +843,7 @@ std::vector<TcAccSeg> acc_segments(const std::vector<cumwin_s*>& wins, const TcP
             g.S = h->S[s];
             g.wblk = h->cum[s].wblk;
             g.begin = tc.wbase[i] + h->Eoff[s];
-            g.E = h->E[s];
+            g.E = h->cum[s].sgemm ? h->ut[s].wsize : h->E[s];  // sums in workspace order: its slots
             g.bs = (int32_t)ipow(h->b, s);
             g.bR = h->cum[s].bR;
             g.head = h->head_rec;
@@ -1096,6 +1109,45 @@ int cumwin_selftest_tables(int n, int b, int s)
             }
         }
         if (canon != cn.canonical) return 11;
+        // 4. compressed update tables: the workspace slots are [0, wsize) once each,
+        //    every canonical element is produced once, and at the slot its rank pair
+        //    (can_lr, map_lr of every offset of its class) gives
+        const UpdateTables tc = build_update_tables(n, b, s, true);
+        const std::vector<int64_t> rowc = build_w_rows(tc);
+        const std::vector<int32_t> wblc = build_w_blocks(tc, n, b);
+        std::vector<int64_t> slot_of(E, -1);
+        std::vector<int> chits(tc.wsize, 0);
+        const int ncc = (int)tc.colvar.size();
+        for (int m = 0; m < nbar; ++m)
+            for (int r = tc.rowstart[m]; r < tc.rowstart[m + 1]; ++r)
+                for (int c = tc.colstart[m]; c < ncc; ++c) {
+                    int vars[kMaxOrder], jj[kMaxOrder];
+                    for (int k = 0; k < tc.h; ++k) vars[k] = (tc.rowvar[r] >> (8 * k)) & 0xff;
+                    for (int k = 0; k < tc.sh; ++k) vars[tc.h + k] = (tc.colvar[c] >> (8 * k)) & 0xff;
+                    for (int k = 0; k < s; ++k) jj[k] = vars[k] / b;
+                    const int64_t rk = rank_sorted(jj, s, nbar);
+                    int64_t off = 0;
+                    for (int k = 0; k < s; ++k) off = off * b + vars[k] % b;
+                    const int64_t e = rk * bs + off, w = rowc[r] + c;
+                    if (rk < 0 || tc.rowoff[r] + tc.coloff[c] != e || w < 0 || w >= tc.wsize) return 12;
+                    if (slot_of[e] >= 0) return 13;
+                    slot_of[e] = w;
+                    chits[w]++;
+                }
+        for (int64_t w = 0; w < tc.wsize; ++w)
+            if (chits[w] != 1) return 14;
+        for (int64_t q = 0; q < nb; ++q) {
+            const int pat = cn.blkpat[q];
+            for (int64_t o = 0; o < bs; ++o) {
+                const int64_t co = cn.map_off[(size_t)pat * bs + o];
+                const int lr = cn.map_lr[(size_t)pat * bs + o];
+                const int64_t w = wblc[2 * q] + (int64_t)((unsigned)lr >> 16) * wblc[2 * q + 1] + (lr & 0xffff);
+                if (lr < 0 || slot_of[q * bs + co] != w) return 15;
+            }
+        }
+        for (int q = 0; q < cn.npat; ++q)
+            for (int c = cn.can_start[q]; c < cn.can_start[q + 1]; ++c)
+                if (cn.can_lr[c] != cn.map_lr[(size_t)q * bs + cn.can_off[c]]) return 15;
     }
     // 3. cumulant tables: sub-block lookups of a synthetic symmetric tensor
     //    f(i) = prod_k (i_k + 1.5) return f of the sub-multi-index.
@@ -1523,7 +1575,8 @@ int cumwin_moments(cumwin_t h, int order, double* out_dev)
     if (h == nullptr || out_dev == nullptr || order < 1 || order > h->d) return CUMWIN_EINVAL;
     if (!h->filled) return CUMWIN_ESTATE;
     CW_TRY(join(h));
-    if (h->cum[order].sgemm)  // kept in workspace order: gather back to the block layout
+    // kept in workspace order, or at canonical elements only: gather back to the block layout
+    if (h->cum[order].sgemm || h->cum[order].canon)
         CW_TRY(launch_gather_sums(h->cum_dev + order, h->E[order], 1.0 / (double)h->T, out_dev, h->stream));
     else
         CW_TRY(launch_scale(h->S[order], 1.0 / (double)h->T, h->E[order], out_dev, h->stream));

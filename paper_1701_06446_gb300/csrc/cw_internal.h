@@ -101,7 +101,8 @@ struct CumArgs {
     int64_t wslice, woff, fstride;
     int32_t ksplit, accum;           // accum: 0 = no workspace, 1 = stacked in/out, 2 = FIFO
     int32_t bR, p;                   // b^(s - h); shift size (accum 2)
-    int32_t sgemm;                   // S_s kept in workspace order (the top order of the mixed forms)
+    int32_t sgemm;                   // S_s kept in workspace order (the top order and the canonical
+                                     // orders of the mixed forms)
     // Mixed forms with d >= kTwoWordMinOrder: the orders below d also keep
     // C_k and S_k as two-word FP32 values (hi + lo, written by their own
     // recovery: `split`), and orders >= kTwoWordMinOrder form the products of
@@ -113,17 +114,26 @@ struct CumArgs {
     // Canonical recovery (CanonTables, cw_layout.h): C_s is computed once per
     // class of entries that super-symmetry makes equal, at the canonical
     // in-block offset, then copied to the other offsets of its block; canon = 0
-    // when the order uses the per-element path.
+    // when the order uses the per-element path.  Its update tables are
+    // compressed (cw_layout.h): the workspace slot of a canonical element is
+    // wblk[2 blk] + rL * wblk[2 blk + 1] + rR, (rL, rR) = can_lr / map_lr, and
+    // its sums (workspace order) exist only at those slots.
     const int32_t* blkpat;
     const int32_t* can_start;
     const int32_t* can_off;
     const int32_t* map_off;
     const int32_t* can_copies;
+    const int32_t* can_lr;     // per canonical offset: rL << 16 | rR
+    const int32_t* map_lr;     // [npat][bs]: can_lr of each offset's canonical offset
     const int32_t* dup_start;
     const int2* dup;
     const int32_t* pblocks;    // the blocks recovered (all, or a shard's range), grouped by pattern
     const int4* units;
     int32_t nunits, canon, npblocks;
+    // k_canon_expand also copies the two-word C_s and S_s to the non-canonical
+    // offsets (only an order above without the canonical recovery reads them:
+    // a canonical element's sub-tuples are canonical in their own blocks)
+    int32_t split_copies;
 };
 constexpr int kTwoWordMinOrder = 5;
 // Orders with the canonical recovery (when b^s >= kCanonMinBlock, single windows).

@@ -84,7 +84,36 @@ static uint32_t pack_vars(const int* v, int cnt)
     return p;
 }
 
-UpdateTables build_update_tables(int n, int b, int s)
+int run_mask(const int* j, int k)
+{
+    int m = 0;
+    for (int i = 1; i < k; ++i)
+        if (j[i] == j[i - 1]) m |= 1 << i;
+    return m;
+}
+
+std::vector<int32_t> half_ranks(int b, int k, int mask)
+{
+    const int64_t bk = ipow(b, k);
+    std::vector<int32_t> rk(bk, -1);
+    int32_t next = 0;
+    int dig[kMaxOrder];
+    for (int64_t a = 0; a < bk; ++a) {
+        int64_t rem = a;
+        for (int i = k - 1; i >= 0; --i) {
+            dig[i] = (int)(rem % b);
+            rem /= b;
+        }
+        bool ok = true;
+        for (int i = 1; i < k && ok; ++i) ok = !((mask >> i) & 1) || dig[i] >= dig[i - 1];
+        if (ok) rk[a] = next++;
+    }
+    return rk;
+}
+
+static std::vector<int64_t> group_bases(const UpdateTables& t);
+
+UpdateTables build_update_tables(int n, int b, int s, bool compressed)
 {
     UpdateTables t;
     const int nbar = (n + b - 1) / b;
@@ -92,6 +121,14 @@ UpdateTables build_update_tables(int n, int b, int s)
     t.s = s;
     t.h = h;
     t.sh = sh;
+    t.compressed = compressed;
+    // rank tables of the runs masks (compressed tables keep the offsets of rank >= 0)
+    std::vector<std::vector<int32_t>> lranks(1 << kMaxOrder), rranks(1 << kMaxOrder);
+    auto keep = [&](std::vector<std::vector<int32_t>>& cache, int k, int mask, int64_t a) {
+        if (!compressed) return true;
+        if (cache[mask].empty()) cache[mask] = half_ranks(b, k, mask);
+        return cache[mask][a] >= 0;
+    };
     const int64_t bs = ipow(b, s), bh = ipow(b, h), bsh = ipow(b, sh);
     auto off_first_below = [&](int m) -> int64_t {  // sorted sh-tuples whose first entry < m
         if (sh == 0) return 0;
@@ -104,6 +141,7 @@ UpdateTables build_update_tables(int n, int b, int s)
     t.rowstart.assign(nbar + 1, 0);
     std::vector<int> full(s), vars(kMaxOrder);
     t.leftrow.assign(nleft, 0);
+    t.leftcnt.assign(nleft, 0);
     for (int m = 0; m < nbar; ++m) {
         t.rowstart[m] = (int32_t)t.rowvar.size();
         const int64_t off_m = off_first_below(m);
@@ -114,7 +152,9 @@ UpdateTables build_update_tables(int n, int b, int s)
             for (int k = 0; k < h; ++k) full[k] = jl[k];
             for (int k = h; k < s; ++k) full[k] = m;
             const int64_t P = rank_sorted(full.data(), s, nbar);
+            const int lm = run_mask(jl, h);
             for (int64_t a = 0; a < bh; ++a) {
+                if (!keep(lranks, h, lm, a)) continue;
                 int64_t rem = a;
                 for (int k = h - 1; k >= 0; --k) {
                     vars[k] = jl[k] * b + (int)(rem % b);
@@ -123,6 +163,7 @@ UpdateTables build_update_tables(int n, int b, int s)
                 t.rowvar.push_back(pack_vars(vars.data(), h));
                 t.rowoff.push_back((P - off_m) * bs + a * bsh);
             }
+            t.leftcnt[q] = (int32_t)t.rowvar.size() - t.leftrow[q];
         }
     }
     t.rowstart[nbar] = (int32_t)t.rowvar.size();
@@ -132,12 +173,17 @@ UpdateTables build_update_tables(int n, int b, int s)
     if (sh == 0) {
         t.colvar.push_back(0u);
         t.coloff.push_back(0);
+        t.rightcol.assign(1, 0);
     } else {
         const std::vector<int> right = enumerate_sorted(nbar, sh);
         const int64_t nright = (int64_t)right.size() / sh;
+        t.rightcol.assign(nright, 0);
         for (int64_t q = 0; q < nright; ++q) {
             const int* jr = &right[q * sh];
+            t.rightcol[q] = (int32_t)t.colvar.size();
+            const int rm = run_mask(jr, sh);
             for (int64_t a = 0; a < bsh; ++a) {
+                if (!keep(rranks, sh, rm, a)) continue;
                 int64_t rem = a;
                 for (int k = sh - 1; k >= 0; --k) {
                     vars[k] = jr[k] * b + (int)(rem % b);
@@ -147,8 +193,13 @@ UpdateTables build_update_tables(int n, int b, int s)
                 t.coloff.push_back(q * bs + a);
             }
         }
-        for (int m = 0; m < nbar; ++m) t.colstart[m] = (int32_t)(off_first_below(m) * bsh);
+        // group m pairs with the columns of the tuples whose first entry is >= m
+        for (int m = 0; m < nbar; ++m) {
+            const int64_t q = off_first_below(m);
+            t.colstart[m] = q < nright ? t.rightcol[q] : (int32_t)t.colvar.size();
+        }
     }
+    t.wsize = group_bases(t)[nbar];
     return t;
 }
 
@@ -185,7 +236,6 @@ std::vector<int32_t> build_w_blocks(const UpdateTables& t, int n, int b)
     const int nbar = (n + b - 1) / b;
     const int s = t.s, h = t.h, sh = t.sh;
     const int64_t ncols = (int64_t)t.colvar.size();
-    const int64_t bsh = ipow(b, sh);
     const std::vector<int64_t> gbase = group_bases(t);
     const std::vector<int> blocks = enumerate_sorted(nbar, s);
     const int64_t nb = (int64_t)blocks.size() / s;
@@ -194,7 +244,7 @@ std::vector<int32_t> build_w_blocks(const UpdateTables& t, int n, int b)
         const int* j = &blocks[q * s];
         const int m = j[h - 1];
         const int64_t r0 = t.leftrow[rank_sorted(j, h, nbar)];
-        const int64_t c0 = sh == 0 ? 0 : rank_sorted(j + h, sh, nbar) * bsh;
+        const int64_t c0 = sh == 0 ? 0 : t.rightcol[rank_sorted(j + h, sh, nbar)];
         const int64_t width = ncols - t.colstart[m];
         out[2 * q] = (int32_t)(gbase[m] + (r0 - t.rowstart[m]) * width + (c0 - t.colstart[m]));
         out[2 * q + 1] = (int32_t)width;
@@ -307,6 +357,21 @@ CanonTables build_canon_tables(int n, int b, int s, int slice, int group, int64_
             }
         }
         for (int c = t.can_start[q]; c < t.can_start[q + 1]; ++c) t.can_copies.push_back(copies[t.can_off[c]]);
+        // ranks of the left / right digits inside the halves' own runs (compressed
+        // update tables); a canonical offset is canonical in each half
+        const int h = split_rows(s);
+        const int64_t bsh = ipow(b, s - h);
+        const std::vector<int32_t> lr = half_ranks(b, h, m & ((1 << h) - 1));
+        const std::vector<int32_t> rr = half_ranks(b, s - h, (m >> h) & ~1);
+        std::vector<int32_t> lr_of(bs, -1);
+        for (int c = t.can_start[q]; c < t.can_start[q + 1]; ++c) {
+            const int64_t o = t.can_off[c];
+            const int32_t rl = lr[o / bsh], rc = rr[o % bsh];
+            lr_of[o] = rl < 0 || rc < 0 ? -1 : (rl << 16) | rc;
+            t.can_lr.push_back(lr_of[o]);
+        }
+        t.map_lr.resize((size_t)(q + 1) * bs);
+        for (int64_t o = 0; o < bs; ++o) t.map_lr[(size_t)q * bs + o] = lr_of[t.map_off[(size_t)q * bs + o]];
         t.canonical += count[q] * (t.can_start[q + 1] - t.can_start[q]);
     }
     t.dup_start.push_back((int32_t)(t.dup.size() / 2));

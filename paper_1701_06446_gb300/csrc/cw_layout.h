@@ -21,24 +21,42 @@ std::vector<int> enumerate_sorted(int nbar, int s);
 double block_multiplicity(const int* j, int s);
 int64_t ipow(int64_t b, int e);
 
+// Runs of equal entries of a sorted k-tuple as a bit mask: bit i (i >= 1)
+// set when j[i] == j[i-1].
+int run_mask(const int* j, int k);
+// Rank of every k-digit in-block offset (digits base b, the first slowest)
+// among the offsets whose digits do not decrease inside the runs of `mask`,
+// in increasing order; -1 for the other offsets.
+std::vector<int32_t> half_ranks(int b, int k, int mask);
+
 // Tables of the order-s update GEMMs (see UpdateArgs in cw_internal.h).
+// compressed: a left tuple jL keeps only the rows whose digits do not
+// decrease inside its own runs of equal block indices, a right tuple only
+// such columns.  Every canonical element of the order (CanonTables) is still
+// produced once, the other elements of diagonal blocks mostly not.
 struct UpdateTables {
     int s = 0, h = 0, sh = 0;
+    bool compressed = false;
     std::vector<uint32_t> rowvar, colvar;
     std::vector<int64_t> rowoff, coloff;
     std::vector<int32_t> rowstart;  // [nbar + 1] rows of group m
     std::vector<int32_t> colstart;  // [nbar] first column of group m
     std::vector<int32_t> leftrow;   // [sorted h-tuples, lexicographic] first row of the tuple
+    std::vector<int32_t> leftcnt;   // [sorted h-tuples] rows of the tuple
+    std::vector<int32_t> rightcol;  // [sorted (s-h)-tuples, lexicographic] first column of the tuple
+    int64_t wsize = 0;              // workspace slots (GEMM outputs) of the order
 };
-UpdateTables build_update_tables(int n, int b, int s);
+UpdateTables build_update_tables(int n, int b, int s, bool compressed = false);
 
 // Workspace ("GEMM") order of the order-s update outputs: group m of the
 // update is a dense row-major block of rows_m x (ncols - colstart[m]) slots.
 // Slot of output (r, c) = roww[r] + c.
 std::vector<int64_t> build_w_rows(const UpdateTables& t);
-// Per sorted block j of order s (lexicographic rank): {slot of its in-block
-// offset 0, row stride}; in-block offset a = aL * b^sh + aR lives at
-// slot + aL * stride + aR.
+// Per sorted block j of order s (lexicographic rank): {slot of its first row
+// and column, row stride}; in-block offset a = aL * b^sh + aR lives at
+// slot + rL * stride + rR, with (rL, rR) = (aL, aR) for full tables and the
+// ranks of aL and aR (half_ranks of the left and right tuples' runs) for
+// compressed ones.
 std::vector<int32_t> build_w_blocks(const UpdateTables& t, int n, int b);
 
 // Tables of the order-s cumulant recovery (see CumArgs in cw_internal.h).
@@ -67,6 +85,10 @@ struct CanonTables {
     std::vector<int32_t> dup;        // pairs {offset, its canonical offset}, per pattern
     std::vector<int32_t> pblocks;    // block ranks grouped by pattern (pattern order, then rank)
     std::vector<int32_t> units;      // [nunits][4] {pattern, slice, first index into pblocks, blocks}
+    // workspace position of a canonical offset in the compressed update
+    // tables: (rank of its left digits) << 16 | (rank of its right digits)
+    std::vector<int32_t> can_lr;     // per canonical offset (as can_off)
+    std::vector<int32_t> map_lr;     // [npat][bs]: can_lr of each offset's canonical offset
     int64_t canonical = 0;           // canonical elements of the order (all blocks)
 };
 // Units of `slice` threads x up to `group` blocks of one pattern, over the

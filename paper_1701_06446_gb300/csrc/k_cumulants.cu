@@ -158,6 +158,14 @@ __device__ __forceinline__ int64_t wslot(const CumArgs& a, int64_t blk, int off)
     return (int64_t)wb.x + (int64_t)offL * wb.y + offRw;
 }
 
+// Workspace slot of a canonical element of block blk whose left / right
+// digits have the ranks lr >> 16, lr & 0xffff (compressed update tables).
+__device__ __forceinline__ int64_t wslot_lr(const CumArgs& a, int64_t blk, int lr)
+{
+    const int2 wb = *reinterpret_cast<const int2*>(a.wblk + 2 * blk);
+    return (int64_t)wb.x + (int64_t)((unsigned)lr >> 16) * wb.y + (lr & 0xffff);
+}
+
 // Load half of the fold of the element at workspace slot w whose sum lives
 // at S_s[si] (si = w when the order's sums are in workspace order).
 __device__ __forceinline__ FoldVal fold_load_at(const CumArgs& a, int64_t w, int64_t si, int64_t fslot)
@@ -967,7 +975,7 @@ __global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ arg
     const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
     const int per = (a.nunits + (int)gridDim.x - 1) / (int)gridDim.x;
     const int u0 = min(a.nunits, (int)blockIdx.x * per), u1 = min(a.nunits, u0 + per);
-    int cur_q = -1, cur_sl = -1, off = 0;
+    int cur_q = -1, cur_sl = -1, off = 0, lr = 0;
     double copies = 0.0;
     bool valid = false;
     double local = 0.0;
@@ -981,6 +989,7 @@ __global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ arg
             const int c0 = a.can_start[cur_q], c1 = a.can_start[cur_q + 1];
             valid = c0 + c < c1;
             off = valid ? a.can_off[c0 + c] : 0;
+            lr = valid && a.sgemm ? a.can_lr[c0 + c] : 0;
             copies = valid ? (double)a.can_copies[c0 + c] : 0.0;
             int dig[S];
             int rem = off;
@@ -1018,7 +1027,7 @@ __global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ arg
             const int64_t e = blk * a.bs + off;
             double sv;
             if (a.sgemm) {
-                const int64_t w = wslot(a, blk, off);
+                const int64_t w = wslot_lr(a, blk, lr);
                 if (fold) {
                     FoldVal fv = fold_load_at(a, w, w, fslot);
                     fold_store(fv);
@@ -1067,8 +1076,10 @@ __global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ arg
 
 // Canonical recovery, pass 2: in every recovered block whose pattern has
 // repeated block indices, each non-canonical offset takes the value of its
-// canonical offset (the same tensor entry), and orders below d write their
-// two-word copies there too.  One block per CTA at a time, threads over the
+// canonical offset (the same tensor entry), and orders below d copy their
+// two-word C_s and S_s there too when an order above without the canonical
+// recovery reads them (the sums, kept at canonical elements only, reach the
+// other offsets this way).  One block per CTA at a time, threads over the
 // pattern's list of non-canonical offsets.
 __global__ void __launch_bounds__(NT) k_canon_expand(const CumArgs* __restrict__ args)
 {
@@ -1078,23 +1089,27 @@ __global__ void __launch_bounds__(NT) k_canon_expand(const CumArgs* __restrict__
         const int q = a.blkpat[blk];
         const int d0 = a.dup_start[q], d1 = a.dup_start[q + 1];
         double* C = a.Cout + blk * a.bs;
+        float2* S2 = a.split && a.split_copies ? a.S2[a.s] + blk * a.bs : nullptr;
         // four copies per thread and round, their loads issued before their stores
         constexpr int U = 4;
         for (int i0 = d0 + (int)threadIdx.x; i0 < d1; i0 += U * NT) {
             int2 oc[U];  // {offset, canonical offset}
             double v[U];
+            float2 sv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) oc[u] = i0 + u * NT < d1 ? a.dup[i0 + u * NT] : make_int2(-1, 0);
 #pragma unroll
-            for (int u = 0; u < U; ++u) v[u] = oc[u].x >= 0 ? C[oc[u].y] : 0.0;
+            for (int u = 0; u < U; ++u) {
+                v[u] = oc[u].x >= 0 ? C[oc[u].y] : 0.0;
+                sv[u] = oc[u].x >= 0 && S2 != nullptr ? S2[oc[u].y] : make_float2(0.0f, 0.0f);
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (oc[u].x < 0) continue;
                 C[oc[u].x] = v[u];
-                if (a.split) {
-                    const int64_t e = blk * a.bs + oc[u].x;
-                    a.C2[a.s][e] = tw_split(v[u]);
-                    a.S2[a.s][e] = tw_split(a.S[a.s][e]);
+                if (S2 != nullptr) {
+                    a.C2[a.s][blk * a.bs + oc[u].x] = tw_split(v[u]);
+                    S2[oc[u].x] = sv[u];
                 }
             }
         }
@@ -1115,15 +1130,22 @@ __global__ void __launch_bounds__(NT) k_split(const CumArgs* __restrict__ args)
 }
 
 // out[e] = S_s[slot(e)] * scale: the sums of an order kept in workspace order,
-// back in storage order.
+// or at canonical elements only, back in storage order (every element reads its
+// canonical element's sum).
 __global__ void __launch_bounds__(NT) k_gather_sums(const CumArgs* __restrict__ args, double scale, double* out)
 {
     const CumArgs& a = *args;
     for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < a.E; e += (int64_t)gridDim.x * NT) {
         const int64_t blk = e / a.bs;
-        int off = (int)(e - blk * a.bs);
-        if (a.canon) off = a.map_off[(int64_t)a.blkpat[blk] * a.bs + off];  // sums kept at canonical elements
-        out[e] = a.S[a.s][wslot(a, blk, off)] * scale;
+        const int off = (int)(e - blk * a.bs);
+        int64_t w;
+        if (!a.canon) {
+            w = wslot(a, blk, off);
+        } else {
+            const int64_t q = (int64_t)a.blkpat[blk] * a.bs + off;
+            w = a.sgemm ? wslot_lr(a, blk, a.map_lr[q]) : blk * a.bs + a.map_off[q];
+        }
+        out[e] = a.S[a.s][w] * scale;
     }
 }
 

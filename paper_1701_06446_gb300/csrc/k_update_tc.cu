@@ -317,9 +317,11 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
     double useful = 0, issued = 0;
     for (int i = 0; i < plan.nstreams; ++i) {
         const TcPlanStream& S = streams[i];
+        // key: (factors, grouped + 2 * compressed); sets of at most one factor
+        // have a single ordering and nothing to compress
         std::map<std::pair<int, int>, int64_t> setoff;
-        auto add_set = [&](int k, int grouped, const std::vector<uint32_t>& vars) -> int64_t {
-            const std::pair<int, int> key(k, k <= 1 ? 0 : grouped);
+        auto add_set = [&](int k, int grouped, bool compressed, const std::vector<uint32_t>& vars) -> int64_t {
+            const std::pair<int, int> key(k, k <= 1 ? 0 : grouped + 2 * (int)compressed);
             auto it = setoff.find(key);
             if (it != setoff.end()) return it->second;
             const int64_t off = (int64_t)opvars.size();
@@ -343,8 +345,8 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
                 if (e != cudaSuccess) return (int)e;
                 o.roww = dw;
             }
-            const int64_t loff = add_set(t.h, 1, t.rowvar);
-            const int64_t roff = add_set(t.sh, 0, t.colvar);
+            const int64_t loff = add_set(t.h, 1, t.compressed, t.rowvar);
+            const int64_t roff = add_set(t.sh, 0, t.compressed, t.colvar);
             const int nbar = (int)t.colstart.size();
             const int ncols = (int)t.colvar.size();
             std::vector<int32_t> colmin(t.rowvar.size());
@@ -373,7 +375,6 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
                     keep1[m] = INT_MIN;
                 }
                 const std::vector<int> left = enumerate_sorted(nbar, t.h);
-                const int64_t bh = ipow(b, t.h);
                 std::vector<int> full(s);
                 for (size_t q = 0; q < left.size() / t.h; ++q) {
                     const int* jl = &left[q * t.h];
@@ -385,7 +386,7 @@ int tc_plan_create(TcPlan& plan, const std::vector<TcPlanStream>& streams, int b
                     const int64_t hi = rank_sorted(full.data(), s, nbar);
                     if (hi < S.top0 || lo >= S.top1) continue;
                     keep0[m] = std::min(keep0[m], t.leftrow[q]);
-                    keep1[m] = std::max(keep1[m], (int)(t.leftrow[q] + bh));
+                    keep1[m] = std::max(keep1[m], t.leftrow[q] + t.leftcnt[q]);
                 }
             }
             for (int m = 0; m < nbar; ++m) {

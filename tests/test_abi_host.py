@@ -74,7 +74,8 @@ def test_element_index_matches_oracle_layout(n, b, s):
 
 
 @pytest.mark.parametrize("n,b,s", [(4, 2, 1), (4, 2, 4), (60, 3, 2), (20, 3, 4), (7, 3, 5),
-                                   (12, 4, 6), (9, 2, 6), (6, 2, 8), (5, 5, 3), (1, 1, 4)])
+                                   (12, 4, 6), (9, 2, 6), (6, 2, 8), (5, 5, 3), (1, 1, 4),
+                                   (24, 4, 5), (16, 4, 6), (13, 3, 6)])
 def test_update_and_cumulant_tables_selftest(n, b, s):
     assert cw.selftest_tables(n, b, s) == 0
 
