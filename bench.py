@@ -120,10 +120,13 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
       batch sums (2): `recovery_fp64` flops.  Orders from TWO_WORD_MIN_ORDER up (mixed
       forms) run each term as a two-word FP32 multiply-accumulate
       (TWO_WORD_OPS_PER_TERM FP32 operations on the FMA pipe): `recovery_fp32_ops`.
-    * recovery bytes, per stored element: the FP64 sum read and written (16), the
-      cumulant written (8), the shift's FP32 tile sum read (4) and the FIFO slot
-      read and written (8, FIFO) or the leaving tile sum read (4); orders below d
-      also write their two-word copies (16) in the forms that have them.
+    * recovery bytes, per element whose sums are kept (every stored element, or the
+      canonical elements of the canonical orders): the FP64 sum read and written
+      (16), the shift's FP32 tile sum read (4) and the FIFO slot read and written
+      (8, FIFO) or the leaving tile sum read (4); the cumulant written at every
+      stored element (8); orders below d also write their two-word copies (16) in
+      the forms that have them, at the canonical elements only for canonical orders
+      (the orders above read no others).
     """
     from paper_1701_06446_gb300 import layout_size
     E = {s: layout_size(W.n, W.b, s) for s in range(1, W.d + 1)}
@@ -136,8 +139,8 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
     upd = sum(2.0 * K * Ecomp[s] for s in E)
     upd_issued = sum(2.0 * K * gemm_outputs(W.n, W.b, s) for s in E)
     fp32_ops = sum(TWO_WORD_OPS_PER_TERM * terms[s] * Ecomp[s] for s in E if two_word and s >= TWO_WORD_MIN_ORDER)
-    per_elem = 16 + 8 + 4 + (8 if fifo else 4)
-    rec_bytes = sum(per_elem * E[s] + (16 * E[s] if two_word and s < W.d else 0) for s in E)
+    per_kept = 16 + 4 + (8 if fifo else 4)
+    rec_bytes = sum(per_kept * Ecomp[s] + 8 * E[s] + (16 * Ecomp[s] if two_word and s < W.d else 0) for s in E)
     return {"update": upd, "update_issued": upd_issued, "recovery_fp64": fp64, "recovery_fp32_ops": fp32_ops,
             "recovery_bytes": rec_bytes, "elements": E, "computed_elements": Ecomp, "two_word": two_word}
 
@@ -146,8 +149,8 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
 # launches_*.md), by workload: the recovery's launches of one shift, and the GEMM.  The n=48
 # workload's were taken with a window of 2^13 samples, whose per-launch work is the same.
 # None where no capture of the current kernels exists.
-RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2048007509, "n60_d4_b3_T32768_p1024": 13007616}
-GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2579758251, "n60_d4_b3_T32768_p1024": 15829120}
+RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 1864350976, "n60_d4_b3_T32768_p1024": 13007616}
+GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2009310976, "n60_d4_b3_T32768_p1024": 15829120}
 
 
 def fp64_peak_tflops(dev) -> float:
@@ -487,8 +490,12 @@ def run_ours(args, W, rank: int, world: int):
     clk_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = sm_count * FP32_LANES_PER_SM * clk_mhz * 1e6 / 1e12  # T FP32 lane ops/s
     rec_s = rec_ms * 1e-3
-    rec_names = ("k_recover_fused" if W.d <= 4 else
-                 "recovery: k_recover_fused<4>, k_split, k_cumulants<5..d>, k_fold_linear, k_norm_final")
+    if W.d <= 4:
+        rec_names = "k_recover_fused"
+    else:
+        hi = [f"k_canon<{s_}> + k_canon_expand" if canonical_order(W.b, s_) else f"k_cumulants<{s_}>"
+              for s_ in range(5, W.d + 1)]
+        rec_names = "recovery: k_recover_fused<4>, k_split, " + ", ".join(hi) + ", k_norm_final"
     rec_common = {"kernel": rec_names, "avg_launch_ms": rec_ms, "share_of_step": rec_ms / ms_per_step,
                   "traffic": RECOVERY_TRAFFIC.get(W.name)}
     if precision == "fp64":
@@ -538,9 +545,10 @@ def run_ours(args, W, rank: int, world: int):
         gbs = work["recovery_bytes"] / rec_s / 1e9
         roof_hbm = dict(rec_common, bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s",
                         frac=gbs / peaks["hbm_gbs"], peak_kind=f"{peak_kind} HBM copy (of {peak_kind})",
-                        per_launch=f"{work['recovery_bytes']:.4g} algorithmic bytes (per stored element: FP64 "
-                                   f"sum read + write, cumulant write, FP32 tile sum read, FIFO slot read + "
-                                   f"write; two-word copies of the orders below d)")
+                        per_launch=f"{work['recovery_bytes']:.4g} algorithmic bytes (per element whose sums "
+                                   f"are kept, the canonical ones of the canonical orders: FP64 sum read + write, "
+                                   f"FP32 tile sum read, FIFO slot read + write, two-word copies of the orders "
+                                   f"below d; per stored element: the cumulant write)")
         # the roofline line is the dominant kernel's; the other is kept beside it
         if rec_ms >= upd_ms:
             roof, roof_other = roof_rec, roof_gemm
