@@ -57,6 +57,10 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# drift limit of the library's automatic re-centring in the mixed forms (standard deviations)
+AUTO_RECENTER = 0.25
+
+
 def canonical_order(b: int, s: int) -> bool:
     """Orders the library recovers per canonical element (single windows)."""
     return 5 <= s <= 6 and b ** s >= 256 and b ** (s - 1) <= 0xffff
@@ -424,6 +428,8 @@ def run_ours(args, W, rank: int, world: int):
     X = stream.rows(base, base + W.T + nsteps * W.p)
     Xd = torch.from_numpy(X).to(dev)
     h = CumWin(W.n, W.d, W.b, W.T, W.p, precision, device=dev)
+    if precision != "fp64":  # the library's drift policy (a user of a drifting stream turns it on)
+        h.set_auto_recenter(AUTO_RECENTER)
     h.fill(Xd[: W.T])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     batches = [Xd[W.T + k * W.p: W.T + (k + 1) * W.p] for k in range(nsteps)]
@@ -509,6 +515,13 @@ def run_ours(args, W, rank: int, world: int):
         return
     fifo = bool(h.fifo)
     tiles = h.tiles()
+    recenter = None
+    if precision != "fp64":
+        r_, k_ = h.drift()
+        recenter = {"limit": AUTO_RECENTER, "recenters": k_, "last_drift": r_,
+                    "note": "re-centre (recompute the window's sums about its column means) when the mean "
+                            "drifts more than `limit` standard deviations from the shift; its cost is inside "
+                            "whichever loop it falls in"}
     work = algorithmic_work(W, fifo)
     peaks, peak_kind = _peaks()
     rec_ms = timing["cumulant_ms"] / max(timing["shifts"], 1)  # timed region
@@ -617,7 +630,8 @@ def run_ours(args, W, rank: int, world: int):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if precision == "fp64" else f"{precision}x3+f32acc+f64sum",
-        "data": "synthetic", "config": dict(config_of(W, precision), ksplit=ksplit, fifo=fifo, tiles=tiles),
+        "data": "synthetic", "config": dict(config_of(W, precision), ksplit=ksplit, fifo=fifo, tiles=tiles,
+                                            auto_recenter=recenter),
         "samples_per_s": value * W.p,
         "tflops": work["update"] / (ms_per_step * 1e-3) / 1e12,
         "stage_ms": stg_ms, "update_ms": upd_ms, "recovery_ms": rec_ms,
