@@ -384,6 +384,30 @@ def test_estimators_enqueue_match_norms(precision):
     np.testing.assert_allclose(nu_h.numpy()[2:], onu[2:], rtol=tol)
 
 
+@pytest.mark.parametrize("n,d,b", [(10, 6, 4), (9, 5, 4), (7, 6, 3)])
+def test_moments_of_canonical_orders_at_every_stored_element(n, d, b):
+    """The update of a canonical order (orders 5-6, b^s >= 256) forms only the rows
+    and columns of its compressed tables, so its sums exist at canonical elements
+    only; cumwin_moments returns every stored element from its canonical one.  FP64
+    form (moments about zero): every stored element of every order against the
+    oracle's raw moments, after shifts and after a recompute."""
+    T, p = 300, 40
+    rng = np.random.default_rng(11 * n + d + b)
+    X = (rng.standard_t(6, size=(T + 3 * p, n)) @ rng.standard_normal((n, n)) / np.sqrt(n) + 0.3)
+    X = X.astype(np.float32)
+    Xd = dev(X)
+    ref = oracle.moments(X[3 * p:], d, b)
+    with CumWin(n, d, b, T, p, "fp64") as h:
+        h.fill(Xd[:T])
+        for w in range(3):
+            h.push(Xd[T + w * p: T + (w + 1) * p])
+        for s in range(1, d + 1):
+            assert rel_fro(h.moments(s).cpu().numpy(), ref[s - 1]) <= TOL_FP64, s
+        h.recompute()
+        for s in range(1, d + 1):
+            assert rel_fro(h.moments(s).cpu().numpy(), ref[s - 1]) <= TOL_FP64, s
+
+
 @pytest.mark.parametrize("precision", ["fp64", "bf16"])
 @pytest.mark.parametrize("n,d,b", [(10, 6, 4), (9, 5, 4), (7, 6, 3)])
 def test_canonical_orders_are_exactly_symmetric(n, d, b, precision):
