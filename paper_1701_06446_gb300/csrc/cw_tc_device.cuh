@@ -137,9 +137,17 @@ __device__ __forceinline__ void kr_build_range(const TcStreamDesc* __restrict__ 
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
     const int total = (int)(rows * nkb);
     const int64_t part = rows * Kcap;  // elements of one part
+    // item e -> (chunk of cw 8-sample steps, row, step): the 32 lanes of a warp write
+    // 32 consecutive steps of one row (512 contiguous bytes per part), consecutive
+    // warps take consecutive rows of the same chunk, so that the CTAs running at
+    // once read the staged samples of one chunk (npad x 8 cw floats) from L1
+    const int cw = nkb % 32 == 0 ? 32 : nkb;
+    const int rw = (int)rows * cw;
     for (int e = begin; e < total; e += stride) {
-        const int row = e / nkb;
-        const int kb = e - row * nkb;
+        const int kc = e / rw;
+        const int rem = e - kc * rw;
+        const int row = rem / cw;
+        const int kb = kc * cw + (rem - row * cw);
         const uint64_t w = opvars[row];
         const uint32_t vars = (uint32_t)w;
         const int nf = (int)((w >> 32) & 0xffu);
