@@ -773,7 +773,7 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
         if (canon) {  // one window, canonical elements
             // grids within the order's norm partial slots (gx * gy of its launch shape)
             const int slots = cum_launch[s].gx * cum_launch[s].gy;
-            CW_TRY(launch_canon(s, args + s, std::min(canon_units[s], slots), st));
+            CW_TRY(launch_canon(s, args + s, std::min(canon_units[s], kCanonCtasPerSm * sm_count), st));
             CW_TRY(launch_canon_expand(args + s, slots, st));
             *launches += 2;
         } else {
@@ -1257,7 +1257,10 @@ int cumwin_create_shard(int n, int d, int b, int64_t T, int p, int precision, vo
     if (nshards > 1) shard_blocks((n + b - 1) / b, d, shard, nshards, &h->top0, &h->top1);
     rc = window_init(h, n, d, b, T, p, precision, (cudaStream_t)cuda_stream, true);
     int parts = 1;
-    for (int s = 1; s <= d; ++s) parts = std::max(parts, h->cum_launch[s].gx * h->cum_launch[s].gy);
+    for (int s = 1; s <= d; ++s) {
+        parts = std::max(parts, h->cum_launch[s].gx * h->cum_launch[s].gy);
+        if (h->canon_units[s] > 0) parts = std::max(parts, kCanonCtasPerSm * h->sm_count);  // k_canon's grid
+    }
     if (rc == CUMWIN_OK && h->tc != nullptr) {
         tune_cache_apply(*h->tc, tune_cache_get(plan_signature(*h->tc, {h}, h->device)));
     }

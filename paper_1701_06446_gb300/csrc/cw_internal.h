@@ -142,6 +142,7 @@ constexpr int kCanonMaxOrder = 6;
 constexpr int kCanonMinBlock = 256;
 constexpr int kCanonSlice = 256;  // threads of a unit (one canonical element each)
 constexpr int kCanonGroup = 8;    // blocks of a unit
+constexpr int kCanonCtasPerSm = 4;  // resident k_canon CTAs per SM (64 registers a thread)
 
 // Adjoint kernels (k_adjoint.cu): full-tensor expansion, contraction over the
 // trailing indices, seeding, compaction over sorted tuples, and dL/dX.

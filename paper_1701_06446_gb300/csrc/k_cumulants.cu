@@ -960,7 +960,7 @@ __global__ void __launch_bounds__(NT) k_fold_linear(const CumArgs* __restrict__ 
 // stored elements.  Each CTA takes a contiguous run of units, so the
 // (pattern, slice) changes rarely.
 template <int S>
-__global__ void __launch_bounds__(NT, 4) k_canon(const CumArgs* __restrict__ args)
+__global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __restrict__ args)
 {
     constexpr int NS = Subsets<S>::N;
     constexpr int GB = kCanonGroup;
