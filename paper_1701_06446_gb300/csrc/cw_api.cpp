@@ -692,6 +692,7 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
             const int64_t nb = s <= h->d ? n_sorted(h->nbar, s) : 0;
             us[w + 1] = us[w] + (nb + L.slots - 1) / L.slots * L.gy;
         }
+        f.utot[s] = us[nwin];
         utot += us[nwin];
     }
     // fold segments: (window, order) with the order's stored elements

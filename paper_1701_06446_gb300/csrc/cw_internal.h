@@ -254,6 +254,7 @@ struct FusedRecovery {
     const int64_t* abeg;     // [nseg + 1] first stored element of each (window, order) segment:
     const int32_t* aarg;     // [nseg] its index into args; orders <= 3 first (nseg_lo), then order 4
     int64_t upoff[kFusedMax + 1];
+    int64_t utot[kFusedMax + 1];  // work units of each order (all windows): ustart[s][nwin]
     int64_t advance;
     int32_t nwin, advance_heads, nseg, nseg_lo, fold;
     int32_t slots[kFusedMax + 1], gy[kFusedMax + 1];

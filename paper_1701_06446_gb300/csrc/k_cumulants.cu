@@ -536,14 +536,14 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArg
 {
     const int tid = vtid<V>();
     const int slots = f.slots[S], gy = f.gy[S];
-    const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);
-    const int64_t total = us[f.nwin];
+    const int64_t* us = f.ustart + (int64_t)S * (f.nwin + 1);  // read only with several windows
+    const int64_t total = f.utot[S];
     const int64_t per = (total + ncta - 1) / ncta;
     const int64_t chunk = ((int64_t)cta + ncta - rot % ncta) % ncta;
     const int64_t u0 = min(total, chunk * per), u1 = min(total, u0 + per);
     if (u0 >= u1) return;  // uniform over the CTA
     double* part = f.upart + f.upoff[S];
-    int w = unit_window(us, f.nwin, u0);
+    int w = f.nwin == 1 ? 0 : unit_window(us, f.nwin, u0);
     const CumArgs* ap = sargs != nullptr ? &sargs[S] : &f.args[(int64_t)S * f.nwin + w];
     const CumArgs* a2 = OTF < 2 ? nullptr : sargs != nullptr ? &sargs[2] : &f.args[(int64_t)2 * f.nwin + w];
     int64_t nblocks = ap->E / ap->bs;
@@ -551,7 +551,7 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArg
     int64_t first = u0;
     double local = 0.0;
     for (int64_t u = u0; u < u1; ++u) {
-        if (u >= us[w + 1]) {  // the next window with units: close the run
+        if (f.nwin > 1 && u >= us[w + 1]) {  // the next window with units: close the run
             const double z = cta_sum<V>(local, red);
             if (tid == 0) part[first] = z;
             first = u;
@@ -564,7 +564,7 @@ __device__ __forceinline__ void fused_order(const FusedRecovery& f, const CumArg
         } else if (u != first && tid == 0) {
             part[u] = 0.0;
         }
-        const int64_t ul = u - us[w];
+        const int64_t ul = f.nwin == 1 ? u : u - us[w];
         int64_t grp = ul;
         if (gy > 1) {
             grp = ul / gy;
@@ -771,7 +771,7 @@ __device__ __forceinline__ void recover_fused_body(const FusedRecovery& f, const
     //    step 3), the first n13 CTAs take the small orders and the others that
     //    fold, so the latency-bound small orders overlap the memory-bound fold.
     int64_t u13 = 0;
-    for (int k = 1; k <= (DF < 3 ? DF : 3); ++k) u13 += f.ustart[(int64_t)k * (f.nwin + 1) + f.nwin];
+    for (int k = 1; k <= (DF < 3 ? DF : 3); ++k) u13 += f.utot[k];
     const bool split = f.fold && f.nseg > f.nseg_lo && G > 1;
     const int n13 = split ? (int)(u13 < G / 2 ? (u13 > 0 ? u13 : 1) : G / 2) : G;
     if (cta >= n13) {
@@ -779,10 +779,10 @@ __device__ __forceinline__ void recover_fused_body(const FusedRecovery& f, const
     } else {
         int64_t rot = 0;
         fused_order<1, 0, V>(f, sargs, red, rot, cta, n13);
-        rot += f.ustart[1 * (f.nwin + 1) + f.nwin];
+        rot += f.utot[1];
         if (DF >= 2) {
             fused_order<(DF >= 2 ? 2 : 1), 1, V>(f, sargs, red, rot, cta, n13);
-            rot += f.ustart[2 * (f.nwin + 1) + f.nwin];
+            rot += f.utot[2];
         }
         if (DF >= 3) fused_order<(DF >= 3 ? 3 : 1), 2, V>(f, sargs, red, rot, cta, n13);
     }
@@ -801,8 +801,8 @@ __device__ __forceinline__ void recover_fused_body(const FusedRecovery& f, const
         if (s <= na.d) {
             const int64_t* us = f.ustart + (int64_t)s * (f.nwin + 1);
             const double* part = f.upart + f.upoff[s];
-            const int64_t q1 = us[w + 1];
-            int64_t q = us[w] + tid;
+            const int64_t q1 = f.nwin == 1 ? f.utot[s] : us[w + 1];
+            int64_t q = (f.nwin == 1 ? 0 : us[w]) + tid;
             for (; q + 3 * NT < q1; q += 4 * NT) {  // four loads in flight, added in index order
                 const double v0 = part[q], v1 = part[q + NT], v2 = part[q + 2 * NT], v3 = part[q + 3 * NT];
                 z += v0;
