@@ -172,6 +172,7 @@ struct cumwin_s {
     CumArgs* cum_dev = nullptr;
     CumLaunch cum_launch[kMaxOrder + 1] = {};
     int canon_units[kMaxOrder + 1] = {};  // units of the canonical recovery of each order (0: not used)
+    int canon_grid[kMaxOrder + 1] = {};   // its CTAs (CumArgs::unit_begin)
     FusedPlan fused;
     int parts = 0;  // norm partial slots per order
     double* normpart = nullptr;
@@ -533,8 +534,15 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         h->cum_launch[s] = plan_cumulants(s, (int)ipow(b, s), n_sorted(nbar, s), h->sm_count);
         if (canonical(s)) {
             const bool sh = s == d && h->top1 >= 0;  // a shard recovers its block range of the top order
-            const CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, kCanonGroup, sh ? h->top0 : 0,
-                                                      sh ? h->top1 : -1);
+            // units of up to kCanonGroup blocks, fewer when that leaves k_canon's CTAs under 8 units each
+            // (finer units balance them better)
+            const int grid = kCanonCtasPerSm * h->sm_count;
+            int group = kCanonGroup;
+            CanonTables cn = build_canon_tables(n, b, s, kCanonSlice, group, sh ? h->top0 : 0, sh ? h->top1 : -1);
+            while (group > 1 && (int64_t)cn.units.size() / 4 < 8LL * grid) {
+                group /= 2;
+                cn = build_canon_tables(n, b, s, kCanonSlice, group, sh ? h->top0 : 0, sh ? h->top1 : -1);
+            }
             CW_TRY(h->upload((int32_t**)&a.blkpat, cn.blkpat));
             CW_TRY(h->upload((int32_t**)&a.can_start, cn.can_start));
             CW_TRY(h->upload((int32_t**)&a.can_off, cn.can_off));
@@ -555,6 +563,7 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
             a.nunits = (int32_t)(cn.units.size() / 4);
             a.npblocks = (int32_t)cn.pblocks.size();
             a.canon = 1;
+            h->canon_grid[s] = std::max(1, std::min(a.nunits, grid));
             for (int k = s + 1; k <= d; ++k) a.split_copies |= canonical(k) ? 0 : 1;
             h->canon_units[s] = a.nunits;
         }
@@ -742,7 +751,7 @@ int fused_setup(FusedPlan& fp, const std::vector<cumwin_s*>& wins, int b, int sm
 // number of launches through *launches.
 int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_launch, const NormArgs* norm_dev,
             int nwin, int d, int64_t advance, int accum, int sm_count, cudaStream_t st, int64_t* launches,
-            const int* canon_units = nullptr)
+            const int* canon_grid = nullptr)
 {
     const CumArgs* args = cum_dev + (size_t)accum * (kMaxOrder + 1) * nwin;
     int s0 = 1;
@@ -764,7 +773,7 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
             CW_TRY(launch_split(args, nwin, s_hi, maxE, sm_count, st));
             *launches += 1;
         }
-        const bool canon = canon_units != nullptr && canon_units[s] > 0;
+        const bool canon = canon_grid != nullptr && canon_grid[s] > 0;
         // the top order (workspace order) is folded first; canonical orders (workspace
         // order too) are folded by k_canon at their canonical elements
         if (accum != 0 && !canon) {
@@ -774,7 +783,7 @@ int recover(const FusedPlan& fp, const CumArgs* cum_dev, const CumLaunch* cum_la
         if (canon) {  // one window, canonical elements
             // grids within the order's norm partial slots (gx * gy of its launch shape)
             const int slots = cum_launch[s].gx * cum_launch[s].gy;
-            CW_TRY(launch_canon(s, args + s, std::min(canon_units[s], kCanonCtasPerSm * sm_count), st));
+            CW_TRY(launch_canon(s, args + s, canon_grid[s], st));
             CW_TRY(launch_canon_expand(args + s, slots, st));
             *launches += 2;
         } else {
@@ -793,7 +802,7 @@ int run_cumulants(cumwin_t h, int64_t advance, int accum = 0, int parity = 0, cu
 {
     cudaStream_t st = on != nullptr ? on : h->stream;
     const int rc = recover(h->fused, h->cum_dev + (size_t)parity * kAccModes * (kMaxOrder + 1), h->cum_launch,
-                           h->norm_dev, 1, h->d, advance, accum, h->sm_count, st, &h->launches, h->canon_units);
+                           h->norm_dev, 1, h->d, advance, accum, h->sm_count, st, &h->launches, h->canon_grid);
     if (rc) return rc;
     if (h->mark(3, st) != nullptr) h->timed++;
     return CUMWIN_OK;
