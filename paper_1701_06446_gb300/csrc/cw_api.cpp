@@ -203,11 +203,12 @@ struct cumwin_s {
         double* Cf[kMaxOrder + 1] = {};   // full C_s (order 1 about the shift)
         double* C1true = nullptr;         // full C_1 + shift
         double* Mf[kMaxOrder + 1] = {};   // full M_s, s < d
+        double* Sblk = nullptr;           // M_s in the block layout, for orders whose sums are not (canonical)
         double* G[kMaxOrder + 1] = {};    // adjoint of C_s
         double* GM[kMaxOrder + 1] = {};   // adjoint of M_s
         int64_t nf[kMaxOrder + 1] = {};   // n^s
         int64_t* nst = nullptr;
-        uint32_t* uvars = nullptr;        // sorted (s-1)-tuples of all orders, concatenated
+        uint64_t* uvars = nullptr;        // sorted (s-1)-tuples of all orders, concatenated (8 bits a variable)
         float* umult = nullptr;
         uint8_t* unf = nullptr;
         int uoff[kMaxOrder + 2] = {};
@@ -1744,31 +1745,34 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
             g_last_error = "the adjoint keeps full n^d tensors; n^d must be at most 2^27";
             return CUMWIN_ENOTSUP;
         }
+        int64_t eblk = 0;
         for (int s = 1; s <= d; ++s) {
             CW_TRY(h->alloc(&g.Cf[s], g.nf[s]));
             CW_TRY(h->alloc(&g.G[s], g.nf[s]));
             CW_TRY(h->alloc(&g.GM[s], g.nf[s]));
             if (s < d) CW_TRY(h->alloc(&g.Mf[s], g.nf[s]));
+            if (s < d && (h->cum[s].sgemm || h->cum[s].canon)) eblk = std::max(eblk, h->E[s]);
         }
+        if (eblk > 0) CW_TRY(h->alloc(&g.Sblk, eblk));
         CW_TRY(h->alloc(&g.C1true, n));
         g.nst = h->nst;
         // sorted (s-1)-tuples of variables with their numbers of distinct orderings
-        std::vector<uint32_t> uv;
+        std::vector<uint64_t> uv;
         std::vector<float> um;
         std::vector<uint8_t> unf;
         for (int s = 1; s <= d; ++s) {
             g.uoff[s] = (int)uv.size();
             const int k = s - 1;
             if (k == 0) {
-                uv.push_back(0u);
+                uv.push_back(0ull);
                 um.push_back(1.0f);
                 unf.push_back(0);
                 continue;
             }
             const std::vector<int> tup = enumerate_sorted(n, k);
             for (size_t q = 0; q < tup.size() / k; ++q) {
-                uint32_t p = 0;
-                for (int i = 0; i < k; ++i) p |= (uint32_t)tup[q * k + i] << (8 * i);
+                uint64_t p = 0;  // up to kMaxOrder - 1 = 7 variables of 8 bits
+                for (int i = 0; i < k; ++i) p |= (uint64_t)tup[q * k + i] << (8 * i);
                 uv.push_back(p);
                 um.push_back((float)block_multiplicity(&tup[q * k], k));
                 unf.push_back((uint8_t)k);
@@ -1786,7 +1790,16 @@ int cumwin_grad(cumwin_t h, const double* w_host, float* dX_dev)
     // full tensors of the current window
     for (int s = 1; s <= d; ++s) {
         CW_TRY(launch_expand(h->C[s], g.nf[s], s, n, h->b, g.nst, 1.0, nullptr, g.Cf[s], st));
-        if (s < d) CW_TRY(launch_expand(h->S[s], g.nf[s], s, n, h->b, g.nst, invT, nullptr, g.Mf[s], st));
+        if (s < d) {
+            // the sums of a canonical order are kept at its canonical elements only (in workspace order
+            // in the mixed forms): gather every stored element from its canonical one first
+            const double* src = h->S[s];
+            if (h->cum[s].sgemm || h->cum[s].canon) {
+                CW_TRY(launch_gather_sums(h->cum_dev + s, h->E[s], 1.0, g.Sblk, st));
+                src = g.Sblk;
+            }
+            CW_TRY(launch_expand(src, g.nf[s], s, n, h->b, g.nst, invT, nullptr, g.Mf[s], st));
+        }
         CW_TRY(cudaMemsetAsync(g.G[s], 0, sizeof(double) * g.nf[s], st));
         CW_TRY(cudaMemsetAsync(g.GM[s], 0, sizeof(double) * g.nf[s], st));
     }

@@ -152,10 +152,10 @@ cudaError_t launch_contract(const double* G, const double* V, int64_t nx, int64_
                             double* out, cudaStream_t st);
 cudaError_t launch_seed(const double* C, double two_w, int64_t nfull, double* G, double* GM,
                         cudaStream_t st);
-cudaError_t launch_compact(const double* GM, int s, int n, const uint32_t* uvars, const float* umult,
+cudaError_t launch_compact(const double* GM, int s, int n, const uint64_t* uvars, const float* umult,
                            int nu, double coef, float* Gc, cudaStream_t st);
 cudaError_t launch_grad_x(const float* ring, int64_t T, const int64_t* head, int n, int npad,
-                          const float* shift, const uint32_t* uvars, const uint8_t* unf, int nu,
+                          const float* shift, const uint64_t* uvars, const uint8_t* unf, int nu,
                           const float* Gc, float* dX, cudaStream_t st);
 
 // Message returned by cumwin_last_error() on the calling thread.

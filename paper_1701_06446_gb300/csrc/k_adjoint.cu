@@ -100,7 +100,7 @@ k_seed(const double* __restrict__ C, double two_w, int64_t nfull, double* __rest
 
 // Gc[u][a] = coef * mult(u) * GM[a, u]  for sorted (s-1)-tuples u (FP32), s = order
 __global__ void __launch_bounds__(NT)
-k_compact(const double* __restrict__ GM, int s, int n, const uint32_t* __restrict__ uvars,
+k_compact(const double* __restrict__ GM, int s, int n, const uint64_t* __restrict__ uvars,
           const float* __restrict__ umult, int nu, double coef, float* __restrict__ Gc)
 {
     const int64_t total = (int64_t)nu * n;
@@ -108,8 +108,8 @@ k_compact(const double* __restrict__ GM, int s, int n, const uint32_t* __restric
          e += (int64_t)gridDim.x * blockDim.x) {
         const int u = (int)(e / n), a = (int)(e - (int64_t)u * n);
         int64_t f = a;
-        const uint32_t vars = uvars[u];
-        for (int k = 0; k < s - 1; ++k) f = f * n + ((vars >> (8 * k)) & 0xffu);
+        const uint64_t vars = uvars[u];
+        for (int k = 0; k < s - 1; ++k) f = f * n + (int)((vars >> (8 * k)) & 0xffu);
         Gc[e] = (float)(coef * (double)umult[u] * GM[f]);
     }
 }
@@ -119,7 +119,7 @@ k_compact(const double* __restrict__ GM, int s, int n, const uint32_t* __restric
 constexpr int AT = 32, AU = 64;
 __global__ void __launch_bounds__(NT)
 k_grad_x(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p, int n, int npad,
-         const float* __restrict__ shift, const uint32_t* __restrict__ uvars, const uint8_t* __restrict__ unf,
+         const float* __restrict__ shift, const uint64_t* __restrict__ uvars, const uint8_t* __restrict__ unf,
          int nu, const float* __restrict__ Gc, float* __restrict__ dX)
 {
     extern __shared__ float sm[];
@@ -154,9 +154,9 @@ k_grad_x(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ 
             float p = 0.0f;
             if (u < nu) {
                 p = 1.0f;
-                const uint32_t vars = uvars[u];
+                const uint64_t vars = uvars[u];
                 const int nf = unf[u];
-                for (int k = 0; k < nf; ++k) p *= ys[r * npad + ((vars >> (8 * k)) & 0xffu)];
+                for (int k = 0; k < nf; ++k) p *= ys[r * npad + (int)((vars >> (8 * k)) & 0xffu)];
             }
             kr[e] = p;
         }
@@ -209,7 +209,7 @@ cudaError_t launch_seed(const double* C, double two_w, int64_t nfull, double* G,
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact(const double* GM, int s, int n, const uint32_t* uvars, const float* umult, int nu,
+cudaError_t launch_compact(const double* GM, int s, int n, const uint64_t* uvars, const float* umult, int nu,
                            double coef, float* Gc, cudaStream_t st)
 {
     k_compact<<<grid_for((int64_t)nu * n), NT, 0, st>>>(GM, s, n, uvars, umult, nu, coef, Gc);
@@ -217,7 +217,7 @@ cudaError_t launch_compact(const double* GM, int s, int n, const uint32_t* uvars
 }
 
 cudaError_t launch_grad_x(const float* ring, int64_t T, const int64_t* head, int n, int npad, const float* shift,
-                          const uint32_t* uvars, const uint8_t* unf, int nu, const float* Gc, float* dX,
+                          const uint64_t* uvars, const uint8_t* unf, int nu, const float* Gc, float* dX,
                           cudaStream_t st)
 {
     const size_t smem = sizeof(float) * ((size_t)AT * npad + AT * AU + (size_t)AU * n);

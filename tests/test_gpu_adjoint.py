@@ -145,3 +145,33 @@ def test_mixed_form_grad_close_to_fp64_form():
         ga = a.grad(w).cpu().numpy()
         gm = m.grad(w).cpu().numpy()
     assert rel_fro(gm, ga) <= 1e-3
+
+
+@pytest.mark.parametrize("form", ["fp64", "bf16"])
+def test_grad_order6_canonical_orders_vs_oracle_loss_differences(form):
+    """d = 6, b = 4: orders 5 and 6 run the canonical recovery, and the sums of
+    order 5 are kept at its canonical elements only (in workspace order in the
+    mixed forms); the adjoint gathers them back to the block layout before it
+    expands the moments.  The gradient at 24 seeded entries against central
+    differences of the oracle's FP64 loss on the same (FP32-representable)
+    window, h = 1e-3 (the oracle's closed form stops at order 4)."""
+    n, d, b, T = 6, 6, 4, 256
+    rng = np.random.default_rng(66)
+    X = (rng.gamma(2.0, size=(T, n)) @ rng.standard_normal((n, n)) / np.sqrt(n)).astype(np.float32)
+    Xd = X.astype(np.float64)
+    w = [0.0, 0.3, 0.5, 1.0, 1.5, 0.8, 0.6]
+    with CumWin(n, d, b, T, T // 4, form) as h:
+        h.fill(dev(X))
+        g = h.grad(w).cpu().numpy()
+    hstep = 1e-3
+    picks = [(int(rng.integers(T)), int(rng.integers(n))) for _ in range(24)]
+    fd = []
+    for t, a in picks:
+        Xp, Xm = Xd.copy(), Xd.copy()
+        Xp[t, a] += hstep
+        Xm[t, a] -= hstep
+        fd.append((oracle.loss(Xp, w) - oracle.loss(Xm, w)) / (2 * hstep))
+    fd = np.array(fd)
+    got = np.array([g[t, a] for t, a in picks])
+    tol = 1e-4 if form == "fp64" else 2e-3
+    assert np.linalg.norm(got - fd) <= tol * np.linalg.norm(fd), (got, fd)
