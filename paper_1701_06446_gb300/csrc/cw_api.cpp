@@ -452,8 +452,19 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
         return own_tc && s >= kCanonMinOrder && s <= kCanonMaxOrder && ipow(b, s) >= kCanonMinBlock &&
                ipow(b, s - 1) <= 0xffff;
     };
+    // compressed update tables: the order's sums exist at canonical elements only, which every
+    // order above reads when it is canonical too; an order above without the canonical recovery
+    // reads all of them (the FP64 sums in the FP64 form; the mixed forms read two-word copies,
+    // which k_canon_expand fills in then)
+    auto compressed = [&](int s) {
+        if (!canonical(s)) return false;
+        if (precision != CUMWIN_FP64) return true;
+        for (int k = s + 1; k <= d; ++k)
+            if (!canonical(k)) return false;
+        return true;
+    };
     for (int s = 1; s <= d; ++s) {
-        h->ut[s] = build_update_tables(n, b, s, canonical(s));
+        h->ut[s] = build_update_tables(n, b, s, compressed(s));
         const UpdateTables& t = h->ut[s];
         OrderTables& ot = h->upd.ord[s];
         CW_TRY(h->upload((uint32_t**)&ot.rowvar, t.rowvar));

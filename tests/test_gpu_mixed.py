@@ -377,7 +377,7 @@ def test_norms_enqueue_per_push_matches_serial():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("n,d,b", [(20, 4, 4), (22, 4, 3), (10, 6, 2), (9, 5, 4)])
+@pytest.mark.parametrize("n,d,b", [(20, 4, 4), (22, 4, 3), (10, 6, 2), (9, 5, 4), (5, 7, 3), (4, 7, 4)])
 @pytest.mark.parametrize("form", FORMS)
 def test_recovery_is_fp64_class_on_the_handles_own_moments(n, d, b, form):
     """The recovery alone (orders >= 4 form their subset sums in two-word FP32

@@ -82,9 +82,11 @@ def test_integer_windows_exact(n, d, b, T, p):
 
 @pytest.mark.parametrize("n,d,b,T,p", [(7, 4, 3, 64, 7), (5, 5, 2, 50, 7), (9, 3, 4, 33, 33),
                                        (6, 4, 1, 40, 1), (10, 6, 3, 80, 16), (33, 3, 4, 300, 64),
-                                       (2, 8, 1, 30, 4)])
+                                       (2, 8, 1, 30, 4), (5, 7, 3, 60, 7), (4, 7, 4, 64, 16)])
 def test_ragged_shapes_and_shift_sizes(n, d, b, T, p):
-    """Padding (b does not divide n), p not dividing T, p = 1, p = T, high orders."""
+    """Padding (b does not divide n), p not dividing T, p = 1, p = T, high orders
+    (d = 7 with canonical orders 5-6 below a top order without the canonical
+    recovery, whose subset terms read their sums at every element)."""
     rng = np.random.default_rng(7 * n + d)
     steps = 5
     X = (rng.standard_t(5, size=(T + steps * p, n)) @ rng.standard_normal((n, n))).astype(np.float32)
