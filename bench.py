@@ -391,13 +391,15 @@ def measure_fp64_form(W, stream, base: int, steps: int, dev) -> dict:
         torch.cuda.synchronize()
         total += e0.elapsed_time(e1)
     t = h.get_timing()
+    fifo = bool(h.fifo)  # regular shifts subtract the leaving batch's stored FP64 sums
     h.close()
     ms = total / steps
     upd = t["update_ms"] / max(t["shifts"], 1)
+    work = algorithmic_work(W, fifo)
     return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "update_ms": upd,
-            "update_tflops": algorithmic_work(W)["update"] / (upd * 1e-3) / 1e12,
-            "update_issued_tflops": algorithmic_work(W)["update_issued"] / (upd * 1e-3) / 1e12, "steps": steps,
-            "l2": "flushed before every timed shift"}
+            "update_tflops": work["update"] / (upd * 1e-3) / 1e12,
+            "update_issued_tflops": work["update_issued"] / (upd * 1e-3) / 1e12, "steps": steps,
+            "fifo": fifo, "l2": "flushed before every timed shift"}
 
 
 # per-order relative Frobenius bounds of the final window against the oracle, about 3x the

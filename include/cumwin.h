@@ -169,14 +169,18 @@ int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx);
  * Requires 1 <= p <= T and a prior cumulant fill.  Errors: EINVAL, ESTATE.
  * Allocates nothing and does not synchronise (capturable into a CUDA graph).
  *
- * Mixed forms with T a multiple of the nominal p: the handle keeps a FIFO of
- * the T/p batch sums (FP32, sum_s E_s each), the alternative scheme of
- * Section 2.4, filled by cumwin_fill / cumwin_recompute.  A shift of exactly
- * p rows with x_out_dev == NULL then subtracts the leaving batch's stored sum
- * instead of recomputing it (half the tensor-core work); the result is bitwise
- * the one of the recomputing form.  Any other shift (x_out_dev != NULL or
- * fewer rows) recomputes X_(-) and retires the FIFO until the next fill or
- * recompute.
+ * T a multiple of the nominal p: the handle keeps a FIFO of the T/p batch
+ * sums (sum_s E_s each; FP32 in the mixed forms, FP64 in the FP64 form), the
+ * alternative scheme of Section 2.4, filled by cumwin_fill / cumwin_recompute,
+ * when it takes at most a quarter of the free device memory.  A shift of
+ * exactly p rows with x_out_dev == NULL then subtracts the leaving batch's
+ * stored sum instead of recomputing it (half the update's multiply-adds).  In
+ * the mixed forms the result is bitwise the one of the recomputing form; in
+ * the FP64 form it differs from it by the rounding of the FP64 additions (the
+ * FIFO form subtracts the leaving batch's sum as a whole, the recomputing form
+ * accumulates the leaving products into the entering batch's sum).  Any other
+ * shift (x_out_dev != NULL or another number of rows) recomputes X_(-) and
+ * retires the FIFO until the next fill or recompute.
  *
  * Pipelined shifts (mixed forms): the recovery of C_1..C_d and of the norms
  * runs on a stream owned by the handle, ordered after the shift's moment
@@ -232,8 +236,8 @@ int cumwin_loss(cumwin_t h, const double* w_host, double* L_dev);
 int cumwin_set_pipeline(cumwin_t h, int enable);
 
 /* 1 when the next shift of the nominal p rows (x_out_dev == NULL) will use
- * the batch-sum FIFO of cumwin_push, 0 when it recomputes X_(-) (FP64 form,
- * T not a multiple of p, no room for the FIFO, or it was retired), EINVAL. */
+ * the batch-sum FIFO of cumwin_push, 0 when it recomputes X_(-) (T not a
+ * multiple of p, no room for the FIFO, or it was retired), EINVAL. */
 int cumwin_fifo(cumwin_t h);
 
 /*

@@ -141,7 +141,8 @@ struct cumwin_s {
     int64_t* head_rec = nullptr;  // device: the same, as the recovery sees it (FIFO slots); the two
                                   // advance once per shift each, in their own kernels
     bool filled = false;
-    bool fifo_valid = false;  // the batch-sum FIFO matches the window (mixed forms)
+    bool fifo_valid = false;  // the batch-sum FIFO matches the window
+    double* fifo64 = nullptr; // FP64 form: [T / p][Eoff[d + 1]] batch sums (UpdateArgs), or null
     Arena mem;
 
     float* ring = nullptr;   // [T][npad] raw samples
@@ -494,6 +495,21 @@ int window_init(cumwin_s* h, int n, int d, int b, int64_t T, int p, int precisio
     }
     h->ntiles = (int)tiles.size();
     if (precision == CUMWIN_FP64) CW_TRY(h->upload(&h->tiles, tiles));
+    if (precision == CUMWIN_FP64 && T % p == 0 && T / p >= 1 && T / p <= INT32_MAX) {
+        // FIFO of FP64 batch sums when the window is a whole number of batches and the
+        // FIFO takes at most a quarter of the free device memory
+        const int64_t slots = T / p, per = h->Eoff[d + 1];
+        size_t free_b = 0, total_b = 0;
+        CW_TRY(cudaMemGetInfo(&free_b, &total_b));
+        if ((double)slots * (double)per * sizeof(double) <= (double)free_b / 4) {
+            CW_TRY(h->alloc(&h->fifo64, (size_t)(slots * per)));
+            h->upd.p = p;
+            h->upd.nslots = (int32_t)slots;
+            h->upd.fstride = per;
+            h->upd.head = h->head;
+            for (int s = 1; s <= d; ++s) h->upd.ord[s].F = h->fifo64 + h->Eoff[s];
+        }
+    }
 
     // cumulant recovery tables (norm partials and workspace pointers are set later)
     for (int k = 1; k < d; ++k)
@@ -887,9 +903,19 @@ int update_window(cumwin_t h)
 {
     h->mark(0);
     h->mark(1);
-    if (h->prec == CUMWIN_FP64) {
+    if (h->prec == CUMWIN_FP64 && h->fifo64 != nullptr) {
+        // batch by batch from the ring's head: each batch's sums enter S and its FIFO slot
+        for (int q = 0; q < h->upd.nslots; ++q) {
+            CW_TRY(launch_window_rows(h->ring, h->T, h->head, (int64_t)q * h->p, h->p, h->npad, h->stage,
+                                      h->stream));
+            CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, h->p, h->p, h->shift,
+                                     kUpdFifoStore, q, h->stream));
+        }
+        h->launches += 2LL * h->upd.nslots;
+        h->fifo_valid = true;
+    } else if (h->prec == CUMWIN_FP64) {
         CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->ring, h->T, h->T, h->shift,
-                                 h->stream));
+                                 kUpdNoFifo, 0, h->stream));
         h->launches += 1;
     } else {
         for (int q = 0; q < h->tc->nbatch; ++q) {
@@ -913,11 +939,14 @@ int update_push(cumwin_t h, const float* x_in, const float* x_out, int p, int64_
     *accum = 0;
     h->mark(0);
     if (h->prec == CUMWIN_FP64) {
+        const bool fifo = h->fifo64 != nullptr && h->fifo_valid && x_out == nullptr && p == h->p;
+        if (!fifo) h->fifo_valid = false;
         CW_TRY(launch_stage(x_in, ld, x_out, ld, h->ring, h->T, h->head, p, h->n, h->npad,
                             h->stage, h->status, h->stream));
         h->mark(1);
-        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, 2 * (int64_t)p, p,
-                                 h->shift, h->stream));
+        // FIFO: only X_(+) is multiplied (the staged X_(-) rows are not read)
+        CW_TRY(launch_update_f64(h->upd, h->tiles, h->ntiles, h->stage, fifo ? (int64_t)p : 2 * (int64_t)p, p,
+                                 h->shift, fifo ? kUpdFifoShift : kUpdNoFifo, 0, h->stream));
     } else {
         const bool fifo = h->tc->fifo != nullptr && h->fifo_valid && x_out == nullptr && p == h->p;
         if (!fifo) h->fifo_valid = false;
@@ -1535,7 +1564,8 @@ int cumwin_set_pipeline(cumwin_t h, int enable)
 int cumwin_fifo(cumwin_t h)
 {
     if (h == nullptr) return CUMWIN_EINVAL;
-    return h->tc != nullptr && h->tc->fifo != nullptr && h->fifo_valid ? 1 : 0;
+    const bool has = h->fifo64 != nullptr || (h->tc != nullptr && h->tc->fifo != nullptr);
+    return has && h->fifo_valid ? 1 : 0;
 }
 
 int cumwin_push_host(cumwin_t h, const float* x_in_host, int p, int64_t ld)

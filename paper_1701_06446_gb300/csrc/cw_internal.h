@@ -52,13 +52,24 @@ struct OrderTables {
     const uint32_t* colvar;
     const int64_t* coloff;
     double* S;      // running FP64 sums of order s (block layout)
+    double* F;      // FP64 form: batch-sum FIFO slot 0 of order s (same indexing as S), or null
     int32_t h, sh;  // factors on the row side / column side
     int32_t nrows, ncols;
 };
 
+// FIFO of batch sums, FP64 form (Section 2.4's alternative to recomputing
+// X_(-)): for a window of T = nslots * p samples, slot f holds the FP64 sums of
+// the batch of p ring rows starting at f * p + (head mod p).  A regular shift
+// forms only the entering batch's sums D and applies S += D - F[slot],
+// F[slot] = D, with slot = head / p (head before the shift advances it).
+enum UpdFifoMode { kUpdNoFifo = 0, kUpdFifoStore = 1, kUpdFifoShift = 2 };
+
 struct UpdateArgs {
     OrderTables ord[kMaxOrder + 1];  // index = order
     int32_t npad;                    // row stride of the sample buffers
+    int32_t p, nslots;               // FIFO: batch length and slots (nslots = 0: no FIFO)
+    int64_t fstride;                 // FIFO: doubles per slot
+    const int64_t* head;             // FIFO: ring head of the window (device)
 };
 
 // One output tile of the update: rows [row0, row0+nrows) and columns
@@ -177,9 +188,14 @@ cudaError_t launch_column_mean(const float* ring, int64_t T, int n, int npad, fl
                                cudaStream_t st);
 cudaError_t launch_window_copy(const float* ring, int64_t T, const int64_t* head, int n, int npad,
                                float* out, cudaStream_t st);
+// fmode (UpdFifoMode): kUpdFifoStore stores the sums in FIFO slot (head / p + fq)
+// mod nslots and adds them; kUpdFifoShift replaces slot head / p (all K rows enter).
 cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int ntiles,
                               const float* rows, int64_t K, int64_t npos, const float* shift,
-                              cudaStream_t st);
+                              int fmode, int fq, cudaStream_t st);
+// rows [r0, r0 + p) of the window (oldest first, from the ring's head) -> out [p][npad]
+cudaError_t launch_window_rows(const float* ring, int64_t T, const int64_t* head, int64_t r0, int p,
+                               int npad, float* out, cudaStream_t st);
 // Launch shape of the recovery kernel of one order (see plan_cumulants).
 struct CumLaunch {
     int slots, gx, gy;

@@ -96,6 +96,22 @@ k_window_copy(const float* __restrict__ ring, int64_t T, const int64_t* __restri
     }
 }
 
+// out[r][v] = window row r0 + r (ring slot head + r0 + r, wrapped), every padded column.
+__global__ void __launch_bounds__(kThreads)
+k_window_rows(const float* __restrict__ ring, int64_t T, const int64_t* __restrict__ head_p, int64_t r0, int p,
+              int npad, float* __restrict__ out)
+{
+    const int64_t total = (int64_t)p * npad;
+    const int64_t head = *head_p;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / npad;
+        const int v = (int)(e - r * npad);
+        const int64_t slot = (head + r0 + r) % T;
+        out[e] = ring[slot * npad + v];
+    }
+}
+
 __global__ void k_zero(double* __restrict__ p, int64_t count)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
@@ -147,6 +163,13 @@ cudaError_t launch_window_copy(const float* ring, int64_t T, const int64_t* head
                                float* out, cudaStream_t st)
 {
     k_window_copy<<<grid_for(T * n), kThreads, 0, st>>>(ring, T, head, n, npad, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_rows(const float* ring, int64_t T, const int64_t* head, int64_t r0, int p,
+                               int npad, float* out, cudaStream_t st)
+{
+    k_window_rows<<<grid_for((int64_t)p * npad), kThreads, 0, st>>>(ring, T, head, r0, p, npad, out);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,10 @@
 // memory as FP64 (x - shift), the Khatri-Rao operands are built per K-chunk in
 // shared memory, and each thread accumulates a 4 x 4 register tile in FP64.
 // Every stored element belongs to exactly one tile, so the read-modify-write of
-// the running sums needs no atomics and the result is deterministic.
+// the running sums needs no atomics and the result is deterministic.  With the
+// batch-sum FIFO (UpdFifoMode) the epilogue also stores the tile's sums in the
+// batch's slot and, for a regular shift, subtracts the leaving batch's stored
+// sums instead of multiplying its samples again.
 #include "cw_internal.h"
 
 namespace cw {
@@ -27,7 +30,7 @@ __device__ __forceinline__ double kr_product(const double* __restrict__ y, uint3
 __global__ void __launch_bounds__(NT)
 k_update_f64(const UpdateArgs args, const UpdTile* __restrict__ tiles,
              const float* __restrict__ rows, int64_t K, int64_t npos,
-             const float* __restrict__ shift)
+             const float* __restrict__ shift, int fmode, int fq)
 {
     extern __shared__ double smem[];
     const int npad = args.npad;
@@ -91,6 +94,11 @@ k_update_f64(const UpdateArgs args, const UpdTile* __restrict__ tiles,
         }
     }
 
+    double* F = nullptr;  // this launch's FIFO slot of order s
+    if (fmode != kUpdNoFifo) {
+        const int64_t hd = *args.head;
+        F = ot.F + (hd / args.p + fq) % args.nslots * args.fstride;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int r = ty + 16 * i;
@@ -99,8 +107,14 @@ k_update_f64(const UpdateArgs args, const UpdTile* __restrict__ tiles,
         for (int j = 0; j < 4; ++j) {
             const int c = tx + 16 * j;
             if (c >= tile.ncols) continue;
-            double* dst = ot.S + ro[r] + co[c];
-            *dst += acc[i][j];
+            const int64_t e = ro[r] + co[c];
+            if (fmode == kUpdNoFifo) {
+                ot.S[e] += acc[i][j];
+            } else {
+                const double leaving = fmode == kUpdFifoShift ? F[e] : 0.0;
+                ot.S[e] += acc[i][j] - leaving;
+                F[e] = acc[i][j];
+            }
         }
     }
 }
@@ -109,13 +123,14 @@ k_update_f64(const UpdateArgs args, const UpdTile* __restrict__ tiles,
 
 cudaError_t launch_update_f64(const UpdateArgs& a, const UpdTile* tiles, int ntiles,
                               const float* rows, int64_t K, int64_t npos, const float* shift,
-                              cudaStream_t st)
+                              int fmode, int fq, cudaStream_t st)
 {
+    if (fmode != kUpdNoFifo && (a.nslots < 1 || a.p < 1 || a.head == nullptr)) return cudaErrorInvalidValue;
     if (ntiles <= 0 || K <= 0) return cudaSuccess;
     const size_t smem = sizeof(double) * ((size_t)KC * a.npad + KC * TM + KC * TN);
     cudaError_t e = smem_opt_in((const void*)k_update_f64, sizeof(double) * ((size_t)KC * kMaxN + KC * TM + KC * TN));
     if (e != cudaSuccess) return e;
-    k_update_f64<<<ntiles, NT, smem, st>>>(a, tiles, rows, K, npos, shift);
+    k_update_f64<<<ntiles, NT, smem, st>>>(a, tiles, rows, K, npos, shift, fmode, fq);
     return cudaGetLastError();
 }
 

@@ -113,18 +113,83 @@ def test_padding_entries_are_exact_zero():
 
 
 def test_explicit_outgoing_rows_match_ring():
-    """push(x_in, x_out = the oldest rows) is bitwise the ring-buffer shift."""
+    """push(x_in, x_out = the oldest rows) is bitwise the ring-buffer shift when
+    both recompute X_(-) (a window that is not a whole number of batches has no
+    batch-sum FIFO)."""
     W = WORKLOADS["n4_d4_b2_T1000_p100"]
     X = W.stream().rows(0, 3000)
     Xd = dev(X)
-    with CumWin(4, 4, 2, 1000, 100) as a, CumWin(4, 4, 2, 1000, 100) as b:
-        a.fill(Xd[:1000])
-        b.fill(Xd[:1000])
+    T, p = 1000, 96
+    with CumWin(4, 4, 2, T, p) as a, CumWin(4, 4, 2, T, p) as b:
+        a.fill(Xd[:T])
+        b.fill(Xd[:T])
+        assert not a.fifo and not b.fifo
         for w in range(20):
-            a.push(Xd[1000 + w * 100: 1100 + w * 100])
-            b.push(Xd[1000 + w * 100: 1100 + w * 100], Xd[w * 100: (w + 1) * 100].clone())
+            a.push(Xd[T + w * p: T + (w + 1) * p])
+            b.push(Xd[T + w * p: T + (w + 1) * p], Xd[w * p: (w + 1) * p].clone())
         for s in range(1, 5):
             assert torch.equal(a.cumulants(s), b.cumulants(s))
+
+
+def test_fp64_fifo_matches_recomputing_form():
+    """FP64 batch-sum FIFO (Section 2.4's alternative): a regular shift subtracts the
+    leaving batch's stored FP64 sums.  The recomputing form (caller-supplied X_(-))
+    forms the same products and adds them in another order, so the two agree to the
+    rounding of FP64 additions, and both match the oracle."""
+    W = WORKLOADS["n4_d4_b2_T1000_p100"]
+    X = W.stream().rows(0, 4000)
+    Xd = dev(X)
+    T, p = 1000, 100
+    with CumWin(4, 4, 2, T, p) as a, CumWin(4, 4, 2, T, p) as b:
+        a.fill(Xd[:T])
+        b.fill(Xd[:T])
+        assert a.fifo and b.fifo
+        for w in range(25):
+            a.push(Xd[T + w * p: T + (w + 1) * p])
+            b.push(Xd[T + w * p: T + (w + 1) * p], Xd[w * p: (w + 1) * p].clone())
+        assert a.fifo and not b.fifo
+        for s in range(1, 5):
+            assert rel_fro(a.moments(s).cpu().numpy(), b.moments(s).cpu().numpy()) <= 1e-14, s
+        assert_window_parity(a, X[25 * p: 25 * p + T])
+        assert_window_parity(b, X[25 * p: 25 * p + T])
+
+
+@pytest.mark.parametrize("n,d,b,T,p", [(6, 4, 2, 600, 50), (5, 6, 4, 256, 32)])
+def test_fp64_fifo_retired_by_short_shift_and_restored_by_recompute(n, d, b, T, p):
+    """An irregular shift retires the FP64 FIFO; recompute refills it batch by batch
+    from the ring's head, which is then no longer a multiple of p, so the slots
+    follow the head; two full turns of the window later the sums still match the
+    oracle and a fresh recomputation."""
+    rng = np.random.default_rng(31)
+    X = (rng.standard_t(5, size=(T + 40 * p, n)) + 0.5).astype(np.float32)
+    Xd = dev(X)
+    with CumWin(n, d, b, T, p) as h:
+        h.fill(Xd[:T])
+        assert h.fifo
+        pos = T
+        for w in range(3):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        assert_window_parity(h, X[pos - T: pos])
+        h.push(Xd[pos: pos + 7])  # fewer rows than p: X_(-) recomputed, FIFO retired
+        pos += 7
+        assert not h.fifo
+        for w in range(3):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        assert not h.fifo
+        assert_window_parity(h, X[pos - T: pos])
+        h.recompute()
+        assert h.fifo
+        for w in range(2 * T // p + 3):
+            h.push(Xd[pos: pos + p])
+            pos += p
+        assert h.fifo
+        assert_window_parity(h, X[pos - T: pos])
+        slide = [h.moments(s).cpu().numpy() for s in range(1, d + 1)]
+        h.recompute()
+        for s in range(1, d + 1):
+            assert rel_fro(slide[s - 1], h.moments(s).cpu().numpy()) <= 1e-13, s
 
 
 def test_sliding_equals_fresh_after_1e4_shifts():
