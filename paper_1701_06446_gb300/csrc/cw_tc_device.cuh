@@ -126,8 +126,162 @@ __device__ __forceinline__ float scale_pow2(float x, int k)
 // samples, split into 16-bit hi + lo, stored at [part][row][sample]
 // (samples contiguous, Kcap per row).
 // ---------------------------------------------------------------------------
-// Elements [begin, rows * nkb) with the given stride of the build: each is
-// one row and 8 consecutive samples.
+// A row has at most this many factors (its variables are packed 8 bits each
+// into 32 bits; a factor of order s <= 8 takes at most ceil(s / 2) of them).
+constexpr int kMaxRowFactors = 4;
+
+// Row `row`, samples [8 kb, 8 kb + 8).  The factors' loads are issued
+// together (unrolled over the largest factor count); the products are formed
+// in factor order, so the result does not depend on the unrolling.
+template <bool BF16>
+__device__ __forceinline__ void kr_build_item(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap,
+                                              uint64_t w, int64_t row, int kb, int64_t rows,
+                                              uint16_t* __restrict__ ops, int P, int32_t* __restrict__ opexp)
+{
+    const uint32_t vars = (uint32_t)w;
+    const int nf = (int)((w >> 32) & 0xffu);
+    const TcStreamDesc* sd = &sdesc[(int)(w >> 40)];
+    const float* XT = sd->XT;
+    const int half = 8 * kb >= P ? 1 : 0;  // entering or leaving samples
+    float4 a[kMaxRowFactors], c[kMaxRowFactors];
+#pragma unroll
+    for (int f = 0; f < kMaxRowFactors; ++f) {
+        if (f < nf) {
+            const int var = (int)((vars >> (8 * f)) & 0xffu);
+            const float* xr = XT + (int64_t)var * Kcap + 8 * kb;
+            a[f] = *reinterpret_cast<const float4*>(xr);
+            c[f] = *reinterpret_cast<const float4*>(xr + 4);
+        }
+    }
+    float p[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) p[t] = 1.0f;
+    int esum = 0;
+#pragma unroll
+    for (int f = 0; f < kMaxRowFactors; ++f) {
+        if (f < nf) {
+            float4 x = a[f], y = c[f];
+            if constexpr (!BF16) {  // every factor scaled into [-1, 1] by a power of two (exact)
+                const int var = (int)((vars >> (8 * f)) & 0xffu);
+                const int e = scale_exp(sd->vmax[half * sd->npad + var]);
+                const float sc = pow2f(-e);
+                esum += e;
+                x.x *= sc; x.y *= sc; x.z *= sc; x.w *= sc;
+                y.x *= sc; y.y *= sc; y.z *= sc; y.w *= sc;
+            }
+            p[0] *= x.x; p[1] *= x.y; p[2] *= x.z; p[3] *= x.w;
+            p[4] *= y.x; p[5] *= y.y; p[6] *= y.z; p[7] *= y.w;
+        }
+    }
+    if constexpr (!BF16) {
+        if (8 * kb == half * P) opexp[(int64_t)half * rows + row] = esum;  // the row's scale, once per half
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if constexpr (BF16) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        } else {
+            const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
+            const float2 hf = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        }
+    }
+    const int64_t part = rows * Kcap;  // elements of one part
+    const int64_t o = row * Kcap + 8 * kb;
+    *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Row `row`, 256-sample chunk kc, as one warp: lane l forms samples
+// 256 kc + 4 l + [0, 4) and 256 kc + 128 + 4 l + [0, 4), so that every load
+// instruction of the warp reads 512 contiguous bytes of a staged variable and
+// every store writes 256 contiguous bytes of a part (half as many L1
+// wavefronts as 8 consecutive samples per lane).  The chunk lies inside one
+// half (entering or leaving samples): P is a multiple of 256.  Products in
+// factor order, bitwise those of kr_build_item.
+template <bool BF16>
+__device__ __forceinline__ void kr_build_chunk(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap,
+                                               uint64_t w, int64_t row, int kc, int lane, int64_t rows,
+                                               uint16_t* __restrict__ ops, int P, int32_t* __restrict__ opexp)
+{
+    const uint32_t vars = (uint32_t)w;
+    const int nf = (int)((w >> 32) & 0xffu);
+    const TcStreamDesc* sd = &sdesc[(int)(w >> 40)];
+    const float* XT = sd->XT;
+    const int s0 = 256 * kc;
+    const int half = s0 >= P ? 1 : 0;  // entering or leaving samples
+    float4 a[kMaxRowFactors], c[kMaxRowFactors];
+#pragma unroll
+    for (int f = 0; f < kMaxRowFactors; ++f) {
+        if (f < nf) {
+            const int var = (int)((vars >> (8 * f)) & 0xffu);
+            const float* xr = XT + (int64_t)var * Kcap + s0 + 4 * lane;
+            a[f] = *reinterpret_cast<const float4*>(xr);
+            c[f] = *reinterpret_cast<const float4*>(xr + 128);
+        }
+    }
+    float p[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) p[t] = 1.0f;
+    int esum = 0;
+#pragma unroll
+    for (int f = 0; f < kMaxRowFactors; ++f) {
+        if (f < nf) {
+            float4 x = a[f], y = c[f];
+            if constexpr (!BF16) {  // every factor scaled into [-1, 1] by a power of two (exact)
+                const int var = (int)((vars >> (8 * f)) & 0xffu);
+                const int e = scale_exp(sd->vmax[half * sd->npad + var]);
+                const float sc = pow2f(-e);
+                esum += e;
+                x.x *= sc; x.y *= sc; x.z *= sc; x.w *= sc;
+                y.x *= sc; y.y *= sc; y.z *= sc; y.w *= sc;
+            }
+            p[0] *= x.x; p[1] *= x.y; p[2] *= x.z; p[3] *= x.w;
+            p[4] *= y.x; p[5] *= y.y; p[6] *= y.z; p[7] *= y.w;
+        }
+    }
+    if constexpr (!BF16) {
+        if (lane == 0 && s0 == half * P) opexp[(int64_t)half * rows + row] = esum;  // once per half
+    }
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if constexpr (BF16) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
+            const float2 hf = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        } else {
+            const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
+            const float2 hf = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        }
+    }
+    const int64_t part = rows * Kcap;  // elements of one part
+    const int64_t o = row * Kcap + s0 + 4 * lane;
+    *reinterpret_cast<uint2*>(ops + o) = make_uint2(h[0], h[1]);
+    *reinterpret_cast<uint2*>(ops + o + 128) = make_uint2(h[2], h[3]);
+    *reinterpret_cast<uint2*>(ops + part + o) = make_uint2(l[0], l[1]);
+    *reinterpret_cast<uint2*>(ops + part + o + 128) = make_uint2(l[2], l[3]);
+}
+
+// Elements [begin, rows * nkb) with the given stride of the build (begin = the
+// thread's index, stride a multiple of 32): each is one row and 8 consecutive
+// samples.  Element e -> (chunk of cw 8-sample steps, row, step): the 32 lanes
+// of a warp write 32 consecutive steps of one row (512 contiguous bytes per
+// part), consecutive warps take consecutive rows of the same chunk, so that the
+// CTAs running at once read the staged samples of one chunk (npad x 8 cw
+// floats) from L1.
 template <bool BF16>
 __device__ __forceinline__ void kr_build_range(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap,
                                                const uint64_t* __restrict__ opvars, int64_t rows, int nkb,
@@ -136,66 +290,43 @@ __device__ __forceinline__ void kr_build_range(const TcStreamDesc* __restrict__ 
 {
     // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
     const int total = (int)(rows * nkb);
-    const int64_t part = rows * Kcap;  // elements of one part
-    // item e -> (chunk of cw 8-sample steps, row, step): the 32 lanes of a warp write
-    // 32 consecutive steps of one row (512 contiguous bytes per part), consecutive
-    // warps take consecutive rows of the same chunk, so that the CTAs running at
-    // once read the staged samples of one chunk (npad x 8 cw floats) from L1
-    const int cw = nkb % 32 == 0 ? 32 : nkb;
+    if (nkb % 32 == 0) {
+        // chunks of 32 steps: one (chunk, row) per warp and round, lane = step; the
+        // next round's row descriptor is loaded before this round's item is built,
+        // so that its latency overlaps the item instead of preceding the next one
+        const int lane = begin & 31;
+        const int nw = total >> 5, nrows = (int)rows, ws = stride >> 5;
+        int wi = begin >> 5;
+        if (wi >= nw) return;
+        int kc = wi / nrows, row = wi - kc * nrows;
+        uint64_t w = opvars[row];
+        for (;;) {
+            const int wn = wi + ws;
+            int kcn = 0, rown = 0;
+            uint64_t wnext = 0;
+            if (wn < nw) {
+                kcn = wn / nrows;
+                rown = wn - kcn * nrows;
+                wnext = opvars[rown];
+            }
+            if (P % 256 == 0) kr_build_chunk<BF16>(sdesc, Kcap, w, row, kc, lane, rows, ops, P, opexp);
+            else kr_build_item<BF16>(sdesc, Kcap, w, row, 32 * kc + lane, rows, ops, P, opexp);
+            if (wn >= nw) break;
+            wi = wn;
+            kc = kcn;
+            row = rown;
+            w = wnext;
+        }
+        return;
+    }
+    const int cw = nkb;  // fewer or ragged steps: one chunk
     const int rw = (int)rows * cw;
     for (int e = begin; e < total; e += stride) {
         const int kc = e / rw;
         const int rem = e - kc * rw;
         const int row = rem / cw;
         const int kb = kc * cw + (rem - row * cw);
-        const uint64_t w = opvars[row];
-        const uint32_t vars = (uint32_t)w;
-        const int nf = (int)((w >> 32) & 0xffu);
-        const TcStreamDesc* sd = &sdesc[(int)(w >> 40)];
-        const float* XT = sd->XT;
-        float p[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) p[t] = 1.0f;
-        const int half = 8 * kb >= P ? 1 : 0;  // entering or leaving samples
-        int esum = 0;
-        for (int f = 0; f < nf; ++f) {
-            const int var = (int)((vars >> (8 * f)) & 0xffu);
-            const float* xr = XT + (int64_t)var * Kcap + 8 * kb;
-            float4 a = *reinterpret_cast<const float4*>(xr);
-            float4 c = *reinterpret_cast<const float4*>(xr + 4);
-            if constexpr (!BF16) {  // every factor scaled into [-1, 1] by a power of two (exact)
-                const int e = scale_exp(sd->vmax[half * sd->npad + var]);
-                const float sc = pow2f(-e);
-                esum += e;
-                a.x *= sc; a.y *= sc; a.z *= sc; a.w *= sc;
-                c.x *= sc; c.y *= sc; c.z *= sc; c.w *= sc;
-            }
-            p[0] *= a.x; p[1] *= a.y; p[2] *= a.z; p[3] *= a.w;
-            p[4] *= c.x; p[5] *= c.y; p[6] *= c.z; p[7] *= c.w;
-        }
-        if constexpr (!BF16) {
-            if (8 * kb == half * P) opexp[(int64_t)half * rows + row] = esum;  // the row's scale, once per half
-        }
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if constexpr (BF16) {
-                const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
-                const float2 hf = __bfloat1622float2(hv);
-                const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
-                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-            } else {
-                const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
-                const float2 hf = __half22float2(hv);
-                const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
-                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-            }
-        }
-        const int64_t o = (int64_t)row * Kcap + 8 * kb;
-        *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        kr_build_item<BF16>(sdesc, Kcap, opvars[row], row, kb, rows, ops, P, opexp);
     }
 }
 

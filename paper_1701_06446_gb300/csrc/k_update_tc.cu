@@ -72,9 +72,12 @@ k_tc_stage_batch(const TcStreamDesc* __restrict__ sdesc, int q, int p, int P, in
     }
 }
 
-// Operand build (cw_tc_device.cuh); advances the staging ring heads.
+// Operand build (cw_tc_device.cuh); advances the staging ring heads.  A
+// persistent grid of kBuildCtasPerSm CTAs per SM, so that each thread builds
+// many items and the next item's row descriptor load overlaps the current one.
+constexpr int kBuildCtasPerSm = 4;
 template <bool BF16>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kBuildCtasPerSm)
 k_kr_build(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap, const uint64_t* __restrict__ opvars,
            int64_t rows, int nkb, uint16_t* __restrict__ ops, int nstreams, int64_t advance, int P,
            int32_t* __restrict__ opexp)
@@ -197,9 +200,10 @@ cudaError_t launch_build(const TcPlan& plan, int nsamples, int64_t advance, cuda
 {
     const int nkb = nsamples / 8;
     const int64_t work = plan.oprows * nkb;
+    const int grid = std::min(grid_for(work), kBuildCtasPerSm * std::max(plan.sm_count, 1));
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
-    pdl_config(cfg, attr, dim3(grid_for(work)), dim3(256), 0, st);
+    pdl_config(cfg, attr, dim3(grid), dim3(256), 0, st);
     if (plan.precision == 1)
         return cudaLaunchKernelEx(&cfg, k_kr_build<true>, (const TcStreamDesc*)plan.sdesc, plan.Kcap,
                                   (const uint64_t*)plan.opvars, plan.oprows, nkb, plan.ops, plan.nstreams, advance,
