@@ -180,11 +180,12 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
 
 
 # DRAM bytes (read + write) per shift from an ncu capture of the current kernels (profiles/
-# launches_*.md), by workload: the recovery's launches of one shift, and the GEMM.  The n=48
-# workload's were taken with a window of 2^13 samples, whose per-launch work is the same.
-# None where no capture of the current kernels exists.
-RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 1864350976, "n60_d4_b3_T32768_p1024": 13007616}
-GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2009310976, "n60_d4_b3_T32768_p1024": 15829120}
+# launches_*.md), by workload: the recovery's launches of one shift, the GEMM, and the staging
+# plus operand build.  The n=48 workload's were taken with a window of 2^13 samples, whose
+# per-launch work is the same.  None where no capture of the current kernels exists.
+RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 1865267780, "n60_d4_b3_T32768_p1024": 13007616}
+GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 2008772130, "n60_d4_b3_T32768_p1024": 15829120}
+BUILD_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 641883051}
 
 
 def fp64_peak_tflops(dev) -> float:
@@ -608,7 +609,8 @@ def run_ours(args, W, rank: int, world: int):
         bgbs = work["build_bytes"] / (stg_ms * 1e-3) / 1e9
         roof_build = {"kernel": "k_tc_stage_push + k_kr_build", "bound": "hbm", "achieved": bgbs,
                       "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": bgbs / peaks["hbm_gbs"],
-                      "peak_kind": f"{peak_kind} HBM copy (of {peak_kind})", "traffic": None,
+                      "peak_kind": f"{peak_kind} HBM copy (of {peak_kind})",
+                      "traffic": BUILD_TRAFFIC.get(W.name) if precision == "bf16" else None,
                       "avg_launch_ms": stg_ms, "share_of_step": stg_ms / ms_per_step,
                       "per_launch": f"{work['build_bytes']:.4g} algorithmic bytes: {operand_rows(W.n, W.b, W.d)} "
                                     f"operand rows x {W.p if fifo else 2 * W.p} samples x hi + lo 16-bit "

@@ -330,6 +330,82 @@ __device__ __forceinline__ void kr_build_range(const TcStreamDesc* __restrict__ 
     }
 }
 
+// The build of kr_build_range in a register-lean form for the single-launch
+// batch shift, whose build shares the launch's registers with the GEMM and
+// recovery phases (the unrolled loads of kr_build_range tripled its spills):
+// one row and 8 consecutive samples per element, factors loaded one after
+// the other.  Bitwise the same operands.
+template <bool BF16>
+__device__ __forceinline__ void kr_build_range_lean(const TcStreamDesc* __restrict__ sdesc, int64_t Kcap,
+                                               const uint64_t* __restrict__ opvars, int64_t rows, int nkb,
+                                               uint16_t* __restrict__ ops, int P, int32_t* __restrict__ opexp,
+                                               int begin, int stride)
+{
+    // rows * nkb < 2^31 (checked on the host): 32-bit index arithmetic
+    const int total = (int)(rows * nkb);
+    const int64_t part = rows * Kcap;  // elements of one part
+    // item e -> (chunk of cw 8-sample steps, row, step): the 32 lanes of a warp write
+    // 32 consecutive steps of one row (512 contiguous bytes per part), consecutive
+    // warps take consecutive rows of the same chunk, so that the CTAs running at
+    // once read the staged samples of one chunk (npad x 8 cw floats) from L1
+    const int cw = nkb % 32 == 0 ? 32 : nkb;
+    const int rw = (int)rows * cw;
+    for (int e = begin; e < total; e += stride) {
+        const int kc = e / rw;
+        const int rem = e - kc * rw;
+        const int row = rem / cw;
+        const int kb = kc * cw + (rem - row * cw);
+        const uint64_t w = opvars[row];
+        const uint32_t vars = (uint32_t)w;
+        const int nf = (int)((w >> 32) & 0xffu);
+        const TcStreamDesc* sd = &sdesc[(int)(w >> 40)];
+        const float* XT = sd->XT;
+        float p[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) p[t] = 1.0f;
+        const int half = 8 * kb >= P ? 1 : 0;  // entering or leaving samples
+        int esum = 0;
+        for (int f = 0; f < nf; ++f) {
+            const int var = (int)((vars >> (8 * f)) & 0xffu);
+            const float* xr = XT + (int64_t)var * Kcap + 8 * kb;
+            float4 a = *reinterpret_cast<const float4*>(xr);
+            float4 c = *reinterpret_cast<const float4*>(xr + 4);
+            if constexpr (!BF16) {  // every factor scaled into [-1, 1] by a power of two (exact)
+                const int e = scale_exp(sd->vmax[half * sd->npad + var]);
+                const float sc = pow2f(-e);
+                esum += e;
+                a.x *= sc; a.y *= sc; a.z *= sc; a.w *= sc;
+                c.x *= sc; c.y *= sc; c.z *= sc; c.w *= sc;
+            }
+            p[0] *= a.x; p[1] *= a.y; p[2] *= a.z; p[3] *= a.w;
+            p[4] *= c.x; p[5] *= c.y; p[6] *= c.z; p[7] *= c.w;
+        }
+        if constexpr (!BF16) {
+            if (8 * kb == half * P) opexp[(int64_t)half * rows + row] = esum;  // the row's scale, once per half
+        }
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (BF16) {
+                const __nv_bfloat162 hv = __floats2bfloat162_rn(p[2 * q], p[2 * q + 1]);
+                const float2 hf = __bfloat1622float2(hv);
+                const __nv_bfloat162 lv = __floats2bfloat162_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+            } else {
+                const __half2 hv = __floats2half2_rn(p[2 * q], p[2 * q + 1]);
+                const float2 hf = __half22float2(hv);
+                const __half2 lv = __floats2half2_rn(p[2 * q] - hf.x, p[2 * q + 1] - hf.y);
+                h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+                l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+            }
+        }
+        const int64_t o = (int64_t)row * Kcap + 8 * kb;
+        *reinterpret_cast<uint4*>(ops + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(ops + part + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
 // 3-D TMA load: box {64 samples, rows, 1} at (k, row, part), 128-byte swizzle.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int k,
                                             int row, int part)

@@ -914,7 +914,8 @@ k_batch_shift(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             int64_t* hp = a.sdesc[i].head;
             *hp = (*hp + a.p) % a.sdesc[i].T;
         }
-    tcdev::kr_build_range<BF16>(a.sdesc, a.Kcap, a.opvars, a.oprows, a.nkb, a.ops, a.P, a.opexp, gtid, gstride);
+    tcdev::kr_build_range_lean<BF16>(a.sdesc, a.Kcap, a.opvars, a.oprows, a.nkb, a.ops, a.P, a.opexp, gtid,
+                                      gstride);
     ptx::fence_proxy_async_global();
     grid_barrier(gb, f.status);
     // 3. the GEMM
