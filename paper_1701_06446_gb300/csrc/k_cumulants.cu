@@ -224,6 +224,106 @@ __device__ __forceinline__ void tw_acc_prod(float& hi, float& lo, float2 a, floa
     hi = s;
 }
 
+// L2 eviction priorities of the canonical recovery.  Its operand gathers
+// (two-word copies of the orders below, about 78 MB at n=48 d=6) are re-read
+// across the whole launch, while ten times that in sums, tile sums, FIFO
+// entries and cumulants pass through L2 once.  The gathers carry an
+// evict-last policy and the once-touched accesses an evict-first one (PTX
+// createpolicy + L2::cache_hint), so that the streamed lines leave L2 first.
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// A gather of read-only data (nothing in the launch writes it).
+__device__ __forceinline__ float2 ld_keep(const float2* a, uint64_t pol)
+{
+    float2 v;
+    asm("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+
+// Once-touched loads and stores; volatile, so that each load stays before the
+// store that follows it to the same address.
+__device__ __forceinline__ float ld_once(const float* a, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ double ld_once(const double* a, uint64_t pol)
+{
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_once(float* a, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void st_once(double* a, double v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+
+// fold_load_at + fold_store for the canonical recovery (sums in workspace
+// order, si = w), with the evict-first policy on every access: the same
+// values and additions (tile slices added in order to 0.0f, as sum_partials
+// and sum_in_partials).  Every load is issued before the first addition: an
+// addition waits for its load, and a load behind it would wait too.
+// Returns the folded sum.
+__device__ __forceinline__ double fold_once(const CumArgs& a, int64_t w, int64_t fslot, uint64_t pol)
+{
+    const float* wp = a.W + a.woff + w;
+    double* sp = a.S[a.s] + w;
+    float* fp = a.accum == 1 ? nullptr : a.fifo + fslot * a.fstride + w;  // FIFO in workspace order
+    float din = 0.0f, dout = 0.0f;
+    double s0;
+    if (a.ksplit == 1) {
+        const float i0 = ld_once(wp, pol);
+        const float o0 = fp == nullptr ? ld_once(wp + a.wslice, pol) : ld_once(fp, pol);
+        s0 = ld_once(sp, pol);
+        din += i0;
+        dout = fp == nullptr ? dout + o0 : o0;
+    } else {
+        constexpr int KB = 4;  // slices loaded per round before they are added
+        for (int k0 = 0; k0 < a.ksplit; k0 += KB) {
+            float vi[KB], vo[KB];
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                const int k = k0 + j;
+                vi[j] = k < a.ksplit ? ld_once(wp + (int64_t)(2 * k) * a.wslice, pol) : 0.0f;
+                vo[j] = k < a.ksplit && fp == nullptr ? ld_once(wp + (int64_t)(2 * k + 1) * a.wslice, pol) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                if (k0 + j < a.ksplit) {
+                    din += vi[j];
+                    if (fp == nullptr) dout += vo[j];
+                }
+            }
+        }
+        if (fp != nullptr) dout = ld_once(fp, pol);
+        s0 = ld_once(sp, pol);
+    }
+    const double sv = s0 + (f32_to_f64(din) - f32_to_f64(dout));
+    st_once(sp, sv, pol);
+    if (fp != nullptr) st_once(fp, din, pol);
+    return sv;
+}
+
 // hi = x rounded to FP32, lo = the rest rounded to FP32.
 __device__ __forceinline__ float2 tw_split(double x)
 {
@@ -974,6 +1074,7 @@ __global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __
     const bool tw = a.twoword != 0;
     const bool fold = a.accum != 0 && a.sgemm;
     const int64_t fslot = a.accum == 2 ? fifo_slot(a) : 0;
+    const uint64_t keep = l2_policy_evict_last(), once = l2_policy_evict_first();
     const int per = (a.nunits + (int)gridDim.x - 1) / (int)gridDim.x;
     const int u0 = min(a.nunits, (int)blockIdx.x * per), u1 = min(a.nunits, u0 + per);
     int cur_q = -1, cur_sl = -1, off = 0, lr = 0;
@@ -1030,9 +1131,7 @@ __global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __
             if (a.sgemm) {
                 const int64_t w = wslot_lr(a, blk, lr);
                 if (fold) {
-                    FoldVal fv = fold_load_at(a, w, w, fslot);
-                    fold_store(fv);
-                    sv = fv.s + (f32_to_f64(fv.din) - f32_to_f64(fv.dout));
+                    sv = fold_once(a, w, fslot, once);
                 } else {
                     sv = a.S[S][w];
                 }
@@ -1047,8 +1146,8 @@ __global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __
                 for (int t = 0; t < NS; ++t) {
                     const ulonglong2 pr = pp[t];
                     const int packed = offs[t * NT + threadIdx.x];
-                    const float2 cA = reinterpret_cast<const float2*>(pr.x)[packed >> 16];
-                    const float2 sR = reinterpret_cast<const float2*>(pr.y)[packed & 0xffff];
+                    const float2 cA = ld_keep(reinterpret_cast<const float2*>(pr.x) + (packed >> 16), keep);
+                    const float2 sR = ld_keep(reinterpret_cast<const float2*>(pr.y) + (packed & 0xffff), keep);
                     tw_acc_prod(hi, lo, cA, sR);
                 }
                 cv = div_T(a, sv - (f32_to_f64(hi) + f32_to_f64(lo)));
@@ -1063,7 +1162,7 @@ __global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __
                 }
                 cv = div_T(a, acc);
             }
-            a.Cout[e] = cv;
+            st_once(a.Cout + e, cv, once);
             if (a.split) {
                 a.C2[S][e] = tw_split(cv);
                 a.S2[S][e] = tw_split(sv);
