@@ -183,7 +183,7 @@ def algorithmic_work(W, fifo: bool = False) -> dict:
 # launches_*.md), by workload: the recovery's launches of one shift, the GEMM, and the staging
 # plus operand build.  The n=48 workload's were taken with a window of 2^13 samples, whose
 # per-launch work is the same.  None where no capture of the current kernels exists.
-RECOVERY_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 1777918907, "n60_d4_b3_T32768_p1024": 13007616}
+RECOVERY_TRAFFIC: dict[str, int] = {"n60_d4_b3_T32768_p1024": 13007616}
 GEMM_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 1508085230, "n60_d4_b3_T32768_p1024": 15829120}
 BUILD_TRAFFIC: dict[str, int] = {"n48_d6_b4_T65536_p4096": 641766161}
 

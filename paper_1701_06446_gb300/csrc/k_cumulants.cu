@@ -278,49 +278,22 @@ __device__ __forceinline__ void st_once(double* a, double v, uint64_t pol)
     asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
 }
 
-// fold_load_at + fold_store for the canonical recovery (sums in workspace
-// order, si = w), with the evict-first policy on every access: the same
-// values and additions (tile slices added in order to 0.0f, as sum_partials
-// and sum_in_partials).  Every load is issued before the first addition: an
-// addition waits for its load, and a load behind it would wait too.
-// Returns the folded sum.
-__device__ __forceinline__ double fold_once(const CumArgs& a, int64_t w, int64_t fslot, uint64_t pol)
+// fold_load_at + fold_store for the canonical recovery's regular shifts
+// (batch-sum FIFO, one K-slice; sums in workspace order, si = w) with the
+// evict-first policy on every access: the same values and additions (the
+// tile slice added to 0.0f, as sum_in_partials).  Straight-line, its three
+// loads issued before the first addition.  Returns the folded sum.
+__device__ __forceinline__ double fold_fifo_once(const CumArgs& a, int64_t w, int64_t fslot, uint64_t pol)
 {
-    const float* wp = a.W + a.woff + w;
     double* sp = a.S[a.s] + w;
-    float* fp = a.accum == 1 ? nullptr : a.fifo + fslot * a.fstride + w;  // FIFO in workspace order
-    float din = 0.0f, dout = 0.0f;
-    double s0;
-    if (a.ksplit == 1) {
-        const float i0 = ld_once(wp, pol);
-        const float o0 = fp == nullptr ? ld_once(wp + a.wslice, pol) : ld_once(fp, pol);
-        s0 = ld_once(sp, pol);
-        din += i0;
-        dout = fp == nullptr ? dout + o0 : o0;
-    } else {
-        constexpr int KB = 4;  // slices loaded per round before they are added
-        for (int k0 = 0; k0 < a.ksplit; k0 += KB) {
-            float vi[KB], vo[KB];
-#pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                const int k = k0 + j;
-                vi[j] = k < a.ksplit ? ld_once(wp + (int64_t)(2 * k) * a.wslice, pol) : 0.0f;
-                vo[j] = k < a.ksplit && fp == nullptr ? ld_once(wp + (int64_t)(2 * k + 1) * a.wslice, pol) : 0.0f;
-            }
-#pragma unroll
-            for (int j = 0; j < KB; ++j) {
-                if (k0 + j < a.ksplit) {
-                    din += vi[j];
-                    if (fp == nullptr) dout += vo[j];
-                }
-            }
-        }
-        if (fp != nullptr) dout = ld_once(fp, pol);
-        s0 = ld_once(sp, pol);
-    }
+    float* fp = a.fifo + fslot * a.fstride + w;  // FIFO in workspace order
+    const float i0 = ld_once(a.W + a.woff + w, pol);
+    const float dout = ld_once(fp, pol);
+    const double s0 = ld_once(sp, pol);
+    const float din = 0.0f + i0;
     const double sv = s0 + (f32_to_f64(din) - f32_to_f64(dout));
     st_once(sp, sv, pol);
-    if (fp != nullptr) st_once(fp, din, pol);
+    st_once(fp, din, pol);
     return sv;
 }
 
@@ -1130,8 +1103,12 @@ __global__ void __launch_bounds__(NT, kCanonCtasPerSm) k_canon(const CumArgs* __
             double sv;
             if (a.sgemm) {
                 const int64_t w = wslot_lr(a, blk, lr);
-                if (fold) {
-                    sv = fold_once(a, w, fslot, once);
+                if (fold && a.accum == 2 && a.ksplit == 1) {
+                    sv = fold_fifo_once(a, w, fslot, once);
+                } else if (fold) {
+                    FoldVal fv = fold_load_at(a, w, w, fslot);
+                    fold_store(fv);
+                    sv = fv.s + (f32_to_f64(fv.din) - f32_to_f64(fv.dout));
                 } else {
                     sv = a.S[S][w];
                 }
