@@ -180,7 +180,10 @@ int cumwin_fill(cumwin_t h, const float* X_dev, int64_t ldx);
  * FIFO form subtracts the leaving batch's sum as a whole, the recomputing form
  * accumulates the leaving products into the entering batch's sum).  Any other
  * shift (x_out_dev != NULL or another number of rows) recomputes X_(-) and
- * retires the FIFO until the next fill or recompute.
+ * retires the FIFO until the next fill or recompute.  A push captured into a
+ * CUDA graph keeps the choice made at capture (cumwin_fifo tells which): after
+ * an irregular shift outside the graph, call cumwin_recompute before replaying
+ * a graph whose pushes use the FIFO.
  *
  * Pipelined shifts (mixed forms): the recovery of C_1..C_d and of the norms
  * runs on a stream owned by the handle, ordered after the shift's moment
