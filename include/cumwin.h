@@ -104,8 +104,11 @@ int64_t cumwin_device_bytes(cumwin_t h);
  * length T samples, nominal shift size p (the paper's t_up, 1 <= p <= T),
  * arithmetic `precision`, issuing work on `cuda_stream` (a cudaStream_t;
  * NULL = legacy default stream).  Allocates all device state (ring buffer of
- * T samples, FP64 moment sums and cumulants of every order, tables) on the
- * current device from the allocator of cumwin_set_allocator.  Synchronous.
+ * T samples, FP64 moment sums and cumulants of every order, tables, and the
+ * batch-sum FIFO of cumwin_push when T is a multiple of p and it takes at most
+ * a quarter of the free memory: T/p x sum_s E_s floats in the mixed forms,
+ * doubles in the FP64 form) on the current device from the allocator of
+ * cumwin_set_allocator.  Synchronous.
  * In the mixed forms the FP32 tile sums are formed per batch of p samples and
  * the first window is summed in batches of p aligned with the later shifts,
  * so when every push has p rows and p divides T a batch's FP32 sum leaving
